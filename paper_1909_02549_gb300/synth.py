@@ -1,0 +1,120 @@
+"""Seeded synthetic inputs for the minibatched SNN time step.
+
+This module only *generates inputs*: MNIST-shaped intensity images, the
+per-sample seeds, the input->excitatory weight matrix on a dyadic grid and the
+network parameter set.  It holds none of the method's arithmetic (no Poisson
+draw, no neuron update, no plasticity), so both the CUDA library and the CPU
+oracle can be fed from it.
+
+Workload recipe (stand-in for the MNIST digits of the unsupervised-learning
+experiment, Sec. "Unsupervised Learning of MNIST digits"; no MNIST item is
+used or reproduced):
+
+* image b: 784 pixels; each pixel draws two uniforms from a SplitMix64 stream
+  seeded with ``1000 + b``; the pixel is 0 when the first is < 0.7, else
+  ``255 * second`` (FP32).  Poisson rate = intensity / 4 Hz.
+* per-sample Poisson seed: ``1000 + b``.
+* weights: one SplitMix64 stream seeded with ``w_seed`` (default 42), one
+  uniform per entry in row-major ``[n_in][n_exc]`` order,
+  ``W = min(floor(u * 0.3 * 4096 + 0.5), 1228) / 4096`` -- uniform on [0, 0.3]
+  rounded to the 2^-12 grid, so every FP32 sum of up to 784 of them is exact.
+* ``bf16_grid=True`` instead uses ``k * 2^-9`` with ``k = min(floor(u*0.3*512+0.5), 153)``,
+  which has at most 8 significant bits and is therefore exactly representable
+  in BF16 (and still sums exactly in FP32).
+
+SplitMix64 follows Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators" (OOPSLA 2014): the state advances by the golden-ratio increment and
+each output is the 64-bit finaliser applied to the new state.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = (z ^ (z >> np.uint64(30))) * _M1
+    z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+class SplitMix64Streams:
+    """Vectorised SplitMix64 streams, one per initial state."""
+
+    def __init__(self, seeds):
+        self.state = np.asarray(seeds, dtype=np.uint64).copy()
+
+    def next_u64(self) -> np.ndarray:
+        with np.errstate(over="ignore"):
+            self.state = self.state + GOLDEN_GAMMA
+            return _mix64(self.state.copy())
+
+    def next_unit(self) -> np.ndarray:
+        """Uniform doubles in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def sample_seeds(batch: int, first: int = 1000) -> np.ndarray:
+    """Per-sample Poisson seeds ``first + b`` (uint64)."""
+    return (np.arange(batch, dtype=np.uint64) + np.uint64(first)).astype(np.uint64)
+
+
+def images(batch: int, n_in: int = 784, first_seed: int = 1000,
+           zero_frac: float = 0.7) -> np.ndarray:
+    """Seeded intensity images in [0, 255], ``[batch][n_in]`` float32."""
+    s = SplitMix64Streams(np.arange(batch, dtype=np.uint64) + np.uint64(first_seed))
+    out = np.empty((batch, n_in), dtype=np.float32)
+    with np.errstate(over="ignore"):
+        for p in range(n_in):
+            z = s.next_unit()
+            v = s.next_unit()
+            out[:, p] = np.where(z < zero_frac, 0.0, 255.0 * v).astype(np.float32)
+    return out
+
+
+def rates_from_images(img: np.ndarray, divisor: float = 4.0) -> np.ndarray:
+    """Poisson rates in Hz: intensity / divisor (float32; /4 is exact)."""
+    return (img.astype(np.float32) / np.float32(divisor)).astype(np.float32)
+
+
+def weights(n_in: int, n_exc: int, w_seed: int = 42, bf16_grid: bool = False) -> np.ndarray:
+    """Dyadic input->excitatory weights, ``[n_in][n_exc]`` float32."""
+    n = n_in * n_exc
+    # One stream drawn in row-major order: its k-th state (k >= 1) is
+    # w_seed + k * gamma, so all draws are computed at once.
+    with np.errstate(over="ignore"):
+        idx = np.arange(1, n + 1, dtype=np.uint64)
+        states = np.uint64(w_seed) + idx * GOLDEN_GAMMA
+        u = (_mix64(states) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    if bf16_grid:
+        k = np.minimum(np.floor(u * 0.3 * 512.0 + 0.5), 153.0)
+        w = k / 512.0
+    else:
+        k = np.minimum(np.floor(u * 0.3 * 4096.0 + 0.5), 1228.0)
+        w = k / 4096.0
+    return w.astype(np.float32).reshape(n_in, n_exc)
+
+
+def diehl_cook_params(n_exc: int, n_in: int = 784) -> dict:
+    """Network parameters of the adaptive-threshold LIF network with lateral
+    inhibition (784 Poisson inputs -> n_exc excitatory -> n_exc inhibitory),
+    mV and ms, as fixed for the 784->100/400/6400 workloads."""
+    return dict(
+        n_in=n_in, n_exc=n_exc,
+        e_rest=-65.0, e_reset=-60.0, e_thresh=-52.0, e_tau=100.0, e_refrac=5.0,
+        theta_plus=0.05, theta_tau=1e7,
+        i_rest=-60.0, i_reset=-45.0, i_thresh=-40.0, i_tau=10.0, i_refrac=2.0,
+        w_ei=22.5, w_ie=-17.5,
+        trace_tau=20.0, nu_pre=1e-4, nu_post=1e-2, w_min=0.0, w_max=1.0,
+    )
+
+
+def workload(batch: int, n_exc: int, n_in: int = 784, w_seed: int = 42,
+             bf16_grid: bool = False):
+    """(params, rates[B][n_in] f32, seeds[B] u64, W[n_in][n_exc] f32)."""
+    p = diehl_cook_params(n_exc, n_in)
+    r = rates_from_images(images(batch, n_in))
+    return p, r, sample_seeds(batch), weights(n_in, n_exc, w_seed, bf16_grid)
