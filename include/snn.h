@@ -1,0 +1,191 @@
+/*
+ * snn.h -- C ABI of the GB300-native minibatched spiking-network time step.
+ *
+ * The library simulates B independent presentations of a Diehl & Cook style
+ * network in lock-step on one GPU (Saunders et al., "Minibatch Processing in
+ * Spiking Neural Networks", arXiv:1909.02549, Sec. "Implementation"):
+ *
+ *   Poisson input (n_in) --W (plastic, shared)--> excitatory adaptive-threshold
+ *   LIF (n_exc) --one-to-one, w_ei--> inhibitory LIF (n_inh = n_exc)
+ *   --all-but-self, w_ie--> excitatory,
+ *
+ * with pair-trace STDP on W and adaptive thresholds theta, both held once and
+ * updated by a reduction of the per-sample updates over the batch
+ * (Sec. "Reduction methods").  Per-sample state (voltages, refractory counters,
+ * traces) is duplicated B times (Sec. "Implementation", Sec. "Complexity").
+ *
+ * Discrete update per step t (the model equations are not printed in the
+ * paper; this is the library's definition):
+ *   input   s_in[b,i] = top32(SM(seed_b ^ SM(t*n_in+i))) < thr[b,i],
+ *           thr = min(floor(((rate*dt)*1e-3)*2^32), 2^32-1) (FP64),
+ *           SM = SplitMix64 finaliser of x + 0x9E3779B97F4A7C15;
+ *   current I_in = sum_i s_in*W[i,j] (ascending i), I_lat = w_ie*(C_inh[b]-s_inh'[b,j]),
+ *           I_inh = w_ei*s_exc'[b,j] (' = previous step);
+ *   neuron  v = rest + (v-rest)*a; if refractory: count down, else v += I;
+ *           spike if v >= thresh (+ theta[j] for excitatory); spike -> reset, refractory;
+ *   traces  x = x*a_x + s;
+ *   STDP    delta_b = nu_post*x_pre*s_exc - nu_pre*s_in*x_post,
+ *           W = clip(W + red_b delta_b, w_min, w_max), red in {sum, mean, max};
+ *   theta   theta = theta*a_theta + theta_plus*red_b s_exc (FP64).
+ *
+ * Conventions
+ *   - Every call returns an snn_status; the library never aborts.  After an
+ *     error, snn_last_error(net) gives a one-line reason.
+ *   - The library owns every device buffer of the network.  Inputs belong to
+ *     the caller and must stay valid until the stream has passed the end of
+ *     the call that uses them.
+ *   - Layouts are row-major C arrays.  "[B][N]" means sample-major: element
+ *     (b, j) at offset b*N + j.
+ *   - Not thread-safe per network: calls on one snn_net must be serialised.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SNN_API __attribute__((visibility("default")))
+#else
+#define SNN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snn_net snn_net; /* opaque */
+
+typedef enum {
+    SNN_OK = 0,
+    SNN_ERR_ARG = 1,      /* invalid argument (sizes, pointers, enum values) */
+    SNN_ERR_OOM = 2,      /* device or host allocation failed */
+    SNN_ERR_CUDA = 3,     /* a CUDA call failed; see snn_last_error */
+    SNN_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    SNN_ERR_CAPACITY = 5, /* request exceeds a configured capacity */
+    SNN_ERR_STATE = 6     /* call not valid in the current state (e.g. continuing with a new B) */
+} snn_status;
+
+/* Batch reductions of the per-sample parameter updates (Sec. "Reduction
+ * methods": averaging is the default; the per-parameter maximum is the
+ * "maximum" method of Sec. "Unsupervised Learning of MNIST digits"). */
+typedef enum { SNN_REDUCE_SUM = 0, SNN_REDUCE_MEAN = 1, SNN_REDUCE_MAX = 2 } snn_reduce;
+
+/* Storage of the weights read by the synaptic-current step.  FP32 is exact;
+ * BF16 / FP8 keep an FP32 master for the STDP accumulation and read a rounded
+ * copy for the current. */
+typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
+
+/* snn_run flags */
+#define SNN_CONTINUE        (1u << 0) /* continuing simulation: no episodic reset
+                                         (Sec. "Episodic vs. continuing simulation") */
+#define SNN_RECORD_RASTER   (1u << 1) /* record excitatory and inhibitory spike rasters */
+#define SNN_RECORD_INPUT    (1u << 2) /* record the input (Poisson) spike raster */
+#define SNN_HOST_INPUTS     (1u << 3) /* rates_hz and seeds are host pointers; the library
+                                         copies them on the stream (pinned memory makes
+                                         the copy asynchronous) */
+#define SNN_MODE_STEP       (0u << 8) /* one kernel launch per phase per time step */
+#define SNN_MODE_GRAPH      (1u << 8) /* the T-step launch sequence captured once as a
+                                         CUDA graph and replayed */
+#define SNN_MODE_PERSISTENT (2u << 8) /* one persistent cooperative kernel for all T steps */
+#define SNN_MODE_AUTO       (3u << 8) /* library picks the mode */
+#define SNN_MODE_MASK       (3u << 8)
+
+/* Network specification (units: mV, ms, Hz).  snn_spec_default fills the
+ * 784 -> n_exc Diehl & Cook parameter set. */
+typedef struct snn_spec {
+    int32_t n_in, n_exc, n_inh;                  /* n_inh must equal n_exc */
+    float e_rest, e_reset, e_thresh, e_tau_ms, e_refrac_ms;
+    float theta_plus, theta_tau_ms;              /* adaptive threshold increment and decay */
+    float i_rest, i_reset, i_thresh, i_tau_ms, i_refrac_ms;
+    float w_ei, w_ie;                            /* exc->inh one-to-one, inh->exc all-but-self */
+    float trace_tau_ms, nu_pre, nu_post, w_min, w_max;
+    int32_t wprec;                               /* snn_wprec */
+    uint64_t w_seed;                             /* used when w_init == NULL */
+    const float* w_init;                         /* host [n_in][n_exc], or NULL: seeded init,
+                                                    uniform [0,0.3] on the 2^-12 grid */
+    const double* theta_init;                    /* host [n_exc], or NULL: zeros */
+} snn_spec;
+
+/* Fill *spec with the adaptive-threshold network parameters for n_exc
+ * excitatory and n_exc inhibitory neurons and 784 inputs. */
+SNN_API void snn_spec_default(snn_spec* spec, int32_t n_exc);
+
+/* Create a network: validate the spec, allocate W and theta on the current
+ * CUDA device and initialise them.  *out receives the handle (NULL on error).
+ * Errors: SNN_ERR_ARG (NULL pointers, sizes <= 0, n_inh != n_exc, taus <= 0,
+ * w_min > w_max, unknown wprec), SNN_ERR_OOM, SNN_ERR_CUDA. */
+SNN_API snn_status snn_create(const snn_spec* spec, snn_net** out);
+
+/* Release every resource of the network (synchronises its last stream).
+ * NULL is accepted. */
+SNN_API snn_status snn_destroy(snn_net* net);
+
+/* Run T steps of dt_ms on a batch of B presentations (Sec. "Implementation").
+ *   rates_hz  [B][n_in] float, Poisson rate of each input of each sample
+ *             (device pointer, or host with SNN_HOST_INPUTS);
+ *   seeds     [B] uint64, per-sample Poisson seed (same residency as rates_hz);
+ *   learn     0: W and theta frozen; 1: STDP and theta updates every step;
+ *   reduce    snn_reduce applied over the batch to the W and theta updates;
+ *   flags     SNN_* bits above; without SNN_CONTINUE the per-sample state is
+ *             reset first (episodic); a B different from the previous run's
+ *             re-initialises the per-sample state (Sec. "Dynamic minibatch
+ *             size") and is an SNN_ERR_STATE with SNN_CONTINUE;
+ *   cuda_stream  cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Asynchronous: returns once the work is enqueued.  Per-run outputs (spike
+ * counts, rasters) are overwritten by each run.
+ * Errors: SNN_ERR_ARG (B <= 0, T < 0, dt_ms <= 0, NULL inputs, bad reduce or
+ * mode), SNN_ERR_STATE, SNN_ERR_OOM, SNN_ERR_CUDA, SNN_ERR_TIMEOUT
+ * (persistent mode: a bounded grid barrier gave up; the state is invalid). */
+SNN_API snn_status snn_run(snn_net* net, const float* rates_hz, const uint64_t* seeds, int B, int T,
+                   float dt_ms, int learn, int reduce, unsigned flags, void* cuda_stream);
+
+/* Fields of the network state (layout, element type). */
+enum {
+    SNN_FIELD_V_EXC = 0,        /* [B][n_exc] float, mV */
+    SNN_FIELD_V_INH = 1,        /* [B][n_exc] float, mV */
+    SNN_FIELD_REF_EXC = 2,      /* [B][n_exc] uint8, refractory steps left */
+    SNN_FIELD_REF_INH = 3,      /* [B][n_exc] uint8 */
+    SNN_FIELD_X_PRE = 4,        /* [B][n_in] float, presynaptic traces */
+    SNN_FIELD_X_POST = 5,       /* [B][n_exc] float, postsynaptic traces */
+    SNN_FIELD_THETA = 6,        /* [n_exc] double, adaptive thresholds (mV) */
+    SNN_FIELD_SPIKE_COUNTS = 7, /* [B][n_exc] uint32, excitatory spikes of the last run */
+    SNN_FIELD_RASTER_EXC = 8,   /* [T][B][ceil(n_exc/32)] uint32 bit-packed (bit j%32 of word j/32) */
+    SNN_FIELD_RASTER_INH = 9,   /* [T][B][ceil(n_exc/32)] uint32 bit-packed */
+    SNN_FIELD_RASTER_INPUT = 10,/* [T][B][ceil(n_in/32)] uint32 bit-packed */
+    SNN_FIELD_STEP = 11,        /* [1] uint64, step counter after the last run */
+    SNN_FIELD_SPIKES_EXC = 12,  /* [B][n_exc] uint8, excitatory spikes of the last step */
+    SNN_FIELD_SPIKES_INH = 13,  /* [B][n_exc] uint8, inhibitory spikes of the last step */
+    SNN_FIELD_COUNT = 14
+};
+
+/* Bytes of a field for the current batch (rasters: of the last recorded run).
+ * Returns 0 for an unknown field or when the field holds nothing yet. */
+SNN_API size_t snn_field_bytes(const snn_net* net, int field);
+
+/* Copy a state field into dst (device memory if dst_on_device, else host).
+ * Synchronises the stream of the last run first.  bytes must equal
+ * snn_field_bytes(net, field).  Errors: SNN_ERR_ARG (unknown field, size
+ * mismatch, NULL dst), SNN_ERR_STATE (no run yet, or a raster not recorded),
+ * SNN_ERR_CUDA. */
+SNN_API snn_status snn_read_state(snn_net* net, int field, void* dst, size_t bytes, int dst_on_device);
+
+/* Copy the FP32 master weights [n_in][n_exc] into dst (device or host).
+ * Synchronises the stream of the last run first.  bytes must equal
+ * n_in*n_exc*4.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+SNN_API snn_status snn_read_weights(snn_net* net, float* dst, size_t bytes, int dst_on_device);
+
+/* Replace the master weights with src [n_in][n_exc] (device or host) and
+ * refresh any reduced-precision copy.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+SNN_API snn_status snn_write_weights(snn_net* net, const float* src, size_t bytes, int src_on_device);
+
+/* One-line description of the last error on this network ("" if none).
+ * Valid until the next call on the network.  NULL net gives the reason of
+ * the last failed snn_create on this thread. */
+SNN_API const char* snn_last_error(const snn_net* net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_H */

@@ -1,0 +1,514 @@
+// C ABI of the minibatched SNN library (declared in include/snn.h).
+//
+// Host-side runtime: spec validation, allocation of the shared parameters
+// (W, theta) and of the per-sample state for the current batch size, the run
+// modes (per-step launches, a captured CUDA graph replayed per run, and the
+// persistent kernel), and the state reads.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "snn_internal.cuh"
+
+namespace snn {
+cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s);
+cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_t s,
+                              int* used_persistent);
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GraphKey {
+    int B = -1, T = -1, learn = -1, reduce = -1, rec_raster = -1, rec_input = -1;
+    uint32_t dt_bits = 0;
+    uint64_t generation = 0;
+    bool operator==(const GraphKey& o) const {
+        return B == o.B && T == o.T && learn == o.learn && reduce == o.reduce &&
+               rec_raster == o.rec_raster && rec_input == o.rec_input && dt_bits == o.dt_bits &&
+               generation == o.generation;
+    }
+};
+
+}  // namespace
+
+struct snn_net {
+    snn_spec spec{};
+    int device = 0;
+    snn::Bufs d{};
+    int B = 0;                 // batch of the allocated per-sample state (0 = none)
+    bool state_valid = false;  // a run completed its enqueue on this state
+    uint64_t generation = 1;   // bumped whenever a device buffer moves
+    // recording of the last run
+    int last_T = 0;
+    bool last_rec_raster = false, last_rec_input = false;
+    size_t raster_e_cap = 0, raster_i_cap = 0, raster_in_cap = 0;   // words
+    // staging for host inputs
+    float* rates_stage = nullptr;
+    uint64_t* seeds_stage = nullptr;
+    // scratch for extracted fields
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    cudaStream_t last = nullptr;
+    // graph cache
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    std::string err;
+};
+
+namespace {
+
+snn_status fail(snn_net* net, snn_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (net) net->err = buf;
+    else g_create_error = buf;
+    return code;
+}
+
+#define CUDA_TRY(net, expr)                                                                 \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            if (e_ == cudaErrorMemoryAllocation)                                            \
+                return fail(net, SNN_ERR_OOM, "%s: %s", #expr, cudaGetErrorString(e_));    \
+            return fail(net, SNN_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_));       \
+        }                                                                                   \
+    } while (0)
+
+int steps_of(float ms, float dt) { return (int)std::lround((double)ms / (double)dt); }
+
+bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
+
+// SplitMix64 stream (Steele, Lea & Flood 2014) for the seeded weight init:
+// uniform [0, 0.3] rounded to the 2^-12 grid, drawn in row-major order.
+uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+void seeded_weights(uint64_t seed, size_t n, std::vector<float>& w) {
+    w.resize(n);
+    uint64_t s = seed;
+    for (size_t k = 0; k < n; ++k) {
+        s += 0x9E3779B97F4A7C15ull;
+        const double u = (double)(mix64(s) >> 11) * 0x1.0p-53;
+        double q = std::floor(u * 0.3 * 4096.0 + 0.5);
+        if (q > 1228.0) q = 1228.0;
+        w[k] = (float)(q / 4096.0);
+    }
+}
+
+void free_batch(snn_net* n) {
+    snn::Bufs& d = n->d;
+    void* ptrs[] = {d.thrT, d.seeds, d.x_preT, d.inb, d.preT, d.v_e, d.v_i, d.x_post, d.st,
+                    d.cnt, d.postT, d.spkT, d.counts, n->rates_stage, n->seeds_stage};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    d.thrT = nullptr; d.seeds = nullptr; d.x_preT = nullptr; d.inb = nullptr; d.preT = nullptr;
+    d.v_e = nullptr; d.v_i = nullptr; d.x_post = nullptr; d.st = nullptr; d.cnt = nullptr;
+    d.postT = nullptr; d.spkT = nullptr; d.counts = nullptr;
+    n->rates_stage = nullptr; n->seeds_stage = nullptr;
+    n->B = 0;
+    n->state_valid = false;
+    n->generation++;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc((void**)p, count * sizeof(T) + 16);
+}
+
+snn_status alloc_batch(snn_net* n, int B) {
+    free_batch(n);
+    const size_t NI = n->spec.n_in, N = n->spec.n_exc;
+    const size_t Bw = ((size_t)B + 31) / 32, Bp = Bw * 32, Iw = (NI + 31) / 32;
+    snn::Bufs& d = n->d;
+    CUDA_TRY(n, dalloc(&d.thrT, NI * Bp));
+    CUDA_TRY(n, dalloc(&d.seeds, (size_t)B));
+    CUDA_TRY(n, dalloc(&d.x_preT, NI * Bp));
+    CUDA_TRY(n, dalloc(&d.inb, (size_t)B * Iw));
+    CUDA_TRY(n, dalloc(&d.preT, NI * Bw));
+    CUDA_TRY(n, dalloc(&d.v_e, (size_t)B * N));
+    CUDA_TRY(n, dalloc(&d.v_i, (size_t)B * N));
+    CUDA_TRY(n, dalloc(&d.x_post, (size_t)B * N));
+    CUDA_TRY(n, dalloc(&d.st, (size_t)B * N));
+    CUDA_TRY(n, dalloc(&d.cnt, 2 * (size_t)B));
+    CUDA_TRY(n, dalloc(&d.postT, 2 * N * Bw));
+    CUDA_TRY(n, dalloc(&d.spkT, N * Bw));
+    CUDA_TRY(n, dalloc(&d.counts, (size_t)B * N));
+    CUDA_TRY(n, dalloc(&n->rates_stage, (size_t)B * NI));
+    CUDA_TRY(n, dalloc(&n->seeds_stage, (size_t)B));
+    CUDA_TRY(n, cudaMemset(d.x_preT, 0, NI * Bp * sizeof(float)));
+    n->B = B;
+    return SNN_OK;
+}
+
+snn_status ensure_raster(snn_net* n, uint32_t** buf, size_t* cap, size_t words) {
+    if (*cap >= words && *buf) return SNN_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    CUDA_TRY(n, dalloc(buf, words));
+    *cap = words;
+    n->generation++;
+    return SNN_OK;
+}
+
+snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce, unsigned flags) {
+    const snn_spec& s = n->spec;
+    snn::Consts c{};
+    c.n_in = s.n_in; c.N = s.n_exc; c.B = B;
+    c.Bw = (B + 31) / 32; c.Bp = c.Bw * 32;
+    c.Iw = (s.n_in + 31) / 32; c.Nw = (s.n_exc + 31) / 32;
+    c.e_rest = s.e_rest; c.e_reset = s.e_reset; c.e_thresh = s.e_thresh;
+    c.a_e = (float)std::exp(-(double)dt / (double)s.e_tau_ms);
+    c.i_rest = s.i_rest; c.i_reset = s.i_reset; c.i_thresh = s.i_thresh;
+    c.a_i = (float)std::exp(-(double)dt / (double)s.i_tau_ms);
+    c.w_ei = s.w_ei; c.w_ie = s.w_ie;
+    c.a_x = (float)std::exp(-(double)dt / (double)s.trace_tau_ms);
+    c.nu_pre = s.nu_pre; c.nu_post = s.nu_post; c.w_min = s.w_min; c.w_max = s.w_max;
+    c.R_e = steps_of(s.e_refrac_ms, dt);
+    c.R_i = steps_of(s.i_refrac_ms, dt);
+    c.a_th = std::exp(-(double)dt / (double)s.theta_tau_ms);
+    c.theta_plus = (double)s.theta_plus;
+    c.dt = dt;
+    c.reduce = reduce;
+    c.learn = learn ? 1 : 0;
+    c.rec_raster = (flags & SNN_RECORD_RASTER) ? 1 : 0;
+    c.rec_input = (flags & SNN_RECORD_INPUT) ? 1 : 0;
+    return c;
+}
+
+snn::Bufs run_bufs(const snn_net* n) { return n->d; }
+
+size_t field_bytes(const snn_net* n, int field) {
+    const size_t B = n->B, N = n->spec.n_exc, NI = n->spec.n_in;
+    const size_t Nw = (N + 31) / 32, Iw = (NI + 31) / 32;
+    switch (field) {
+        case SNN_FIELD_V_EXC: case SNN_FIELD_V_INH: case SNN_FIELD_X_POST:
+            return B * N * 4;
+        case SNN_FIELD_REF_EXC: case SNN_FIELD_REF_INH:
+        case SNN_FIELD_SPIKES_EXC: case SNN_FIELD_SPIKES_INH:
+            return B * N;
+        case SNN_FIELD_X_PRE: return B * NI * 4;
+        case SNN_FIELD_THETA: return N * 8;
+        case SNN_FIELD_SPIKE_COUNTS: return B * N * 4;
+        case SNN_FIELD_RASTER_EXC: case SNN_FIELD_RASTER_INH:
+            return n->last_rec_raster ? (size_t)n->last_T * B * Nw * 4 : 0;
+        case SNN_FIELD_RASTER_INPUT:
+            return n->last_rec_input ? (size_t)n->last_T * B * Iw * 4 : 0;
+        case SNN_FIELD_STEP: return 8;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+void snn_spec_default(snn_spec* s, int32_t n_exc) {
+    if (!s) return;
+    std::memset(s, 0, sizeof *s);
+    s->n_in = 784; s->n_exc = n_exc; s->n_inh = n_exc;
+    s->e_rest = -65.0f; s->e_reset = -60.0f; s->e_thresh = -52.0f;
+    s->e_tau_ms = 100.0f; s->e_refrac_ms = 5.0f;
+    s->theta_plus = 0.05f; s->theta_tau_ms = 1e7f;
+    s->i_rest = -60.0f; s->i_reset = -45.0f; s->i_thresh = -40.0f;
+    s->i_tau_ms = 10.0f; s->i_refrac_ms = 2.0f;
+    s->w_ei = 22.5f; s->w_ie = -17.5f;
+    s->trace_tau_ms = 20.0f; s->nu_pre = 1e-4f; s->nu_post = 1e-2f;
+    s->w_min = 0.0f; s->w_max = 1.0f;
+    s->wprec = SNN_W_FP32;
+    s->w_seed = 42;
+}
+
+snn_status snn_create(const snn_spec* spec, snn_net** out) {
+    if (!out) return fail(nullptr, SNN_ERR_ARG, "snn_create: out is NULL");
+    *out = nullptr;
+    if (!spec) return fail(nullptr, SNN_ERR_ARG, "snn_create: spec is NULL");
+    const snn_spec& s = *spec;
+    if (s.n_in <= 0 || s.n_exc <= 0)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: n_in and n_exc must be > 0");
+    if (s.n_inh != s.n_exc)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: n_inh must equal n_exc (one-to-one exc->inh)");
+    if ((size_t)s.n_in * (size_t)s.n_exc > ((size_t)1 << 31))
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: n_in*n_exc exceeds 2^31");
+    if (!finite_pos(s.e_tau_ms) || !finite_pos(s.i_tau_ms) || !finite_pos(s.trace_tau_ms) ||
+        !(s.theta_tau_ms > 0.0f))
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: time constants must be > 0");
+    if (!(s.e_refrac_ms >= 0.0f) || !(s.i_refrac_ms >= 0.0f))
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: refractory periods must be >= 0");
+    if (!(s.w_min <= s.w_max))
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: w_min must be <= w_max");
+    if (s.wprec != SNN_W_FP32)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: wprec %d is not available in this build",
+                    (int)s.wprec);
+
+    snn_net* n = new (std::nothrow) snn_net();
+    if (!n) return fail(nullptr, SNN_ERR_OOM, "snn_create: host allocation failed");
+    n->spec = s;
+    n->spec.w_init = nullptr;
+    n->spec.theta_init = nullptr;
+    cudaError_t e = cudaGetDevice(&n->device);
+    const size_t nw = (size_t)s.n_in * s.n_exc;
+    if (e == cudaSuccess) e = dalloc(&n->d.W, nw);
+    if (e == cudaSuccess) e = dalloc(&n->d.theta, (size_t)s.n_exc);
+    if (e == cudaSuccess) e = dalloc(&n->d.step, 2);
+    if (e == cudaSuccess) e = dalloc(&n->d.err, 4);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking);
+    std::vector<float> w;
+    if (e == cudaSuccess) {
+        if (s.w_init) w.assign(s.w_init, s.w_init + nw);
+        else seeded_weights(s.w_seed, nw, w);
+        e = cudaMemcpy(n->d.W, w.data(), nw * 4, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = snn::launch_clip_weights(n->d.W, nw, s.w_min, s.w_max, nullptr);
+    if (e == cudaSuccess) {
+        std::vector<double> th(s.n_exc, 0.0);
+        if (s.theta_init) th.assign(s.theta_init, s.theta_init + s.n_exc);
+        e = cudaMemcpy(n->d.theta, th.data(), th.size() * 8, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(n->d.step, 0, 16);
+    if (e == cudaSuccess) e = cudaMemset(n->d.err, 0, 16);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        snn_status code = e == cudaErrorMemoryAllocation ? SNN_ERR_OOM : SNN_ERR_CUDA;
+        fail(nullptr, code, "snn_create: %s", cudaGetErrorString(e));
+        snn_destroy(n);
+        return code;
+    }
+    *out = n;
+    return SNN_OK;
+}
+
+snn_status snn_destroy(snn_net* n) {
+    if (!n) return SNN_OK;
+    if (n->last) cudaStreamSynchronize(n->last);
+    free_batch(n);
+    void* ptrs[] = {n->d.W, n->d.theta, n->d.step, n->d.err, n->d.raster_e, n->d.raster_i,
+                    n->d.raster_in, n->scratch};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    if (n->gexec) cudaGraphExecDestroy(n->gexec);
+    if (n->cap) cudaStreamDestroy(n->cap);
+    delete n;
+    return SNN_OK;
+}
+
+snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B, int T,
+                   float dt, int learn, int reduce, unsigned flags, void* stream_) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_run: net is NULL");
+    n->err.clear();
+    if (B <= 0) return fail(n, SNN_ERR_ARG, "snn_run: B must be > 0 (got %d)", B);
+    if (T < 0) return fail(n, SNN_ERR_ARG, "snn_run: T must be >= 0 (got %d)", T);
+    if (!finite_pos(dt)) return fail(n, SNN_ERR_ARG, "snn_run: dt_ms must be finite and > 0");
+    if (!rates || !seeds)
+        return fail(n, SNN_ERR_ARG, "snn_run: rates_hz and seeds must be non-NULL");
+    if (reduce < SNN_REDUCE_SUM || reduce > SNN_REDUCE_MAX)
+        return fail(n, SNN_ERR_ARG, "snn_run: unknown reduce %d", reduce);
+    const unsigned known = SNN_CONTINUE | SNN_RECORD_RASTER | SNN_RECORD_INPUT | SNN_HOST_INPUTS |
+                           SNN_MODE_MASK;
+    if (flags & ~known)
+        return fail(n, SNN_ERR_ARG, "snn_run: unknown flag bits 0x%x", flags & ~known);
+    const int R_e = steps_of(n->spec.e_refrac_ms, dt), R_i = steps_of(n->spec.i_refrac_ms, dt);
+    if (R_e > 255 || R_i > 255)
+        return fail(n, SNN_ERR_ARG, "snn_run: refractory period exceeds 255 steps at this dt");
+    if ((size_t)B * (size_t)n->spec.n_exc > ((size_t)1 << 31) ||
+        (size_t)B * (size_t)n->spec.n_in > ((size_t)1 << 31))
+        return fail(n, SNN_ERR_ARG, "snn_run: B*n_exc or B*n_in exceeds 2^31");
+    const bool cont = (flags & SNN_CONTINUE) != 0;
+    cudaStream_t st = (cudaStream_t)stream_;
+    CUDA_TRY(n, cudaSetDevice(n->device));
+
+    // Dynamic minibatch size: a new B re-initialises the per-sample state.
+    if (B != n->B) {
+        if (cont)
+            return fail(n, SNN_ERR_STATE,
+                        "snn_run: SNN_CONTINUE with batch %d but the state holds batch %d", B, n->B);
+        if (n->last) CUDA_TRY(n, cudaStreamSynchronize(n->last));
+        CUDA_TRY(n, cudaStreamSynchronize(st));
+        snn_status r = alloc_batch(n, B);
+        if (r != SNN_OK) return r;
+    } else if (cont && !n->state_valid) {
+        return fail(n, SNN_ERR_STATE, "snn_run: SNN_CONTINUE without a previous run");
+    }
+    const size_t Nw = ((size_t)n->spec.n_exc + 31) / 32, Iw = ((size_t)n->spec.n_in + 31) / 32;
+    const bool rec_r = (flags & SNN_RECORD_RASTER) != 0, rec_i = (flags & SNN_RECORD_INPUT) != 0;
+    if (rec_r || rec_i) {
+        // Growing a recording buffer frees the old one: drain both streams first.
+        if (n->last) CUDA_TRY(n, cudaStreamSynchronize(n->last));
+        CUDA_TRY(n, cudaStreamSynchronize(st));
+    }
+    if (rec_r) {
+        const size_t words = (size_t)T * B * Nw;
+        snn_status r = ensure_raster(n, &n->d.raster_e, &n->raster_e_cap, words);
+        if (r == SNN_OK) r = ensure_raster(n, &n->d.raster_i, &n->raster_i_cap, words);
+        if (r != SNN_OK) return r;
+        CUDA_TRY(n, cudaMemsetAsync(n->d.raster_e, 0, words * 4, st));
+        CUDA_TRY(n, cudaMemsetAsync(n->d.raster_i, 0, words * 4, st));
+    }
+    if (rec_i) {
+        const size_t words = (size_t)T * B * Iw;
+        snn_status r = ensure_raster(n, &n->d.raster_in, &n->raster_in_cap, words);
+        if (r != SNN_OK) return r;
+    }
+
+    const float* r_dev = rates;
+    const uint64_t* s_dev = seeds;
+    if (flags & SNN_HOST_INPUTS) {
+        CUDA_TRY(n, cudaMemcpyAsync(n->rates_stage, rates, (size_t)B * n->spec.n_in * 4,
+                                    cudaMemcpyHostToDevice, st));
+        CUDA_TRY(n, cudaMemcpyAsync(n->seeds_stage, seeds, (size_t)B * 8, cudaMemcpyHostToDevice, st));
+        r_dev = n->rates_stage;
+        s_dev = n->seeds_stage;
+    }
+    const snn::Consts c = make_consts(n, B, dt, learn, reduce, flags);
+    const snn::Bufs d = run_bufs(n);
+    CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st));
+
+    const unsigned mode = flags & SNN_MODE_MASK;
+    if (mode == SNN_MODE_STEP) {
+        for (int t = 0; t < T; ++t) CUDA_TRY(n, snn::launch_step(c, d, t, st));
+    } else if (mode == SNN_MODE_GRAPH || mode == SNN_MODE_AUTO) {
+        GraphKey key;
+        key.B = B; key.T = T; key.learn = c.learn; key.reduce = reduce;
+        key.rec_raster = c.rec_raster; key.rec_input = c.rec_input;
+        std::memcpy(&key.dt_bits, &dt, 4);
+        key.generation = n->generation;
+        if (!n->gexec || !(key == n->gkey)) {
+            if (n->gexec) {
+                CUDA_TRY(n, cudaStreamSynchronize(st));
+                cudaGraphExecDestroy(n->gexec);
+                n->gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            CUDA_TRY(n, cudaStreamBeginCapture(n->cap, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = cudaSuccess;
+            for (int t = 0; t < T && le == cudaSuccess; ++t) le = snn::launch_step(c, d, t, n->cap);
+            cudaError_t ee = cudaStreamEndCapture(n->cap, &g);
+            CUDA_TRY(n, le);
+            CUDA_TRY(n, ee);
+            cudaError_t ie = cudaGraphInstantiate(&n->gexec, g, 0);
+            cudaGraphDestroy(g);
+            CUDA_TRY(n, ie);
+            n->gkey = key;
+        }
+        CUDA_TRY(n, cudaGraphLaunch(n->gexec, st));
+    } else {
+        int used = 0;
+        CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used));
+        if (!used)
+            return fail(n, SNN_ERR_ARG,
+                        "snn_run: the persistent kernel cannot hold this configuration resident");
+    }
+    n->last = st;
+    n->state_valid = true;
+    n->last_T = T;
+    n->last_rec_raster = rec_r;
+    n->last_rec_input = rec_i;
+    return SNN_OK;
+}
+
+size_t snn_field_bytes(const snn_net* n, int field) {
+    if (!n || field < 0 || field >= SNN_FIELD_COUNT) return 0;
+    if (field != SNN_FIELD_THETA && field != SNN_FIELD_STEP && n->B == 0) return 0;
+    return field_bytes(n, field);
+}
+
+snn_status snn_read_state(snn_net* n, int field, void* dst, size_t bytes, int dst_on_device) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_read_state: net is NULL");
+    n->err.clear();
+    if (!dst) return fail(n, SNN_ERR_ARG, "snn_read_state: dst is NULL");
+    if (field < 0 || field >= SNN_FIELD_COUNT)
+        return fail(n, SNN_ERR_ARG, "snn_read_state: unknown field %d", field);
+    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP;
+    if (per_sample && !n->state_valid)
+        return fail(n, SNN_ERR_STATE, "snn_read_state: no run has produced this state yet");
+    const size_t want = field_bytes(n, field);
+    if (want == 0) return fail(n, SNN_ERR_STATE, "snn_read_state: field %d was not recorded", field);
+    if (bytes != want)
+        return fail(n, SNN_ERR_ARG, "snn_read_state: field %d needs %zu bytes, got %zu", field,
+                    want, bytes);
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    cudaStream_t st = n->last;
+    CUDA_TRY(n, cudaStreamSynchronize(st));
+    const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const void* src = nullptr;
+    switch (field) {
+        case SNN_FIELD_V_EXC: src = n->d.v_e; break;
+        case SNN_FIELD_V_INH: src = n->d.v_i; break;
+        case SNN_FIELD_X_POST: src = n->d.x_post; break;
+        case SNN_FIELD_THETA: src = n->d.theta; break;
+        case SNN_FIELD_SPIKE_COUNTS: src = n->d.counts; break;
+        case SNN_FIELD_RASTER_EXC: src = n->d.raster_e; break;
+        case SNN_FIELD_RASTER_INH: src = n->d.raster_i; break;
+        case SNN_FIELD_RASTER_INPUT: src = n->d.raster_in; break;
+        case SNN_FIELD_STEP: src = n->d.step + 1; break;
+        default: break;
+    }
+    if (!src) {   // fields stored in another layout: extract on the device
+        const snn::Consts c = make_consts(n, n->B, 1.0f, 0, 0, 0);
+        void* out = dst;
+        if (!dst_on_device) {
+            if (n->scratch_bytes < want) {
+                if (n->scratch) cudaFree(n->scratch);
+                n->scratch = nullptr;
+                n->scratch_bytes = 0;
+                CUDA_TRY(n, cudaMalloc(&n->scratch, want));
+                n->scratch_bytes = want;
+            }
+            out = n->scratch;
+        }
+        CUDA_TRY(n, snn::launch_extract(c, n->d, field, out, st));
+        if (!dst_on_device) CUDA_TRY(n, cudaMemcpyAsync(dst, out, want, kind, st));
+    } else {
+        CUDA_TRY(n, cudaMemcpyAsync(dst, src, want, kind, st));
+    }
+    CUDA_TRY(n, cudaStreamSynchronize(st));
+    return SNN_OK;
+}
+
+snn_status snn_read_weights(snn_net* n, float* dst, size_t bytes, int dst_on_device) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_read_weights: net is NULL");
+    n->err.clear();
+    const size_t want = (size_t)n->spec.n_in * n->spec.n_exc * 4;
+    if (!dst || bytes != want)
+        return fail(n, SNN_ERR_ARG, "snn_read_weights: need a %zu-byte buffer", want);
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    CUDA_TRY(n, cudaMemcpyAsync(dst, n->d.W, want,
+                                dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                n->last));
+    CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    return SNN_OK;
+}
+
+snn_status snn_write_weights(snn_net* n, const float* src, size_t bytes, int src_on_device) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_write_weights: net is NULL");
+    n->err.clear();
+    const size_t count = (size_t)n->spec.n_in * n->spec.n_exc;
+    if (!src || bytes != count * 4)
+        return fail(n, SNN_ERR_ARG, "snn_write_weights: need a %zu-byte buffer", count * 4);
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    CUDA_TRY(n, cudaMemcpyAsync(n->d.W, src, bytes,
+                                src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                n->last));
+    CUDA_TRY(n, snn::launch_clip_weights(n->d.W, count, n->spec.w_min, n->spec.w_max, n->last));
+    CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    return SNN_OK;
+}
+
+const char* snn_last_error(const snn_net* n) {
+    return n ? n->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal declarations shared by the kernels and the C ABI implementation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "snn.h"
+
+namespace snn {
+
+// Per-run constants.  Decay factors are computed on the host in double and
+// rounded once (a = (float)exp(-dt/tau)); the theta decay stays in double
+// because exp(-dt/tau_theta) = 1 - 1e-7 is below FP32 resolution.
+struct Consts {
+    int n_in, N, B;     // inputs, excitatory (= inhibitory) neurons, batch
+    int Bp, Bw;         // batch padded to 32, and its 32-bit word count
+    int Iw, Nw;         // words per sample of the input / neuron bitmasks
+    float e_rest, e_reset, e_thresh, a_e;
+    float i_rest, i_reset, i_thresh, a_i;
+    float w_ei, w_ie, a_x, nu_pre, nu_post, w_min, w_max;
+    int R_e, R_i;       // refractory periods in steps
+    double a_th, theta_plus;
+    float dt;
+    int reduce, learn;
+    int rec_raster, rec_input;
+};
+
+// Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j;
+// input-major "[n_in][Bp]" arrays index i*Bp + b (samples are the fast axis
+// so a warp of 32 samples reads one 128-byte line).
+struct Bufs {
+    float* W;            // [n_in][N]  FP32 master weights
+    double* theta;       // [N]        adaptive thresholds (FP64)
+    uint32_t* thrT;      // [n_in][Bp] Poisson thresholds of this run
+    uint64_t* seeds;     // [B]        per-sample Poisson seeds
+    float* x_preT;       // [n_in][Bp] presynaptic traces
+    uint32_t* inb;       // [B][Iw]    input spikes of this step, sample-major bits
+    uint32_t* preT;      // [n_in][Bw] input spikes of this step, input-major bits
+    float* v_e;          // [B][N]
+    float* v_i;          // [B][N]
+    float* x_post;       // [B][N]
+    uint32_t* st;        // [B][N]  ref_e | ref_i<<8 | s_e'<<16 | s_i'<<17
+    uint32_t* cnt;       // [2][B]  inhibitory spike count per step parity
+    uint32_t* postT;     // [2][N][Bw] excitatory spikes per step parity, column-major bits
+    uint32_t* spkT;      // [N][Bw] samples in which neuron j has spiked this episode
+    uint32_t* counts;    // [B][N]  excitatory spike counts of this run
+    uint32_t* raster_e;  // [T][B][Nw] (optional)
+    uint32_t* raster_i;  // [T][B][Nw] (optional)
+    uint32_t* raster_in; // [T][B][Iw] (optional)
+    unsigned long long* step;  // [2]: first step of this run, step after it
+    uint32_t* err;       // [4]  device error word (bounded waits), diagnostic
+};
+
+// Packed per-(b,j) state word.
+constexpr uint32_t ST_SE = 1u << 16;
+constexpr uint32_t ST_SI = 1u << 17;
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the first output of a
+// generator whose state is x.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Launchers (snn_step.cu).
+cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
+                             const uint64_t* seeds, int episodic, int T, cudaStream_t s);
+cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s);
+cudaError_t launch_extract(const Consts& c, const Bufs& d, int field, void* scratch,
+                           cudaStream_t s);
+
+}  // namespace snn

@@ -1,0 +1,342 @@
+// Per-step kernels of the minibatched SNN time step (the plain "one launch per
+// phase per step" form; the CUDA-graph form replays exactly these launches).
+//
+// One step is three launches:
+//   k_encode : Poisson input spikes (integer hash vs threshold), presynaptic
+//              traces, and the two bitmask layouts of the input spikes
+//              (sample-major for the current gather, input-major for STDP);
+//   k_neuron : synaptic current gathered over the active inputs in ascending
+//              order, all-but-self inhibition from a per-sample popcount,
+//              excitatory adaptive-threshold LIF, inhibitory LIF, postsynaptic
+//              traces;
+//   k_stdp   : (learning only) adaptive thresholds, and the pair-STDP update
+//              reduced over the batch, visiting for each synapse only the
+//              samples whose update can be non-zero, in ascending order.
+//
+// All floating-point arithmetic uses explicit round-to-nearest intrinsics in a
+// fixed order so no multiply-add is contracted; with FP32 weights the result
+// does not depend on the launch configuration.
+#include <cfloat>
+
+#include "snn_internal.cuh"
+
+namespace snn {
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr int STDP_ROWS = 64;   // input rows per k_stdp block
+
+// Bernoulli threshold of one time bin: p = rate * dt / 1000 scaled to 2^32,
+// computed in FP64 (Sec. "Scaling a Two Layer Network": Poisson spike trains).
+__device__ __forceinline__ uint32_t poisson_threshold(float rate, float dt) {
+    double p = __dmul_rn((double)rate, (double)dt);
+    p = __dmul_rn(p, 1e-3);
+    const double x = __dmul_rn(p, 4294967296.0);
+    if (!(x > 0.0)) return 0u;
+    if (x >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)floor(x);
+}
+
+__global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
+                            const uint64_t* __restrict__ seeds, int episodic, int T) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    const size_t n_thr = (size_t)c.n_in * c.Bp;
+    for (size_t k = tid; k < n_thr; k += nth) {
+        const int i = (int)(k / c.Bp), b = (int)(k % c.Bp);
+        d.thrT[k] = b < c.B ? poisson_threshold(rates[(size_t)b * c.n_in + i], c.dt) : 0u;
+        if (episodic) d.x_preT[k] = 0.0f;
+    }
+    const size_t n_bn = (size_t)c.B * c.N;
+    for (size_t k = tid; k < n_bn; k += nth) {
+        if (episodic) {
+            d.v_e[k] = c.e_rest;
+            d.v_i[k] = c.i_rest;
+            d.x_post[k] = 0.0f;
+            d.st[k] = 0u;
+        }
+        d.counts[k] = 0u;
+    }
+    if (episodic) {
+        const size_t n_nw = (size_t)c.N * c.Bw;
+        for (size_t k = tid; k < n_nw; k += nth) {
+            d.spkT[k] = 0u;
+            d.postT[k] = 0u;
+            d.postT[n_nw + k] = 0u;
+        }
+        for (size_t k = tid; k < 2 * (size_t)c.B; k += nth) d.cnt[k] = 0u;
+    }
+    for (size_t k = tid; k < (size_t)c.B; k += nth) d.seeds[k] = seeds[k];
+    if (tid == 0) {
+        const unsigned long long base = episodic ? 0ull : d.step[1];
+        d.step[0] = base;
+        d.step[1] = base + (unsigned long long)T;
+    }
+}
+
+// grid (Bw, ceil(Iw/8)), 256 threads: warp = 32 samples x one 32-input word.
+__global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
+    const int par = (int)(tt & 1ull);
+    {   // clear this step's accumulators; their previous readers finished two launches ago
+        const size_t nblk = (size_t)gridDim.x * gridDim.y;
+        const size_t gtid = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+        const size_t nth = nblk * blockDim.x;
+        const size_t n_nw = (size_t)c.N * c.Bw;
+        uint32_t* post = d.postT + (size_t)par * n_nw;
+        for (size_t k = gtid; k < n_nw; k += nth) post[k] = 0u;
+        uint32_t* cnt = d.cnt + (size_t)par * c.B;
+        for (size_t k = gtid; k < (size_t)c.B; k += nth) cnt[k] = 0u;
+    }
+    const int iw = blockIdx.y * 8 + warp;
+    if (iw >= c.Iw) return;
+    const int g = blockIdx.x;
+    const int b = g * 32 + lane;
+    const uint64_t seed = b < c.B ? d.seeds[b] : 0ull;
+    const int i0 = iw * 32;
+    const int n = min(32, c.n_in - i0);
+    uint32_t word = 0;
+    for (int k = 0; k < n; ++k) {
+        const int i = i0 + k;
+        const size_t o = (size_t)i * c.Bp + b;
+        const uint32_t thr = d.thrT[o];
+        uint32_t s = 0;
+        if (thr != 0u) {
+            const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)i;
+            const uint32_t h = (uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32);
+            s = h < thr ? 1u : 0u;
+        }
+        float x = d.x_preT[o];
+        x = __fmul_rn(x, c.a_x);
+        x = __fadd_rn(x, s ? 1.0f : 0.0f);
+        d.x_preT[o] = x;
+        const uint32_t bal = __ballot_sync(FULL, s);
+        if (lane == 0) d.preT[(size_t)i * c.Bw + g] = bal;
+        word |= s << k;
+    }
+    if (b < c.B) {
+        d.inb[(size_t)b * c.Iw + iw] = word;
+        if (c.rec_input) d.raster_in[((size_t)t_local * c.B + b) * c.Iw + iw] = word;
+    }
+}
+
+// One thread per (b, j).
+__global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)c.B * c.N) return;
+    const int b = (int)(idx / c.N), j = (int)(idx % c.N);
+    const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
+    const int par = (int)(tt & 1ull);
+
+    // Synaptic current: sum of W[i][j] over the active inputs, ascending i.
+    float I = 0.0f;
+    const uint32_t* ib = d.inb + (size_t)b * c.Iw;
+    const float* Wj = d.W + j;
+    for (int w = 0; w < c.Iw; ++w) {
+        uint32_t m = ib[w];
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            I = __fadd_rn(I, Wj[(size_t)(w * 32 + k) * c.N]);
+        }
+    }
+    const uint32_t s = d.st[idx];
+    int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
+    const int se_prev = (s & ST_SE) ? 1 : 0, si_prev = (s & ST_SI) ? 1 : 0;
+    const int C = (int)d.cnt[(size_t)(par ^ 1) * c.B + b];
+    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));   // all-but-self
+    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);         // one-to-one
+
+    // Excitatory, adaptive threshold.
+    float v = d.v_e[idx];
+    float dv = __fsub_rn(v, c.e_rest);
+    dv = __fmul_rn(dv, c.a_e);
+    v = __fadd_rn(c.e_rest, dv);
+    const bool free_e = ref_e == 0;
+    if (!free_e) ref_e -= 1;
+    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
+    const float th = __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j]));
+    const bool se = free_e && v >= th;
+    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    d.v_e[idx] = v;
+
+    // Inhibitory.
+    float vi = d.v_i[idx];
+    dv = __fsub_rn(vi, c.i_rest);
+    dv = __fmul_rn(dv, c.a_i);
+    vi = __fadd_rn(c.i_rest, dv);
+    const bool free_i = ref_i == 0;
+    if (!free_i) ref_i -= 1;
+    else vi = __fadd_rn(vi, I_inh);
+    const bool si = free_i && vi >= c.i_thresh;
+    if (si) { vi = c.i_reset; ref_i = c.R_i; }
+    d.v_i[idx] = vi;
+
+    // Postsynaptic trace.
+    float x = d.x_post[idx];
+    x = __fmul_rn(x, c.a_x);
+    x = __fadd_rn(x, se ? 1.0f : 0.0f);
+    d.x_post[idx] = x;
+
+    d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+    if (se) {
+        d.counts[idx] += 1u;
+        const uint32_t bit = 1u << (b & 31);
+        atomicOr(&d.postT[((size_t)par * c.N + j) * c.Bw + (b >> 5)], bit);
+        atomicOr(&d.spkT[(size_t)j * c.Bw + (b >> 5)], bit);
+        if (c.rec_raster)
+            atomicOr(&d.raster_e[((size_t)t_local * c.B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+    }
+    if (si) {
+        atomicAdd(&d.cnt[(size_t)par * c.B + b], 1u);
+        if (c.rec_raster)
+            atomicOr(&d.raster_i[((size_t)t_local * c.B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+    }
+}
+
+// grid (ceil(N/32), ceil(n_in/STDP_ROWS)), 256 threads; lane = column j,
+// warps stride over the rows of the tile.  For synapse (i, j) the update of
+// sample b can be non-zero only if j fired in b this step (potentiation) or
+// input i fired in b and j has fired in b earlier in the episode (x_post > 0,
+// depression).  Those samples are visited in ascending b, so the sum is the
+// ascending-b sum of the definition with its zero terms left out.
+template <int REDUCE>
+__global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + lane;
+    const bool vj = j < c.N;
+    const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
+    const int par = (int)(tt & 1ull);
+    const uint32_t* Sj = d.spkT + (size_t)(vj ? j : 0) * c.Bw;
+    const uint32_t* Qj = d.postT + ((size_t)par * c.N + (vj ? j : 0)) * c.Bw;
+
+    // Adaptive thresholds of this column group, once (row tile 0, warp 0).
+    if (blockIdx.y == 0 && warp == 0 && vj) {
+        int n = 0;
+        for (int w = 0; w < c.Bw; ++w) n += __popc(Qj[w]);
+        double r;
+        if (REDUCE == SNN_REDUCE_SUM) r = (double)n;
+        else if (REDUCE == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)c.B);
+        else r = n > 0 ? 1.0 : 0.0;
+        d.theta[j] = __dadd_rn(__dmul_rn(d.theta[j], c.a_th), __dmul_rn(c.theta_plus, r));
+    }
+
+    int active = 0;
+    if (vj)
+        for (int w = 0; w < c.Bw; ++w) active |= (Sj[w] | Qj[w]) != 0u;
+    if (!__syncthreads_or(active)) return;   // no neuron of the group has fired yet
+
+    const int i_end = min(c.n_in, (int)(blockIdx.y + 1) * STDP_ROWS);
+    for (int i = blockIdx.y * STDP_ROWS + warp; i < i_end; i += 8) {
+        const uint32_t* P = d.preT + (size_t)i * c.Bw;
+        float acc = (REDUCE == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
+        int nev = 0;
+        if (vj) {
+            for (int w = 0; w < c.Bw; ++w) {
+                const uint32_t p = P[w], q = Qj[w];
+                uint32_t m = (p & Sj[w]) | q;
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int b = w * 32 + bit;
+                    float a = 0.0f, e = 0.0f;
+                    if ((q >> bit) & 1u) a = __fmul_rn(c.nu_post, d.x_preT[(size_t)i * c.Bp + b]);
+                    if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, d.x_post[(size_t)b * c.N + j]);
+                    const float dl = __fsub_rn(a, e);
+                    if (REDUCE == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
+                    else acc = __fadd_rn(acc, dl);
+                    ++nev;
+                }
+            }
+        }
+        if (nev > 0) {
+            float D = acc;
+            if (REDUCE == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)c.B);
+            if (REDUCE == SNN_REDUCE_MAX && nev < c.B) D = fmaxf(D, 0.0f);  // idle samples add 0
+            float wv = d.W[(size_t)i * c.N + j];
+            wv = __fadd_rn(wv, D);
+            wv = wv < c.w_min ? c.w_min : wv;
+            wv = wv > c.w_max ? c.w_max : wv;
+            d.W[(size_t)i * c.N + j] = wv;
+        }
+    }
+}
+
+__global__ void k_extract(Consts c, Bufs d, int field, void* out) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    if (field == SNN_FIELD_X_PRE) {
+        float* o = (float*)out;
+        const size_t n = (size_t)c.B * c.n_in;
+        for (size_t k = tid; k < n; k += nth) {
+            const size_t b = k / c.n_in, i = k % c.n_in;
+            o[k] = d.x_preT[i * c.Bp + b];
+        }
+        return;
+    }
+    uint8_t* o = (uint8_t*)out;
+    const size_t n = (size_t)c.B * c.N;
+    for (size_t k = tid; k < n; k += nth) {
+        const uint32_t s = d.st[k];
+        uint32_t v = 0;
+        if (field == SNN_FIELD_REF_EXC) v = s & 0xFFu;
+        else if (field == SNN_FIELD_REF_INH) v = (s >> 8) & 0xFFu;
+        else if (field == SNN_FIELD_SPIKES_EXC) v = (s & ST_SE) ? 1u : 0u;
+        else if (field == SNN_FIELD_SPIKES_INH) v = (s & ST_SI) ? 1u : 0u;
+        o[k] = (uint8_t)v;
+    }
+}
+
+__global__ void k_clip_weights(float* W, size_t n, float w_min, float w_max) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (size_t k = tid; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        float w = __fadd_rn(W[k], 0.0f);          // -0 -> +0
+        w = w < w_min ? w_min : w;
+        w = w > w_max ? w_max : w;
+        W[k] = w;
+    }
+}
+
+int grid_for(size_t n, int threads, int cap) {
+    size_t g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (size_t)cap) g = cap;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
+                             const uint64_t* seeds, int episodic, int T, cudaStream_t s) {
+    const size_t n = (size_t)c.n_in * c.Bp > (size_t)c.B * c.N ? (size_t)c.n_in * c.Bp
+                                                                : (size_t)c.B * c.N;
+    k_begin_run<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(c, d, rates, seeds, episodic, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s) {
+    k_encode<<<dim3(c.Bw, (c.Iw + 7) / 8), 256, 0, s>>>(c, d, t_local);
+    const size_t bn = (size_t)c.B * c.N;
+    k_neuron<<<(unsigned)((bn + 255) / 256), 256, 0, s>>>(c, d, t_local);
+    if (c.learn) {
+        const dim3 g((c.N + 31) / 32, (c.n_in + STDP_ROWS - 1) / STDP_ROWS);
+        if (c.reduce == SNN_REDUCE_SUM) k_stdp<SNN_REDUCE_SUM><<<g, 256, 0, s>>>(c, d, t_local);
+        else if (c.reduce == SNN_REDUCE_MEAN) k_stdp<SNN_REDUCE_MEAN><<<g, 256, 0, s>>>(c, d, t_local);
+        else k_stdp<SNN_REDUCE_MAX><<<g, 256, 0, s>>>(c, d, t_local);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const Consts& c, const Bufs& d, int field, void* out, cudaStream_t s) {
+    const size_t n = field == SNN_FIELD_X_PRE ? (size_t)c.B * c.n_in : (size_t)c.B * c.N;
+    k_extract<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(c, d, field, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s) {
+    k_clip_weights<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(W, n, w_min, w_max);
+    return cudaGetLastError();
+}
+
+}  // namespace snn

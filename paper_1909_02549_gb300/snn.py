@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in ``include/snn.h`` (ctypes; marshalling only).
+
+Every function keeps the C name and argument order.  Device buffers are
+``torch`` CUDA tensors (their ``data_ptr()``), host buffers are numpy arrays;
+streams are ``torch.cuda.Stream`` objects or raw ``cudaStream_t`` integers.
+All computation happens in the CUDA library; if it has not been built this
+module raises at import of the library -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SNN_OK, SNN_ERR_ARG, SNN_ERR_OOM, SNN_ERR_CUDA, SNN_ERR_TIMEOUT, SNN_ERR_CAPACITY, SNN_ERR_STATE = range(7)
+STATUS_NAMES = ["SNN_OK", "SNN_ERR_ARG", "SNN_ERR_OOM", "SNN_ERR_CUDA", "SNN_ERR_TIMEOUT",
+                "SNN_ERR_CAPACITY", "SNN_ERR_STATE"]
+SNN_REDUCE_SUM, SNN_REDUCE_MEAN, SNN_REDUCE_MAX = 0, 1, 2
+REDUCE = {"sum": SNN_REDUCE_SUM, "mean": SNN_REDUCE_MEAN, "max": SNN_REDUCE_MAX}
+SNN_W_FP32, SNN_W_BF16, SNN_W_FP8E4M3 = 0, 1, 2
+SNN_CONTINUE = 1 << 0
+SNN_RECORD_RASTER = 1 << 1
+SNN_RECORD_INPUT = 1 << 2
+SNN_HOST_INPUTS = 1 << 3
+SNN_MODE_STEP = 0 << 8
+SNN_MODE_GRAPH = 1 << 8
+SNN_MODE_PERSISTENT = 2 << 8
+SNN_MODE_AUTO = 3 << 8
+MODES = {"step": SNN_MODE_STEP, "graph": SNN_MODE_GRAPH, "persistent": SNN_MODE_PERSISTENT,
+         "auto": SNN_MODE_AUTO}
+
+(SNN_FIELD_V_EXC, SNN_FIELD_V_INH, SNN_FIELD_REF_EXC, SNN_FIELD_REF_INH, SNN_FIELD_X_PRE,
+ SNN_FIELD_X_POST, SNN_FIELD_THETA, SNN_FIELD_SPIKE_COUNTS, SNN_FIELD_RASTER_EXC,
+ SNN_FIELD_RASTER_INH, SNN_FIELD_RASTER_INPUT, SNN_FIELD_STEP, SNN_FIELD_SPIKES_EXC,
+ SNN_FIELD_SPIKES_INH) = range(14)
+FIELDS = {"v_exc": SNN_FIELD_V_EXC, "v_inh": SNN_FIELD_V_INH, "ref_exc": SNN_FIELD_REF_EXC,
+          "ref_inh": SNN_FIELD_REF_INH, "x_pre": SNN_FIELD_X_PRE, "x_post": SNN_FIELD_X_POST,
+          "theta": SNN_FIELD_THETA, "spike_counts": SNN_FIELD_SPIKE_COUNTS,
+          "raster_exc": SNN_FIELD_RASTER_EXC, "raster_inh": SNN_FIELD_RASTER_INH,
+          "raster_input": SNN_FIELD_RASTER_INPUT, "step": SNN_FIELD_STEP,
+          "spikes_exc": SNN_FIELD_SPIKES_EXC, "spikes_inh": SNN_FIELD_SPIKES_INH}
+FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
+               SNN_FIELD_REF_EXC: np.uint8, SNN_FIELD_REF_INH: np.uint8,
+               SNN_FIELD_X_PRE: np.float32, SNN_FIELD_X_POST: np.float32,
+               SNN_FIELD_THETA: np.float64, SNN_FIELD_SPIKE_COUNTS: np.uint32,
+               SNN_FIELD_RASTER_EXC: np.uint32, SNN_FIELD_RASTER_INH: np.uint32,
+               SNN_FIELD_RASTER_INPUT: np.uint32, SNN_FIELD_STEP: np.uint64,
+               SNN_FIELD_SPIKES_EXC: np.uint8, SNN_FIELD_SPIKES_INH: np.uint8}
+
+EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
+            "snn_read_state", "snn_read_weights", "snn_write_weights", "snn_last_error"]
+
+
+class snn_spec(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_exc", C.c_int32), ("n_inh", C.c_int32)] + [
+        (n, C.c_float) for n in (
+            "e_rest", "e_reset", "e_thresh", "e_tau_ms", "e_refrac_ms", "theta_plus",
+            "theta_tau_ms", "i_rest", "i_reset", "i_thresh", "i_tau_ms", "i_refrac_ms",
+            "w_ei", "w_ie", "trace_tau_ms", "nu_pre", "nu_post", "w_min", "w_max")] + [
+        ("wprec", C.c_int32), ("w_seed", C.c_uint64), ("w_init", C.c_void_p),
+        ("theta_init", C.c_void_p)]
+
+
+class SNNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 7 else status, msg))
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError("CUDA library %s is missing: build it with "
+                               "paper_1909_02549_gb300.build.build()" % _build.LIB)
+        L = C.CDLL(_build.LIB)
+        L.snn_spec_default.argtypes = [C.POINTER(snn_spec), C.c_int32]
+        L.snn_spec_default.restype = None
+        L.snn_create.argtypes = [C.POINTER(snn_spec), C.POINTER(C.c_void_p)]
+        L.snn_destroy.argtypes = [C.c_void_p]
+        L.snn_run.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float,
+                              C.c_int, C.c_int, C.c_uint, C.c_void_p]
+        L.snn_field_bytes.argtypes = [C.c_void_p, C.c_int]
+        L.snn_field_bytes.restype = C.c_size_t
+        L.snn_read_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_read_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_write_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_last_error.argtypes = [C.c_void_p]
+        L.snn_last_error.restype = C.c_char_p
+        for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state",
+                     "snn_read_weights", "snn_write_weights"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(net, rc):
+    if rc != SNN_OK:
+        raise SNNError(rc, snn_last_error(net))
+
+
+def _buf(x):
+    """(pointer, nbytes, on_device) of a torch tensor, numpy array or int."""
+    if x is None:
+        return None, 0, 0
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data, x.nbytes, 0
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr(), x.numel() * x.element_size(), 1 if x.is_cuda else 0
+    return int(x), 0, 1
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+# ------------------------------------------------------------ C names ---
+
+def snn_spec_default(n_exc: int) -> snn_spec:
+    s = snn_spec()
+    lib().snn_spec_default(C.byref(s), n_exc)
+    return s
+
+
+def snn_create(spec: snn_spec):
+    out = C.c_void_p()
+    rc = lib().snn_create(C.byref(spec), C.byref(out))
+    _check(None, rc)
+    return out.value
+
+
+def snn_destroy(net) -> None:
+    _check(net, lib().snn_destroy(net))
+
+
+def snn_run(net, rates, seeds, B: int, T: int, dt_ms: float = 1.0, learn: int = 1,
+            reduce: int = SNN_REDUCE_MEAN, flags: int = 0, stream=None) -> None:
+    rp, _, rdev = _buf(rates)
+    sp, _, _ = _buf(seeds)
+    if not rdev:
+        flags |= SNN_HOST_INPUTS
+    _check(net, lib().snn_run(net, rp, sp, B, T, dt_ms, int(learn), int(reduce), flags,
+                              _stream(stream)))
+
+
+def snn_field_bytes(net, field: int) -> int:
+    return lib().snn_field_bytes(net, field)
+
+
+def snn_read_state(net, field: int, dst) -> None:
+    p, n, dev = _buf(dst)
+    _check(net, lib().snn_read_state(net, field, p, n, dev))
+
+
+def snn_read_weights(net, dst) -> None:
+    p, n, dev = _buf(dst)
+    _check(net, lib().snn_read_weights(net, p, n, dev))
+
+
+def snn_write_weights(net, src) -> None:
+    p, n, dev = _buf(src)
+    _check(net, lib().snn_write_weights(net, p, n, dev))
+
+
+def snn_last_error(net) -> str:
+    r = lib().snn_last_error(net)
+    return r.decode() if r else ""
+
+
+# ------------------------------------------------------- convenience ---
+
+_SPEC_KEYS = {"e_tau": "e_tau_ms", "e_refrac": "e_refrac_ms", "theta_tau": "theta_tau_ms",
+              "i_tau": "i_tau_ms", "i_refrac": "i_refrac_ms", "trace_tau": "trace_tau_ms"}
+
+
+def spec_from_params(params: dict, w_init=None, theta_init=None, wprec: int = SNN_W_FP32,
+                     w_seed: int = 42):
+    """snn_spec from a parameter dict (``synth.diehl_cook_params`` keys).
+    Returns (spec, keep-alive arrays)."""
+    s = snn_spec()
+    for k, v in params.items():
+        setattr(s, _SPEC_KEYS.get(k, k), v)
+    s.n_inh = params["n_exc"]
+    s.wprec = wprec
+    s.w_seed = w_seed
+    keep = []
+    if w_init is not None:
+        w = np.ascontiguousarray(w_init, np.float32)
+        keep.append(w)
+        s.w_init = w.ctypes.data
+    if theta_init is not None:
+        th = np.ascontiguousarray(theta_init, np.float64)
+        keep.append(th)
+        s.theta_init = th.ctypes.data
+    return s, keep
+
+
+class Network:
+    """Owns one ``snn_net``; thin object wrapper over the C calls."""
+
+    def __init__(self, params: dict, w_init=None, theta_init=None, wprec: int = SNN_W_FP32,
+                 w_seed: int = 42):
+        spec, keep = spec_from_params(params, w_init, theta_init, wprec, w_seed)
+        self.params = dict(params)
+        self.handle = snn_create(spec)
+        del keep
+        self.B = 0
+
+    def run(self, rates, seeds, T: int, *, dt: float = 1.0, learn: bool = True,
+            reduce: str = "mean", mode: str = "step", continue_: bool = False,
+            record: bool = False, record_input: bool = False, stream=None) -> None:
+        B = rates.shape[0]
+        flags = MODES[mode]
+        if continue_:
+            flags |= SNN_CONTINUE
+        if record:
+            flags |= SNN_RECORD_RASTER
+        if record_input:
+            flags |= SNN_RECORD_INPUT
+        snn_run(self.handle, rates, seeds, B, T, dt, int(learn), REDUCE[reduce], flags, stream)
+        self.B = B
+        self.T = T
+
+    def read(self, field: str) -> np.ndarray:
+        f = FIELDS[field]
+        nbytes = snn_field_bytes(self.handle, f)
+        dt = np.dtype(FIELD_DTYPE[f])
+        out = np.empty(nbytes // dt.itemsize, dt)
+        if nbytes:
+            snn_read_state(self.handle, f, out)
+        N, NI = self.params["n_exc"], self.params["n_in"]
+        if f in (SNN_FIELD_THETA, SNN_FIELD_STEP):
+            return out
+        if f == SNN_FIELD_X_PRE:
+            return out.reshape(self.B, NI)
+        if f in (SNN_FIELD_RASTER_EXC, SNN_FIELD_RASTER_INH):
+            return out.reshape(self.T, self.B, (N + 31) // 32)
+        if f == SNN_FIELD_RASTER_INPUT:
+            return out.reshape(self.T, self.B, (NI + 31) // 32)
+        return out.reshape(self.B, N)
+
+    def raster(self, field: str = "raster_exc") -> np.ndarray:
+        """Unpacked 0/1 raster [T][B][n] (uint8)."""
+        words = self.read(field)
+        n = self.params["n_in"] if field == "raster_input" else self.params["n_exc"]
+        bits = np.unpackbits(words.view(np.uint8), axis=-1, bitorder="little")
+        return bits[..., :n]
+
+    def weights(self) -> np.ndarray:
+        out = np.empty((self.params["n_in"], self.params["n_exc"]), np.float32)
+        snn_read_weights(self.handle, out)
+        return out
+
+    def set_weights(self, w) -> None:
+        snn_write_weights(self.handle, w)
+
+    def close(self) -> None:
+        if self.handle:
+            snn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,254 @@
+"""Parity of the CUDA path with the CPU oracle, through the C ABI.
+
+With FP32 weights the library evaluates every sum in the oracle's order
+(ascending input index for the synaptic current, ascending sample index for
+the batch reduction of the STDP updates), so rasters, voltages, traces,
+refractory counters, weights and thresholds must agree bit for bit, with
+learning on or off, for every reduction and run mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_02549_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1909_02549_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def snn():
+    from paper_1909_02549_gb300 import snn as m
+    return m
+
+
+def dev(a):
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def bits(a):
+    a = np.ascontiguousarray(a)
+    return a.view({1: np.uint8, 4: np.uint32, 8: np.uint64}[a.dtype.itemsize])
+
+
+def read_all(net):
+    return dict(raster_e=net.raster("raster_exc"), raster_i=net.raster("raster_inh"),
+                raster_in=net.raster("raster_input"), v_e=net.read("v_exc"),
+                v_i=net.read("v_inh"), x_pre=net.read("x_pre"), x_post=net.read("x_post"),
+                ref_e=net.read("ref_exc"), ref_i=net.read("ref_inh"), w=net.weights(),
+                theta=net.read("theta"), counts=net.read("spike_counts"),
+                s_e=net.read("spikes_exc"), s_i=net.read("spikes_inh"),
+                step=int(net.read("step")[0]))
+
+
+def gpu_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", mode="step", theta=None,
+            net=None, continue_=False):
+    m = snn()
+    if net is None:
+        net = m.Network(p, w_init=w, theta_init=theta)
+    net.run(dev(rates), dev(seeds), T, learn=learn, reduce=reduce, mode=mode, record=True,
+            record_input=True, continue_=continue_)
+    torch.cuda.synchronize()
+    return net, read_all(net)
+
+
+def oracle_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", theta=None, st=None,
+               episodic=True):
+    if st is None:
+        st = oracle.new_state(p, len(seeds), w, theta=theta)
+    rec = oracle.run(p, st, rates, seeds, T, learn=learn, reduce=reduce, episodic=episodic)
+    return st, rec
+
+
+def first_diff_step(a, b):
+    d = np.flatnonzero((a != b).reshape(a.shape[0], -1).any(1))
+    return int(d[0]) if d.size else None
+
+
+def assert_parity(g, st, rec):
+    for name, ref in (("raster_in", rec.raster_in), ("raster_e", rec.raster_e),
+                      ("raster_i", rec.raster_i)):
+        assert g[name].shape == ref.shape, name
+        assert np.array_equal(g[name], ref), "%s differs first at step %s" % (
+            name, first_diff_step(g[name], ref))
+    expect = dict(v_e=st.v_e, v_i=st.v_i, x_pre=st.x_pre, x_post=st.x_post,
+                  ref_e=st.ref_e.astype(np.uint8), ref_i=st.ref_i.astype(np.uint8),
+                  w=st.w, theta=st.theta, counts=rec.counts_e, s_e=st.s_e, s_i=st.s_i)
+    for k, ref in expect.items():
+        got = g[k]
+        assert got.shape == ref.shape, k
+        if not np.array_equal(bits(got), bits(ref)):
+            bad = np.flatnonzero(bits(got).ravel() != bits(ref).ravel())
+            pytest.fail("%s: %d of %d elements differ, first at %d: gpu %r oracle %r" % (
+                k, bad.size, got.size, bad[0], got.ravel()[bad[0]], ref.ravel()[bad[0]]))
+    assert g["step"] == st.step
+
+
+# ------------------------------------------------------------------ cases ---
+
+@pytest.mark.parametrize("mode", ["step", "graph"])
+def test_784x100_single_presentation_learning(mode):
+    """B=1, 784 -> 100, T=250, pair STDP with mean reduction."""
+    p, r, s, w = synth.workload(1, 100)
+    net, g = gpu_run(p, r, s, w, 250, mode=mode)
+    st, rec = oracle_run(p, r, s, w, 250)
+    assert rec.raster_e.sum() > 20 and not np.array_equal(st.w, w)
+    assert_parity(g, st, rec)
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+def test_784x400_batch16_learning(reduce):
+    p, r, s, w = synth.workload(16, 400)
+    _, g = gpu_run(p, r, s, w, 250, reduce=reduce, mode="graph")
+    st, rec = oracle_run(p, r, s, w, 250, reduce=reduce)
+    assert_parity(g, st, rec)
+
+
+@pytest.mark.parametrize("B,N", [(37, 100), (33, 70), (1, 1), (5, 31), (64, 32)])
+def test_ragged_shapes_learning(B, N):
+    """Batches and layers that are not multiples of 32 (ragged warps and words)."""
+    p, r, s, w = synth.workload(B, N)
+    _, g = gpu_run(p, r, s, w, 80, reduce="sum")
+    st, rec = oracle_run(p, r, s, w, 80, reduce="sum")
+    assert_parity(g, st, rec)
+
+
+def test_small_input_layer_and_saturated_rates():
+    """n_in = 40 (two words, ragged); some rates >= 1000 Hz (always spike)."""
+    B, N, NI = 6, 12, 40
+    p = synth.diehl_cook_params(N, NI)
+    w = synth.weights(NI, N)
+    r = synth.rates_from_images(synth.images(B, NI)) * 3
+    r[:, :3] = 1500.0
+    s = synth.sample_seeds(B)
+    _, g = gpu_run(p, r, s, w, 120, reduce="mean")
+    st, rec = oracle_run(p, r, s, w, 120, reduce="mean")
+    assert rec.raster_in[:, :, :3].all()
+    assert_parity(g, st, rec)
+
+
+def test_learning_off_batch64():
+    p, r, s, w = synth.workload(64, 400)
+    _, g = gpu_run(p, r, s, w, 250, learn=False)
+    st, rec = oracle_run(p, r, s, w, 250, learn=False)
+    assert np.array_equal(g["w"], w)
+    assert_parity(g, st, rec)
+
+
+def test_zero_rates_and_zero_steps():
+    p, r, s, w = synth.workload(3, 50)
+    r[:] = 0.0
+    _, g = gpu_run(p, r, s, w, 30)
+    st, rec = oracle_run(p, r, s, w, 30)
+    assert g["raster_in"].sum() == 0 and g["raster_e"].sum() == 0
+    assert_parity(g, st, rec)
+    # T = 0: only the episodic reset
+    net, g0 = gpu_run(p, r, s, w, 0)
+    assert g0["step"] == 0 and np.all(g0["v_e"] == np.float32(p["e_rest"]))
+
+
+def test_continuing_run_and_batch_change():
+    """Continuing (no reset) continues the episode; a new batch size
+    re-initialises the per-sample state; W and theta persist throughout."""
+    m = snn()
+    p, r, s, w = synth.workload(7, 100)
+    net, g1 = gpu_run(p, r[:4], s[:4], w, 100)
+    st, rec1 = oracle_run(p, r[:4], s[:4], w, 100)
+    assert_parity(g1, st, rec1)
+    _, g2 = gpu_run(p, r[:4], s[:4], w, 150, net=net, continue_=True)
+    rec2 = oracle.run(p, st, r[:4], s[:4], 150, learn=True, reduce="mean", episodic=False)
+    assert_parity(g2, st, rec2)
+    # continuing with another batch size is refused
+    with pytest.raises(m.SNNError) as e:
+        net.run(dev(r), dev(s), 10, continue_=True)
+    assert e.value.status == m.SNN_ERR_STATE
+    # a new batch size re-initialises the samples but keeps W and theta
+    _, g3 = gpu_run(p, r, s, w, 60, net=net)
+    st3 = oracle.new_state(p, 7, st.w, theta=st.theta)
+    rec3 = oracle.run(p, st3, r, s, 60, learn=True, reduce="mean")
+    assert_parity(g3, st3, rec3)
+
+
+def test_host_inputs_match_device_inputs():
+    m = snn()
+    p, r, s, w = synth.workload(8, 100)
+    a = m.Network(p, w_init=w)
+    a.run(dev(r), dev(s), 100, record=True)
+    b = m.Network(p, w_init=w)
+    b.run(r, s, 100, record=True)         # numpy arrays: SNN_HOST_INPUTS
+    torch.cuda.synchronize()
+    assert np.array_equal(a.raster(), b.raster()) and np.array_equal(a.weights(), b.weights())
+
+
+def test_modes_agree_and_graph_replays():
+    """The captured graph is reused across runs and matches per-step launches."""
+    m = snn()
+    p, r, s, w = synth.workload(16, 128)
+    outs = []
+    for mode in ("step", "graph", "graph"):
+        net = m.Network(p, w_init=w)
+        for _ in range(2):
+            net.run(dev(r), dev(s), 90, mode=mode, record=True)
+        torch.cuda.synchronize()
+        outs.append((net.raster(), net.weights(), net.read("theta")))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(bits(a), bits(b))
+
+
+def test_seeded_weight_init_matches_the_input_generator():
+    m = snn()
+    p = synth.diehl_cook_params(50)
+    net = m.Network(p, w_init=None, w_seed=42)
+    assert np.array_equal(net.weights(), synth.weights(784, 50, 42))
+
+
+def test_bad_arguments_return_status():
+    m = snn()
+    p, r, s, w = synth.workload(2, 20)
+    net = m.Network(p, w_init=w)
+    for kwargs in (dict(T=-1), dict(dt=0.0), dict(reduce=5)):
+        T = kwargs.get("T", 5)
+        with pytest.raises(m.SNNError) as e:
+            m.snn_run(net.handle, dev(r), dev(s), 2, T, kwargs.get("dt", 1.0), 1,
+                      kwargs.get("reduce", 1), 0, None)
+        assert e.value.status == m.SNN_ERR_ARG
+    with pytest.raises(m.SNNError) as e:
+        m.snn_read_state(net.handle, m.SNN_FIELD_V_EXC, np.empty(3, np.float32))
+    assert e.value.status in (m.SNN_ERR_ARG, m.SNN_ERR_STATE)
+
+
+# ------------------------------------------------- full-size workloads ---
+
+def test_784x6400_batch256_learning_off_sampled():
+    """The 784 -> 6400, B = 256 workload: each sampled sample of the batch
+    equals the oracle's single-sample run (learning off, T = 250)."""
+    p, r, s, w = synth.workload(256, 6400)
+    _, g = gpu_run(p, r, s, w, 250, learn=False, mode="graph")
+    for b in (0, 101, 255):
+        st, rec = oracle_run(p, r[b:b + 1], s[b:b + 1], w, 250, learn=False)
+        assert np.array_equal(g["raster_e"][:, b:b + 1], rec.raster_e), b
+        assert np.array_equal(g["raster_in"][:, b:b + 1], rec.raster_in), b
+        assert np.array_equal(bits(g["v_e"][b:b + 1]), bits(st.v_e)), b
+        assert np.array_equal(bits(g["x_post"][b:b + 1]), bits(st.x_post)), b
+
+
+def test_784x6400_batch256_learning_first_steps():
+    """Learning on at full size for the first 12 steps (the first excitatory
+    spikes and the first weight updates fall inside)."""
+    p, r, s, w = synth.workload(256, 6400)
+    _, g = gpu_run(p, r, s, w, 12, mode="graph")
+    st, rec = oracle_run(p, r, s, w, 12)
+    assert rec.raster_e.sum() > 0 and not np.array_equal(st.w, w)
+    assert_parity(g, st, rec)
