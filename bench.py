@@ -1,0 +1,374 @@
+#!/usr/bin/env python3
+"""Throughput of the minibatched SNN time step on one GB300 (or N replicas).
+
+A bench *step* is one ``snn_run``: a full presentation of T = 250 time steps of
+the 784 -> 6400 adaptive-threshold network with lateral inhibition and
+pair-trace STDP reduced by the batch mean, over a batch of B = 256 seeded
+synthetic images (stand-ins for MNIST digits: 70 % zero pixels, the rest
+uniform in [0, 255], rate = intensity / 4 Hz).  Every step runs the whole hot
+path: Poisson input, synaptic current, both neuron populations, traces, STDP
+and the adaptive thresholds.
+
+value    = sample-timesteps/s, B*T*steps / (device time of the timed steps),
+           inputs resident in HBM, L2 flushed (256 MiB write) before every step;
+e2e      = the same metric through the C ABI with host inputs: pinned host
+           rates+seeds copied in and the spike counts copied out every step;
+roofline = the dominant kernel's algorithmic bytes per launch / its measured
+           average launch time (a second, event-bracketed pass of the timed
+           workload), against the measured HBM copy bandwidth;
+cpu_baseline = the CPU oracle timed on a bounded sample of the same workload.
+
+Multi-GPU: the path does not shard (W and theta are updated every step from
+the whole batch), so ``--gpus N`` runs N independent replicas (weak scaling).
+``--impl reference`` times the CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sample-timesteps/s vs batch, 784→6400 STDP; % roofline; serving p50/p99 ms"
+UNIT = "sample-timesteps/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="graph", choices=["step", "graph", "persistent", "auto"])
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--n-exc", type=int, default=6400)
+    ap.add_argument("--T", type=int, default=250)
+    ap.add_argument("--reduce", default="mean", choices=["mean", "sum", "max"])
+    ap.add_argument("--no-learn", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a, mode):
+    return {
+        "workload": "784->%d adaptive-threshold LIF + all-but-self inhibition, pair STDP, "
+                    "%s reduction, B=%d, T=%d, dt=1 ms, FP32 weights" % (
+                        a.n_exc, a.reduce, a.batch, a.T),
+        "B": a.batch, "n_in": 784, "n_exc": a.n_exc, "n_inh": a.n_exc, "T": a.T,
+        "reduce": a.reduce, "learn": not a.no_learn, "weights": "fp32", "mode": mode,
+        "l2": "flushed by a 256 MiB write before every step",
+        "inputs": "seeded synthetic 28x28 images (70% zeros, U[0,255]), rate=intensity/4 Hz",
+    }
+
+
+# ------------------------------------------------------------- helpers ---
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured"}
+    except Exception:
+        return dict(FALLBACK_PEAKS, source="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "snn_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mx = max(r[1] for r in rows)
+        loaded = [r[0] for r in rows if r[0] > 0.5 * mx] or [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower() == "active"})
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def algorithmic_bytes(kernel: str, B: int, N: int, NI: int, learn: bool, T: int = 1) -> float:
+    """Bytes a launch of each kernel must move at minimum.
+
+    encode : per (sample, input): threshold read 4 + presynaptic trace r/w 8.
+    neuron : per (sample, neuron): v_exc, v_inh, x_post r/w (24) + the two
+             refractory counters and previous-step spike flags r/w (4); plus
+             one read of W (n_in*N*4; at B >= 256 over 90 % of the input rows
+             are active in some sample every step).
+    stdp   : one read and one write of W (n_in*N*8).
+    persistent : all three per step, T steps per launch.
+    """
+    if kernel == "encode":
+        return B * NI * 12.0
+    if kernel == "neuron":
+        return B * N * 28.0 + NI * N * 4.0
+    if kernel == "stdp":
+        return NI * N * 8.0
+    if kernel == "persistent":
+        return T * (algorithmic_bytes("encode", B, N, NI, learn)
+                    + algorithmic_bytes("neuron", B, N, NI, learn)
+                    + (algorithmic_bytes("stdp", B, N, NI, learn) if learn else 0.0))
+    return 0.0
+
+
+def launches_per_run(mode: str, T: int, learn: bool) -> int:
+    if mode == "persistent":
+        return 2
+    return 1 + T * (3 if learn else 2)
+
+
+# ------------------------------------------------------- reference arm ---
+
+def time_oracle(a, seconds: float, max_T: int | None = None):
+    """CPU oracle (FP32 instantiation, one thread) on a bounded sample of the workload."""
+    import oracle
+    from paper_1909_02549_gb300 import synth
+    oracle.build()
+    B = min(16, a.batch)
+    p, r, s, w = synth.workload(B, a.n_exc)
+    T = 2
+    st = oracle.new_state(p, B, w)
+    t0 = time.perf_counter()
+    oracle.run(p, st, r, s, T, learn=not a.no_learn, reduce=a.reduce, record=False)
+    dt = time.perf_counter() - t0
+    T2 = max(1, min(max_T or a.T, int(seconds / max(dt / T, 1e-9))))
+    st = oracle.new_state(p, B, w)
+    t0 = time.perf_counter()
+    oracle.run(p, st, r, s, T2, learn=not a.no_learn, reduce=a.reduce, record=False)
+    el = time.perf_counter() - t0
+    return {"value": B * T2 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "first %d of %d steps of %d of the %d samples (784->%d, learning on, %s), "
+                      "FP32 oracle, 1 thread, %.1f s" % (T2, a.T, B, a.batch, a.n_exc, a.reduce, el)}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1909_02549_gb300 import synth
+    oracle.build()
+    B, T = 4, 4
+    p, r, s, w = synth.workload(B, a.n_exc)
+
+    def one():
+        st = oracle.new_state(p, B, w)
+        t0 = time.perf_counter()
+        oracle.run(p, st, r, s, T, learn=not a.no_learn, reduce=a.reduce, record=False)
+        return time.perf_counter() - t0
+
+    for _ in range(a.warmup):
+        one()
+    times = [one() for _ in range(a.steps)]
+    tot = sum(times)
+    value = B * T * a.steps / tot
+    sample = ("each step: %d samples x %d time steps of the 784->%d workload (learning on, %s), "
+              "FP32 oracle, 1 thread" % (B, T, a.n_exc, a.reduce))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a, "cpu-oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def profile_roofline(a, net, snn, flush, run, B, N, T, learn):
+    """Dominant kernel's achieved algorithmic bandwidth from an event-bracketed pass."""
+    try:
+        n_prof = min(a.steps, 10)
+        agg = {}
+        for _ in range(n_prof):
+            flush.zero_()
+            run(profile=True)
+            for k, (kms, kl) in snn.snn_profile(net.handle).items():
+                tms, tl = agg.get(k, (0.0, 0))
+                agg[k] = (tms + kms, tl + kl)
+        prof_total = sum(v[0] for v in agg.values())
+        dom = max(agg, key=lambda k: agg[k][0])
+        dom_ms, dom_launches = agg[dom]
+        avg_s = dom_ms / dom_launches * 1e-3
+        pk = peaks()
+        nbytes = algorithmic_bytes(dom, B, N, 784, learn, T)
+        achieved = nbytes / avg_s / 1e9
+        return {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_source": pk["source"] + " hbm_gbs (burst copy), of measured",
+                "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
+                "share_of_device_time": dom_ms / prof_total if prof_total else None,
+                "kernel_ms_per_run": {k: v[0] / n_prof for k, v in agg.items() if v[1]},
+                "launches_per_run": {k: v[1] // n_prof for k, v in agg.items() if v[1]}}
+    except Exception as e:                       # report, never hide the headline number
+        return {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s", "frac": None,
+                "traffic": None, "error": str(e)[:300]}
+
+
+# ------------------------------------------------------------ our arm ---
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1909_02549_gb300 import snn, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    B, N, T, learn = a.batch, a.n_exc, a.T, not a.no_learn
+    p, rates, seeds, w = synth.workload(B, N)
+    seeds = seeds + np.uint64(100000 * rank)     # replicas draw independent spikes
+    net = snn.Network(p, w_init=w)
+    r_d = torch.from_numpy(rates).cuda()
+    s_d = torch.from_numpy(seeds.view(np.int64)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(profile=False):
+        net.run(r_d, s_d, T, learn=learn, reduce=a.reduce, mode=a.mode, profile=profile)
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        run()
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    dev_index = visible.split(",")[local] if visible else str(local)
+    with ClockSampler(dev_index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(a.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            run()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B * T * a.steps / (ms * 1e-3)
+
+    # ---- per-kernel device time (same workload, every launch bracketed by events)
+    roofline = profile_roofline(a, net, snn, flush, run, B, N, T, learn)
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not a.no_e2e:
+        h_rates = torch.from_numpy(rates).pin_memory().numpy()
+        h_seeds = torch.from_numpy(seeds.view(np.int64)).pin_memory().numpy().view(np.uint64)
+        h_counts = torch.empty(B * N, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        k_e2e = max(3, min(a.steps, 20))
+        flags = snn.MODES[a.mode] | snn.SNN_HOST_INPUTS
+        red = snn.REDUCE[a.reduce]
+        tot = 0.0
+        for k in range(k_e2e + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            snn.snn_run(net.handle, h_rates, h_seeds, B, T, 1.0, int(learn), red, flags, stream)
+            snn.snn_read_state(net.handle, snn.SNN_FIELD_SPIKE_COUNTS, h_counts)
+            if k > 0:                               # first one warms the host path
+                tot += time.perf_counter() - t0
+        e2e = {"value": world * B * T * k_e2e / tot, "unit": UNIT,
+               "h2d_bytes_per_step": int(h_rates.nbytes + h_seeds.nbytes),
+               "d2h_bytes_per_step": int(h_counts.nbytes), "steps": k_e2e}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = time_oracle(a, a.cpu_seconds)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(a, a.mode), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches_per_run(a.mode, T, learn) * a.steps,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,6 +84,8 @@ typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
 #define SNN_HOST_INPUTS     (1u << 3) /* rates_hz and seeds are host pointers; the library
                                          copies them on the stream (pinned memory makes
                                          the copy asynchronous) */
+#define SNN_PROFILE         (1u << 4) /* bracket every kernel launch of the run with CUDA
+                                         events; read the times with snn_profile */
 #define SNN_MODE_STEP       (0u << 8) /* one kernel launch per phase per time step */
 #define SNN_MODE_GRAPH      (1u << 8) /* the T-step launch sequence captured once as a
                                          CUDA graph and replayed */
@@ -178,6 +180,23 @@ SNN_API snn_status snn_read_weights(snn_net* net, float* dst, size_t bytes, int 
 /* Replace the master weights with src [n_in][n_exc] (device or host) and
  * refresh any reduced-precision copy.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
 SNN_API snn_status snn_write_weights(snn_net* net, const float* src, size_t bytes, int src_on_device);
+
+/* Kernel classes reported by snn_profile. */
+enum {
+    SNN_KERNEL_BEGIN_RUN = 0,  /* thresholds, episodic reset, seeds */
+    SNN_KERNEL_ENCODE = 1,     /* Poisson input spikes and presynaptic traces */
+    SNN_KERNEL_NEURON = 2,     /* current, excitatory/inhibitory neurons, postsynaptic traces */
+    SNN_KERNEL_STDP = 3,       /* batch-reduced STDP and adaptive thresholds */
+    SNN_KERNEL_PERSISTENT = 4, /* all phases of all steps in one launch */
+    SNN_KERNEL_COUNT = 5
+};
+
+/* Device time of the last run made with SNN_PROFILE, per kernel class:
+ * ms[k] = summed milliseconds, launches[k] = number of launches, for
+ * k < n (n <= SNN_KERNEL_COUNT).  Synchronises the run's stream.
+ * Errors: SNN_ERR_ARG (NULL arrays, n out of range), SNN_ERR_STATE (the last
+ * run was not profiled), SNN_ERR_CUDA. */
+SNN_API snn_status snn_profile(snn_net* net, double* ms, int* launches, int n);
 
 /* One-line description of the last error on this network ("" if none).
  * Valid until the next call on the network.  NULL net gives the reason of

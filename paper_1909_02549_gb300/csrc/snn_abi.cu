@@ -16,7 +16,7 @@
 namespace snn {
 cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s);
 cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_t s,
-                              int* used_persistent);
+                              int* used_persistent, Prof* prof);
 }
 
 namespace {
@@ -24,12 +24,13 @@ namespace {
 thread_local std::string g_create_error;
 
 struct GraphKey {
-    int B = -1, T = -1, learn = -1, reduce = -1, rec_raster = -1, rec_input = -1;
+    int B = -1, T = -1, learn = -1, reduce = -1, rec_raster = -1, rec_input = -1, profile = -1;
     uint32_t dt_bits = 0;
     uint64_t generation = 0;
     bool operator==(const GraphKey& o) const {
         return B == o.B && T == o.T && learn == o.learn && reduce == o.reduce &&
-               rec_raster == o.rec_raster && rec_input == o.rec_input && dt_bits == o.dt_bits &&
+               rec_raster == o.rec_raster && rec_input == o.rec_input && profile == o.profile &&
+               dt_bits == o.dt_bits &&
                generation == o.generation;
     }
 };
@@ -58,6 +59,12 @@ struct snn_net {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
+    int gprof_n = 0;           // profile events used by a run that replays the cached graph
+    // SNN_PROFILE events of the last run
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_cls;
+    int prof_n = 0;
+    bool last_profiled = false;
     std::string err;
 };
 
@@ -299,6 +306,7 @@ snn_status snn_destroy(snn_net* n) {
     for (void* p : ptrs) if (p) cudaFree(p);
     if (n->gexec) cudaGraphExecDestroy(n->gexec);
     if (n->cap) cudaStreamDestroy(n->cap);
+    for (cudaEvent_t e : n->prof_ev) cudaEventDestroy(e);
     delete n;
     return SNN_OK;
 }
@@ -315,7 +323,7 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     if (reduce < SNN_REDUCE_SUM || reduce > SNN_REDUCE_MAX)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown reduce %d", reduce);
     const unsigned known = SNN_CONTINUE | SNN_RECORD_RASTER | SNN_RECORD_INPUT | SNN_HOST_INPUTS |
-                           SNN_MODE_MASK;
+                           SNN_PROFILE | SNN_MODE_MASK;
     if (flags & ~known)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown flag bits 0x%x", flags & ~known);
     const int R_e = steps_of(n->spec.e_refrac_ms, dt), R_i = steps_of(n->spec.i_refrac_ms, dt);
@@ -370,17 +378,40 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
         r_dev = n->rates_stage;
         s_dev = n->seeds_stage;
     }
+    const bool profile = (flags & SNN_PROFILE) != 0;
+    snn::Prof prof;
+    snn::Prof* pp = nullptr;
+    n->last_profiled = false;
+    if (profile) {
+        const size_t need = 2 * (2 + 3 * (size_t)T);
+        if (n->prof_ev.size() < need) {
+            // The cached graph may record the old events: drop it with them.
+            if (n->last) CUDA_TRY(n, cudaStreamSynchronize(n->last));
+            CUDA_TRY(n, cudaStreamSynchronize(st));
+            while (n->prof_ev.size() < need) {
+                cudaEvent_t e;
+                CUDA_TRY(n, cudaEventCreate(&e));
+                n->prof_ev.push_back(e);
+            }
+            n->prof_cls.resize(need / 2);
+            n->generation++;
+        }
+        prof.ev = n->prof_ev.data();
+        prof.cls = n->prof_cls.data();
+        prof.cap = (int)n->prof_ev.size();
+        pp = &prof;
+    }
     const snn::Consts c = make_consts(n, B, dt, learn, reduce, flags);
     const snn::Bufs d = run_bufs(n);
-    CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st));
+    CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st, pp));
 
     const unsigned mode = flags & SNN_MODE_MASK;
     if (mode == SNN_MODE_STEP) {
-        for (int t = 0; t < T; ++t) CUDA_TRY(n, snn::launch_step(c, d, t, st));
+        for (int t = 0; t < T; ++t) CUDA_TRY(n, snn::launch_step(c, d, t, st, pp));
     } else if (mode == SNN_MODE_GRAPH || mode == SNN_MODE_AUTO) {
         GraphKey key;
         key.B = B; key.T = T; key.learn = c.learn; key.reduce = reduce;
-        key.rec_raster = c.rec_raster; key.rec_input = c.rec_input;
+        key.rec_raster = c.rec_raster; key.rec_input = c.rec_input; key.profile = profile ? 1 : 0;
         std::memcpy(&key.dt_bits, &dt, 4);
         key.generation = n->generation;
         if (!n->gexec || !(key == n->gkey)) {
@@ -392,7 +423,8 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
             cudaGraph_t g = nullptr;
             CUDA_TRY(n, cudaStreamBeginCapture(n->cap, cudaStreamCaptureModeThreadLocal));
             cudaError_t le = cudaSuccess;
-            for (int t = 0; t < T && le == cudaSuccess; ++t) le = snn::launch_step(c, d, t, n->cap);
+            for (int t = 0; t < T && le == cudaSuccess; ++t)
+                le = snn::launch_step(c, d, t, n->cap, pp);
             cudaError_t ee = cudaStreamEndCapture(n->cap, &g);
             CUDA_TRY(n, le);
             CUDA_TRY(n, ee);
@@ -400,14 +432,21 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
             cudaGraphDestroy(g);
             CUDA_TRY(n, ie);
             n->gkey = key;
+            n->gprof_n = pp ? pp->n : 0;
+        } else if (pp) {
+            pp->n = n->gprof_n;   // the cached graph records the same events
         }
         CUDA_TRY(n, cudaGraphLaunch(n->gexec, st));
     } else {
         int used = 0;
-        CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used));
+        CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used, pp));
         if (!used)
             return fail(n, SNN_ERR_ARG,
-                        "snn_run: the persistent kernel cannot hold this configuration resident");
+                        "snn_run: the persistent kernel cannot keep this configuration resident");
+    }
+    if (pp) {
+        n->prof_n = pp->n;
+        n->last_profiled = true;
     }
     n->last = st;
     n->state_valid = true;
@@ -504,6 +543,25 @@ snn_status snn_write_weights(snn_net* n, const float* src, size_t bytes, int src
                                 n->last));
     CUDA_TRY(n, snn::launch_clip_weights(n->d.W, count, n->spec.w_min, n->spec.w_max, n->last));
     CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    return SNN_OK;
+}
+
+snn_status snn_profile(snn_net* n, double* ms, int* launches, int count) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_profile: net is NULL");
+    n->err.clear();
+    if (!ms || !launches || count < 0 || count > SNN_KERNEL_COUNT)
+        return fail(n, SNN_ERR_ARG, "snn_profile: need arrays of 0..%d entries", SNN_KERNEL_COUNT);
+    if (!n->last_profiled)
+        return fail(n, SNN_ERR_STATE, "snn_profile: the last run was not made with SNN_PROFILE");
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    for (int k = 0; k < count; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (int e = 0; e + 1 < n->prof_n; e += 2) {
+        float t = 0.0f;
+        CUDA_TRY(n, cudaEventElapsedTime(&t, n->prof_ev[e], n->prof_ev[e + 1]));
+        const int k = n->prof_cls[e / 2];
+        if (k < count) { ms[k] += t; launches[k] += 1; }
+    }
     return SNN_OK;
 }
 

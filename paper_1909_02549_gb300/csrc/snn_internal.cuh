@@ -64,10 +64,33 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
+// Optional event brackets around launches (SNN_PROFILE): two events and one
+// class id per launch.  Recorded as external events so that, inside stream
+// capture, they become event-record nodes of the graph with real timestamps.
+struct Prof {
+    cudaEvent_t* ev = nullptr;
+    int* cls = nullptr;
+    int cap = 0;  // events available
+    int n = 0;    // events used
+};
+
+inline cudaError_t prof_start(Prof* p, int cls, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    if (p->n + 2 > p->cap) return cudaErrorInvalidValue;
+    p->cls[p->n / 2] = cls;
+    return cudaEventRecordWithFlags(p->ev[p->n++], s, cudaEventRecordExternal);
+}
+
+inline cudaError_t prof_stop(Prof* p, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    return cudaEventRecordWithFlags(p->ev[p->n++], s, cudaEventRecordExternal);
+}
+
 // Launchers (snn_step.cu).
 cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
-                             const uint64_t* seeds, int episodic, int T, cudaStream_t s);
-cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s);
+                             const uint64_t* seeds, int episodic, int T, cudaStream_t s,
+                             Prof* prof);
+cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s, Prof* prof);
 cudaError_t launch_extract(const Consts& c, const Bufs& d, int field, void* scratch,
                            cudaStream_t s);
 

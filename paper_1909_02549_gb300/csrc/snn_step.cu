@@ -307,25 +307,43 @@ int grid_for(size_t n, int threads, int cap) {
 
 }  // namespace
 
+#define PROF_TRY(expr)                       \
+    do {                                     \
+        cudaError_t e_ = (expr);             \
+        if (e_ != cudaSuccess) return e_;    \
+    } while (0)
+
 cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
-                             const uint64_t* seeds, int episodic, int T, cudaStream_t s) {
+                             const uint64_t* seeds, int episodic, int T, cudaStream_t s,
+                             Prof* prof) {
     const size_t n = (size_t)c.n_in * c.Bp > (size_t)c.B * c.N ? (size_t)c.n_in * c.Bp
                                                                 : (size_t)c.B * c.N;
+    PROF_TRY(prof_start(prof, SNN_KERNEL_BEGIN_RUN, s));
     k_begin_run<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(c, d, rates, seeds, episodic, T);
-    return cudaGetLastError();
+    PROF_TRY(cudaGetLastError());
+    return prof_stop(prof, s);
 }
 
-cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s) {
+cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s, Prof* prof) {
+    PROF_TRY(prof_start(prof, SNN_KERNEL_ENCODE, s));
     k_encode<<<dim3(c.Bw, (c.Iw + 7) / 8), 256, 0, s>>>(c, d, t_local);
+    PROF_TRY(cudaGetLastError());
+    PROF_TRY(prof_stop(prof, s));
     const size_t bn = (size_t)c.B * c.N;
+    PROF_TRY(prof_start(prof, SNN_KERNEL_NEURON, s));
     k_neuron<<<(unsigned)((bn + 255) / 256), 256, 0, s>>>(c, d, t_local);
+    PROF_TRY(cudaGetLastError());
+    PROF_TRY(prof_stop(prof, s));
     if (c.learn) {
         const dim3 g((c.N + 31) / 32, (c.n_in + STDP_ROWS - 1) / STDP_ROWS);
+        PROF_TRY(prof_start(prof, SNN_KERNEL_STDP, s));
         if (c.reduce == SNN_REDUCE_SUM) k_stdp<SNN_REDUCE_SUM><<<g, 256, 0, s>>>(c, d, t_local);
         else if (c.reduce == SNN_REDUCE_MEAN) k_stdp<SNN_REDUCE_MEAN><<<g, 256, 0, s>>>(c, d, t_local);
         else k_stdp<SNN_REDUCE_MAX><<<g, 256, 0, s>>>(c, d, t_local);
+        PROF_TRY(cudaGetLastError());
+        PROF_TRY(prof_stop(prof, s));
     }
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 cudaError_t launch_extract(const Consts& c, const Bufs& d, int field, void* out, cudaStream_t s) {

@@ -25,6 +25,8 @@ SNN_CONTINUE = 1 << 0
 SNN_RECORD_RASTER = 1 << 1
 SNN_RECORD_INPUT = 1 << 2
 SNN_HOST_INPUTS = 1 << 3
+SNN_PROFILE = 1 << 4
+KERNEL_NAMES = ["begin_run", "encode", "neuron", "stdp", "persistent"]
 SNN_MODE_STEP = 0 << 8
 SNN_MODE_GRAPH = 1 << 8
 SNN_MODE_PERSISTENT = 2 << 8
@@ -51,7 +53,8 @@ FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
                SNN_FIELD_SPIKES_EXC: np.uint8, SNN_FIELD_SPIKES_INH: np.uint8}
 
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
-            "snn_read_state", "snn_read_weights", "snn_write_weights", "snn_last_error"]
+            "snn_read_state", "snn_read_weights", "snn_write_weights", "snn_profile",
+            "snn_last_error"]
 
 
 class snn_spec(C.Structure):
@@ -96,10 +99,11 @@ def lib():
         L.snn_read_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_read_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_write_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
         for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state",
-                     "snn_read_weights", "snn_write_weights"):
+                     "snn_read_weights", "snn_write_weights", "snn_profile"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -183,6 +187,15 @@ def snn_write_weights(net, src) -> None:
     _check(net, lib().snn_write_weights(net, p, n, dev))
 
 
+def snn_profile(net) -> dict:
+    """{kernel class: (ms, launches)} of the last SNN_PROFILE run."""
+    n = len(KERNEL_NAMES)
+    ms = (C.c_double * n)()
+    la = (C.c_int * n)()
+    _check(net, lib().snn_profile(net, ms, la, n))
+    return {KERNEL_NAMES[k]: (ms[k], la[k]) for k in range(n)}
+
+
 def snn_last_error(net) -> str:
     r = lib().snn_last_error(net)
     return r.decode() if r else ""
@@ -229,7 +242,8 @@ class Network:
 
     def run(self, rates, seeds, T: int, *, dt: float = 1.0, learn: bool = True,
             reduce: str = "mean", mode: str = "step", continue_: bool = False,
-            record: bool = False, record_input: bool = False, stream=None) -> None:
+            record: bool = False, record_input: bool = False, profile: bool = False,
+            stream=None) -> None:
         B = rates.shape[0]
         flags = MODES[mode]
         if continue_:
@@ -238,6 +252,8 @@ class Network:
             flags |= SNN_RECORD_RASTER
         if record_input:
             flags |= SNN_RECORD_INPUT
+        if profile:
+            flags |= SNN_PROFILE
         snn_run(self.handle, rates, seeds, B, T, dt, int(learn), REDUCE[reduce], flags, stream)
         self.B = B
         self.T = T

@@ -207,6 +207,22 @@ def test_modes_agree_and_graph_replays():
             assert np.array_equal(bits(a), bits(b))
 
 
+@pytest.mark.parametrize("mode", ["step", "graph"])
+def test_profile_reports_every_launch(mode):
+    m = snn()
+    p, r, s, w = synth.workload(4, 64)
+    net = m.Network(p, w_init=w)
+    for _ in range(2):                       # second graph run replays the cached graph
+        net.run(dev(r), dev(s), 20, mode=mode, profile=True)
+        prof = m.snn_profile(net.handle)
+        assert prof["begin_run"][1] == 1
+        for k in ("encode", "neuron", "stdp"):
+            assert prof[k][1] == 20 and prof[k][0] > 0.0, (k, prof[k])
+    net.run(dev(r), dev(s), 5, mode=mode)    # an unprofiled run has nothing to report
+    with pytest.raises(m.SNNError):
+        m.snn_profile(net.handle)
+
+
 def test_seeded_weight_init_matches_the_input_generator():
     m = snn()
     p = synth.diehl_cook_params(50)
