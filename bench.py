@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="graph", choices=["step", "graph", "persistent", "auto"])
+    ap.add_argument("--mode", default="persistent", choices=["step", "graph", "persistent", "auto"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--n-exc", type=int, default=6400)
     ap.add_argument("--T", type=int, default=250)

@@ -117,10 +117,12 @@ void seeded_weights(uint64_t seed, size_t n, std::vector<float>& w) {
 
 void free_batch(snn_net* n) {
     snn::Bufs& d = n->d;
-    void* ptrs[] = {d.thrT, d.seeds, d.x_preT, d.inb, d.preT, d.v_e, d.v_i, d.x_post, d.st,
-                    d.cnt, d.postT, d.spkT, d.counts, n->rates_stage, n->seeds_stage};
+    void* ptrs[] = {d.thr, d.seeds, d.x_pre, d.inb, d.preT, d.act_idx, d.act_cnt, d.v_e, d.v_i,
+                    d.x_post, d.st, d.cnt, d.postT, d.spkT, d.counts, n->rates_stage,
+                    n->seeds_stage};
     for (void* p : ptrs) if (p) cudaFree(p);
-    d.thrT = nullptr; d.seeds = nullptr; d.x_preT = nullptr; d.inb = nullptr; d.preT = nullptr;
+    d.thr = nullptr; d.seeds = nullptr; d.x_pre = nullptr; d.inb = nullptr; d.preT = nullptr;
+    d.act_idx = nullptr; d.act_cnt = nullptr;
     d.v_e = nullptr; d.v_i = nullptr; d.x_post = nullptr; d.st = nullptr; d.cnt = nullptr;
     d.postT = nullptr; d.spkT = nullptr; d.counts = nullptr;
     n->rates_stage = nullptr; n->seeds_stage = nullptr;
@@ -137,24 +139,25 @@ cudaError_t dalloc(T** p, size_t count) {
 snn_status alloc_batch(snn_net* n, int B) {
     free_batch(n);
     const size_t NI = n->spec.n_in, N = n->spec.n_exc;
-    const size_t Bw = ((size_t)B + 31) / 32, Bp = Bw * 32, Iw = (NI + 31) / 32;
+    const size_t Bw = ((size_t)B + 31) / 32, Iw = (NI + 31) / 32;
     snn::Bufs& d = n->d;
-    CUDA_TRY(n, dalloc(&d.thrT, NI * Bp));
+    CUDA_TRY(n, dalloc(&d.thr, (size_t)B * NI));
     CUDA_TRY(n, dalloc(&d.seeds, (size_t)B));
-    CUDA_TRY(n, dalloc(&d.x_preT, NI * Bp));
-    CUDA_TRY(n, dalloc(&d.inb, (size_t)B * Iw));
-    CUDA_TRY(n, dalloc(&d.preT, NI * Bw));
+    CUDA_TRY(n, dalloc(&d.x_pre, 2 * (size_t)B * NI));
+    CUDA_TRY(n, dalloc(&d.inb, 2 * (size_t)B * Iw));
+    CUDA_TRY(n, dalloc(&d.preT, 3 * NI * Bw));
+    CUDA_TRY(n, dalloc(&d.act_idx, 2 * (size_t)B * NI));
+    CUDA_TRY(n, dalloc(&d.act_cnt, 2 * (size_t)B));
     CUDA_TRY(n, dalloc(&d.v_e, (size_t)B * N));
     CUDA_TRY(n, dalloc(&d.v_i, (size_t)B * N));
     CUDA_TRY(n, dalloc(&d.x_post, (size_t)B * N));
     CUDA_TRY(n, dalloc(&d.st, (size_t)B * N));
-    CUDA_TRY(n, dalloc(&d.cnt, 2 * (size_t)B));
+    CUDA_TRY(n, dalloc(&d.cnt, 3 * (size_t)B));
     CUDA_TRY(n, dalloc(&d.postT, 2 * N * Bw));
     CUDA_TRY(n, dalloc(&d.spkT, N * Bw));
     CUDA_TRY(n, dalloc(&d.counts, (size_t)B * N));
     CUDA_TRY(n, dalloc(&n->rates_stage, (size_t)B * NI));
     CUDA_TRY(n, dalloc(&n->seeds_stage, (size_t)B));
-    CUDA_TRY(n, cudaMemset(d.x_preT, 0, NI * Bp * sizeof(float)));
     n->B = B;
     return SNN_OK;
 }
@@ -174,7 +177,7 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     const snn_spec& s = n->spec;
     snn::Consts c{};
     c.n_in = s.n_in; c.N = s.n_exc; c.B = B;
-    c.Bw = (B + 31) / 32; c.Bp = c.Bw * 32;
+    c.Bw = (B + 31) / 32;
     c.Iw = (s.n_in + 31) / 32; c.Nw = (s.n_exc + 31) / 32;
     c.e_rest = s.e_rest; c.e_reset = s.e_reset; c.e_thresh = s.e_thresh;
     c.a_e = (float)std::exp(-(double)dt / (double)s.e_tau_ms);
@@ -196,6 +199,23 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
 }
 
 snn::Bufs run_bufs(const snn_net* n) { return n->d; }
+
+// Sticky device error bits (bounded waits of the persistent form).  Reported,
+// then cleared, by the next call that synchronises.
+snn_status check_device_error(snn_net* n) {
+    uint32_t e = 0;
+    cudaError_t ce = cudaMemcpy(&e, n->d.err, 4, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return fail(n, SNN_ERR_CUDA, "reading the device error word: %s",
+                                       cudaGetErrorString(ce));
+    if (e != 0u) {
+        cudaMemset(n->d.err, 0, 4);
+        n->state_valid = false;
+        return fail(n, SNN_ERR_TIMEOUT,
+                    "a grid barrier of the persistent kernel timed out (code 0x%x); the state of "
+                    "that run is invalid", e);
+    }
+    return SNN_OK;
+}
 
 size_t field_bytes(const snn_net* n, int field) {
     const size_t B = n->B, N = n->spec.n_exc, NI = n->spec.n_in;
@@ -405,10 +425,20 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     const snn::Bufs d = run_bufs(n);
     CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st, pp));
 
-    const unsigned mode = flags & SNN_MODE_MASK;
+    unsigned mode = flags & SNN_MODE_MASK;
+    if (mode == SNN_MODE_PERSISTENT || mode == SNN_MODE_AUTO) {
+        int used = 0;
+        CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used, pp));
+        if (!used && mode == SNN_MODE_PERSISTENT)
+            return fail(n, SNN_ERR_ARG,
+                        "snn_run: the persistent form needs the weight columns and traces of one "
+                        "CTA in shared memory; this batch and layer do not fit (use the graph "
+                        "or step mode)");
+        mode = used ? SNN_MODE_PERSISTENT : SNN_MODE_GRAPH;
+    }
     if (mode == SNN_MODE_STEP) {
         for (int t = 0; t < T; ++t) CUDA_TRY(n, snn::launch_step(c, d, t, st, pp));
-    } else if (mode == SNN_MODE_GRAPH || mode == SNN_MODE_AUTO) {
+    } else if (mode == SNN_MODE_GRAPH) {
         GraphKey key;
         key.B = B; key.T = T; key.learn = c.learn; key.reduce = reduce;
         key.rec_raster = c.rec_raster; key.rec_input = c.rec_input; key.profile = profile ? 1 : 0;
@@ -423,8 +453,10 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
             cudaGraph_t g = nullptr;
             CUDA_TRY(n, cudaStreamBeginCapture(n->cap, cudaStreamCaptureModeThreadLocal));
             cudaError_t le = cudaSuccess;
+            if (pp) pp->capturing = true;
             for (int t = 0; t < T && le == cudaSuccess; ++t)
                 le = snn::launch_step(c, d, t, n->cap, pp);
+            if (pp) pp->capturing = false;
             cudaError_t ee = cudaStreamEndCapture(n->cap, &g);
             CUDA_TRY(n, le);
             CUDA_TRY(n, ee);
@@ -437,12 +469,6 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
             pp->n = n->gprof_n;   // the cached graph records the same events
         }
         CUDA_TRY(n, cudaGraphLaunch(n->gexec, st));
-    } else {
-        int used = 0;
-        CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used, pp));
-        if (!used)
-            return fail(n, SNN_ERR_ARG,
-                        "snn_run: the persistent kernel cannot keep this configuration resident");
     }
     if (pp) {
         n->prof_n = pp->n;
@@ -479,6 +505,7 @@ snn_status snn_read_state(snn_net* n, int field, void* dst, size_t bytes, int ds
     CUDA_TRY(n, cudaSetDevice(n->device));
     cudaStream_t st = n->last;
     CUDA_TRY(n, cudaStreamSynchronize(st));
+    if (snn_status r = check_device_error(n)) return r;
     const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const void* src = nullptr;
     switch (field) {
@@ -523,6 +550,7 @@ snn_status snn_read_weights(snn_net* n, float* dst, size_t bytes, int dst_on_dev
         return fail(n, SNN_ERR_ARG, "snn_read_weights: need a %zu-byte buffer", want);
     CUDA_TRY(n, cudaSetDevice(n->device));
     CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    if (snn_status r = check_device_error(n)) return r;
     CUDA_TRY(n, cudaMemcpyAsync(dst, n->d.W, want,
                                 dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                 n->last));
@@ -555,6 +583,7 @@ snn_status snn_profile(snn_net* n, double* ms, int* launches, int count) {
         return fail(n, SNN_ERR_STATE, "snn_profile: the last run was not made with SNN_PROFILE");
     CUDA_TRY(n, cudaSetDevice(n->device));
     CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    if (snn_status r = check_device_error(n)) return r;
     for (int k = 0; k < count; ++k) { ms[k] = 0.0; launches[k] = 0; }
     for (int e = 0; e + 1 < n->prof_n; e += 2) {
         float t = 0.0f;

@@ -13,7 +13,7 @@ namespace snn {
 // because exp(-dt/tau_theta) = 1 - 1e-7 is below FP32 resolution.
 struct Consts {
     int n_in, N, B;     // inputs, excitatory (= inhibitory) neurons, batch
-    int Bp, Bw;         // batch padded to 32, and its 32-bit word count
+    int Bw;             // 32-bit words per batch bitmask
     int Iw, Nw;         // words per sample of the input / neuron bitmasks
     float e_rest, e_reset, e_thresh, a_e;
     float i_rest, i_reset, i_thresh, a_i;
@@ -25,30 +25,33 @@ struct Consts {
     int rec_raster, rec_input;
 };
 
-// Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j;
-// input-major "[n_in][Bp]" arrays index i*Bp + b (samples are the fast axis
-// so a warp of 32 samples reads one 128-byte line).
+// Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.
+// Buffers indexed by the absolute step tt rotate so that one step's writers
+// never overwrite what the previous step's readers may still use:
+//   [2]: buffer tt&1 holds the value of step tt;  [3]: buffer tt%3.
 struct Bufs {
     float* W;            // [n_in][N]  FP32 master weights
     double* theta;       // [N]        adaptive thresholds (FP64)
-    uint32_t* thrT;      // [n_in][Bp] Poisson thresholds of this run
+    uint32_t* thr;       // [B][n_in]  Poisson thresholds of this run
     uint64_t* seeds;     // [B]        per-sample Poisson seeds
-    float* x_preT;       // [n_in][Bp] presynaptic traces
-    uint32_t* inb;       // [B][Iw]    input spikes of this step, sample-major bits
-    uint32_t* preT;      // [n_in][Bw] input spikes of this step, input-major bits
+    float* x_pre;        // [2][B][n_in] presynaptic traces after step tt
+    uint32_t* inb;       // [2][B][Iw]   input spikes of step tt, sample-major bits
+    uint32_t* preT;      // [3][n_in][Bw] input spikes of step tt, input-major bits
+    uint16_t* act_idx;   // [2][B][n_in] active inputs of step tt, ascending (persistent form)
+    uint32_t* act_cnt;   // [2][B]
     float* v_e;          // [B][N]
     float* v_i;          // [B][N]
     float* x_post;       // [B][N]
     uint32_t* st;        // [B][N]  ref_e | ref_i<<8 | s_e'<<16 | s_i'<<17
-    uint32_t* cnt;       // [2][B]  inhibitory spike count per step parity
-    uint32_t* postT;     // [2][N][Bw] excitatory spikes per step parity, column-major bits
+    uint32_t* cnt;       // [3][B]  inhibitory spike count of step tt
+    uint32_t* postT;     // [2][N][Bw] excitatory spikes of step tt, column-major bits
     uint32_t* spkT;      // [N][Bw] samples in which neuron j has spiked this episode
     uint32_t* counts;    // [B][N]  excitatory spike counts of this run
     uint32_t* raster_e;  // [T][B][Nw] (optional)
     uint32_t* raster_i;  // [T][B][Nw] (optional)
     uint32_t* raster_in; // [T][B][Iw] (optional)
     unsigned long long* step;  // [2]: first step of this run, step after it
-    uint32_t* err;       // [4]  device error word (bounded waits), diagnostic
+    uint32_t* err;       // [0] sticky device error bits, [1] grid-barrier counter
 };
 
 // Packed per-(b,j) state word.
@@ -70,20 +73,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 struct Prof {
     cudaEvent_t* ev = nullptr;
     int* cls = nullptr;
-    int cap = 0;  // events available
-    int n = 0;    // events used
+    int cap = 0;           // events available
+    int n = 0;             // events used
+    bool capturing = false;  // recording into a stream capture
 };
+
+inline cudaError_t prof_record(Prof* p, cudaStream_t s) {
+    cudaEvent_t e = p->ev[p->n++];
+    return p->capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                        : cudaEventRecord(e, s);
+}
 
 inline cudaError_t prof_start(Prof* p, int cls, cudaStream_t s) {
     if (!p) return cudaSuccess;
     if (p->n + 2 > p->cap) return cudaErrorInvalidValue;
     p->cls[p->n / 2] = cls;
-    return cudaEventRecordWithFlags(p->ev[p->n++], s, cudaEventRecordExternal);
+    return prof_record(p, s);
 }
 
 inline cudaError_t prof_stop(Prof* p, cudaStream_t s) {
     if (!p) return cudaSuccess;
-    return cudaEventRecordWithFlags(p->ev[p->n++], s, cudaEventRecordExternal);
+    return prof_record(p, s);
 }
 
 // Launchers (snn_step.cu).

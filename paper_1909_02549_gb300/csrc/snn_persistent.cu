@@ -1,10 +1,455 @@
-// Persistent cooperative form of the time step (all T steps in one launch).
+// Persistent cooperative form of the minibatched time step: all T steps of a
+// presentation in one launch, one CTA per SM.
+//
+// Partition.  CTA c owns a contiguous range of neurons J_c (excitatory j and
+// its inhibitory partner j) for *every* sample of the batch.  Everything the
+// plasticity touches is then CTA-local: the weight columns W[:, J_c] (held in
+// shared memory for the whole run), theta[J_c], and the postsynaptic traces of
+// J_c.  The batch reduction of the STDP update (Sec. "Reduction methods") is
+// a reduction over b of columns the CTA owns, so it needs no cross-CTA
+// exchange.  Only two things cross CTAs each step:
+//   - the input spikes (computed for the next step, samples spread over CTAs),
+//   - the per-sample count of inhibitory spikes (all-but-self inhibition).
+// Both are double/triple-buffered by step, so one grid barrier per step
+// separates producers from consumers.  The barrier waits are bounded: on
+// timeout the kernel sets a device error bit and returns.
+//
+// Per step, inside a CTA:
+//   neuron phase : current from the staged active-input lists of every sample
+//                  (ascending input order) against W[:, J_c] in shared memory,
+//                  excitatory adaptive-threshold and inhibitory LIF updates;
+//   STDP phase   : theta, then for every synapse (i, j in J_c) the samples
+//                  whose update can be non-zero, visited in ascending b;
+//   encode phase : Poisson input spikes of the next step for this CTA's
+//                  samples, presynaptic traces, and their compaction into
+//                  ascending active-input lists;
+//   grid barrier.
+// The arithmetic is the per-step kernels' (same intrinsics, same order), so the
+// three run modes give bit-identical results.
+#include <cfloat>
+
 #include "snn_internal.cuh"
 
 namespace snn {
+namespace {
 
-cudaError_t launch_persistent(const Consts&, const Bufs&, int, cudaStream_t, int* used, Prof*) {
+constexpr int PT = 512;                    // threads per CTA
+constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
+constexpr unsigned SPIN_LIMIT = 1u << 24;  // bounded grid-barrier wait (~seconds)
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct Layout {
+    int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
+    size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_u;   // byte offsets
+    // union region (phase-local)
+    size_t o_cnts, o_actn, o_acts;    // neuron phase
+    size_t o_pres, o_nzp;             // STDP phase
+    size_t o_wbuf;                    // encode phase
+    size_t bytes;
+};
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+Layout make_layout(const Consts& c, int G) {
+    Layout L{};
+    L.G = G;
+    L.ncmax = (c.N + G - 1) / G;
+    L.spc = (c.B + G - 1) / G;
+    size_t o = 0;
+    L.o_ws = o;  o = align16(o + (size_t)c.n_in * L.ncmax * 4);
+    L.o_xps = o; o = align16(o + (size_t)c.B * L.ncmax * 4);
+    L.o_sm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
+    L.o_qm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
+    L.o_nzq = o; o = align16(o + (size_t)L.ncmax * 4);
+    L.o_ths = o; o = align16(o + (size_t)L.ncmax * 8);
+    L.o_thj = o; o = align16(o + (size_t)L.ncmax * 4);
+    L.o_u = o;
+    size_t u_neuron = 0, u_stdp = 0, u_enc = 0;
+    L.o_cnts = o;                u_neuron = align16((size_t)c.B * 4);
+    L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
+    L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
+    L.o_pres = o;                u_stdp = align16((size_t)c.n_in * c.Bw * 4);
+    L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
+    L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
+    size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
+    if (u_enc > u) u = u_enc;
+    L.bytes = o + u;
+    return L;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false if this or another
+// CTA gave up (device error bit 1).
+__device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target) {
+    __shared__ int s_fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int fail = 0;
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        unsigned spins = 0;
+        while (ld_acquire(ctr) < target) {
+            if (ld_acquire(err) != 0u) { fail = 1; break; }
+            if (++spins > SPIN_LIMIT) { atomicOr(err, 1u); fail = 1; break; }
+            __nanosleep(64);
+        }
+        __threadfence();
+        s_fail = fail;
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+// Poisson input spikes of step tt for this CTA's samples (b = cta + G*r),
+// presynaptic traces, input-major masks, and ascending active-input lists.
+__device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
+                             unsigned long long tt, int t_local) {
+    const int cta = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cur = (int)(tt & 1ull), prv = cur ^ 1, p3 = (int)(tt % 3ull);
+    uint32_t* wbuf = (uint32_t*)(sm + L.o_wbuf);
+    const int nmy = cta < c.B ? (c.B - cta + L.G - 1) / L.G : 0;
+    const size_t nbi = (size_t)c.B * c.n_in;
+    const int units = nmy * c.Iw;
+    for (int u = warp; u < units; u += PT / 32) {
+        const int r = u / c.Iw, iw = u % c.Iw;
+        const int b = cta + L.G * r;
+        const int i = iw * 32 + lane;
+        uint32_t s = 0;
+        if (i < c.n_in) {
+            const size_t o = (size_t)b * c.n_in + i;
+            const uint32_t thr = d.thr[o];
+            if (thr != 0u) {
+                const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)i;
+                const uint32_t h = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32);
+                s = h < thr ? 1u : 0u;
+            }
+            float x = __ldcg(&d.x_pre[(size_t)prv * nbi + o]);
+            x = __fmul_rn(x, c.a_x);
+            x = __fadd_rn(x, s ? 1.0f : 0.0f);
+            d.x_pre[(size_t)cur * nbi + o] = x;
+            if (s) atomicOr(&d.preT[((size_t)p3 * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
+        }
+        const uint32_t word = __ballot_sync(FULL, s);
+        if (lane == 0) {
+            wbuf[r * c.Iw + iw] = word;
+            d.inb[((size_t)cur * c.B + b) * c.Iw + iw] = word;
+            if (c.rec_input) d.raster_in[((size_t)t_local * c.B + b) * c.Iw + iw] = word;
+        }
+    }
+    __syncthreads();
+    for (int r = warp; r < nmy; r += PT / 32) {       // one warp per sample
+        const int b = cta + L.G * r;
+        uint16_t* out = d.act_idx + ((size_t)cur * c.B + b) * c.n_in;
+        uint32_t running = 0;
+        for (int w0 = 0; w0 < c.Iw; w0 += 32) {
+            const int w = w0 + lane;
+            uint32_t word = w < c.Iw ? wbuf[r * c.Iw + w] : 0u;
+            const uint32_t n = __popc(word);
+            uint32_t incl = n;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t off = running + incl - n;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                out[off++] = (uint16_t)(w * 32 + bit);
+            }
+            running += __shfl_sync(FULL, incl, 31);
+        }
+        if (lane == 0) d.act_cnt[(size_t)cur * c.B + b] = running;
+    }
+}
+
+// The samples of batch word w whose update of synapse (i, j) can be non-zero:
+// j fired this step (q: potentiation by x_pre), or input i fired and j has
+// fired earlier in the episode (p & s: depression by x_post).  Ascending b.
+__device__ __forceinline__ void stdp_word(const Consts& c, int w, uint32_t p, uint32_t q,
+                                          uint32_t s, const float* xpre_i, int NI,
+                                          const float* xps_j, int nc, float& acc, int& nev) {
+    uint32_t m = (p & s) | q;
+    while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        const int b = w * 32 + bit;
+        float a = 0.0f, e = 0.0f;
+        if ((q >> bit) & 1u) a = __fmul_rn(c.nu_post, __ldcg(&xpre_i[(size_t)b * NI]));
+        if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps_j[b * nc]);
+        const float dl = __fsub_rn(a, e);
+        if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
+        else acc = __fadd_rn(acc, dl);
+        ++nev;
+    }
+}
+
+__global__ void __launch_bounds__(PT, 1)
+k_persistent(Consts c, Bufs d, int T, Layout L) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    float* Ws = (float*)(sm + L.o_ws);
+    float* xps = (float*)(sm + L.o_xps);
+    uint32_t* Sm = (uint32_t*)(sm + L.o_sm);
+    uint32_t* Qm = (uint32_t*)(sm + L.o_qm);
+    uint32_t* nzQ = (uint32_t*)(sm + L.o_nzq);
+    double* thS = (double*)(sm + L.o_ths);
+    float* thj = (float*)(sm + L.o_thj);
+    uint32_t* cntS = (uint32_t*)(sm + L.o_cnts);
+    uint32_t* actN = (uint32_t*)(sm + L.o_actn);
+    uint16_t* actS = (uint16_t*)(sm + L.o_acts);
+    uint32_t* preS = (uint32_t*)(sm + L.o_pres);
+    uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
+
+    const int cta = blockIdx.x, tid = threadIdx.x;
+    const int G = L.G;
+    const int j0 = (int)((long long)cta * c.N / G), j1 = (int)((long long)(cta + 1) * c.N / G);
+    const int nc = j1 - j0;
+    const int N = c.N, B = c.B, NI = c.n_in, Bw = c.Bw;
+    uint32_t* const bar = d.err + 1;
+    if (ld_acquire(d.err) != 0u) return;          // an earlier run failed: do nothing
+    const unsigned long long base = d.step[0];
+
+    // ---- the CTA's columns: weights, postsynaptic traces, masks, thresholds
+    for (int k = tid; k < NI * nc; k += PT) {
+        const int i = k / nc, jl = k % nc;
+        Ws[k] = d.W[(size_t)i * N + j0 + jl];
+    }
+    for (int k = tid; k < B * nc; k += PT) {
+        const int b = k / nc, jl = k % nc;
+        xps[k] = d.x_post[(size_t)b * N + j0 + jl];
+    }
+    for (int k = tid; k < Bw * nc; k += PT) {
+        const int w = k / nc, jl = k % nc;
+        Sm[k] = d.spkT[(size_t)(j0 + jl) * Bw + w];
+    }
+    for (int jl = tid; jl < nc; jl += PT) thS[jl] = d.theta[j0 + jl];
+
+    // ---- prologue: input spikes of the first step
+    if (cta == 0)
+        for (int b = tid; b < B; b += PT) d.cnt[(size_t)(base % 3ull) * B + b] = 0u;
+    encode_phase(c, d, L, sm, base, 0);
+    unsigned nbar = 1;
+    bool ok = grid_sync(bar, d.err, G * nbar);
+
+    for (int t = 0; t < T && ok; ++t) {
+        const unsigned long long tt = base + (unsigned long long)t;
+        const int cur = (int)(tt & 1ull), p3 = (int)(tt % 3ull);
+
+        // ================= neuron phase =================
+        for (int b = tid; b < B; b += PT) {
+            cntS[b] = __ldcg(&d.cnt[(size_t)((p3 + 2) % 3) * B + b]);
+            actN[b] = __ldcg(&d.act_cnt[(size_t)cur * B + b]);
+        }
+        for (int k = tid; k < Bw * nc; k += PT) Qm[k] = 0u;
+        for (int jl = tid; jl < nc; jl += PT)
+            thj[jl] = __fadd_rn(c.e_thresh, __double2float_rn(thS[jl]));
+        if (cta == 0)   // accumulator of the next step (its last reader was step tt-1)
+            for (int b = tid; b < B; b += PT) d.cnt[(size_t)((p3 + 1) % 3) * B + b] = 0u;
+        {   // input-major masks of step tt+2 (last read by the STDP phase of step tt-1)
+            const size_t n_pre = (size_t)NI * Bw;
+            uint32_t* z = d.preT + (size_t)((p3 + 2) % 3) * n_pre;
+            for (size_t k = (size_t)cta * PT + tid; k < n_pre; k += (size_t)G * PT) z[k] = 0u;
+        }
+        __syncthreads();
+        for (int k = tid; k < B * CAPS; k += PT) {
+            const int b = k / CAPS, q = k % CAPS;
+            if ((uint32_t)q < actN[b])
+                actS[k] = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + q]);
+        }
+        __syncthreads();
+
+        for (int k = tid; k < B * nc; k += PT) {
+            const int b = k / nc, jl = k % nc, j = j0 + jl;
+            const size_t idx = (size_t)b * N + j;
+            // synaptic current: ascending active inputs of sample b
+            float I = 0.0f;
+            const int na = (int)actN[b];
+            const int ns = na < CAPS ? na : CAPS;
+            for (int q = 0; q < ns; ++q) I = __fadd_rn(I, Ws[(int)actS[b * CAPS + q] * nc + jl]);
+            for (int q = CAPS; q < na; ++q) {
+                const int i = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + q]);
+                I = __fadd_rn(I, Ws[i * nc + jl]);
+            }
+            const uint32_t s = d.st[idx];
+            int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
+            const int se_prev = (s & ST_SE) ? 1 : 0, si_prev = (s & ST_SI) ? 1 : 0;
+            const int C = (int)cntS[b];
+            const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
+            const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
+
+            float v = d.v_e[idx];
+            float dv = __fsub_rn(v, c.e_rest);
+            dv = __fmul_rn(dv, c.a_e);
+            v = __fadd_rn(c.e_rest, dv);
+            const bool free_e = ref_e == 0;
+            if (!free_e) ref_e -= 1;
+            else v = __fadd_rn(v, __fadd_rn(I, I_lat));
+            const bool se = free_e && v >= thj[jl];
+            if (se) { v = c.e_reset; ref_e = c.R_e; }
+            d.v_e[idx] = v;
+
+            float vi = d.v_i[idx];
+            dv = __fsub_rn(vi, c.i_rest);
+            dv = __fmul_rn(dv, c.a_i);
+            vi = __fadd_rn(c.i_rest, dv);
+            const bool free_i = ref_i == 0;
+            if (!free_i) ref_i -= 1;
+            else vi = __fadd_rn(vi, I_inh);
+            const bool si = free_i && vi >= c.i_thresh;
+            if (si) { vi = c.i_reset; ref_i = c.R_i; }
+            d.v_i[idx] = vi;
+
+            float x = xps[k];
+            x = __fmul_rn(x, c.a_x);
+            x = __fadd_rn(x, se ? 1.0f : 0.0f);
+            xps[k] = x;
+
+            d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) |
+                        (si ? ST_SI : 0u);
+            if (se) {
+                d.counts[idx] += 1u;
+                const uint32_t bit = 1u << (b & 31);
+                atomicOr(&Qm[(b >> 5) * nc + jl], bit);
+                atomicOr(&Sm[(b >> 5) * nc + jl], bit);
+                if (c.rec_raster)
+                    atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+            }
+            if (si) {
+                atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
+                if (c.rec_raster)
+                    atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+            }
+        }
+        __syncthreads();
+
+        // ================= STDP phase =================
+        if (c.learn) {
+            const float* xpre = d.x_pre + (size_t)cur * B * NI;
+            for (int jl = tid; jl < nc; jl += PT) {
+                int n = 0;
+                uint32_t nz = 0;
+                for (int w = 0; w < Bw; ++w) {
+                    const uint32_t q = Qm[w * nc + jl];
+                    n += __popc(q);
+                    if (q && w < 32) nz |= 1u << w;
+                }
+                nzQ[jl] = nz;
+                double r;
+                if (c.reduce == SNN_REDUCE_SUM) r = (double)n;
+                else if (c.reduce == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)B);
+                else r = n > 0 ? 1.0 : 0.0;
+                thS[jl] = __dadd_rn(__dmul_rn(thS[jl], c.a_th), __dmul_rn(c.theta_plus, r));
+            }
+            for (int k = tid; k < NI * Bw; k += PT)
+                preS[k] = __ldcg(&d.preT[(size_t)p3 * NI * Bw + k]);
+            __syncthreads();
+            for (int i = tid; i < NI; i += PT) {
+                uint32_t nz = 0;
+                for (int w = 0; w < Bw && w < 32; ++w) nz |= (preS[i * Bw + w] != 0u) ? (1u << w) : 0u;
+                nzP[i] = nz;
+            }
+            __syncthreads();
+            const bool masks = Bw <= 32;
+            for (int k = tid; k < NI * nc; k += PT) {
+                const int i = k / nc, jl = k % nc;
+                float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
+                int nev = 0;
+                if (masks) {   // only the words where an update can be non-zero
+                    uint32_t words = nzP[i] | nzQ[jl];
+                    while (words) {
+                        const int w = __ffs(words) - 1;
+                        words &= words - 1;
+                        stdp_word(c, w, preS[i * Bw + w], Qm[w * nc + jl], Sm[w * nc + jl],
+                                  xpre + i, NI, xps + jl, nc, acc, nev);
+                    }
+                } else {
+                    for (int w = 0; w < Bw; ++w)
+                        stdp_word(c, w, preS[i * Bw + w], Qm[w * nc + jl], Sm[w * nc + jl],
+                                  xpre + i, NI, xps + jl, nc, acc, nev);
+                }
+                if (nev > 0) {
+                    float D = acc;
+                    if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
+                    if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
+                    float wv = __fadd_rn(Ws[k], D);
+                    wv = wv < c.w_min ? c.w_min : wv;
+                    wv = wv > c.w_max ? c.w_max : wv;
+                    Ws[k] = wv;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ================= next step's input =================
+        if (t + 1 < T) {
+            encode_phase(c, d, L, sm, tt + 1, t + 1);
+            ++nbar;
+            ok = grid_sync(bar, d.err, G * nbar);
+        }
+    }
+
+    // ---- write the CTA's columns back
+    __syncthreads();
+    if (c.learn) {
+        for (int k = tid; k < NI * nc; k += PT) {
+            const int i = k / nc, jl = k % nc;
+            d.W[(size_t)i * N + j0 + jl] = Ws[k];
+        }
+        for (int jl = tid; jl < nc; jl += PT) d.theta[j0 + jl] = thS[jl];
+    }
+    for (int k = tid; k < B * nc; k += PT) {
+        const int b = k / nc, jl = k % nc;
+        d.x_post[(size_t)b * N + j0 + jl] = xps[k];
+    }
+    for (int k = tid; k < Bw * nc; k += PT) {
+        const int w = k / nc, jl = k % nc;
+        d.spkT[(size_t)(j0 + jl) * Bw + w] = Sm[k];
+    }
+}
+
+}  // namespace
+
+// Launches the persistent form if its shared-memory layout fits one CTA per
+// SM; *used = 0 (and nothing launched) otherwise.
+cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_t s, int* used,
+                              Prof* prof) {
     *used = 0;
+    if (T == 0) {   // nothing to step: the reset already happened
+        *used = 1;
+        return cudaSuccess;
+    }
+    int dev = 0, sms = 0, smem_optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const int G = sms < c.N ? sms : c.N;
+    const Layout L = make_layout(c, G);
+    if (L.bytes + 1024 > (size_t)smem_optin) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)L.bytes);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, PT, L.bytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaSuccess;
+    Consts cc = c;
+    Bufs dd = d;
+    int TT = T;
+    Layout LL = L;
+    void* args[] = {&cc, &dd, &TT, &LL};
+    e = prof_start(prof, SNN_KERNEL_PERSISTENT, s);
+    if (e != cudaSuccess) return e;
+    e = cudaLaunchCooperativeKernel((const void*)k_persistent, dim3(G), dim3(PT), args, L.bytes, s);
+    if (e != cudaSuccess) return e;
+    e = prof_stop(prof, s);
+    if (e != cudaSuccess) return e;
+    *used = 1;
     return cudaSuccess;
 }
 

@@ -41,11 +41,10 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
                             const uint64_t* __restrict__ seeds, int episodic, int T) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
-    const size_t n_thr = (size_t)c.n_in * c.Bp;
+    const size_t n_thr = (size_t)c.B * c.n_in;
     for (size_t k = tid; k < n_thr; k += nth) {
-        const int i = (int)(k / c.Bp), b = (int)(k % c.Bp);
-        d.thrT[k] = b < c.B ? poisson_threshold(rates[(size_t)b * c.n_in + i], c.dt) : 0u;
-        if (episodic) d.x_preT[k] = 0.0f;
+        d.thr[k] = poisson_threshold(rates[k], c.dt);
+        if (episodic) { d.x_pre[k] = 0.0f; d.x_pre[n_thr + k] = 0.0f; }
     }
     const size_t n_bn = (size_t)c.B * c.N;
     for (size_t k = tid; k < n_bn; k += nth) {
@@ -57,66 +56,66 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
         }
         d.counts[k] = 0u;
     }
-    if (episodic) {
-        const size_t n_nw = (size_t)c.N * c.Bw;
-        for (size_t k = tid; k < n_nw; k += nth) {
-            d.spkT[k] = 0u;
-            d.postT[k] = 0u;
-            d.postT[n_nw + k] = 0u;
-        }
-        for (size_t k = tid; k < 2 * (size_t)c.B; k += nth) d.cnt[k] = 0u;
+    const size_t n_nw = (size_t)c.N * c.Bw;
+    for (size_t k = tid; k < n_nw; k += nth) {
+        if (episodic) d.spkT[k] = 0u;
+        d.postT[k] = 0u;
+        d.postT[n_nw + k] = 0u;
     }
+    const size_t n_pre = (size_t)c.n_in * c.Bw;   // input masks are per step: clear all three
+    for (size_t k = tid; k < 3 * n_pre; k += nth) d.preT[k] = 0u;
+    if (episodic)
+        for (size_t k = tid; k < 3 * (size_t)c.B; k += nth) d.cnt[k] = 0u;
     for (size_t k = tid; k < (size_t)c.B; k += nth) d.seeds[k] = seeds[k];
     if (tid == 0) {
         const unsigned long long base = episodic ? 0ull : d.step[1];
         d.step[0] = base;
         d.step[1] = base + (unsigned long long)T;
+        d.err[1] = 0u;    // grid-barrier counter of the persistent form
     }
 }
 
-// grid (Bw, ceil(Iw/8)), 256 threads: warp = 32 samples x one 32-input word.
+// 256 threads; warp = one sample x one 32-input word (lanes = inputs).
 __global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
-    const int par = (int)(tt & 1ull);
-    {   // clear this step's accumulators; their previous readers finished two launches ago
-        const size_t nblk = (size_t)gridDim.x * gridDim.y;
-        const size_t gtid = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
-        const size_t nth = nblk * blockDim.x;
+    const int cur = (int)(tt & 1ull), prv = cur ^ 1, p3 = (int)(tt % 3ull);
+    {   // clear this step's accumulators and the next step's input-major masks;
+        // their last readers ran at least one launch earlier
+        const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const size_t nth = (size_t)gridDim.x * blockDim.x;
         const size_t n_nw = (size_t)c.N * c.Bw;
-        uint32_t* post = d.postT + (size_t)par * n_nw;
+        uint32_t* post = d.postT + (size_t)cur * n_nw;
         for (size_t k = gtid; k < n_nw; k += nth) post[k] = 0u;
-        uint32_t* cnt = d.cnt + (size_t)par * c.B;
+        uint32_t* cnt = d.cnt + (size_t)p3 * c.B;
         for (size_t k = gtid; k < (size_t)c.B; k += nth) cnt[k] = 0u;
+        const size_t n_pre = (size_t)c.n_in * c.Bw;
+        uint32_t* nxt = d.preT + (size_t)((p3 + 1) % 3) * n_pre;
+        for (size_t k = gtid; k < n_pre; k += nth) nxt[k] = 0u;
     }
-    const int iw = blockIdx.y * 8 + warp;
-    if (iw >= c.Iw) return;
-    const int g = blockIdx.x;
-    const int b = g * 32 + lane;
-    const uint64_t seed = b < c.B ? d.seeds[b] : 0ull;
-    const int i0 = iw * 32;
-    const int n = min(32, c.n_in - i0);
-    uint32_t word = 0;
-    for (int k = 0; k < n; ++k) {
-        const int i = i0 + k;
-        const size_t o = (size_t)i * c.Bp + b;
-        const uint32_t thr = d.thrT[o];
-        uint32_t s = 0;
+    const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (size_t)c.B * c.Iw) return;
+    const int b = (int)(gw / c.Iw), iw = (int)(gw % c.Iw);
+    const int i = iw * 32 + lane;
+    uint32_t s = 0;
+    if (i < c.n_in) {
+        const size_t o = (size_t)b * c.n_in + i;
+        const uint32_t thr = d.thr[o];
         if (thr != 0u) {
             const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)i;
-            const uint32_t h = (uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32);
+            const uint32_t h = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32);
             s = h < thr ? 1u : 0u;
         }
-        float x = d.x_preT[o];
+        const size_t nbi = (size_t)c.B * c.n_in;
+        float x = d.x_pre[(size_t)prv * nbi + o];
         x = __fmul_rn(x, c.a_x);
         x = __fadd_rn(x, s ? 1.0f : 0.0f);
-        d.x_preT[o] = x;
-        const uint32_t bal = __ballot_sync(FULL, s);
-        if (lane == 0) d.preT[(size_t)i * c.Bw + g] = bal;
-        word |= s << k;
+        d.x_pre[(size_t)cur * nbi + o] = x;
+        if (s) atomicOr(&d.preT[((size_t)p3 * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
     }
-    if (b < c.B) {
-        d.inb[(size_t)b * c.Iw + iw] = word;
+    const uint32_t word = __ballot_sync(FULL, s);
+    if (lane == 0) {
+        d.inb[((size_t)cur * c.B + b) * c.Iw + iw] = word;
         if (c.rec_input) d.raster_in[((size_t)t_local * c.B + b) * c.Iw + iw] = word;
     }
 }
@@ -131,7 +130,8 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
 
     // Synaptic current: sum of W[i][j] over the active inputs, ascending i.
     float I = 0.0f;
-    const uint32_t* ib = d.inb + (size_t)b * c.Iw;
+    const int cur = par;
+    const uint32_t* ib = d.inb + ((size_t)cur * c.B + b) * c.Iw;
     const float* Wj = d.W + j;
     for (int w = 0; w < c.Iw; ++w) {
         uint32_t m = ib[w];
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
     const uint32_t s = d.st[idx];
     int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
     const int se_prev = (s & ST_SE) ? 1 : 0, si_prev = (s & ST_SI) ? 1 : 0;
-    const int C = (int)d.cnt[(size_t)(par ^ 1) * c.B + b];
+    const int p3 = (int)(tt % 3ull);
+    const int C = (int)d.cnt[(size_t)((p3 + 2) % 3) * c.B + b];
     const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));   // all-but-self
     const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);         // one-to-one
 
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
             atomicOr(&d.raster_e[((size_t)t_local * c.B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
     }
     if (si) {
-        atomicAdd(&d.cnt[(size_t)par * c.B + b], 1u);
+        atomicAdd(&d.cnt[(size_t)p3 * c.B + b], 1u);
         if (c.rec_raster)
             atomicOr(&d.raster_i[((size_t)t_local * c.B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
     }
@@ -227,9 +228,10 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
         for (int w = 0; w < c.Bw; ++w) active |= (Sj[w] | Qj[w]) != 0u;
     if (!__syncthreads_or(active)) return;   // no neuron of the group has fired yet
 
+    const float* xp_cur = d.x_pre + (size_t)par * c.B * c.n_in;
     const int i_end = min(c.n_in, (int)(blockIdx.y + 1) * STDP_ROWS);
     for (int i = blockIdx.y * STDP_ROWS + warp; i < i_end; i += 8) {
-        const uint32_t* P = d.preT + (size_t)i * c.Bw;
+        const uint32_t* P = d.preT + ((size_t)(tt % 3ull) * c.n_in + i) * c.Bw;
         float acc = (REDUCE == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
         int nev = 0;
         if (vj) {
@@ -241,7 +243,8 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
                     m &= m - 1;
                     const int b = w * 32 + bit;
                     float a = 0.0f, e = 0.0f;
-                    if ((q >> bit) & 1u) a = __fmul_rn(c.nu_post, d.x_preT[(size_t)i * c.Bp + b]);
+                    if ((q >> bit) & 1u)
+                        a = __fmul_rn(c.nu_post, xp_cur[(size_t)b * c.n_in + i]);
                     if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, d.x_post[(size_t)b * c.N + j]);
                     const float dl = __fsub_rn(a, e);
                     if (REDUCE == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
@@ -269,10 +272,9 @@ __global__ void k_extract(Consts c, Bufs d, int field, void* out) {
     if (field == SNN_FIELD_X_PRE) {
         float* o = (float*)out;
         const size_t n = (size_t)c.B * c.n_in;
-        for (size_t k = tid; k < n; k += nth) {
-            const size_t b = k / c.n_in, i = k % c.n_in;
-            o[k] = d.x_preT[i * c.Bp + b];
-        }
+        const int last = (int)((d.step[1] + 1ull) & 1ull);   // buffer of step end-1
+        const float* src = d.x_pre + (size_t)last * n;
+        for (size_t k = tid; k < n; k += nth) o[k] = src[k];
         return;
     }
     uint8_t* o = (uint8_t*)out;
@@ -316,8 +318,8 @@ int grid_for(size_t n, int threads, int cap) {
 cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
                              const uint64_t* seeds, int episodic, int T, cudaStream_t s,
                              Prof* prof) {
-    const size_t n = (size_t)c.n_in * c.Bp > (size_t)c.B * c.N ? (size_t)c.n_in * c.Bp
-                                                                : (size_t)c.B * c.N;
+    const size_t n = (size_t)c.n_in * c.B > (size_t)c.B * c.N ? (size_t)c.n_in * c.B
+                                                               : (size_t)c.B * c.N;
     PROF_TRY(prof_start(prof, SNN_KERNEL_BEGIN_RUN, s));
     k_begin_run<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(c, d, rates, seeds, episodic, T);
     PROF_TRY(cudaGetLastError());
@@ -326,7 +328,8 @@ cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,
 
 cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_t s, Prof* prof) {
     PROF_TRY(prof_start(prof, SNN_KERNEL_ENCODE, s));
-    k_encode<<<dim3(c.Bw, (c.Iw + 7) / 8), 256, 0, s>>>(c, d, t_local);
+    const size_t warps = (size_t)c.B * c.Iw;
+    k_encode<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(c, d, t_local);
     PROF_TRY(cudaGetLastError());
     PROF_TRY(prof_stop(prof, s));
     const size_t bn = (size_t)c.B * c.N;

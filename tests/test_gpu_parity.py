@@ -95,78 +95,85 @@ def assert_parity(g, st, rec):
     assert g["step"] == st.step
 
 
+MODES = ("step", "graph", "persistent")
+
+
+def parity_all_modes(p, r, s, w, T, *, learn=True, reduce="mean", modes=MODES):
+    """One oracle run, every run mode of the library compared with it."""
+    st, rec = oracle_run(p, r, s, w, T, learn=learn, reduce=reduce)
+    for mode in modes:
+        _, g = gpu_run(p, r, s, w, T, learn=learn, reduce=reduce, mode=mode)
+        try:
+            assert_parity(g, st, rec)
+        except AssertionError as e:
+            raise AssertionError("mode %s: %s" % (mode, e)) from None
+    return st, rec
+
+
 # ------------------------------------------------------------------ cases ---
 
-@pytest.mark.parametrize("mode", ["step", "graph"])
-def test_784x100_single_presentation_learning(mode):
+def test_784x100_single_presentation_learning():
     """B=1, 784 -> 100, T=250, pair STDP with mean reduction."""
     p, r, s, w = synth.workload(1, 100)
-    net, g = gpu_run(p, r, s, w, 250, mode=mode)
-    st, rec = oracle_run(p, r, s, w, 250)
+    st, rec = parity_all_modes(p, r, s, w, 250)
     assert rec.raster_e.sum() > 20 and not np.array_equal(st.w, w)
-    assert_parity(g, st, rec)
 
 
 @pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
 def test_784x400_batch16_learning(reduce):
     p, r, s, w = synth.workload(16, 400)
-    _, g = gpu_run(p, r, s, w, 250, reduce=reduce, mode="graph")
-    st, rec = oracle_run(p, r, s, w, 250, reduce=reduce)
-    assert_parity(g, st, rec)
+    parity_all_modes(p, r, s, w, 250, reduce=reduce)
 
 
-@pytest.mark.parametrize("B,N", [(37, 100), (33, 70), (1, 1), (5, 31), (64, 32)])
+@pytest.mark.parametrize("B,N", [(37, 100), (33, 70), (1, 1), (5, 31), (64, 32), (40, 500)])
 def test_ragged_shapes_learning(B, N):
-    """Batches and layers that are not multiples of 32 (ragged warps and words)."""
+    """Batches and layers that are not multiples of 32 (ragged warps and words),
+    and layers narrower or wider than one column per SM."""
     p, r, s, w = synth.workload(B, N)
-    _, g = gpu_run(p, r, s, w, 80, reduce="sum")
-    st, rec = oracle_run(p, r, s, w, 80, reduce="sum")
-    assert_parity(g, st, rec)
+    parity_all_modes(p, r, s, w, 80, reduce="sum")
 
 
 def test_small_input_layer_and_saturated_rates():
-    """n_in = 40 (two words, ragged); some rates >= 1000 Hz (always spike)."""
+    """n_in = 40 (two words, ragged); some rates >= 1000 Hz (always spike), so
+    samples carry more active inputs than the persistent form stages."""
     B, N, NI = 6, 12, 40
     p = synth.diehl_cook_params(N, NI)
     w = synth.weights(NI, N)
     r = synth.rates_from_images(synth.images(B, NI)) * 3
     r[:, :3] = 1500.0
+    r[0, :] = 1500.0
     s = synth.sample_seeds(B)
-    _, g = gpu_run(p, r, s, w, 120, reduce="mean")
-    st, rec = oracle_run(p, r, s, w, 120, reduce="mean")
-    assert rec.raster_in[:, :, :3].all()
-    assert_parity(g, st, rec)
+    st, rec = parity_all_modes(p, r, s, w, 120, reduce="mean")
+    assert rec.raster_in[:, :, :3].all() and rec.raster_in[:, 0].all()
 
 
 def test_learning_off_batch64():
     p, r, s, w = synth.workload(64, 400)
-    _, g = gpu_run(p, r, s, w, 250, learn=False)
-    st, rec = oracle_run(p, r, s, w, 250, learn=False)
-    assert np.array_equal(g["w"], w)
-    assert_parity(g, st, rec)
+    parity_all_modes(p, r, s, w, 250, learn=False)
 
 
 def test_zero_rates_and_zero_steps():
     p, r, s, w = synth.workload(3, 50)
     r[:] = 0.0
-    _, g = gpu_run(p, r, s, w, 30)
-    st, rec = oracle_run(p, r, s, w, 30)
-    assert g["raster_in"].sum() == 0 and g["raster_e"].sum() == 0
-    assert_parity(g, st, rec)
-    # T = 0: only the episodic reset
-    net, g0 = gpu_run(p, r, s, w, 0)
-    assert g0["step"] == 0 and np.all(g0["v_e"] == np.float32(p["e_rest"]))
+    st, rec = parity_all_modes(p, r, s, w, 30)
+    assert rec.raster_in.sum() == 0 and rec.raster_e.sum() == 0
+    for mode in MODES:      # T = 0: only the episodic reset
+        net, g0 = gpu_run(p, r, s, w, 0, mode=mode)
+        assert g0["step"] == 0 and np.all(g0["v_e"] == np.float32(p["e_rest"]))
 
 
-def test_continuing_run_and_batch_change():
-    """Continuing (no reset) continues the episode; a new batch size
-    re-initialises the per-sample state; W and theta persist throughout."""
+@pytest.mark.parametrize("modes", [("step", "step", "step"), ("persistent", "graph", "persistent"),
+                                   ("graph", "persistent", "step")])
+def test_continuing_run_and_batch_change(modes):
+    """Continuing (no reset) continues the episode, also when the run mode
+    changes between calls; a new batch size re-initialises the per-sample
+    state; W and theta persist throughout."""
     m = snn()
     p, r, s, w = synth.workload(7, 100)
-    net, g1 = gpu_run(p, r[:4], s[:4], w, 100)
+    net, g1 = gpu_run(p, r[:4], s[:4], w, 100, mode=modes[0])
     st, rec1 = oracle_run(p, r[:4], s[:4], w, 100)
     assert_parity(g1, st, rec1)
-    _, g2 = gpu_run(p, r[:4], s[:4], w, 150, net=net, continue_=True)
+    _, g2 = gpu_run(p, r[:4], s[:4], w, 150, net=net, continue_=True, mode=modes[1])
     rec2 = oracle.run(p, st, r[:4], s[:4], 150, learn=True, reduce="mean", episodic=False)
     assert_parity(g2, st, rec2)
     # continuing with another batch size is refused
@@ -174,7 +181,7 @@ def test_continuing_run_and_batch_change():
         net.run(dev(r), dev(s), 10, continue_=True)
     assert e.value.status == m.SNN_ERR_STATE
     # a new batch size re-initialises the samples but keeps W and theta
-    _, g3 = gpu_run(p, r, s, w, 60, net=net)
+    _, g3 = gpu_run(p, r, s, w, 60, net=net, mode=modes[2])
     st3 = oracle.new_state(p, 7, st.w, theta=st.theta)
     rec3 = oracle.run(p, st3, r, s, 60, learn=True, reduce="mean")
     assert_parity(g3, st3, rec3)
@@ -192,11 +199,11 @@ def test_host_inputs_match_device_inputs():
 
 
 def test_modes_agree_and_graph_replays():
-    """The captured graph is reused across runs and matches per-step launches."""
+    """The captured graph is reused across runs; all modes agree bit for bit."""
     m = snn()
     p, r, s, w = synth.workload(16, 128)
     outs = []
-    for mode in ("step", "graph", "graph"):
+    for mode in ("step", "graph", "graph", "persistent", "auto"):
         net = m.Network(p, w_init=w)
         for _ in range(2):
             net.run(dev(r), dev(s), 90, mode=mode, record=True)
@@ -207,7 +214,21 @@ def test_modes_agree_and_graph_replays():
             assert np.array_equal(bits(a), bits(b))
 
 
-@pytest.mark.parametrize("mode", ["step", "graph"])
+def test_persistent_mode_refuses_what_does_not_fit():
+    """B=1024 at 6400 neurons needs more shared memory per CTA than an SM has:
+    the persistent mode says so; auto falls back to the graph form."""
+    m = snn()
+    p, r, s, w = synth.workload(1024, 6400)
+    net = m.Network(p, w_init=w)
+    with pytest.raises(m.SNNError) as e:
+        net.run(dev(r), dev(s), 2, mode="persistent")
+    assert e.value.status == m.SNN_ERR_ARG
+    net.run(dev(r), dev(s), 2, mode="auto")
+    torch.cuda.synchronize()
+    assert net.read("step")[0] == 2
+
+
+@pytest.mark.parametrize("mode", ["step", "graph", "persistent"])
 def test_profile_reports_every_launch(mode):
     m = snn()
     p, r, s, w = synth.workload(4, 64)
@@ -216,8 +237,10 @@ def test_profile_reports_every_launch(mode):
         net.run(dev(r), dev(s), 20, mode=mode, profile=True)
         prof = m.snn_profile(net.handle)
         assert prof["begin_run"][1] == 1
-        for k in ("encode", "neuron", "stdp"):
-            assert prof[k][1] == 20 and prof[k][0] > 0.0, (k, prof[k])
+        kinds = ("persistent",) if mode == "persistent" else ("encode", "neuron", "stdp")
+        for k in kinds:
+            n = 1 if mode == "persistent" else 20
+            assert prof[k][1] == n and prof[k][0] > 0.0, (k, prof[k])
     net.run(dev(r), dev(s), 5, mode=mode)    # an unprofiled run has nothing to report
     with pytest.raises(m.SNNError):
         m.snn_profile(net.handle)
@@ -251,7 +274,7 @@ def test_784x6400_batch256_learning_off_sampled():
     """The 784 -> 6400, B = 256 workload: each sampled sample of the batch
     equals the oracle's single-sample run (learning off, T = 250)."""
     p, r, s, w = synth.workload(256, 6400)
-    _, g = gpu_run(p, r, s, w, 250, learn=False, mode="graph")
+    _, g = gpu_run(p, r, s, w, 250, learn=False, mode="persistent")
     for b in (0, 101, 255):
         st, rec = oracle_run(p, r[b:b + 1], s[b:b + 1], w, 250, learn=False)
         assert np.array_equal(g["raster_e"][:, b:b + 1], rec.raster_e), b
@@ -264,7 +287,8 @@ def test_784x6400_batch256_learning_first_steps():
     """Learning on at full size for the first 12 steps (the first excitatory
     spikes and the first weight updates fall inside)."""
     p, r, s, w = synth.workload(256, 6400)
-    _, g = gpu_run(p, r, s, w, 12, mode="graph")
     st, rec = oracle_run(p, r, s, w, 12)
     assert rec.raster_e.sum() > 0 and not np.array_equal(st.w, w)
-    assert_parity(g, st, rec)
+    for mode in ("persistent", "graph"):
+        _, g = gpu_run(p, r, s, w, 12, mode=mode)
+        assert_parity(g, st, rec)
