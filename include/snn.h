@@ -198,6 +198,33 @@ enum {
  * run was not profiled), SNN_ERR_CUDA. */
 SNN_API snn_status snn_profile(snn_net* net, double* ms, int* launches, int n);
 
+/* Allocation-free, learning-off presentation of a batch.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory,
+ * such as a plug-in running inside another runtime that owns all device
+ * memory, or a latency-critical loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc.  It computes the excitatory spike counts
+ * that snn_create(spec with w, theta) + snn_run(rates, seeds, B, T, dt_ms,
+ * learn = 0, episodic) + snn_read_state(SNN_FIELD_SPIKE_COUNTS) would give,
+ * without allocating anything: all per-sample state lives in one fixed
+ * device array of SNN_NOALLOC_SCRATCH_BYTES inside the library (held on every
+ * GPU that loads the library, until the process exits).
+ *   spec          network parameters (w_init / theta_init are ignored);
+ *   w, theta      device [n_in][n_exc] float and [n_exc] double (caller's);
+ *   rates, seeds  device [B][n_in] float and [B] uint64 (caller's);
+ *   spike_counts  device [B][n_exc] uint32 output (caller's).
+ * Asynchronous on cuda_stream.  The first call on a device looks up the
+ * array's device address with that device current (make that first call
+ * before any stream capture).  Every call reuses the same array and
+ * re-initialises it; calls whose GPU work overlaps (e.g. on unordered
+ * streams) race on it.  The scratch needs 12*B*n_exc + 4*B*n_in +
+ * 4*B*ceil(n_in/32) + 12*B bytes.
+ * Errors (reason in snn_last_error(NULL)): SNN_ERR_ARG, SNN_ERR_CAPACITY
+ * (scratch too small for this B and layer), SNN_ERR_CUDA. */
+#define SNN_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+SNN_API snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, const double* theta,
+                                     const float* rates_hz, const uint64_t* seeds, int B, int T,
+                                     float dt_ms, uint32_t* spike_counts, void* cuda_stream);
+
 /* One-line description of the last error on this network ("" if none).
  * Valid until the next call on the network.  NULL net gives the reason of
  * the last failed snn_create on this thread. */

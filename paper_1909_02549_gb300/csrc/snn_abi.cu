@@ -240,6 +240,11 @@ size_t field_bytes(const snn_net* n, int field) {
 
 }  // namespace
 
+namespace snn {
+// Error text for calls without a network (read back by snn_last_error(NULL)).
+void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace snn
+
 extern "C" {
 
 void snn_spec_default(snn_spec* s, int32_t n_exc) {

@@ -1,0 +1,232 @@
+// Allocation-free inference entry point (snn_infer_noalloc).
+//
+// Some callers cannot call cudaMalloc: code running as a plug-in inside another
+// runtime that owns all device memory (a serving framework's custom operator,
+// an arena allocator that must stay the only allocator), or latency-critical
+// loops where the implicit device synchronisation of an allocation is not
+// acceptable.  For them this file runs a learning-off presentation of a batch
+// with every intermediate buffer carved out of one file-scope device array of
+// fixed size; the caller passes only the inputs and the output.
+//
+// The array is shared by every call in the process and keeps the last call's
+// contents; each call re-initialises what must start at zero.  Two calls whose
+// work overlaps on the GPU (different streams, no ordering between them) race
+// on the array.
+#include <cmath>
+#include <mutex>
+
+#include "snn_internal.cuh"
+
+namespace snn {
+void set_thread_error(const char* msg);
+}
+
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = SNN_NOALLOC_SCRATCH_BYTES;   // 32 MiB per device
+constexpr int MAX_DEVICES = 64;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current.
+std::mutex g_setup_mutex;
+void* g_scratch_ptr[MAX_DEVICES] = {nullptr};
+
+struct NaConsts {
+    int n_in, N, B, Iw;
+    float e_rest, e_reset, e_thresh, a_e;
+    float i_rest, i_reset, i_thresh, a_i;
+    float w_ei, w_ie, dt;
+    int R_e, R_i;
+};
+
+struct NaBufs {
+    const float* W;        // [n_in][N]  caller's weights
+    const double* theta;   // [N]        caller's thresholds
+    const uint64_t* seeds; // [B]        caller's seeds
+    uint32_t* counts;      // [B][N]     caller's output
+    float* v_e;            // [B][N]     scratch
+    float* v_i;            // [B][N]
+    uint32_t* st;          // [B][N]  ref_e | ref_i<<8 | s_e'<<16 | s_i'<<17
+    uint32_t* thr;         // [B][n_in]
+    uint32_t* inb;         // [B][Iw]
+    uint32_t* cnt;         // [3][B]
+};
+
+size_t scratch_bytes(size_t B, size_t N, size_t n_in) {
+    const size_t Iw = (n_in + 31) / 32;
+    return 12 * B * N + 4 * B * n_in + 4 * B * Iw + 12 * B;
+}
+
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_na_init(NaConsts c, NaBufs d, const float* __restrict__ rates) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth) {
+        double p = __dmul_rn((double)rates[k], (double)c.dt);
+        p = __dmul_rn(p, 1e-3);
+        const double x = __dmul_rn(p, 4294967296.0);
+        uint32_t thr = 0u;
+        if (x > 0.0) thr = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(x);
+        d.thr[k] = thr;
+    }
+    for (size_t k = tid; k < (size_t)c.B * c.N; k += nth) {
+        d.v_e[k] = c.e_rest;
+        d.v_i[k] = c.i_rest;
+        d.st[k] = 0u;
+        d.counts[k] = 0u;
+    }
+    for (size_t k = tid; k < 3 * (size_t)c.B; k += nth) d.cnt[k] = 0u;
+}
+
+// warp = one sample x one 32-input word
+__global__ void __launch_bounds__(256) k_na_encode(NaConsts c, NaBufs d, int t) {
+    const int lane = threadIdx.x & 31;
+    const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    uint32_t* acc = d.cnt + (size_t)(t % 3) * c.B;      // inhibitory count of step t
+    for (size_t k = gtid; k < (size_t)c.B; k += nth) acc[k] = 0u;
+    const size_t gw = gtid >> 5;
+    if (gw >= (size_t)c.B * c.Iw) return;
+    const int b = (int)(gw / c.Iw), iw = (int)(gw % c.Iw);
+    const int i = iw * 32 + lane;
+    uint32_t s = 0;
+    if (i < c.n_in) {
+        const uint32_t thr = d.thr[(size_t)b * c.n_in + i];
+        if (thr != 0u) {
+            const uint64_t ctr = (uint64_t)t * (uint64_t)c.n_in + (uint64_t)i;
+            const uint32_t h = (uint32_t)(sm64(d.seeds[b] ^ sm64(ctr)) >> 32);
+            s = h < thr ? 1u : 0u;
+        }
+    }
+    const uint32_t word = __ballot_sync(FULL, s);
+    if (lane == 0) d.inb[(size_t)b * c.Iw + iw] = word;
+}
+
+// one thread per (b, j)
+__global__ void __launch_bounds__(256) k_na_neuron(NaConsts c, NaBufs d, int t) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)c.B * c.N) return;
+    const int b = (int)(idx / c.N), j = (int)(idx % c.N);
+    float I = 0.0f;
+    const uint32_t* ib = d.inb + (size_t)b * c.Iw;
+    for (int w = 0; w < c.Iw; ++w) {
+        uint32_t m = ib[w];
+        while (m) {
+            const int k = __ffs(m) - 1;
+            m &= m - 1;
+            I = __fadd_rn(I, d.W[(size_t)(w * 32 + k) * c.N + j]);
+        }
+    }
+    const uint32_t s = d.st[idx];
+    int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
+    const int se_prev = (s >> 16) & 1, si_prev = (s >> 17) & 1;
+    const int C = (int)d.cnt[(size_t)((t + 2) % 3) * c.B + b];
+    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
+    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
+    float v = d.v_e[idx];
+    float dv = __fsub_rn(v, c.e_rest);
+    dv = __fmul_rn(dv, c.a_e);
+    v = __fadd_rn(c.e_rest, dv);
+    const bool free_e = ref_e == 0;
+    if (!free_e) ref_e -= 1;
+    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
+    const bool se = free_e && v >= __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j]));
+    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    d.v_e[idx] = v;
+    float vi = d.v_i[idx];
+    dv = __fsub_rn(vi, c.i_rest);
+    dv = __fmul_rn(dv, c.a_i);
+    vi = __fadd_rn(c.i_rest, dv);
+    const bool free_i = ref_i == 0;
+    if (!free_i) ref_i -= 1;
+    else vi = __fadd_rn(vi, I_inh);
+    const bool si = free_i && vi >= c.i_thresh;
+    if (si) { vi = c.i_reset; ref_i = c.R_i; }
+    d.v_i[idx] = vi;
+    d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? 1u << 16 : 0u) | (si ? 1u << 17 : 0u);
+    if (se) d.counts[idx] += 1u;
+    if (si) atomicAdd(&d.cnt[(size_t)(t % 3) * c.B + b], 1u);
+}
+
+snn_status na_fail(snn_status code, const char* msg) {
+    snn::set_thread_error(msg);
+    return code;
+}
+
+}  // namespace
+
+extern "C" snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, const double* theta,
+                                        const float* rates, const uint64_t* seeds, int B, int T,
+                                        float dt_ms, uint32_t* spike_counts, void* stream_) {
+    if (!spec || !w || !theta || !rates || !seeds || !spike_counts)
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: NULL pointer argument");
+    const snn_spec& s = *spec;
+    if (s.n_in <= 0 || s.n_exc <= 0 || s.n_inh != s.n_exc || B <= 0 || T < 0 ||
+        !(dt_ms > 0.0f) || !(s.e_tau_ms > 0.0f) || !(s.i_tau_ms > 0.0f) ||
+        !(s.e_refrac_ms >= 0.0f) || !(s.i_refrac_ms >= 0.0f))
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: invalid sizes or parameters");
+    const int R_e = (int)std::lround((double)s.e_refrac_ms / (double)dt_ms);
+    const int R_i = (int)std::lround((double)s.i_refrac_ms / (double)dt_ms);
+    if (R_e > 255 || R_i > 255)
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: refractory period over 255 steps");
+    if (scratch_bytes((size_t)B, (size_t)s.n_exc, (size_t)s.n_in) > NOALLOC_SCRATCH_BYTES)
+        return na_fail(SNN_ERR_CAPACITY,
+                       "snn_infer_noalloc: B * n_exc too large for the 32 MiB scratch array "
+                       "(needs 12*B*n_exc + 4*B*n_in + 4*B*ceil(n_in/32) + 12*B bytes)");
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES)
+        return na_fail(SNN_ERR_CUDA, "snn_infer_noalloc: no usable current CUDA device");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return na_fail(SNN_ERR_CUDA, "snn_infer_noalloc: cudaGetSymbolAddress failed");
+            g_scratch_ptr[dev] = p;
+        }
+        base = g_scratch_ptr[dev];
+    }
+
+    NaConsts c{};
+    c.n_in = s.n_in; c.N = s.n_exc; c.B = B; c.Iw = (s.n_in + 31) / 32;
+    c.e_rest = s.e_rest; c.e_reset = s.e_reset; c.e_thresh = s.e_thresh;
+    c.a_e = (float)std::exp(-(double)dt_ms / (double)s.e_tau_ms);
+    c.i_rest = s.i_rest; c.i_reset = s.i_reset; c.i_thresh = s.i_thresh;
+    c.a_i = (float)std::exp(-(double)dt_ms / (double)s.i_tau_ms);
+    c.w_ei = s.w_ei; c.w_ie = s.w_ie; c.dt = dt_ms;
+    c.R_e = R_e; c.R_i = R_i;
+
+    const size_t BN = (size_t)B * s.n_exc, BI = (size_t)B * s.n_in;
+    unsigned char* p = (unsigned char*)base;
+    NaBufs d{};
+    d.W = w; d.theta = theta; d.seeds = seeds; d.counts = spike_counts;
+    d.v_e = (float*)p;            p += 4 * BN;
+    d.v_i = (float*)p;            p += 4 * BN;
+    d.st = (uint32_t*)p;          p += 4 * BN;
+    d.thr = (uint32_t*)p;         p += 4 * BI;
+    d.inb = (uint32_t*)p;         p += 4 * (size_t)B * c.Iw;
+    d.cnt = (uint32_t*)p;
+
+    cudaStream_t st = (cudaStream_t)stream_;
+    k_na_init<<<152 * 8, 256, 0, st>>>(c, d, rates);
+    const size_t warps = (size_t)B * c.Iw;
+    for (int t = 0; t < T; ++t) {
+        k_na_encode<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(c, d, t);
+        k_na_neuron<<<(unsigned)((BN + 255) / 256), 256, 0, st>>>(c, d, t);
+    }
+    if (cudaGetLastError() != cudaSuccess)
+        return na_fail(SNN_ERR_CUDA, "snn_infer_noalloc: kernel launch failed");
+    return SNN_OK;
+}

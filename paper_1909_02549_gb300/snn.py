@@ -54,7 +54,8 @@ FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
 
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
             "snn_read_state", "snn_read_weights", "snn_write_weights", "snn_profile",
-            "snn_last_error"]
+            "snn_infer_noalloc", "snn_last_error"]
+SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class snn_spec(C.Structure):
@@ -100,6 +101,10 @@ def lib():
         L.snn_read_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_write_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
+        L.snn_infer_noalloc.argtypes = [C.POINTER(snn_spec), C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p,
+                                        C.c_void_p]
+        L.snn_infer_noalloc.restype = C.c_int
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
         for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state",
@@ -194,6 +199,16 @@ def snn_profile(net) -> dict:
     la = (C.c_int * n)()
     _check(net, lib().snn_profile(net, ms, la, n))
     return {KERNEL_NAMES[k]: (ms[k], la[k]) for k in range(n)}
+
+
+def snn_infer_noalloc(spec: snn_spec, w, theta, rates, seeds, B: int, T: int, dt_ms: float,
+                      spike_counts, stream=None) -> None:
+    """Learning-off presentation without any device allocation (all buffers
+    are the caller's; intermediate state lives in the library's fixed array)."""
+    rc = lib().snn_infer_noalloc(C.byref(spec), _buf(w)[0], _buf(theta)[0], _buf(rates)[0],
+                                 _buf(seeds)[0], B, T, dt_ms, _buf(spike_counts)[0],
+                                 _stream(stream))
+    _check(None, rc)
 
 
 def snn_last_error(net) -> str:
