@@ -295,7 +295,7 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
     if (e == cudaSuccess) e = dalloc(&n->d.W, nw);
     if (e == cudaSuccess) e = dalloc(&n->d.theta, (size_t)s.n_exc);
     if (e == cudaSuccess) e = dalloc(&n->d.step, 2);
-    if (e == cudaSuccess) e = dalloc(&n->d.err, 4);
+    if (e == cudaSuccess) e = dalloc(&n->d.err, 64);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking);
     std::vector<float> w;
     if (e == cudaSuccess) {
@@ -310,7 +310,7 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
         e = cudaMemcpy(n->d.theta, th.data(), th.size() * 8, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = cudaMemset(n->d.step, 0, 16);
-    if (e == cudaSuccess) e = cudaMemset(n->d.err, 0, 16);
+    if (e == cudaSuccess) e = cudaMemset(n->d.err, 0, 256);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         snn_status code = e == cudaErrorMemoryAllocation ? SNN_ERR_OOM : SNN_ERR_CUDA;

@@ -51,7 +51,7 @@ struct Bufs {
     uint32_t* raster_i;  // [T][B][Nw] (optional)
     uint32_t* raster_in; // [T][B][Iw] (optional)
     unsigned long long* step;  // [2]: first step of this run, step after it
-    uint32_t* err;       // [0] sticky device error bits, [1] grid-barrier counter
+    uint32_t* err;       // [64]: [0] sticky device error bits, [32] grid-barrier counter
 };
 
 // Packed per-(b,j) state word.

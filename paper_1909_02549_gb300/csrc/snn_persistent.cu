@@ -33,9 +33,10 @@
 namespace snn {
 namespace {
 
-constexpr int PT = 512;                    // threads per CTA
+constexpr int PT = 1024;                   // threads per CTA
 constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
-constexpr unsigned SPIN_LIMIT = 1u << 24;  // bounded grid-barrier wait (~seconds)
+constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
+constexpr int KMAX_CAP = 32;               // post-spiking samples whose x_pre rows are staged
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -43,14 +44,15 @@ struct Layout {
     size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_u;   // byte offsets
     // union region (phase-local)
     size_t o_cnts, o_actn, o_acts;    // neuron phase
-    size_t o_pres, o_nzp;             // STDP phase
+    size_t o_pres, o_nzp, o_qall, o_qrank, o_qlist, o_xp;   // STDP phase
+    int kmax;                         // staged x_pre rows
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-Layout make_layout(const Consts& c, int G) {
+Layout make_layout(const Consts& c, int G, size_t smem_budget) {
     Layout L{};
     L.G = G;
     L.ncmax = (c.N + G - 1) / G;
@@ -70,6 +72,18 @@ Layout make_layout(const Consts& c, int G) {
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
     L.o_pres = o;                u_stdp = align16((size_t)c.n_in * c.Bw * 4);
     L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
+    L.o_qall = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)c.Bw * 4);
+    L.o_qrank = o + u_stdp;      u_stdp = align16(u_stdp + (size_t)c.Bw * 4);
+    L.o_qlist = o + u_stdp;      u_stdp = align16(u_stdp + (size_t)KMAX_CAP * 4);
+    L.o_xp = o + u_stdp;
+    {   // as many staged x_pre rows as the budget leaves (at most KMAX_CAP)
+        const size_t row = (size_t)c.n_in * 4;
+        const size_t used = o + u_stdp;
+        size_t k = used < smem_budget ? (smem_budget - used) / row : 0;
+        if (k > (size_t)KMAX_CAP) k = KMAX_CAP;
+        L.kmax = (int)k;
+        u_stdp = align16(u_stdp + k * row);
+    }
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
     if (u_enc > u) u = u_enc;
@@ -92,11 +106,12 @@ __device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target) {
         int fail = 0;
         __threadfence();
         atomicAdd(ctr, 1u);
-        unsigned spins = 0;
+        unsigned spins = 0, ns = 32;
         while (ld_acquire(ctr) < target) {
-            if (ld_acquire(err) != 0u) { fail = 1; break; }
-            if (++spins > SPIN_LIMIT) { atomicOr(err, 1u); fail = 1; break; }
-            __nanosleep(64);
+            if ((++spins & 31u) == 0u && ld_acquire(err) != 0u) { fail = 1; break; }
+            if (spins > SPIN_LIMIT) { atomicOr(err, 1u); fail = 1; break; }
+            __nanosleep(ns);
+            if (ns < 512) ns <<= 1;
         }
         __threadfence();
         s_fail = fail;
@@ -167,26 +182,45 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
     }
 }
 
-// The samples of batch word w whose update of synapse (i, j) can be non-zero:
-// j fired this step (q: potentiation by x_pre), or input i fired and j has
-// fired earlier in the episode (p & s: depression by x_post).  Ascending b.
-__device__ __forceinline__ void stdp_word(const Consts& c, int w, uint32_t p, uint32_t q,
-                                          uint32_t s, const float* xpre_i, int NI,
-                                          const float* xps_j, int nc, float& acc, int& nev) {
-    uint32_t m = (p & s) | q;
-    while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        const int b = w * 32 + bit;
-        float a = 0.0f, e = 0.0f;
-        if ((q >> bit) & 1u) a = __fmul_rn(c.nu_post, __ldcg(&xpre_i[(size_t)b * NI]));
-        if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps_j[b * nc]);
-        const float dl = __fsub_rn(a, e);
-        if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
-        else acc = __fadd_rn(acc, dl);
-        ++nev;
-    }
+// One LIF update of the excitatory/inhibitory pair (b, j); same operations in
+// the same order as the per-step kernel.
+struct Item {
+    float v, vi;
+    uint32_t st;
+};
+
+__device__ __forceinline__ void neuron_update(const Consts& c, Item& it, float I, int C,
+                                              float thj, float& x, bool& se, bool& si) {
+    int ref_e = (int)(it.st & 0xFFu), ref_i = (int)((it.st >> 8) & 0xFFu);
+    const int se_prev = (it.st & ST_SE) ? 1 : 0, si_prev = (it.st & ST_SI) ? 1 : 0;
+    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
+    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
+    float v = it.v;
+    float dv = __fsub_rn(v, c.e_rest);
+    dv = __fmul_rn(dv, c.a_e);
+    v = __fadd_rn(c.e_rest, dv);
+    const bool free_e = ref_e == 0;
+    if (!free_e) ref_e -= 1;
+    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
+    se = free_e && v >= thj;
+    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    float vi = it.vi;
+    dv = __fsub_rn(vi, c.i_rest);
+    dv = __fmul_rn(dv, c.a_i);
+    vi = __fadd_rn(c.i_rest, dv);
+    const bool free_i = ref_i == 0;
+    if (!free_i) ref_i -= 1;
+    else vi = __fadd_rn(vi, I_inh);
+    si = free_i && vi >= c.i_thresh;
+    if (si) { vi = c.i_reset; ref_i = c.R_i; }
+    x = __fmul_rn(x, c.a_x);
+    x = __fadd_rn(x, se ? 1.0f : 0.0f);
+    it.v = v;
+    it.vi = vi;
+    it.st = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
 }
+
+constexpr int NB = 4;   // neuron items per thread whose state loads are issued together
 
 __global__ void __launch_bounds__(PT, 1)
 k_persistent(Consts c, Bufs d, int T, Layout L) {
@@ -203,15 +237,23 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
     uint32_t* preS = (uint32_t*)(sm + L.o_pres);
     uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
+    uint32_t* Qall = (uint32_t*)(sm + L.o_qall);
+    uint32_t* qrank = (uint32_t*)(sm + L.o_qrank);
+    int* qlist = (int*)(sm + L.o_qlist);
+    float* XP = (float*)(sm + L.o_xp);
+    __shared__ int s_nq;
 
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int G = L.G;
     const int j0 = (int)((long long)cta * c.N / G), j1 = (int)((long long)(cta + 1) * c.N / G);
     const int nc = j1 - j0;
     const int N = c.N, B = c.B, NI = c.n_in, Bw = c.Bw;
-    uint32_t* const bar = d.err + 1;
+    const int caps = CAPS < NI ? CAPS : NI;
+    uint32_t* const bar = d.err + 32;             // own 128-byte line
     if (ld_acquire(d.err) != 0u) return;          // an earlier run failed: do nothing
     const unsigned long long base = d.step[0];
+    // strides of the division-free walks over (row, column) items
+    const int dq = PT / nc, dr = PT % nc;
 
     // ---- the CTA's columns: weights, postsynaptic traces, masks, thresholds
     for (int k = tid; k < NI * nc; k += PT) {
@@ -254,74 +296,88 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
             uint32_t* z = d.preT + (size_t)((p3 + 2) % 3) * n_pre;
             for (size_t k = (size_t)cta * PT + tid; k < n_pre; k += (size_t)G * PT) z[k] = 0u;
         }
-        __syncthreads();
-        for (int k = tid; k < B * CAPS; k += PT) {
-            const int b = k / CAPS, q = k % CAPS;
-            if ((uint32_t)q < actN[b])
-                actS[k] = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + q]);
+        {   // first entries of every sample's active-input list (in bounds: caps <= n_in)
+            const uint16_t* src = d.act_idx + (size_t)cur * B * NI;
+            const int n = B * caps;
+            for (int k0 = tid; k0 < n; k0 += 4 * PT) {
+                uint16_t v4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * PT;
+                    if (k < n) v4[q] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int k = k0 + q * PT;
+                    if (k < n) actS[(k / caps) * CAPS + (k % caps)] = v4[q];
+                }
+            }
         }
         __syncthreads();
 
-        for (int k = tid; k < B * nc; k += PT) {
-            const int b = k / nc, jl = k % nc, j = j0 + jl;
-            const size_t idx = (size_t)b * N + j;
-            // synaptic current: ascending active inputs of sample b
-            float I = 0.0f;
-            const int na = (int)actN[b];
-            const int ns = na < CAPS ? na : CAPS;
-            for (int q = 0; q < ns; ++q) I = __fadd_rn(I, Ws[(int)actS[b * CAPS + q] * nc + jl]);
-            for (int q = CAPS; q < na; ++q) {
-                const int i = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + q]);
-                I = __fadd_rn(I, Ws[i * nc + jl]);
-            }
-            const uint32_t s = d.st[idx];
-            int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
-            const int se_prev = (s & ST_SE) ? 1 : 0, si_prev = (s & ST_SI) ? 1 : 0;
-            const int C = (int)cntS[b];
-            const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
-            const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-
-            float v = d.v_e[idx];
-            float dv = __fsub_rn(v, c.e_rest);
-            dv = __fmul_rn(dv, c.a_e);
-            v = __fadd_rn(c.e_rest, dv);
-            const bool free_e = ref_e == 0;
-            if (!free_e) ref_e -= 1;
-            else v = __fadd_rn(v, __fadd_rn(I, I_lat));
-            const bool se = free_e && v >= thj[jl];
-            if (se) { v = c.e_reset; ref_e = c.R_e; }
-            d.v_e[idx] = v;
-
-            float vi = d.v_i[idx];
-            dv = __fsub_rn(vi, c.i_rest);
-            dv = __fmul_rn(dv, c.a_i);
-            vi = __fadd_rn(c.i_rest, dv);
-            const bool free_i = ref_i == 0;
-            if (!free_i) ref_i -= 1;
-            else vi = __fadd_rn(vi, I_inh);
-            const bool si = free_i && vi >= c.i_thresh;
-            if (si) { vi = c.i_reset; ref_i = c.R_i; }
-            d.v_i[idx] = vi;
-
-            float x = xps[k];
-            x = __fmul_rn(x, c.a_x);
-            x = __fadd_rn(x, se ? 1.0f : 0.0f);
-            xps[k] = x;
-
-            d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) |
-                        (si ? ST_SI : 0u);
-            if (se) {
-                d.counts[idx] += 1u;
-                const uint32_t bit = 1u << (b & 31);
-                atomicOr(&Qm[(b >> 5) * nc + jl], bit);
-                atomicOr(&Sm[(b >> 5) * nc + jl], bit);
-                if (c.rec_raster)
-                    atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
-            }
-            if (si) {
-                atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
-                if (c.rec_raster)
-                    atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+        {
+            const int BN = B * nc;
+            int b0 = tid / nc, jl0 = tid % nc;
+            for (int k0 = tid; k0 < BN; k0 += NB * PT) {
+                int bq[NB], jq[NB];
+                Item it[NB];
+                {
+                    int b = b0, jl = jl0;
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        bq[q] = b;
+                        jq[q] = jl;
+                        b += dq;
+                        jl += dr;
+                        if (jl >= nc) { jl -= nc; ++b; }
+                    }
+                    b0 = b;
+                    jl0 = jl;
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {          // all state loads first
+                    if (k0 + q * PT < BN) {
+                        const size_t idx = (size_t)bq[q] * N + j0 + jq[q];
+                        it[q].st = d.st[idx];
+                        it[q].v = d.v_e[idx];
+                        it[q].vi = d.v_i[idx];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < NB; ++q) {
+                    if (k0 + q * PT >= BN) break;
+                    const int b = bq[q], jl = jq[q], j = j0 + jl;
+                    const size_t idx = (size_t)b * N + j;
+                    // synaptic current: ascending active inputs of sample b
+                    float I = 0.0f;
+                    const int na = (int)actN[b];
+                    const int ns = na < caps ? na : caps;
+                    for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)actS[b * CAPS + a] * nc + jl]);
+                    for (int a = caps; a < na; ++a) {
+                        const int i = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + a]);
+                        I = __fadd_rn(I, Ws[i * nc + jl]);
+                    }
+                    float x = xps[b * nc + jl];
+                    bool se, si;
+                    neuron_update(c, it[q], I, (int)cntS[b], thj[jl], x, se, si);
+                    xps[b * nc + jl] = x;
+                    d.v_e[idx] = it[q].v;
+                    d.v_i[idx] = it[q].vi;
+                    d.st[idx] = it[q].st;
+                    if (se) {
+                        d.counts[idx] += 1u;
+                        const uint32_t bit = 1u << (b & 31);
+                        atomicOr(&Qm[(b >> 5) * nc + jl], bit);
+                        atomicOr(&Sm[(b >> 5) * nc + jl], bit);
+                        if (c.rec_raster)
+                            atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                    }
+                    if (si) {
+                        atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
+                        if (c.rec_raster)
+                            atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                    }
+                }
             }
         }
         __syncthreads();
@@ -344,32 +400,92 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
                 else r = n > 0 ? 1.0 : 0.0;
                 thS[jl] = __dadd_rn(__dmul_rn(thS[jl], c.a_th), __dmul_rn(c.theta_plus, r));
             }
-            for (int k = tid; k < NI * Bw; k += PT)
-                preS[k] = __ldcg(&d.preT[(size_t)p3 * NI * Bw + k]);
+            for (int w = tid; w < Bw; w += PT) {      // samples with a post spike in this CTA
+                uint32_t q = 0;
+                for (int jl = 0; jl < nc; ++jl) q |= Qm[w * nc + jl];
+                Qall[w] = q;
+            }
+            {   // input-major masks of this step (written by every CTA's encode)
+                const uint32_t* src = d.preT + (size_t)p3 * NI * Bw;
+                const int n = NI * Bw;
+                for (int k0 = tid; k0 < n; k0 += 4 * PT) {
+                    uint32_t v4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q * PT < n) v4[q] = __ldcg(&src[k0 + q * PT]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (k0 + q * PT < n) preS[k0 + q * PT] = v4[q];
+                }
+            }
             __syncthreads();
+            if (tid == 0) {   // ranks of the post-spiking samples, first kmax listed
+                int nq = 0;
+                for (int w = 0; w < Bw; ++w) {
+                    qrank[w] = (uint32_t)nq;
+                    uint32_t q = Qall[w];
+                    while (q) {
+                        const int bit = __ffs(q) - 1;
+                        q &= q - 1;
+                        if (nq < L.kmax) qlist[nq] = w * 32 + bit;
+                        ++nq;
+                    }
+                }
+                s_nq = nq < L.kmax ? nq : L.kmax;
+            }
             for (int i = tid; i < NI; i += PT) {
                 uint32_t nz = 0;
                 for (int w = 0; w < Bw && w < 32; ++w) nz |= (preS[i * Bw + w] != 0u) ? (1u << w) : 0u;
                 nzP[i] = nz;
             }
             __syncthreads();
+            {   // x_pre rows of the post-spiking samples (potentiation operands)
+                const int nq = s_nq;
+                for (int m0 = 0; m0 < nq; m0 += 4) {
+                    float v4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (m0 + q < nq && tid < NI) v4[q] = __ldcg(&xpre[(size_t)qlist[m0 + q] * NI + tid]);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (m0 + q < nq && tid < NI) XP[(m0 + q) * NI + tid] = v4[q];
+                }
+                for (int i = PT + tid; i < NI; i += PT)       // n_in > PT
+                    for (int m = 0; m < nq; ++m) XP[m * NI + i] = __ldcg(&xpre[(size_t)qlist[m] * NI + i]);
+            }
+            __syncthreads();
             const bool masks = Bw <= 32;
+            const int kmax = L.kmax;
+            int i = tid / nc, jl = tid % nc;
             for (int k = tid; k < NI * nc; k += PT) {
-                const int i = k / nc, jl = k % nc;
                 float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
                 int nev = 0;
-                if (masks) {   // only the words where an update can be non-zero
-                    uint32_t words = nzP[i] | nzQ[jl];
-                    while (words) {
-                        const int w = __ffs(words) - 1;
+                uint32_t words = masks ? (nzP[i] | nzQ[jl]) : 0xFFFFFFFFu;
+                for (int w = 0; w < Bw; ++w) {
+                    if (masks) {
+                        if (!words) break;
+                        w = __ffs(words) - 1;
                         words &= words - 1;
-                        stdp_word(c, w, preS[i * Bw + w], Qm[w * nc + jl], Sm[w * nc + jl],
-                                  xpre + i, NI, xps + jl, nc, acc, nev);
                     }
-                } else {
-                    for (int w = 0; w < Bw; ++w)
-                        stdp_word(c, w, preS[i * Bw + w], Qm[w * nc + jl], Sm[w * nc + jl],
-                                  xpre + i, NI, xps + jl, nc, acc, nev);
+                    const uint32_t p = preS[i * Bw + w];
+                    const uint32_t q = Qm[w * nc + jl];
+                    uint32_t m = (p & Sm[w * nc + jl]) | q;
+                    while (m) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int b = w * 32 + bit;
+                        float a = 0.0f, e = 0.0f;
+                        if ((q >> bit) & 1u) {
+                            const int r = (int)qrank[w] + __popc(Qall[w] & ((1u << bit) - 1u));
+                            const float xp = r < kmax ? XP[r * NI + i] : __ldcg(&xpre[(size_t)b * NI + i]);
+                            a = __fmul_rn(c.nu_post, xp);
+                        }
+                        if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
+                        const float dl = __fsub_rn(a, e);
+                        if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
+                        else acc = __fadd_rn(acc, dl);
+                        ++nev;
+                    }
                 }
                 if (nev > 0) {
                     float D = acc;
@@ -380,6 +496,9 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
                     wv = wv > c.w_max ? c.w_max : wv;
                     Ws[k] = wv;
                 }
+                i += dq;
+                jl += dr;
+                if (jl >= nc) { jl -= nc; ++i; }
             }
             __syncthreads();
         }
@@ -429,8 +548,9 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
         e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     const int G = sms < c.N ? sms : c.N;
-    const Layout L = make_layout(c, G);
-    if (L.bytes + 1024 > (size_t)smem_optin) return cudaSuccess;
+    const size_t budget = smem_optin > 2048 ? (size_t)smem_optin - 2048 : 0;
+    const Layout L = make_layout(c, G, budget);
+    if (L.bytes > budget) return cudaSuccess;
     e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L.bytes);
     if (e != cudaSuccess) return e;

@@ -71,7 +71,7 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
         const unsigned long long base = episodic ? 0ull : d.step[1];
         d.step[0] = base;
         d.step[1] = base + (unsigned long long)T;
-        d.err[1] = 0u;    // grid-barrier counter of the persistent form
+        d.err[32] = 0u;   // grid-barrier counter of the persistent form (own 128-byte line)
     }
 }
 
