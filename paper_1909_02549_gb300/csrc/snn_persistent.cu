@@ -36,7 +36,8 @@ namespace {
 constexpr int PT = 1024;                   // threads per CTA
 constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
-constexpr int KMAX_CAP = 32;               // post-spiking samples whose x_pre rows are staged
+constexpr int NW = PT / 32;                // warps per CTA
+constexpr int XQ = 2;                      // post samples per column whose x_pre is preloaded
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -44,15 +45,15 @@ struct Layout {
     size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_u;   // byte offsets
     // union region (phase-local)
     size_t o_cnts, o_actn, o_acts;    // neuron phase
-    size_t o_pres, o_nzp, o_qall, o_qrank, o_qlist, o_xp;   // STDP phase
-    int kmax;                         // staged x_pre rows
+    size_t o_pres, o_nzp, o_pcol;     // STDP phase
+    int ps;                           // row stride of the staged input-major masks
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-Layout make_layout(const Consts& c, int G, size_t smem_budget) {
+Layout make_layout(const Consts& c, int G) {
     Layout L{};
     L.G = G;
     L.ncmax = (c.N + G - 1) / G;
@@ -70,20 +71,10 @@ Layout make_layout(const Consts& c, int G, size_t smem_budget) {
     L.o_cnts = o;                u_neuron = align16((size_t)c.B * 4);
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
-    L.o_pres = o;                u_stdp = align16((size_t)c.n_in * c.Bw * 4);
+    L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
+    L.o_pres = o;                u_stdp = align16((size_t)c.n_in * L.ps * 4);
     L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
-    L.o_qall = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)c.Bw * 4);
-    L.o_qrank = o + u_stdp;      u_stdp = align16(u_stdp + (size_t)c.Bw * 4);
-    L.o_qlist = o + u_stdp;      u_stdp = align16(u_stdp + (size_t)KMAX_CAP * 4);
-    L.o_xp = o + u_stdp;
-    {   // as many staged x_pre rows as the budget leaves (at most KMAX_CAP)
-        const size_t row = (size_t)c.n_in * 4;
-        const size_t used = o + u_stdp;
-        size_t k = used < smem_budget ? (smem_budget - used) / row : 0;
-        if (k > (size_t)KMAX_CAP) k = KMAX_CAP;
-        L.kmax = (int)k;
-        u_stdp = align16(u_stdp + k * row);
-    }
+    L.o_pcol = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
     if (u_enc > u) u = u_enc;
@@ -183,14 +174,15 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
 }
 
 // One LIF update of the excitatory/inhibitory pair (b, j); same operations in
-// the same order as the per-step kernel.
+// the same order as the per-step kernel.  Kept out of line: the batched loop
+// that calls it then fits 1024 threads without register spills.
 struct Item {
-    float v, vi;
-    uint32_t st;
+    float v, vi, x;
+    uint32_t st;      // packed refractory counters and this step's spike flags
 };
 
-__device__ __forceinline__ void neuron_update(const Consts& c, Item& it, float I, int C,
-                                              float thj, float& x, bool& se, bool& si) {
+__device__ __noinline__ Item neuron_update(const Consts* cp, Item it, float I, int C, float thj) {
+    const Consts& c = *cp;
     int ref_e = (int)(it.st & 0xFFu), ref_i = (int)((it.st >> 8) & 0xFFu);
     const int se_prev = (it.st & ST_SE) ? 1 : 0, si_prev = (it.st & ST_SI) ? 1 : 0;
     const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
@@ -202,7 +194,7 @@ __device__ __forceinline__ void neuron_update(const Consts& c, Item& it, float I
     const bool free_e = ref_e == 0;
     if (!free_e) ref_e -= 1;
     else v = __fadd_rn(v, __fadd_rn(I, I_lat));
-    se = free_e && v >= thj;
+    const bool se = free_e && v >= thj;
     if (se) { v = c.e_reset; ref_e = c.R_e; }
     float vi = it.vi;
     dv = __fsub_rn(vi, c.i_rest);
@@ -211,19 +203,23 @@ __device__ __forceinline__ void neuron_update(const Consts& c, Item& it, float I
     const bool free_i = ref_i == 0;
     if (!free_i) ref_i -= 1;
     else vi = __fadd_rn(vi, I_inh);
-    si = free_i && vi >= c.i_thresh;
+    const bool si = free_i && vi >= c.i_thresh;
     if (si) { vi = c.i_reset; ref_i = c.R_i; }
-    x = __fmul_rn(x, c.a_x);
+    float x = __fmul_rn(it.x, c.a_x);
     x = __fadd_rn(x, se ? 1.0f : 0.0f);
-    it.v = v;
-    it.vi = vi;
-    it.st = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+    Item o;
+    o.v = v;
+    o.vi = vi;
+    o.x = x;
+    o.st = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+    return o;
 }
 
-constexpr int NB = 4;   // neuron items per thread whose state loads are issued together
+constexpr int NB = 2;   // neuron items per thread whose state loads are issued together
 
 __global__ void __launch_bounds__(PT, 1)
-k_persistent(Consts c, Bufs d, int T, Layout L) {
+k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, const int T,
+             const __grid_constant__ Layout L) {
     extern __shared__ __align__(16) unsigned char sm[];
     float* Ws = (float*)(sm + L.o_ws);
     float* xps = (float*)(sm + L.o_xps);
@@ -235,12 +231,6 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
     uint32_t* cntS = (uint32_t*)(sm + L.o_cnts);
     uint32_t* actN = (uint32_t*)(sm + L.o_actn);
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
-    uint32_t* preS = (uint32_t*)(sm + L.o_pres);
-    uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
-    uint32_t* Qall = (uint32_t*)(sm + L.o_qall);
-    uint32_t* qrank = (uint32_t*)(sm + L.o_qrank);
-    int* qlist = (int*)(sm + L.o_qlist);
-    float* XP = (float*)(sm + L.o_xp);
     __shared__ int s_nq;
 
     const int cta = blockIdx.x, tid = threadIdx.x;
@@ -252,7 +242,7 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
     uint32_t* const bar = d.err + 32;             // own 128-byte line
     if (ld_acquire(d.err) != 0u) return;          // an earlier run failed: do nothing
     const unsigned long long base = d.step[0];
-    // strides of the division-free walks over (row, column) items
+    // strides of the division-free walk over (sample, column) items
     const int dq = PT / nc, dr = PT % nc;
 
     // ---- the CTA's columns: weights, postsynaptic traces, masks, thresholds
@@ -298,19 +288,25 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
         }
         {   // first entries of every sample's active-input list (in bounds: caps <= n_in)
             const uint16_t* src = d.act_idx + (size_t)cur * B * NI;
-            const int n = B * caps;
-            for (int k0 = tid; k0 < n; k0 += 4 * PT) {
-                uint16_t v4[4];
+            if (caps == CAPS && (NI & 7) == 0) {      // rows 16-byte aligned: 8 entries per load
+                const int per = CAPS / 8, n = B * per;
+                for (int k0 = tid; k0 < n; k0 += 2 * PT) {
+                    uint4 v4[2];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = k0 + q * PT;
-                    if (k < n) v4[q] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
-                }
+                    for (int q = 0; q < 2; ++q) {
+                        const int k = k0 + q * PT;
+                        if (k < n) v4[q] = __ldcg((const uint4*)(src + (size_t)(k / per) * NI) + (k % per));
+                    }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int k = k0 + q * PT;
-                    if (k < n) actS[(k / caps) * CAPS + (k % caps)] = v4[q];
+                    for (int q = 0; q < 2; ++q) {
+                        const int k = k0 + q * PT;
+                        if (k < n) ((uint4*)actS)[k] = v4[q];
+                    }
                 }
+            } else {
+                const int n = B * caps;
+                for (int k = tid; k < n; k += PT)
+                    actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
             }
         }
         __syncthreads();
@@ -357,13 +353,13 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
                         const int i = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + a]);
                         I = __fadd_rn(I, Ws[i * nc + jl]);
                     }
-                    float x = xps[b * nc + jl];
-                    bool se, si;
-                    neuron_update(c, it[q], I, (int)cntS[b], thj[jl], x, se, si);
-                    xps[b * nc + jl] = x;
-                    d.v_e[idx] = it[q].v;
-                    d.v_i[idx] = it[q].vi;
-                    d.st[idx] = it[q].st;
+                    it[q].x = xps[b * nc + jl];
+                    const Item o = neuron_update(&c, it[q], I, (int)cntS[b], thj[jl]);
+                    const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
+                    xps[b * nc + jl] = o.x;
+                    d.v_e[idx] = o.v;
+                    d.v_i[idx] = o.vi;
+                    d.st[idx] = o.st;
                     if (se) {
                         d.counts[idx] += 1u;
                         const uint32_t bit = 1u << (b & 31);
@@ -385,7 +381,11 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
         // ================= STDP phase =================
         if (c.learn) {
             const float* xpre = d.x_pre + (size_t)cur * B * NI;
-            for (int jl = tid; jl < nc; jl += PT) {
+            uint32_t* preS = (uint32_t*)(sm + L.o_pres);
+            uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
+            int* pcol = (int*)(sm + L.o_pcol);
+            const int PS = L.ps;
+            for (int jl = tid; jl < nc; jl += PT) {   // theta, and which columns fired
                 int n = 0;
                 uint32_t nz = 0;
                 for (int w = 0; w < Bw; ++w) {
@@ -393,112 +393,187 @@ k_persistent(Consts c, Bufs d, int T, Layout L) {
                     n += __popc(q);
                     if (q && w < 32) nz |= 1u << w;
                 }
-                nzQ[jl] = nz;
+                nzQ[jl] = n;                          // post spikes of column jl this step
                 double r;
                 if (c.reduce == SNN_REDUCE_SUM) r = (double)n;
                 else if (c.reduce == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)B);
                 else r = n > 0 ? 1.0 : 0.0;
                 thS[jl] = __dadd_rn(__dmul_rn(thS[jl], c.a_th), __dmul_rn(c.theta_plus, r));
             }
-            for (int w = tid; w < Bw; w += PT) {      // samples with a post spike in this CTA
-                uint32_t q = 0;
-                for (int jl = 0; jl < nc; ++jl) q |= Qm[w * nc + jl];
-                Qall[w] = q;
-            }
-            {   // input-major masks of this step (written by every CTA's encode)
+            {   // input-major masks of this step (written by every CTA's encode), padded rows
                 const uint32_t* src = d.preT + (size_t)p3 * NI * Bw;
                 const int n = NI * Bw;
-                for (int k0 = tid; k0 < n; k0 += 4 * PT) {
-                    uint32_t v4[4];
+                if ((Bw & 3) == 0) {
+                    const uint4* s4 = (const uint4*)src;
+                    const int n4 = n >> 2;
+                    for (int k0 = tid; k0 < n4; k0 += 4 * PT) {
+                        uint4 v4[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (k0 + q * PT < n) v4[q] = __ldcg(&src[k0 + q * PT]);
+                        for (int q = 0; q < 4; ++q)
+                            if (k0 + q * PT < n4) v4[q] = __ldcg(&s4[k0 + q * PT]);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (k0 + q * PT < n) preS[k0 + q * PT] = v4[q];
+                        for (int q = 0; q < 4; ++q) {
+                            const int k = (k0 + q * PT) << 2;
+                            if (k < n) {
+                                const int i = k / Bw, w = k % Bw;
+                                uint32_t* dst = preS + i * PS + w;
+                                dst[0] = v4[q].x; dst[1] = v4[q].y; dst[2] = v4[q].z; dst[3] = v4[q].w;
+                            }
+                        }
+                    }
+                } else {
+                    for (int k = tid; k < n; k += PT) preS[(k / Bw) * PS + (k % Bw)] = __ldcg(&src[k]);
                 }
             }
             __syncthreads();
-            if (tid == 0) {   // ranks of the post-spiking samples, first kmax listed
-                int nq = 0;
-                for (int w = 0; w < Bw; ++w) {
-                    qrank[w] = (uint32_t)nq;
-                    uint32_t q = Qall[w];
-                    while (q) {
-                        const int bit = __ffs(q) - 1;
-                        q &= q - 1;
-                        if (nq < L.kmax) qlist[nq] = w * 32 + bit;
-                        ++nq;
-                    }
-                }
-                s_nq = nq < L.kmax ? nq : L.kmax;
-            }
             for (int i = tid; i < NI; i += PT) {
                 uint32_t nz = 0;
-                for (int w = 0; w < Bw && w < 32; ++w) nz |= (preS[i * Bw + w] != 0u) ? (1u << w) : 0u;
+                for (int w = 0; w < Bw && w < 32; ++w) nz |= (preS[i * PS + w] != 0u) ? (1u << w) : 0u;
                 nzP[i] = nz;
             }
-            __syncthreads();
-            {   // x_pre rows of the post-spiking samples (potentiation operands)
-                const int nq = s_nq;
-                for (int m0 = 0; m0 < nq; m0 += 4) {
-                    float v4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (m0 + q < nq && tid < NI) v4[q] = __ldcg(&xpre[(size_t)qlist[m0 + q] * NI + tid]);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (m0 + q < nq && tid < NI) XP[(m0 + q) * NI + tid] = v4[q];
+            if (tid < 32) {   // list of the columns with a post spike
+                int npc = 0;
+                for (int jl0 = 0; jl0 < nc; jl0 += 32) {
+                    const int jl = jl0 + tid;
+                    const bool f = jl < nc && nzQ[jl] != 0u;
+                    const uint32_t bal = __ballot_sync(FULL, f);
+                    if (f) pcol[npc + __popc(bal & ((1u << tid) - 1u))] = jl;
+                    npc += __popc(bal);
                 }
-                for (int i = PT + tid; i < NI; i += PT)       // n_in > PT
-                    for (int m = 0; m < nq; ++m) XP[m * NI + i] = __ldcg(&xpre[(size_t)qlist[m] * NI + i]);
+                if (tid == 0) s_nq = npc;
             }
             __syncthreads();
-            const bool masks = Bw <= 32;
-            const int kmax = L.kmax;
-            int i = tid / nc, jl = tid % nc;
-            for (int k = tid; k < NI * nc; k += PT) {
-                float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
-                int nev = 0;
-                uint32_t words = masks ? (nzP[i] | nzQ[jl]) : 0xFFFFFFFFu;
-                for (int w = 0; w < Bw; ++w) {
-                    if (masks) {
-                        if (!words) break;
-                        w = __ffs(words) - 1;
-                        words &= words - 1;
-                    }
-                    const uint32_t p = preS[i * Bw + w];
-                    const uint32_t q = Qm[w * nc + jl];
-                    uint32_t m = (p & Sm[w * nc + jl]) | q;
-                    while (m) {
-                        const int bit = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int b = w * 32 + bit;
-                        float a = 0.0f, e = 0.0f;
-                        if ((q >> bit) & 1u) {
-                            const int r = (int)qrank[w] + __popc(Qall[w] & ((1u << bit) - 1u));
-                            const float xp = r < kmax ? XP[r * NI + i] : __ldcg(&xpre[(size_t)b * NI + i]);
-                            a = __fmul_rn(c.nu_post, xp);
+            const int warp = tid >> 5, lane = tid & 31;
+
+            // (A) columns without a post spike: depression only.  Lanes walk
+            //     consecutive (row, column) pairs, so a warp shares one or a few
+            //     rows' input-spike words whatever the number of columns.
+            {
+                int i = tid / nc, jl = tid % nc;
+                for (int k = tid; k < NI * nc; k += PT) {
+                    const uint32_t nz = nzP[i];
+                    if (nzQ[jl] == 0u && (nz != 0u || Bw > 32)) {
+                        const uint32_t* Pi = preS + i * PS;
+                        float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
+                        int nev = 0;
+                        uint32_t words = Bw <= 32 ? nz : 0xFFFFFFFFu;
+                        for (int w = 0; w < Bw; ++w) {
+                            if (Bw <= 32) {
+                                if (!words) break;
+                                w = __ffs(words) - 1;
+                                words &= words - 1;
+                            }
+                            uint32_t m = Pi[w] & Sm[w * nc + jl];
+                            while (m) {
+                                const int bit = __ffs(m) - 1;
+                                m &= m - 1;
+                                const int b = w * 32 + bit;
+                                const float dl = __fsub_rn(0.0f, __fmul_rn(c.nu_pre, xps[b * nc + jl]));
+                                if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
+                                else acc = __fadd_rn(acc, dl);
+                                ++nev;
+                            }
                         }
-                        if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
-                        const float dl = __fsub_rn(a, e);
-                        if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
-                        else acc = __fadd_rn(acc, dl);
-                        ++nev;
+                        if (nev > 0) {
+                            float D = acc;
+                            if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
+                            if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
+                            float wv = __fadd_rn(Ws[k], D);
+                            wv = wv < c.w_min ? c.w_min : wv;
+                            wv = wv > c.w_max ? c.w_max : wv;
+                            Ws[k] = wv;
+                        }
+                    }
+                    i += dq;
+                    jl += dr;
+                    if (jl >= nc) { jl -= nc; ++i; }
+                }
+            }
+
+            // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.
+            //     The column's first XQ post samples' x_pre values are loaded
+            //     (coalesced) for several tasks before any is processed.
+            {
+                const int npc = s_nq;
+                const int nch = (NI + 31) / 32;
+                const int ntask = npc * nch;
+                for (int u0 = warp; u0 < ntask; u0 += NW * 4) {
+                    float xk[4][XQ];
+                    int jlq[4], iq[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int u = u0 + q * NW;
+                        jlq[q] = -1;
+                        iq[q] = 0;
+                        int bs[XQ], k = 0;
+#pragma unroll
+                        for (int z = 0; z < XQ; ++z) bs[z] = 0;
+                        if (u < ntask) {
+                            jlq[q] = pcol[u / nch];
+                            iq[q] = (u % nch) * 32 + lane;
+                            for (int w = 0; w < Bw && k < XQ; ++w) {
+                                uint32_t qb = Qm[w * nc + jlq[q]];
+                                while (qb && k < XQ) {
+                                    const int bit = __ffs(qb) - 1;
+                                    qb &= qb - 1;
+#pragma unroll
+                                    for (int z = 0; z < XQ; ++z)
+                                        if (k == z) bs[z] = w * 32 + bit;
+                                    ++k;
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int z = 0; z < XQ; ++z)
+                            xk[q][z] = (z < k && iq[q] < NI) ? __ldcg(&xpre[(size_t)bs[z] * NI + iq[q]])
+                                                            : 0.0f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int jl = jlq[q], i = iq[q];
+                        if (jl < 0 || i >= NI) continue;
+                        const uint32_t* Pi = preS + i * PS;
+                        float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
+                        int nev = 0, kq = 0;
+                        for (int w = 0; w < Bw; ++w) {
+                            const uint32_t p = Pi[w];
+                            const uint32_t qq = Qm[w * nc + jl];
+                            uint32_t m = (p & Sm[w * nc + jl]) | qq;
+                            while (m) {
+                                const int bit = __ffs(m) - 1;
+                                m &= m - 1;
+                                const int b = w * 32 + bit;
+                                float a = 0.0f, e = 0.0f;
+                                if ((qq >> bit) & 1u) {
+                                    float xv;
+                                    if (kq < XQ) {
+                                        xv = xk[q][0];
+#pragma unroll
+                                        for (int z = 1; z < XQ; ++z) xv = kq == z ? xk[q][z] : xv;
+                                    } else {
+                                        xv = __ldcg(&xpre[(size_t)b * NI + i]);
+                                    }
+                                    ++kq;
+                                    a = __fmul_rn(c.nu_post, xv);
+                                }
+                                if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
+                                const float dl = __fsub_rn(a, e);
+                                if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
+                                else acc = __fadd_rn(acc, dl);
+                                ++nev;
+                            }
+                        }
+                        if (nev > 0) {
+                            float D = acc;
+                            if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
+                            if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
+                            float wv = __fadd_rn(Ws[i * nc + jl], D);
+                            wv = wv < c.w_min ? c.w_min : wv;
+                            wv = wv > c.w_max ? c.w_max : wv;
+                            Ws[i * nc + jl] = wv;
+                        }
                     }
                 }
-                if (nev > 0) {
-                    float D = acc;
-                    if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
-                    if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
-                    float wv = __fadd_rn(Ws[k], D);
-                    wv = wv < c.w_min ? c.w_min : wv;
-                    wv = wv > c.w_max ? c.w_max : wv;
-                    Ws[k] = wv;
-                }
-                i += dq;
-                jl += dr;
-                if (jl >= nc) { jl -= nc; ++i; }
             }
             __syncthreads();
         }
@@ -549,7 +624,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     if (e != cudaSuccess) return e;
     const int G = sms < c.N ? sms : c.N;
     const size_t budget = smem_optin > 2048 ? (size_t)smem_optin - 2048 : 0;
-    const Layout L = make_layout(c, G, budget);
+    const Layout L = make_layout(c, G);
     if (L.bytes > budget) return cudaSuccess;
     e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)L.bytes);
