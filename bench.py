@@ -229,12 +229,13 @@ def run_reference(a):
     return 0
 
 
-def profile_roofline(a, net, snn, flush, run, B, N, T, learn):
+def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
     """Dominant kernel's achieved algorithmic bandwidth from an event-bracketed pass."""
     try:
         n_prof = min(a.steps, 10)
         agg = {}
         for _ in range(n_prof):
+            restore()
             flush.zero_()
             run(profile=True)
             for k, (kms, kl) in snn.snn_profile(net.handle).items():
@@ -289,15 +290,26 @@ def run_ours(a):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    # Every step presents the batch to the same network: W and theta are
+    # restored before each step (outside the timed region), so the timed
+    # work does not drift as learning accumulates across steps.
+    w0 = torch.from_numpy(w).cuda()
+    th0 = torch.from_numpy(net.read("theta")).cuda()
+
+    def restore():
+        snn.snn_write_weights(net.handle, w0)
+        snn.snn_write_state(net.handle, snn.SNN_FIELD_THETA, th0)
+
     def run(profile=False):
         net.run(r_d, s_d, T, learn=learn, reduce=a.reduce, mode=a.mode, profile=profile)
 
     for _ in range(a.warmup):
+        restore()
         flush.zero_()
         run()
     torch.cuda.synchronize()
 
-    # ---- timed region
+    # ---- timed region (the restore before each step synchronises: not timed)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(a.steps)]
     visible = os.environ.get("CUDA_VISIBLE_DEVICES")
@@ -306,6 +318,7 @@ def run_ours(a):
         barrier()
         torch.cuda.synchronize()
         for k in range(a.steps):
+            restore()
             flush.zero_()
             ev[k][0].record(stream)
             run()
@@ -320,7 +333,7 @@ def run_ours(a):
     value = world * B * T * a.steps / (ms * 1e-3)
 
     # ---- per-kernel device time (same workload, every launch bracketed by events)
-    roofline = profile_roofline(a, net, snn, flush, run, B, N, T, learn)
+    roofline = profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -333,6 +346,7 @@ def run_ours(a):
         red = snn.REDUCE[a.reduce]
         tot = 0.0
         for k in range(k_e2e + 1):
+            restore()
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()

@@ -172,6 +172,18 @@ SNN_API size_t snn_field_bytes(const snn_net* net, int field);
  * SNN_ERR_CUDA. */
 SNN_API snn_status snn_read_state(snn_net* net, int field, void* dst, size_t bytes, int dst_on_device);
 
+/* Replace a state field with src (device memory if src_on_device, else host),
+ * in the layout snn_read_state gives it; with snn_read_state this checkpoints
+ * and resumes a simulation.  Writable: V_EXC, V_INH, X_PRE, X_POST, REF_EXC,
+ * REF_INH, SPIKES_EXC, SPIKES_INH (the network must hold a batch: run once
+ * with it, T may be 0), THETA, and STEP (the step counter a continuing run
+ * starts from).  The library re-derives what it keeps alongside (which samples
+ * have a non-zero postsynaptic trace, the previous step's inhibitory counts).
+ * Synchronises.  Errors: SNN_ERR_ARG (unknown or read-only field, size
+ * mismatch, NULL src), SNN_ERR_STATE (no batch allocated), SNN_ERR_CUDA. */
+SNN_API snn_status snn_write_state(snn_net* net, int field, const void* src, size_t bytes,
+                                   int src_on_device);
+
 /* Copy the FP32 master weights [n_in][n_exc] into dst (device or host).
  * Synchronises the stream of the last run first.  bytes must equal
  * n_in*n_exc*4.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */

@@ -15,6 +15,8 @@
 
 namespace snn {
 cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s);
+cudaError_t launch_insert(const Consts& c, const Bufs& d, int field, const void* in, cudaStream_t s);
+cudaError_t launch_derive(const Consts& c, const Bufs& d, cudaStream_t s);
 cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_t s,
                               int* used_persistent, Prof* prof);
 }
@@ -576,6 +578,66 @@ snn_status snn_write_weights(snn_net* n, const float* src, size_t bytes, int src
                                 n->last));
     CUDA_TRY(n, snn::launch_clip_weights(n->d.W, count, n->spec.w_min, n->spec.w_max, n->last));
     CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    return SNN_OK;
+}
+
+snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes, int src_on_device) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_write_state: net is NULL");
+    n->err.clear();
+    if (!src) return fail(n, SNN_ERR_ARG, "snn_write_state: src is NULL");
+    switch (field) {
+        case SNN_FIELD_V_EXC: case SNN_FIELD_V_INH: case SNN_FIELD_X_POST: case SNN_FIELD_X_PRE:
+        case SNN_FIELD_REF_EXC: case SNN_FIELD_REF_INH: case SNN_FIELD_SPIKES_EXC:
+        case SNN_FIELD_SPIKES_INH: case SNN_FIELD_THETA: case SNN_FIELD_STEP:
+            break;
+        default:
+            return fail(n, SNN_ERR_ARG, "snn_write_state: field %d is not writable", field);
+    }
+    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP;
+    if (per_sample && n->B == 0)
+        return fail(n, SNN_ERR_STATE,
+                    "snn_write_state: no batch is allocated (run once with this batch, T may be 0)");
+    const size_t want = field_bytes(n, field);
+    if (bytes != want)
+        return fail(n, SNN_ERR_ARG, "snn_write_state: field %d needs %zu bytes, got %zu", field,
+                    want, bytes);
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    cudaStream_t st = n->last;
+    CUDA_TRY(n, cudaStreamSynchronize(st));
+    if (snn_status r = check_device_error(n)) return r;
+    const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    void* dst = nullptr;
+    switch (field) {
+        case SNN_FIELD_V_EXC: dst = n->d.v_e; break;
+        case SNN_FIELD_V_INH: dst = n->d.v_i; break;
+        case SNN_FIELD_X_POST: dst = n->d.x_post; break;
+        case SNN_FIELD_THETA: dst = n->d.theta; break;
+        case SNN_FIELD_STEP: dst = n->d.step + 1; break;
+        default: break;
+    }
+    const snn::Consts c = make_consts(n, n->B, 1.0f, 0, 0, 0);
+    if (dst) {
+        CUDA_TRY(n, cudaMemcpyAsync(dst, src, want, kind, st));
+    } else {   // fields stored in another layout: stage, then insert on the device
+        const void* in = src;
+        if (!src_on_device) {
+            if (n->scratch_bytes < want) {
+                if (n->scratch) cudaFree(n->scratch);
+                n->scratch = nullptr;
+                n->scratch_bytes = 0;
+                CUDA_TRY(n, cudaMalloc(&n->scratch, want));
+                n->scratch_bytes = want;
+            }
+            CUDA_TRY(n, cudaMemcpyAsync(n->scratch, src, want, cudaMemcpyHostToDevice, st));
+            in = n->scratch;
+        }
+        CUDA_TRY(n, snn::launch_insert(c, n->d, field, in, st));
+    }
+    if (per_sample) {
+        CUDA_TRY(n, snn::launch_derive(c, n->d, st));
+        n->state_valid = true;
+    }
+    CUDA_TRY(n, cudaStreamSynchronize(st));
     return SNN_OK;
 }
 

@@ -45,7 +45,7 @@ struct Layout {
     size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_u;   // byte offsets
     // union region (phase-local)
     size_t o_cnts, o_actn, o_acts;    // neuron phase
-    size_t o_pres, o_nzp, o_pcol;     // STDP phase
+    size_t o_pres, o_nzp, o_pcol, o_nzqw;   // STDP phase
     int ps;                           // row stride of the staged input-major masks
     size_t o_wbuf;                    // encode phase
     size_t bytes;
@@ -75,6 +75,7 @@ Layout make_layout(const Consts& c, int G) {
     L.o_pres = o;                u_stdp = align16((size_t)c.n_in * L.ps * 4);
     L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
     L.o_pcol = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
+    L.o_nzqw = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
     if (u_enc > u) u = u_enc;
@@ -384,6 +385,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             uint32_t* preS = (uint32_t*)(sm + L.o_pres);
             uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
             int* pcol = (int*)(sm + L.o_pcol);
+            uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
             const int PS = L.ps;
             for (int jl = tid; jl < nc; jl += PT) {   // theta, and which columns fired
                 int n = 0;
@@ -394,6 +396,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     if (q && w < 32) nz |= 1u << w;
                 }
                 nzQ[jl] = n;                          // post spikes of column jl this step
+                nzQw[jl] = nz;                        // and the batch words holding them
                 double r;
                 if (c.reduce == SNN_REDUCE_SUM) r = (double)n;
                 else if (c.reduce == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)B);
@@ -535,7 +538,13 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         const uint32_t* Pi = preS + i * PS;
                         float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
                         int nev = 0, kq = 0;
+                        uint32_t words = Bw <= 32 ? (nzP[i] | nzQw[jl]) : 0xFFFFFFFFu;
                         for (int w = 0; w < Bw; ++w) {
+                            if (Bw <= 32) {
+                                if (!words) break;
+                                w = __ffs(words) - 1;
+                                words &= words - 1;
+                            }
                             const uint32_t p = Pi[w];
                             const uint32_t qq = Qm[w * nc + jl];
                             uint32_t m = (p & Sm[w * nc + jl]) | qq;
@@ -616,23 +625,35 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
         *used = 1;
         return cudaSuccess;
     }
-    int dev = 0, sms = 0, smem_optin = 0;
+    // Device properties and the kernel's shared-memory opt-in are looked up
+    // once per device and layout size, not on every run.
+    struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes = 0; };
+    static Setup setup[64];
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const int G = sms < c.N ? sms : c.N;
-    const size_t budget = smem_optin > 2048 ? (size_t)smem_optin - 2048 : 0;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    Setup& su = setup[dev];
+    if (su.sms == 0) {
+        e = cudaDeviceGetAttribute(&su.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&su.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) { su.sms = 0; return e; }
+    }
+    const int G = su.sms < c.N ? su.sms : c.N;
+    const size_t budget = su.smem_optin > 2048 ? (size_t)su.smem_optin - 2048 : 0;
     const Layout L = make_layout(c, G);
     if (L.bytes > budget) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)L.bytes);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, PT, L.bytes);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaSuccess;
+    if (su.attr_bytes < L.bytes) {
+        e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)L.bytes);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, PT, L.bytes);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaSuccess;
+        su.attr_bytes = L.bytes;
+    }
     Consts cc = c;
     Bufs dd = d;
     int TT = T;

@@ -290,6 +290,52 @@ __global__ void k_extract(Consts c, Bufs d, int field, void* out) {
     }
 }
 
+// Writes a state field given in its read layout back into the internal layout.
+__global__ void k_insert(Consts c, Bufs d, int field, const void* in) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    if (field == SNN_FIELD_X_PRE) {
+        const size_t n = (size_t)c.B * c.n_in;
+        const int last = (int)((d.step[1] + 1ull) & 1ull);   // buffer of step end-1
+        const float* src = (const float*)in;
+        for (size_t k = tid; k < n; k += nth) d.x_pre[(size_t)last * n + k] = src[k];
+        return;
+    }
+    const uint8_t* src = (const uint8_t*)in;
+    const size_t n = (size_t)c.B * c.N;
+    for (size_t k = tid; k < n; k += nth) {
+        uint32_t s = d.st[k];
+        const uint32_t v = src[k];
+        if (field == SNN_FIELD_REF_EXC) s = (s & ~0xFFu) | (v & 0xFFu);
+        else if (field == SNN_FIELD_REF_INH) s = (s & ~0xFF00u) | ((v & 0xFFu) << 8);
+        else if (field == SNN_FIELD_SPIKES_EXC) s = (s & ~ST_SE) | (v ? ST_SE : 0u);
+        else if (field == SNN_FIELD_SPIKES_INH) s = (s & ~ST_SI) | (v ? ST_SI : 0u);
+        d.st[k] = s;
+    }
+}
+
+// After a state write: the samples in which each neuron may have a non-zero
+// postsynaptic trace, and the previous step's inhibitory spike count.
+__global__ void k_derive(Consts c, Bufs d) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = tid; k < (size_t)c.N * c.Bw; k += nth) {
+        const int j = (int)(k / c.Bw), w = (int)(k % c.Bw);
+        uint32_t m = 0;
+        for (int bit = 0; bit < 32; ++bit) {
+            const int b = w * 32 + bit;
+            if (b < c.B && d.x_post[(size_t)b * c.N + j] != 0.0f) m |= 1u << bit;
+        }
+        d.spkT[k] = m;
+    }
+    const int prev = (int)((d.step[1] + 2ull) % 3ull);         // counts of step end-1
+    for (size_t b = tid; b < (size_t)c.B; b += nth) {
+        uint32_t n = 0;
+        for (int j = 0; j < c.N; ++j) n += (d.st[b * c.N + j] & ST_SI) ? 1u : 0u;
+        d.cnt[(size_t)prev * c.B + b] = n;
+    }
+}
+
 __global__ void k_clip_weights(float* W, size_t n, float w_min, float w_max) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (size_t k = tid; k < n; k += (size_t)gridDim.x * blockDim.x) {
@@ -352,6 +398,18 @@ cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_
 cudaError_t launch_extract(const Consts& c, const Bufs& d, int field, void* out, cudaStream_t s) {
     const size_t n = field == SNN_FIELD_X_PRE ? (size_t)c.B * c.n_in : (size_t)c.B * c.N;
     k_extract<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(c, d, field, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert(const Consts& c, const Bufs& d, int field, const void* in, cudaStream_t s) {
+    const size_t n = field == SNN_FIELD_X_PRE ? (size_t)c.B * c.n_in : (size_t)c.B * c.N;
+    k_insert<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(c, d, field, in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_derive(const Consts& c, const Bufs& d, cudaStream_t s) {
+    const size_t n = (size_t)c.N * c.Bw > (size_t)c.B ? (size_t)c.N * c.Bw : (size_t)c.B;
+    k_derive<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(c, d);
     return cudaGetLastError();
 }
 

@@ -53,7 +53,8 @@ FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
                SNN_FIELD_SPIKES_EXC: np.uint8, SNN_FIELD_SPIKES_INH: np.uint8}
 
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
-            "snn_read_state", "snn_read_weights", "snn_write_weights", "snn_profile",
+            "snn_read_state", "snn_write_state", "snn_read_weights", "snn_write_weights",
+            "snn_profile",
             "snn_infer_noalloc", "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -98,6 +99,7 @@ def lib():
         L.snn_field_bytes.argtypes = [C.c_void_p, C.c_int]
         L.snn_field_bytes.restype = C.c_size_t
         L.snn_read_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_write_state.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_read_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_write_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
@@ -107,7 +109,7 @@ def lib():
         L.snn_infer_noalloc.restype = C.c_int
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
-        for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state",
+        for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state", "snn_write_state",
                      "snn_read_weights", "snn_write_weights", "snn_profile"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -180,6 +182,11 @@ def snn_field_bytes(net, field: int) -> int:
 def snn_read_state(net, field: int, dst) -> None:
     p, n, dev = _buf(dst)
     _check(net, lib().snn_read_state(net, field, p, n, dev))
+
+
+def snn_write_state(net, field: int, src) -> None:
+    p, n, dev = _buf(src)
+    _check(net, lib().snn_write_state(net, field, p, n, dev))
 
 
 def snn_read_weights(net, dst) -> None:
@@ -305,6 +312,14 @@ class Network:
 
     def set_weights(self, w) -> None:
         snn_write_weights(self.handle, w)
+
+    def write(self, field: str, src) -> None:
+        """Replace a state field (layout as returned by read)."""
+        f = FIELDS[field]
+        dt = np.dtype(FIELD_DTYPE[f])
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dt)
+        snn_write_state(self.handle, f, src)
 
     def close(self) -> None:
         if self.handle:

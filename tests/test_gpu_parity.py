@@ -187,6 +187,50 @@ def test_continuing_run_and_batch_change(modes):
     assert_parity(g3, st3, rec3)
 
 
+@pytest.mark.parametrize("mode", ["step", "persistent"])
+def test_checkpoint_and_resume_in_a_fresh_network(mode):
+    """snn_read_state + snn_write_state: a fresh network given the saved
+    state, weights, thresholds and step counter continues bit for bit."""
+    m = snn()
+    p, r, s, w = synth.workload(9, 100)
+    a = m.Network(p, w_init=w)
+    a.run(dev(r), dev(s), 100, mode=mode)
+    fields = ["v_exc", "v_inh", "x_pre", "x_post", "ref_exc", "ref_inh", "spikes_exc",
+              "spikes_inh"]
+    ck = {f: a.read(f) for f in fields}
+    b = m.Network(p, w_init=a.weights(), theta_init=a.read("theta"))
+    b.run(dev(r), dev(s), 0, mode=mode)              # holds the batch, no step taken
+    for f in fields:
+        b.write(f, ck[f])
+    b.write("step", a.read("step"))
+    for net in (a, b):
+        net.run(dev(r), dev(s), 150, mode=mode, continue_=True, record=True)
+    torch.cuda.synchronize()
+    ga, gb = read_all(a), read_all(b)
+    assert ga["raster_e"].sum() > 0
+    for k in ga:
+        if k == "step":
+            assert ga[k] == gb[k] == 250
+        else:
+            assert np.array_equal(bits(ga[k]), bits(gb[k])), k
+
+
+def test_write_state_rejects_bad_requests():
+    m = snn()
+    p, r, s, w = synth.workload(2, 20)
+    net = m.Network(p, w_init=w)
+    with pytest.raises(m.SNNError) as e:                      # no batch yet
+        net.write("v_exc", np.zeros((2, 20), np.float32))
+    assert e.value.status == m.SNN_ERR_STATE
+    net.run(dev(r), dev(s), 0)
+    with pytest.raises(m.SNNError) as e:                      # read-only field
+        m.snn_write_state(net.handle, m.SNN_FIELD_SPIKE_COUNTS, np.zeros(40, np.uint32))
+    assert e.value.status == m.SNN_ERR_ARG
+    with pytest.raises(m.SNNError) as e:                      # wrong size
+        m.snn_write_state(net.handle, m.SNN_FIELD_V_EXC, np.zeros(39, np.float32))
+    assert e.value.status == m.SNN_ERR_ARG
+
+
 def test_host_inputs_match_device_inputs():
     m = snn()
     p, r, s, w = synth.workload(8, 100)
