@@ -204,7 +204,7 @@ def test_checkpoint_and_resume_in_a_fresh_network(mode):
         b.write(f, ck[f])
     b.write("step", a.read("step"))
     for net in (a, b):
-        net.run(dev(r), dev(s), 150, mode=mode, continue_=True, record=True)
+        net.run(dev(r), dev(s), 150, mode=mode, continue_=True, record=True, record_input=True)
     torch.cuda.synchronize()
     ga, gb = read_all(a), read_all(b)
     assert ga["raster_e"].sum() > 0
