@@ -193,6 +193,8 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.a_th = std::exp(-(double)dt / (double)s.theta_tau_ms);
     c.theta_plus = (double)s.theta_plus;
     c.dt = dt;
+    c.B_pow2 = (B & (B - 1)) == 0 ? 1 : 0;
+    c.inv_B = c.B_pow2 ? (float)std::ldexp(1.0, -(int)std::lround(std::log2((double)B))) : 0.0f;
     c.reduce = reduce;
     c.learn = learn ? 1 : 0;
     c.rec_raster = (flags & SNN_RECORD_RASTER) ? 1 : 0;

@@ -21,6 +21,8 @@ struct Consts {
     int R_e, R_i;       // refractory periods in steps
     double a_th, theta_plus;
     float dt;
+    float inv_B;        // 1/B, exact when B is a power of two
+    int B_pow2;         // B is a power of two
     int reduce, learn;
     int rec_raster, rec_input;
 };
@@ -65,6 +67,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+// Batch mean of an accumulated update, acc / B correctly rounded.  For B a
+// power of two, acc * 2^-k is the same exact quotient rounded the same way,
+// and a multiplication is much cheaper than an IEEE division.
+__device__ __forceinline__ float batch_mean(const Consts& c, float acc) {
+    return c.B_pow2 ? __fmul_rn(acc, c.inv_B) : __fdiv_rn(acc, (float)c.B);
 }
 
 // Optional event brackets around launches (SNN_PROFILE): two events and one

@@ -479,7 +479,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         }
                         if (nev > 0) {
                             float D = acc;
-                            if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
+                            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
                             if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
                             float wv = __fadd_rn(Ws[k], D);
                             wv = wv < c.w_min ? c.w_min : wv;
@@ -574,7 +574,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         }
                         if (nev > 0) {
                             float D = acc;
-                            if (c.reduce == SNN_REDUCE_MEAN) D = __fdiv_rn(acc, (float)B);
+                            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
                             if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
                             float wv = __fadd_rn(Ws[i * nc + jl], D);
                             wv = wv < c.w_min ? c.w_min : wv;
