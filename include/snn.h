@@ -86,6 +86,10 @@ typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
                                          the copy asynchronous) */
 #define SNN_PROFILE         (1u << 4) /* bracket every kernel launch of the run with CUDA
                                          events; read the times with snn_profile */
+#define SNN_TEST_BARRIER_TIMEOUT (1u << 5) /* test only: the persistent kernel's first grid
+                                         barrier waits for an arrival that never comes, so
+                                         its bounded wait (a few ms here) runs out and the run
+                                         reports SNN_ERR_TIMEOUT; no real hang occurs */
 #define SNN_MODE_STEP       (0u << 8) /* one kernel launch per phase per time step */
 #define SNN_MODE_GRAPH      (1u << 8) /* the T-step launch sequence captured once as a
                                          CUDA graph and replayed */

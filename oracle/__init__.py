@@ -40,7 +40,7 @@ class _Params(C.Structure):
         (n, C.c_float) for n in (
             "e_rest", "e_reset", "e_thresh", "e_tau", "e_refrac", "theta_plus", "theta_tau",
             "i_rest", "i_reset", "i_thresh", "i_tau", "i_refrac", "w_ei", "w_ie",
-            "trace_tau", "nu_pre", "nu_post", "w_min", "w_max", "dt")]
+            "trace_tau", "nu_pre", "nu_post", "w_min", "w_max", "dt")] + [("wprec", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -69,6 +69,8 @@ def lib():
                            C.c_int, C.c_int, C.c_int, C.POINTER(_State), C.POINTER(_Record)]
         _lib.oracle_splitmix64.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         _lib.oracle_poisson_thresholds.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int64]
+        for name in ("oracle_round_bf16", "oracle_round_e4m3", "oracle_e4m3_column_scale"):
+            getattr(_lib, name).argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     return _lib
 
 
@@ -122,7 +124,7 @@ class Record:
 
 def run(params: dict, state: State, rates: np.ndarray, seeds: np.ndarray, T: int, *,
         dt: float = 1.0, learn: bool = True, reduce: str = "mean", episodic: bool = True,
-        record: bool = True, record_currents: bool = False) -> Record:
+        record: bool = True, record_currents: bool = False, wprec: int = 0) -> Record:
     """Advance ``state`` by T steps in place; return the per-step records."""
     dtype = state.v_e.dtype
     B = state.v_e.shape[0]
@@ -130,7 +132,8 @@ def run(params: dict, state: State, rates: np.ndarray, seeds: np.ndarray, T: int
     assert rates.shape == (B, NI) and seeds.shape == (B,)
     rates = np.ascontiguousarray(rates, np.float32)
     seeds = np.ascontiguousarray(seeds, np.uint64)
-    P = _Params(**{k: params[k] for k, _ in _Params._fields_ if k != "dt"}, dt=dt)
+    P = _Params(**{k: params[k] for k, _ in _Params._fields_ if k not in ("dt", "wprec")}, dt=dt,
+                wprec=wprec)
     arrs = {k: getattr(state, k) for k in ("v_e", "v_i", "ref_e", "ref_i", "s_e", "s_i",
                                             "x_pre", "x_post", "w", "theta")}
     for k, a in arrs.items():
@@ -159,6 +162,27 @@ def splitmix64(x) -> np.ndarray:
     x = np.ascontiguousarray(x, np.uint64)
     out = np.empty_like(x)
     lib().oracle_splitmix64(x.ctypes.data, out.ctypes.data, x.size)
+    return out
+
+
+def round_bf16(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float32)
+    out = np.empty_like(x)
+    lib().oracle_round_bf16(x.ctypes.data, out.ctypes.data, x.size)
+    return out
+
+
+def round_e4m3(x) -> np.ndarray:
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(x)
+    lib().oracle_round_e4m3(x.ctypes.data, out.ctypes.data, x.size)
+    return out
+
+
+def e4m3_column_scale(m) -> np.ndarray:
+    m = np.ascontiguousarray(m, np.float64)
+    out = np.empty_like(m)
+    lib().oracle_e4m3_column_scale(m.ctypes.data, out.ctypes.data, m.size)
     return out
 
 

@@ -38,6 +38,9 @@
 //   O7 theta:  theta = theta*a_theta + theta_plus*r_j, FP64, r_j = red_b s_e[b,j].
 //   O8 constants: a_* = (R)exp(-dt/tau) from double; a_theta = exp(-dt/tau_theta)
 //              in double; R_e = round(refrac_e/dt), R_i = round(refrac_i/dt).
+//   O9 weight precision of the current (W itself stays in R for STDP):
+//              BF16: I_in sums round_bf16(W); FP8: I_in = s_j * sum round_e4m3(W/s_j),
+//              s_j = smallest 2^k with 448*2^k >= max_i |W[i,j]|, from this step's W.
 //
 // Each line of the per-step update is one IEEE operation in the order written;
 // the file is compiled with -ffp-contract=off and without -ffast-math so the
@@ -62,6 +65,7 @@ struct oracle_params {
     float w_ei, w_ie;
     float trace_tau, nu_pre, nu_post, w_min, w_max;
     float dt;
+    int32_t wprec;   // storage of W read by the current: 0 FP32, 1 BF16, 2 FP8 e4m3 + column scale
 };
 
 // Complete simulation state; every array is owned by the caller.
@@ -119,6 +123,46 @@ uint32_t poisson_draw(uint64_t seed, uint64_t t, int n_in, int i) {
     return (uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32);
 }
 
+// BF16 (1 sign, 8 exponent, 7 fraction bits) nearest to x, ties to even:
+// keep the top 16 bits of the binary32 pattern after adding half an ulp of
+// the kept part (plus one if the kept part is odd).  Finite inputs only.
+float round_bf16(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    const uint32_t keep_odd = (u >> 16) & 1u;
+    u = (u + 0x7FFFu + keep_odd) & 0xFFFF0000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+// FP8 E4M3 (1 sign, 4 exponent bits with bias 7, 3 fraction bits, no
+// infinities, largest finite 448, subnormal step 2^-9) nearest to x, ties to
+// even, saturating to +-448.  Exact in double.
+double round_e4m3(double x) {
+    const double a = std::fabs(x);
+    if (a == 0.0) return x;
+    double q;
+    if (a < std::ldexp(1.0, -6)) {                  // subnormal range: multiples of 2^-9
+        q = std::nearbyint(std::ldexp(a, 9)) * std::ldexp(1.0, -9);
+    } else {
+        int e;
+        std::frexp(a, &e);                          // a = f * 2^e, f in [0.5, 1)
+        const int ulp_exp = (e - 1) - 3;            // 3 fraction bits below the leading bit
+        q = std::nearbyint(std::ldexp(a, -ulp_exp)) * std::ldexp(1.0, ulp_exp);
+    }
+    if (q > 448.0) q = 448.0;
+    return x < 0 ? -q : q;
+}
+
+// Power-of-two column scale for FP8: the smallest 2^k with 448 * 2^k >= m.
+double e4m3_column_scale(double m) {
+    if (!(m > 0.0)) return 1.0;
+    int e;
+    const double f = std::frexp(m, &e);             // m = f * 2^e, 448 = 0.875 * 2^9
+    return std::ldexp(1.0, f <= 0.875 ? e - 9 : e - 8);
+}
+
 template <typename R>
 R decay_factor(float dt, float tau) {
     return (R)std::exp(-(double)dt / (double)tau);
@@ -131,6 +175,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         int learn, int reduce, int episodic, oracle_state* S, oracle_record* rec) {
     if (!P || !S || B <= 0 || T < 0 || !rates || !seeds) return 1;
     if (reduce < 0 || reduce > 2) return 1;
+    if (P && (P->wprec < 0 || P->wprec > 2)) return 1;
     const int NI = P->n_in, N = P->n_exc;
     if (NI <= 0 || N <= 0 || !(P->dt > 0.0f)) return 1;
 
@@ -171,6 +216,8 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
     std::vector<uint8_t> s_in((size_t)B * NI), se_new((size_t)B * N), si_new((size_t)B * N);
     std::vector<R> I_in((size_t)B * N), I_lat((size_t)B * N), I_inh((size_t)B * N);
     std::vector<R> D((size_t)NI * N);
+    std::vector<R> Wr(P->wprec == 0 ? 0 : (size_t)NI * N);
+    std::vector<double> scale(P->wprec == 2 ? (size_t)N : 0);
 
     for (int tt = 0; tt < T; ++tt) {
         const uint64_t t = S->step;
@@ -187,18 +234,39 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
             x_pre[k] = m + (R)s_in[k];
         }
 
-        // O2 currents.  I_in: for every (b, j) the sum runs over ascending i.
+        // Weights as read by the current: FP32 as stored, or rounded to BF16,
+        // or FP8 E4M3 after division by a power-of-two column scale.
+        if (P->wprec == 1) {
+            for (size_t k = 0; k < Wr.size(); ++k) Wr[k] = (R)round_bf16((float)W[k]);
+        } else if (P->wprec == 2) {
+            for (int j = 0; j < N; ++j) {
+                double m = 0.0;
+                for (int i = 0; i < NI; ++i) {
+                    const double a = std::fabs((double)W[(size_t)i * N + j]);
+                    m = a > m ? a : m;
+                }
+                scale[j] = e4m3_column_scale(m);
+                for (int i = 0; i < NI; ++i)
+                    Wr[(size_t)i * N + j] = (R)round_e4m3((double)W[(size_t)i * N + j] / scale[j]);
+            }
+        }
+        const R* Wc = P->wprec == 0 ? W : Wr.data();
+
+        // O2 currents.  I_in: for every (b, j) the sum runs over ascending i
+        // (FP8: the sum of the scaled codes, times the column scale).
         for (int b = 0; b < B; ++b) {
             R* Ib = &I_in[(size_t)b * N];
             for (int j = 0; j < N; ++j) Ib[j] = (R)0;
             for (int i = 0; i < NI; ++i) {
                 const R s = (R)s_in[(size_t)b * NI + i];
-                const R* Wi = &W[(size_t)i * N];
+                const R* Wi = &Wc[(size_t)i * N];
                 for (int j = 0; j < N; ++j) {
                     R term = s * Wi[j];
                     Ib[j] = Ib[j] + term;
                 }
             }
+            if (P->wprec == 2)
+                for (int j = 0; j < N; ++j) Ib[j] = Ib[j] * (R)scale[j];
             int C = 0;
             for (int k = 0; k < N; ++k) C += s_i[(size_t)b * N + k];
             for (int j = 0; j < N; ++j) {
@@ -338,6 +406,18 @@ int oracle_run_f64(const oracle_params* P, int B, int T, const float* rates,
 // Exposed so the tests can pin the generator against its published outputs.
 void oracle_splitmix64(const uint64_t* x, uint64_t* out, int64_t n) {
     for (int64_t k = 0; k < n; ++k) out[k] = splitmix64(x[k]);
+}
+
+void oracle_round_bf16(const float* x, float* out, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) out[k] = round_bf16(x[k]);
+}
+
+void oracle_round_e4m3(const double* x, double* out, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) out[k] = round_e4m3(x[k]);
+}
+
+void oracle_e4m3_column_scale(const double* m, double* out, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) out[k] = e4m3_column_scale(m[k]);
 }
 
 void oracle_poisson_thresholds(const float* rates, float dt, uint32_t* out, int64_t n) {

@@ -199,6 +199,7 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.learn = learn ? 1 : 0;
     c.rec_raster = (flags & SNN_RECORD_RASTER) ? 1 : 0;
     c.rec_input = (flags & SNN_RECORD_INPUT) ? 1 : 0;
+    c.test_timeout = (flags & SNN_TEST_BARRIER_TIMEOUT) ? 1 : 0;
     return c;
 }
 
@@ -352,7 +353,7 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     if (reduce < SNN_REDUCE_SUM || reduce > SNN_REDUCE_MAX)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown reduce %d", reduce);
     const unsigned known = SNN_CONTINUE | SNN_RECORD_RASTER | SNN_RECORD_INPUT | SNN_HOST_INPUTS |
-                           SNN_PROFILE | SNN_MODE_MASK;
+                           SNN_PROFILE | SNN_TEST_BARRIER_TIMEOUT | SNN_MODE_MASK;
     if (flags & ~known)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown flag bits 0x%x", flags & ~known);
     const int R_e = steps_of(n->spec.e_refrac_ms, dt), R_i = steps_of(n->spec.i_refrac_ms, dt);

@@ -25,6 +25,7 @@ struct Consts {
     int B_pow2;         // B is a power of two
     int reduce, learn;
     int rec_raster, rec_input;
+    int test_timeout;   // make the first grid barrier of the persistent form time out
 };
 
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.

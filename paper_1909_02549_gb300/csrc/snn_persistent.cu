@@ -36,6 +36,7 @@ namespace {
 constexpr int PT = 1024;                   // threads per CTA
 constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
+constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 constexpr int XQ = 2;                      // post samples per column whose x_pre is preloaded
 constexpr unsigned FULL = 0xFFFFFFFFu;
@@ -91,7 +92,7 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 
 // Grid-wide barrier with a bounded wait.  Returns false if this or another
 // CTA gave up (device error bit 1).
-__device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target) {
+__device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target, unsigned limit) {
     __shared__ int s_fail;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -101,7 +102,7 @@ __device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target) {
         unsigned spins = 0, ns = 32;
         while (ld_acquire(ctr) < target) {
             if ((++spins & 31u) == 0u && ld_acquire(err) != 0u) { fail = 1; break; }
-            if (spins > SPIN_LIMIT) { atomicOr(err, 1u); fail = 1; break; }
+            if (spins > limit) { atomicOr(err, 1u); fail = 1; break; }
             __nanosleep(ns);
             if (ns < 512) ns <<= 1;
         }
@@ -266,7 +267,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         for (int b = tid; b < B; b += PT) d.cnt[(size_t)(base % 3ull) * B + b] = 0u;
     encode_phase(c, d, L, sm, base, 0);
     unsigned nbar = 1;
-    bool ok = grid_sync(bar, d.err, G * nbar);
+    // (test knob: wait for one arrival more than there are CTAs, with a short limit)
+    bool ok = grid_sync(bar, d.err, G * nbar + (c.test_timeout ? 1u : 0u),
+                        c.test_timeout ? TEST_SPIN_LIMIT : SPIN_LIMIT);
 
     for (int t = 0; t < T && ok; ++t) {
         const unsigned long long tt = base + (unsigned long long)t;
@@ -591,7 +594,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         if (t + 1 < T) {
             encode_phase(c, d, L, sm, tt + 1, t + 1);
             ++nbar;
-            ok = grid_sync(bar, d.err, G * nbar);
+            ok = grid_sync(bar, d.err, G * nbar, SPIN_LIMIT);
         }
     }
 

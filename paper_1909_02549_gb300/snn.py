@@ -26,6 +26,7 @@ SNN_RECORD_RASTER = 1 << 1
 SNN_RECORD_INPUT = 1 << 2
 SNN_HOST_INPUTS = 1 << 3
 SNN_PROFILE = 1 << 4
+SNN_TEST_BARRIER_TIMEOUT = 1 << 5
 KERNEL_NAMES = ["begin_run", "encode", "neuron", "stdp", "persistent"]
 SNN_MODE_STEP = 0 << 8
 SNN_MODE_GRAPH = 1 << 8

@@ -231,6 +231,31 @@ def test_write_state_rejects_bad_requests():
     assert e.value.status == m.SNN_ERR_ARG
 
 
+def test_bounded_barrier_wait_reports_timeout_and_context_survives():
+    """Failure detection without a GPU fault: the test knob makes the first
+    grid barrier wait for an arrival that never comes; the bounded wait runs
+    out (~ms), the run reports SNN_ERR_TIMEOUT on the next synchronising call,
+    continuing from the broken state is refused, and the next episodic run
+    equals a fresh network's."""
+    m = snn()
+    p, r, s, w = synth.workload(8, 100)
+    net = m.Network(p, w_init=w)
+    m.snn_run(net.handle, dev(r), dev(s), 8, 20, 1.0, 0, m.SNN_REDUCE_MEAN,
+              m.SNN_MODE_PERSISTENT | m.SNN_TEST_BARRIER_TIMEOUT, None)
+    with pytest.raises(m.SNNError) as e:
+        net.read("v_exc")
+    assert e.value.status == m.SNN_ERR_TIMEOUT
+    with pytest.raises(m.SNNError) as e:
+        net.run(dev(r), dev(s), 5, mode="persistent", continue_=True)
+    assert e.value.status == m.SNN_ERR_STATE
+    net.run(dev(r), dev(s), 60, learn=False, mode="persistent", record=True)
+    fresh = m.Network(p, w_init=w)
+    fresh.run(dev(r), dev(s), 60, learn=False, mode="persistent", record=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(net.raster(), fresh.raster())
+    assert np.array_equal(net.read("v_exc"), fresh.read("v_exc"))
+
+
 def test_host_inputs_match_device_inputs():
     m = snn()
     p, r, s, w = synth.workload(8, 100)

@@ -427,3 +427,91 @@ def test_episodic_reset_restores_initial_state():
     r1 = oracle.run(p, st, r, s, 120, learn=False)
     r2 = oracle.run(p, st, r, s, 120, learn=False)     # episodic: reset then rerun
     assert np.array_equal(r1.raster_e, r2.raster_e) and np.array_equal(r1.raster_in, r2.raster_in)
+
+
+# ---------------------------------------------- O9 weight precision ---
+
+def _e4m3_values():
+    """Every finite non-negative E4M3 value, from the format's definition:
+    4 exponent bits (bias 7), 3 fraction bits, exponent field 0 subnormal,
+    the all-ones pattern (exponent 15, fraction 7) is NaN."""
+    vals = []
+    for e in range(16):
+        for m in range(8):
+            if e == 15 and m == 7:
+                continue
+            vals.append((m / 8.0) * 2.0 ** -6 if e == 0 else (1 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(sorted(vals))
+
+
+def test_bf16_rounding_is_round_to_nearest_even():
+    rng = np.random.default_rng(5)
+    x = (rng.standard_normal(20000) * rng.choice([1e-3, 1.0, 300.0], 20000)).astype(np.float32)
+    got = oracle.round_bf16(x).astype(np.float64)
+    xd = x.astype(np.float64)
+    e = np.floor(np.log2(np.abs(xd)))
+    step = 2.0 ** (e - 7)                                   # 8 significant bits
+    want = np.round(xd / step) * step                       # numpy rounds half to even
+    assert np.array_equal(got, want)
+    grid = (np.arange(154) / 512.0).astype(np.float32)     # the 2^-9 grid on [0, 0.3]
+    assert np.array_equal(oracle.round_bf16(grid), grid)
+    ties = np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8], np.float32)
+    assert oracle.round_bf16(ties).tolist() == [1.0, 1 + 2 ** -6]
+
+
+def test_e4m3_rounding_picks_the_nearest_value_ties_to_even():
+    v = _e4m3_values()
+    assert v[-1] == 448.0 and v[1] == 2.0 ** -9
+    assert np.array_equal(oracle.round_e4m3(v), v)           # representable values are fixed
+    rng = np.random.default_rng(6)
+    x = np.concatenate([rng.uniform(0, 460, 4000), rng.uniform(0, 0.05, 4000),
+                        (v[:-1] + v[1:]) / 2])               # includes every tie
+    got = oracle.round_e4m3(x)
+    for xi, gi in zip(x, got):
+        d = np.abs(v - min(xi, 448.0))
+        best = np.flatnonzero(d == d.min())
+        if best.size == 1:
+            assert gi == v[best[0]], xi
+        else:                                                # tie: the even code
+            codes = [int(np.flatnonzero(v == v[k])[0]) for k in best]
+            assert gi == v[best[[c % 2 == 0 for c in codes].index(True)]], xi
+    assert oracle.round_e4m3(np.array([500.0, -1000.0, -3.3])).tolist() == [448.0, -448.0, -3.25]
+
+
+def test_e4m3_column_scale_is_the_smallest_sufficient_power_of_two():
+    rng = np.random.default_rng(7)
+    m = np.concatenate([rng.uniform(1e-4, 2.0, 5000), [448.0, 448.0 * 2 ** -9, 0.3]])
+    s = oracle.e4m3_column_scale(m)
+    k = np.log2(s)
+    assert np.array_equal(k, np.round(k))
+    assert np.all(448.0 * s >= m) and np.all(448.0 * s / 2 < m)
+    assert oracle.e4m3_column_scale(np.array([0.0]))[0] == 1.0
+
+
+def test_bf16_current_equals_fp32_on_a_bf16_exact_grid():
+    """W on the 2^-9 grid is BF16-exact, so with learning off a BF16 run is
+    the FP32 run, bit for bit; on the 2^-12 grid it is not."""
+    p, r, s, _ = synth.workload(3, 100)
+    w9 = synth.weights(784, 100, bf16_grid=True)
+    a, b = oracle.new_state(p, 3, w9), oracle.new_state(p, 3, w9)
+    ra = oracle.run(p, a, r, s, 150, learn=False, wprec=0)
+    rb = oracle.run(p, b, r, s, 150, learn=False, wprec=1)
+    assert np.array_equal(ra.raster_e, rb.raster_e) and np.array_equal(a.v_e, b.v_e)
+    w12 = synth.weights(784, 100)
+    c = oracle.new_state(p, 3, w12)
+    rc = oracle.run(p, c, r, s, 150, learn=False, wprec=1, record_currents=True)
+    d = oracle.new_state(p, 3, w12)
+    rd = oracle.run(p, d, r, s, 150, learn=False, wprec=0, record_currents=True)
+    assert not np.array_equal(rc.cur_in, rd.cur_in)
+
+
+def test_fp8_current_is_within_the_format_error_of_fp32():
+    """|I_fp8 - I_fp32| <= sum over active inputs of |W| * 2^-4 (half an ulp
+    of 3 fraction bits, relative), step by step with learning off."""
+    p, r, s, w = synth.workload(2, 60)
+    a, b = oracle.new_state(p, 2, w), oracle.new_state(p, 2, w)
+    ra = oracle.run(p, a, r, s, 1, learn=False, wprec=2, record_currents=True)
+    rb = oracle.run(p, b, r, s, 1, learn=False, wprec=0, record_currents=True)
+    bound = ra.raster_in[0].astype(np.float64) @ (np.abs(w).astype(np.float64) * 2.0 ** -4)
+    diff = np.abs(ra.cur_in[0].astype(np.float64) - rb.cur_in[0].astype(np.float64))
+    assert np.all(diff <= bound + 1e-6) and diff.max() > 0
