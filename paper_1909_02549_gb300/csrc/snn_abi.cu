@@ -200,6 +200,7 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.rec_raster = (flags & SNN_RECORD_RASTER) ? 1 : 0;
     c.rec_input = (flags & SNN_RECORD_INPUT) ? 1 : 0;
     c.test_timeout = (flags & SNN_TEST_BARRIER_TIMEOUT) ? 1 : 0;
+    c.wprec = s.wprec;
     return c;
 }
 
@@ -286,9 +287,8 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
         return fail(nullptr, SNN_ERR_ARG, "snn_create: refractory periods must be >= 0");
     if (!(s.w_min <= s.w_max))
         return fail(nullptr, SNN_ERR_ARG, "snn_create: w_min must be <= w_max");
-    if (s.wprec != SNN_W_FP32)
-        return fail(nullptr, SNN_ERR_ARG, "snn_create: wprec %d is not available in this build",
-                    (int)s.wprec);
+    if (s.wprec < SNN_W_FP32 || s.wprec > SNN_W_FP8E4M3)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown wprec %d", (int)s.wprec);
 
     snn_net* n = new (std::nothrow) snn_net();
     if (!n) return fail(nullptr, SNN_ERR_OOM, "snn_create: host allocation failed");
@@ -301,6 +301,7 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
     if (e == cudaSuccess) e = dalloc(&n->d.theta, (size_t)s.n_exc);
     if (e == cudaSuccess) e = dalloc(&n->d.step, 2);
     if (e == cudaSuccess) e = dalloc(&n->d.err, 64);
+    if (e == cudaSuccess) e = dalloc(&n->d.wscale, (size_t)s.n_exc);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking);
     std::vector<float> w;
     if (e == cudaSuccess) {
@@ -331,7 +332,7 @@ snn_status snn_destroy(snn_net* n) {
     if (!n) return SNN_OK;
     if (n->last) cudaStreamSynchronize(n->last);
     free_batch(n);
-    void* ptrs[] = {n->d.W, n->d.theta, n->d.step, n->d.err, n->d.raster_e, n->d.raster_i,
+    void* ptrs[] = {n->d.W, n->d.theta, n->d.step, n->d.err, n->d.wscale, n->d.raster_e, n->d.raster_i,
                     n->d.raster_in, n->scratch};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (n->gexec) cudaGraphExecDestroy(n->gexec);

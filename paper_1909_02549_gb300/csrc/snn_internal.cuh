@@ -1,6 +1,8 @@
 // Internal declarations shared by the kernels and the C ABI implementation.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +28,7 @@ struct Consts {
     int reduce, learn;
     int rec_raster, rec_input;
     int test_timeout;   // make the first grid barrier of the persistent form time out
+    int wprec;          // snn_wprec of the weights read by the synaptic current
 };
 
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.
@@ -55,6 +58,7 @@ struct Bufs {
     uint32_t* raster_in; // [T][B][Iw] (optional)
     unsigned long long* step;  // [2]: first step of this run, step after it
     uint32_t* err;       // [64]: [0] sticky device error bits, [32] grid-barrier counter
+    float* wscale;       // [N] per-column power-of-two scale of the FP8 weights (this step)
 };
 
 // Packed per-(b,j) state word.
@@ -68,6 +72,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+// Weight as read by the synaptic current.  BF16: round to nearest even.
+// FP8: the E4M3 code (nearest, ties to even, saturating) of W / s_j, with the
+// column's power-of-two scale applied to the finished sum.
+__device__ __forceinline__ float w_read_bf16(float w) {
+    return __bfloat162float(__float2bfloat16_rn(w));
+}
+
+__device__ __forceinline__ float w_read_e4m3(float w, float inv_scale) {
+    const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fmul_rn(w, inv_scale), __NV_SATFINITE,
+                                                        __NV_E4M3);
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw(q, __NV_E4M3)));
+}
+
+// Smallest power of two 2^k with 448 * 2^k >= m (the FP8 column scale).
+__device__ __forceinline__ float e4m3_scale_of(float m) {
+    if (!(m > 0.0f)) return 1.0f;
+    int e;
+    const float f = frexpf(m, &e);            // m = f * 2^e, 448 = 0.875 * 2^9
+    return ldexpf(1.0f, f <= 0.875f ? e - 9 : e - 8);
 }
 
 // Batch mean of an accumulated update, acc / B correctly rounded.  For B a

@@ -174,6 +174,8 @@ extern "C" snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, co
         !(dt_ms > 0.0f) || !(s.e_tau_ms > 0.0f) || !(s.i_tau_ms > 0.0f) ||
         !(s.e_refrac_ms >= 0.0f) || !(s.i_refrac_ms >= 0.0f))
         return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: invalid sizes or parameters");
+    if (s.wprec != SNN_W_FP32)
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: only FP32 weights (wprec 0)");
     const int R_e = (int)std::lround((double)s.e_refrac_ms / (double)dt_ms);
     const int R_i = (int)std::lround((double)s.i_refrac_ms / (double)dt_ms);
     if (R_e > 255 || R_i > 255)

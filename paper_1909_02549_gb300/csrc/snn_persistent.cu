@@ -43,7 +43,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
     int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
-    size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_u;   // byte offsets
+    size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
     // union region (phase-local)
     size_t o_cnts, o_actn, o_acts;    // neuron phase
     size_t o_pres, o_nzp, o_pcol, o_nzqw;   // STDP phase
@@ -67,6 +67,7 @@ Layout make_layout(const Consts& c, int G) {
     L.o_nzq = o; o = align16(o + (size_t)L.ncmax * 4);
     L.o_ths = o; o = align16(o + (size_t)L.ncmax * 8);
     L.o_thj = o; o = align16(o + (size_t)L.ncmax * 4);
+    L.o_wsc = o; o = align16(o + (size_t)L.ncmax * 8);   // FP8 column scale and its inverse
     L.o_u = o;
     size_t u_neuron = 0, u_stdp = 0, u_enc = 0;
     L.o_cnts = o;                u_neuron = align16((size_t)c.B * 4);
@@ -230,6 +231,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     uint32_t* nzQ = (uint32_t*)(sm + L.o_nzq);
     double* thS = (double*)(sm + L.o_ths);
     float* thj = (float*)(sm + L.o_thj);
+    float* wsc = (float*)(sm + L.o_wsc);             // [0, nc): scale, [ncmax, ncmax+nc): inverse
     uint32_t* cntS = (uint32_t*)(sm + L.o_cnts);
     uint32_t* actN = (uint32_t*)(sm + L.o_actn);
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
@@ -313,6 +315,19 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
             }
         }
+        if (c.wprec == SNN_W_FP8E4M3) {   // column scales of this step's weights
+            const int warp = tid >> 5, lane = tid & 31;
+            for (int jl = warp; jl < nc; jl += NW) {
+                float m = 0.0f;
+                for (int i = lane; i < NI; i += 32) m = fmaxf(m, fabsf(Ws[i * nc + jl]));
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
+                if (lane == 0) {
+                    const float sc = e4m3_scale_of(m);
+                    wsc[jl] = sc;
+                    wsc[L.ncmax + jl] = __frcp_rn(sc);
+                }
+            }
+        }
         __syncthreads();
 
         {
@@ -352,10 +367,23 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     float I = 0.0f;
                     const int na = (int)actN[b];
                     const int ns = na < caps ? na : caps;
-                    for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)actS[b * CAPS + a] * nc + jl]);
-                    for (int a = caps; a < na; ++a) {
-                        const int i = __ldcg(&d.act_idx[((size_t)cur * B + b) * NI + a]);
-                        I = __fadd_rn(I, Ws[i * nc + jl]);
+                    const uint16_t* al = actS + b * CAPS;
+                    const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+                    if (c.wprec == SNN_W_FP32) {
+                        for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)al[a] * nc + jl]);
+                        for (int a = caps; a < na; ++a) I = __fadd_rn(I, Ws[(int)__ldcg(&ag[a]) * nc + jl]);
+                    } else if (c.wprec == SNN_W_BF16) {
+                        for (int a = 0; a < ns; ++a)
+                            I = __fadd_rn(I, w_read_bf16(Ws[(int)al[a] * nc + jl]));
+                        for (int a = caps; a < na; ++a)
+                            I = __fadd_rn(I, w_read_bf16(Ws[(int)__ldcg(&ag[a]) * nc + jl]));
+                    } else {
+                        const float inv = wsc[L.ncmax + jl];
+                        for (int a = 0; a < ns; ++a)
+                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)al[a] * nc + jl], inv));
+                        for (int a = caps; a < na; ++a)
+                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)__ldcg(&ag[a]) * nc + jl], inv));
+                        I = __fmul_rn(I, wsc[jl]);
                     }
                     it[q].x = xps[b * nc + jl];
                     const Item o = neuron_update(&c, it[q], I, (int)cntS[b], thj[jl]);

@@ -128,18 +128,42 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
     const int par = (int)(tt & 1ull);
 
-    // Synaptic current: sum of W[i][j] over the active inputs, ascending i.
+    // Synaptic current: sum of W[i][j] over the active inputs, ascending i,
+    // with W read at the configured precision.
     float I = 0.0f;
     const int cur = par;
     const uint32_t* ib = d.inb + ((size_t)cur * c.B + b) * c.Iw;
     const float* Wj = d.W + j;
-    for (int w = 0; w < c.Iw; ++w) {
-        uint32_t m = ib[w];
-        while (m) {
-            const int k = __ffs(m) - 1;
-            m &= m - 1;
-            I = __fadd_rn(I, Wj[(size_t)(w * 32 + k) * c.N]);
+    if (c.wprec == SNN_W_FP32) {
+        for (int w = 0; w < c.Iw; ++w) {
+            uint32_t m = ib[w];
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                I = __fadd_rn(I, Wj[(size_t)(w * 32 + k) * c.N]);
+            }
         }
+    } else if (c.wprec == SNN_W_BF16) {
+        for (int w = 0; w < c.Iw; ++w) {
+            uint32_t m = ib[w];
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                I = __fadd_rn(I, w_read_bf16(Wj[(size_t)(w * 32 + k) * c.N]));
+            }
+        }
+    } else {
+        const float sc = d.wscale[j];
+        const float inv = __frcp_rn(sc);            // exact: sc is a power of two
+        for (int w = 0; w < c.Iw; ++w) {
+            uint32_t m = ib[w];
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                I = __fadd_rn(I, w_read_e4m3(Wj[(size_t)(w * 32 + k) * c.N], inv));
+            }
+        }
+        I = __fmul_rn(I, sc);
     }
     const uint32_t s = d.st[idx];
     int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
@@ -194,6 +218,15 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
         if (c.rec_raster)
             atomicOr(&d.raster_i[((size_t)t_local * c.B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
     }
+}
+
+// FP8 weights: each column's power-of-two scale from this step's W.
+__global__ void k_colscale(Consts c, Bufs d) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.N) return;
+    float m = 0.0f;
+    for (int i = 0; i < c.n_in; ++i) m = fmaxf(m, fabsf(d.W[(size_t)i * c.N + j]));
+    d.wscale[j] = e4m3_scale_of(m);
 }
 
 // grid (ceil(N/32), ceil(n_in/STDP_ROWS)), 256 threads; lane = column j,
@@ -379,6 +412,10 @@ cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_
     PROF_TRY(cudaGetLastError());
     PROF_TRY(prof_stop(prof, s));
     const size_t bn = (size_t)c.B * c.N;
+    if (c.wprec == SNN_W_FP8E4M3) {
+        k_colscale<<<(c.N + 255) / 256, 256, 0, s>>>(c, d);
+        PROF_TRY(cudaGetLastError());
+    }
     PROF_TRY(prof_start(prof, SNN_KERNEL_NEURON, s));
     k_neuron<<<(unsigned)((bn + 255) / 256), 256, 0, s>>>(c, d, t_local);
     PROF_TRY(cudaGetLastError());

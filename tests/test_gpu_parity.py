@@ -53,10 +53,10 @@ def read_all(net):
 
 
 def gpu_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", mode="step", theta=None,
-            net=None, continue_=False):
+            net=None, continue_=False, wprec=0):
     m = snn()
     if net is None:
-        net = m.Network(p, w_init=w, theta_init=theta)
+        net = m.Network(p, w_init=w, theta_init=theta, wprec=wprec)
     net.run(dev(rates), dev(seeds), T, learn=learn, reduce=reduce, mode=mode, record=True,
             record_input=True, continue_=continue_)
     torch.cuda.synchronize()
@@ -64,10 +64,11 @@ def gpu_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", mode="step", th
 
 
 def oracle_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", theta=None, st=None,
-               episodic=True):
+               episodic=True, wprec=0):
     if st is None:
         st = oracle.new_state(p, len(seeds), w, theta=theta)
-    rec = oracle.run(p, st, rates, seeds, T, learn=learn, reduce=reduce, episodic=episodic)
+    rec = oracle.run(p, st, rates, seeds, T, learn=learn, reduce=reduce, episodic=episodic,
+                     wprec=wprec)
     return st, rec
 
 
@@ -98,11 +99,11 @@ def assert_parity(g, st, rec):
 MODES = ("step", "graph", "persistent")
 
 
-def parity_all_modes(p, r, s, w, T, *, learn=True, reduce="mean", modes=MODES):
+def parity_all_modes(p, r, s, w, T, *, learn=True, reduce="mean", modes=MODES, wprec=0):
     """One oracle run, every run mode of the library compared with it."""
-    st, rec = oracle_run(p, r, s, w, T, learn=learn, reduce=reduce)
+    st, rec = oracle_run(p, r, s, w, T, learn=learn, reduce=reduce, wprec=wprec)
     for mode in modes:
-        _, g = gpu_run(p, r, s, w, T, learn=learn, reduce=reduce, mode=mode)
+        _, g = gpu_run(p, r, s, w, T, learn=learn, reduce=reduce, mode=mode, wprec=wprec)
         try:
             assert_parity(g, st, rec)
         except AssertionError as e:
@@ -145,6 +146,23 @@ def test_small_input_layer_and_saturated_rates():
     s = synth.sample_seeds(B)
     st, rec = parity_all_modes(p, r, s, w, 120, reduce="mean")
     assert rec.raster_in[:, :, :3].all() and rec.raster_in[:, 0].all()
+
+
+@pytest.mark.parametrize("wprec", [1, 2])
+def test_reduced_precision_weights_bit_exact(wprec):
+    """BF16 and FP8-E4M3 (per-column power-of-two scale) weights for the
+    current, FP32 accumulation and FP32 master weights: bit-exact with the
+    oracle computing with the same weight precision, learning on."""
+    p, r, s, w = synth.workload(16, 400)
+    parity_all_modes(p, r, s, w, 250, wprec=wprec)
+
+
+def test_bf16_weights_on_the_bf16_exact_grid_equal_fp32():
+    p, r, s, _ = synth.workload(8, 128)
+    w9 = synth.weights(784, 128, bf16_grid=True)
+    _, a = gpu_run(p, r, s, w9, 200, learn=False, mode="persistent", wprec=0)
+    _, b = gpu_run(p, r, s, w9, 200, learn=False, mode="persistent", wprec=1)
+    assert np.array_equal(a["raster_e"], b["raster_e"]) and np.array_equal(bits(a["v_e"]), bits(b["v_e"]))
 
 
 def test_learning_off_batch64():
