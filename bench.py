@@ -40,6 +40,9 @@ sys.path.insert(0, ROOT)
 METRIC = "sample-timesteps/s vs batch, 784→6400 STDP; % roofline; serving p50/p99 ms"
 UNIT = "sample-timesteps/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+WPREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+WPREC_NAME = {"fp32": "FP32", "bf16": "BF16 (FP32 master, FP32 accumulation)",
+              "fp8": "FP8 E4M3 with per-column scales (FP32 master, FP32 accumulation)"}
 
 
 def parse():
@@ -53,6 +56,8 @@ def parse():
     ap.add_argument("--n-exc", type=int, default=6400)
     ap.add_argument("--T", type=int, default=250)
     ap.add_argument("--reduce", default="mean", choices=["mean", "sum", "max"])
+    ap.add_argument("--wprec", default="fp32", choices=["fp32", "bf16", "fp8"],
+                    help="weights read by the synaptic current (accumulation is FP32)")
     ap.add_argument("--no-learn", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -63,10 +68,10 @@ def parse():
 def workload_config(a, mode):
     return {
         "workload": "784->%d adaptive-threshold LIF + all-but-self inhibition, pair STDP, "
-                    "%s reduction, B=%d, T=%d, dt=1 ms, FP32 weights" % (
-                        a.n_exc, a.reduce, a.batch, a.T),
+                    "%s reduction, B=%d, T=%d, dt=1 ms, %s weights" % (
+                        a.n_exc, a.reduce, a.batch, a.T, WPREC_NAME[a.wprec]),
         "B": a.batch, "n_in": 784, "n_exc": a.n_exc, "n_inh": a.n_exc, "T": a.T,
-        "reduce": a.reduce, "learn": not a.no_learn, "weights": "fp32", "mode": mode,
+        "reduce": a.reduce, "learn": not a.no_learn, "weights": WPREC_NAME[a.wprec], "mode": mode,
         "l2": "flushed by a 256 MiB write before every step",
         "inputs": "seeded synthetic 28x28 images (70% zeros, U[0,255]), rate=intensity/4 Hz",
     }
@@ -284,7 +289,7 @@ def run_ours(a):
     B, N, T, learn = a.batch, a.n_exc, a.T, not a.no_learn
     p, rates, seeds, w = synth.workload(B, N)
     seeds = seeds + np.uint64(100000 * rank)     # replicas draw independent spikes
-    net = snn.Network(p, w_init=w)
+    net = snn.Network(p, w_init=w, wprec=WPREC[a.wprec])
     r_d = torch.from_numpy(rates).cuda()
     s_d = torch.from_numpy(seeds.view(np.int64)).cuda()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
