@@ -47,7 +47,7 @@ def _gpu(p, r, s, w, T, wprec, vs_steps):
 
 def test_error_against_fp64_oracle():
     B, N, T = 8, 400, 250
-    vs_steps = [10, 25, 50, 100]
+    vs_steps = [1, 2, 4, 6, 8, 10, 15, 25, 50, 100]
     p, r, s, w = synth.workload(B, N)
     st = oracle.new_state(p, B, w, dtype=np.float64)
     ref_r, ref_v, t0 = [], [], 0
@@ -63,13 +63,13 @@ def test_error_against_fp64_oracle():
         diff = np.flatnonzero((g_r != ref_r).reshape(T, -1).any(1))
         first = int(diff[0]) if diff.size else T
         agree = float((g_r == ref_r).mean())
-        verr = max((np.abs(gv - rv) / np.abs(rv)).max()
-                   for gv, rv, t in zip(g_v, ref_v, vs_steps + [T]) if t <= first)
+        verr = max([(np.abs(gv - rv) / np.abs(rv)).max()
+                    for gv, rv, t in zip(g_v, ref_v, vs_steps + [T]) if t <= first], default=0.0)
         werr = float(np.abs(g_w.astype(np.float64) - st.w).max())
         rows.append((name, first, agree, verr, werr))
     print("\nform       first-divergence  raster-agreement  max-rel-V-err(before)  max|dW|")
     for row in rows:
         print("%-10s %16d  %16.5f  %21.3e  %.3e" % row)
     fp32 = rows[0]
-    assert fp32[2] > 0.99 and fp32[3] < 1e-4
+    assert fp32[2] > 0.99 and fp32[3] < 1e-4 and fp32[1] > 10
     assert all(row[2] > 0.95 for row in rows)
