@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
     return ap.parse_args()
 
 
@@ -265,6 +267,79 @@ def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
                 "traffic": None, "error": str(e)[:300]}
 
 
+def serving_leg(a, torch, snn, synth):
+    """Continuous batching on the frozen 784->400 network: requests arrive as a
+    Poisson process at 2000/s, each one image with a length uniform in
+    50..500 steps; p50/p99 latency and throughput, beside the plain
+    fixed-batch form (batches of 256 in arrival order, each run to its
+    longest member) on the same arrivals."""
+    import time as _t
+    N, rate, dur = 400, 2000.0, a.serve_seconds
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(1.0 / rate, int(rate * dur * 1.5) + 16)
+    arr = np.cumsum(gaps)
+    arr = arr[arr < dur]
+    n = len(arr)
+    lengths = rng.integers(50, 501, n)
+    rates = synth.rates_from_images(synth.images(n))
+    seeds = synth.sample_seeds(n, first=20000)
+    p = synth.diehl_cook_params(N)
+    net = snn.Network(p, w_init=synth.weights(784, N))
+    srv = snn.snn_serve_create(net.handle, 4096, 64 << 30)
+    slots = snn.snn_serve_status(srv)["slots"]
+    lat = np.zeros(n)
+    done = 0
+    q = 0
+    id2q = {}
+    t0 = _t.perf_counter()
+    while done < n:
+        now = _t.perf_counter() - t0
+        while q < n and arr[q] <= now:
+            id2q[snn.snn_serve_submit(srv, rates[q], int(seeds[q]), int(lengths[q]))] = q
+            q += 1
+        st = snn.snn_serve_status(srv)
+        if st["active"] == 0 and st["queued"] == 0:
+            if q < n:
+                while _t.perf_counter() - t0 < arr[q]:
+                    pass
+            continue
+        snn.snn_serve_step(srv, 10)
+        ids, _ = snn.snn_serve_poll(srv, N)
+        tnow = _t.perf_counter() - t0
+        for rid in ids:
+            k = id2q[int(rid)]
+            lat[k] = tnow - arr[k]
+            done += 1
+    wall = _t.perf_counter() - t0
+    snn.snn_serve_destroy(srv)
+    steps = int(lengths.sum())
+    cont = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "requests": n, "req_per_s": n / wall, "sample_timesteps_per_s": steps / wall,
+            "wall_s": wall, "slots": slots, "slot_bytes": snn.snn_serve_slot_bytes(net.handle)}
+    # fixed-batch form on the same arrivals
+    Bf = 256
+    lat2 = np.zeros(n)
+    t0 = _t.perf_counter()
+    for b0 in range(0, n, Bf):
+        b1 = min(n, b0 + Bf)
+        while _t.perf_counter() - t0 < arr[b1 - 1]:
+            pass
+        r = torch.from_numpy(rates[b0:b1]).cuda()
+        sd = torch.from_numpy(seeds[b0:b1].view(np.int64)).cuda()
+        net.run(r, sd, int(lengths[b0:b1].max()), learn=False, mode="auto")
+        net.read("spike_counts")
+        tnow = _t.perf_counter() - t0
+        lat2[b0:b1] = tnow - arr[b0:b1]
+    wall2 = _t.perf_counter() - t0
+    fixed = {"B": Bf, "p50_ms": float(np.percentile(lat2, 50) * 1e3),
+             "p99_ms": float(np.percentile(lat2, 99) * 1e3), "req_per_s": n / wall2,
+             "sample_timesteps_per_s": steps / wall2}
+    net.close()
+    return {"workload": "frozen 784->400, Poisson arrivals %.0f/s for %.1f s, lengths U{50..500}, "
+                        "state cap 64 GB" % (rate, dur),
+            "continuous": cont, "fixed_batch": fixed}
+
+
 # ------------------------------------------------------------ our arm ---
 
 def run_ours(a):
@@ -370,12 +445,18 @@ def run_ours(a):
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = time_oracle(a, a.cpu_seconds)
+    serving = None
+    if not a.no_serve and world == 1:
+        try:
+            serving = serving_leg(a, torch, snn, synth)
+        except Exception as e:                       # report, never hide the headline
+            serving = {"error": str(e)[:300]}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(a, a.mode), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches_per_run(a.mode, T, learn) * a.steps,
-            "clocks": clk.summary()}
+            "clocks": clk.summary(), "serving": serving}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -197,6 +197,48 @@ SNN_API snn_status snn_read_weights(snn_net* net, float* dst, size_t bytes, int 
  * refresh any reduced-precision copy.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
 SNN_API snn_status snn_write_weights(snn_net* net, const float* src, size_t bytes, int src_on_device);
 
+/* ---- Serving: continuous batching of inference presentations ----------
+ * A server keeps per-sample state for S slots resident on the device, S the
+ * largest count whose state fits state_cap_bytes (and <= max_slots).  Queued
+ * requests are admitted into free slots, whose state alone is reset (an
+ * episodic start), all active slots advance together, and a slot whose
+ * presentation ended is retired and refilled on the next call while the
+ * others keep running: the batch changes per slot (Sec. "Dynamic minibatch
+ * size", Sec. "Episodic vs. continuing simulation").  The network is frozen
+ * (learning off) and must not be modified while a server uses it.  Each slot
+ * counts its own steps, so a request's spike counts equal those of running it
+ * alone with snn_run (B = 1, learning off).  Not thread-safe per server. */
+typedef struct snn_server snn_server;
+
+/* Device bytes of one slot's state (what admission counts against the cap). */
+SNN_API size_t snn_serve_slot_bytes(const snn_net* net);
+
+/* Create a server for net.  Errors: SNN_ERR_ARG, SNN_ERR_CAPACITY (the cap
+ * holds no slot), SNN_ERR_OOM, SNN_ERR_CUDA.  *out is NULL on error. */
+SNN_API snn_status snn_serve_create(snn_net* net, int max_slots, size_t state_cap_bytes,
+                                    float dt_ms, snn_server** out);
+SNN_API snn_status snn_serve_destroy(snn_server* server);
+
+/* Queue one request: host rates [n_in] (copied), Poisson seed, presentation
+ * length T > 0 steps; *id receives its identifier.  Errors: SNN_ERR_ARG. */
+SNN_API snn_status snn_serve_submit(snn_server* server, const float* rates_hz, uint64_t seed,
+                                    int T, uint64_t* id);
+
+/* Admit queued requests into free slots, advance every active slot by up to
+ * k steps (fewer if all active presentations end sooner; *steps_run, if not
+ * NULL, receives the number), and retire the finished slots.  Synchronises
+ * cuda_stream before returning.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+SNN_API snn_status snn_serve_step(snn_server* server, int k, void* cuda_stream, int* steps_run);
+
+/* Drain up to max finished requests: ids [max], excitatory spike counts
+ * [max][n_exc] (host); *n_out receives how many were written. */
+SNN_API snn_status snn_serve_poll(snn_server* server, uint64_t* ids, uint32_t* counts, int max,
+                                  int* n_out);
+
+/* Slots, active slots, queued and finished-but-unpolled requests (any may be NULL). */
+SNN_API snn_status snn_serve_status(const snn_server* server, int* slots, int* active,
+                                    int* queued, int* done);
+
 /* Kernel classes reported by snn_profile. */
 enum {
     SNN_KERNEL_BEGIN_RUN = 0,  /* thresholds, episodic reset, seeds */

@@ -249,6 +249,13 @@ size_t field_bytes(const snn_net* n, int field) {
 namespace snn {
 // Error text for calls without a network (read back by snn_last_error(NULL)).
 void set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
+// Read-only views of a network for the serving loop (snn_serve.cu).
+const snn_spec& net_spec(const snn_net* n) { return n->spec; }
+Bufs net_bufs(const snn_net* n) { return n->d; }
+int net_device(const snn_net* n) { return n->device; }
+Consts net_consts(const snn_net* n, int B, float dt) { return make_consts(n, B, dt, 0, 0, 0); }
+void net_set_error(snn_net* n, const char* msg) { if (n) n->err = msg ? msg : ""; }
 }  // namespace snn
 
 extern "C" {

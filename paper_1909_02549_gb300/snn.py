@@ -56,7 +56,9 @@ FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
             "snn_read_state", "snn_write_state", "snn_read_weights", "snn_write_weights",
             "snn_profile",
-            "snn_infer_noalloc", "snn_last_error"]
+            "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
+            "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
+            "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -108,6 +110,20 @@ def lib():
                                         C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p,
                                         C.c_void_p]
         L.snn_infer_noalloc.restype = C.c_int
+        L.snn_serve_slot_bytes.argtypes = [C.c_void_p]
+        L.snn_serve_slot_bytes.restype = C.c_size_t
+        L.snn_serve_create.argtypes = [C.c_void_p, C.c_int, C.c_size_t, C.c_float,
+                                       C.POINTER(C.c_void_p)]
+        L.snn_serve_destroy.argtypes = [C.c_void_p]
+        L.snn_serve_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int,
+                                       C.POINTER(C.c_uint64)]
+        L.snn_serve_step.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]
+        L.snn_serve_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.POINTER(C.c_int)]
+        L.snn_serve_status.argtypes = [C.c_void_p] + [C.POINTER(C.c_int)] * 4
+        for name in ("snn_serve_create", "snn_serve_destroy", "snn_serve_submit",
+                     "snn_serve_step", "snn_serve_poll", "snn_serve_status"):
+            getattr(L, name).restype = C.c_int
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
         for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state", "snn_write_state",
@@ -217,6 +233,48 @@ def snn_infer_noalloc(spec: snn_spec, w, theta, rates, seeds, B: int, T: int, dt
                                  _buf(seeds)[0], B, T, dt_ms, _buf(spike_counts)[0],
                                  _stream(stream))
     _check(None, rc)
+
+
+def snn_serve_slot_bytes(net) -> int:
+    return lib().snn_serve_slot_bytes(net)
+
+
+def snn_serve_create(net, max_slots: int, state_cap_bytes: int, dt_ms: float = 1.0):
+    out = C.c_void_p()
+    _check(None, lib().snn_serve_create(net, max_slots, state_cap_bytes, dt_ms, C.byref(out)))
+    return out.value
+
+
+def snn_serve_destroy(server) -> None:
+    lib().snn_serve_destroy(server)
+
+
+def snn_serve_submit(server, rates, seed: int, T: int) -> int:
+    r = np.ascontiguousarray(rates, np.float32)
+    rid = C.c_uint64()
+    _check(None, lib().snn_serve_submit(server, r.ctypes.data, int(seed), T, C.byref(rid)))
+    return rid.value
+
+
+def snn_serve_step(server, k: int, stream=None) -> int:
+    n = C.c_int()
+    _check(None, lib().snn_serve_step(server, k, _stream(stream), C.byref(n)))
+    return n.value
+
+
+def snn_serve_poll(server, n_exc: int, max_n: int = 4096):
+    ids = np.empty(max_n, np.uint64)
+    counts = np.empty((max_n, n_exc), np.uint32)
+    n = C.c_int()
+    _check(None, lib().snn_serve_poll(server, ids.ctypes.data, counts.ctypes.data, max_n,
+                                      C.byref(n)))
+    return ids[:n.value], counts[:n.value]
+
+
+def snn_serve_status(server) -> dict:
+    v = [C.c_int() for _ in range(4)]
+    _check(None, lib().snn_serve_status(server, *[C.byref(x) for x in v]))
+    return dict(zip(("slots", "active", "queued", "done"), (x.value for x in v)))
 
 
 def snn_last_error(net) -> str:

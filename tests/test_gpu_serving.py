@@ -1,0 +1,82 @@
+"""Serving with continuous batching: requests of different lengths arrive while
+others run, are admitted as slots free up, retire mid-run and are backfilled.
+Each result must equal the request run alone (snn_run, B = 1, learning off),
+bit for bit like every parity check here."""
+import numpy as np
+import pytest
+
+from paper_1909_02549_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1909_02549_gb300 import build
+    build.build()
+
+
+def snn():
+    from paper_1909_02549_gb300 import snn as m
+    return m
+
+
+def alone_counts(p, w, wprec, rates, seed, T):
+    m = snn()
+    net = m.Network(p, w_init=w, wprec=wprec)
+    net.run(rates[None, :].copy(), np.array([seed], np.uint64), T, learn=False, mode="step")
+    out = net.read("spike_counts")[0]
+    net.close()
+    return out
+
+
+@pytest.mark.parametrize("wprec", [0, 2])
+def test_each_request_equals_its_alone_run_in_the_mix(wprec):
+    m = snn()
+    N, nreq = 400, 36
+    p = synth.diehl_cook_params(N)
+    w = synth.weights(784, N)
+    net = m.Network(p, w_init=w, wprec=wprec)
+    srv = m.snn_serve_create(net.handle, 8, 1 << 30)
+    rng = np.random.default_rng(3)
+    rates = synth.rates_from_images(synth.images(nreq))
+    seeds = synth.sample_seeds(nreq, first=5000)
+    lengths = rng.integers(20, 121, nreq)
+    ids, got = {}, {}
+    q = 0
+    while len(got) < nreq:
+        for _ in range(int(rng.integers(0, 5))):          # arrivals while others run
+            if q < nreq:
+                ids[m.snn_serve_submit(srv, rates[q], int(seeds[q]), int(lengths[q]))] = q
+                q += 1
+        st = m.snn_serve_status(srv)
+        if st["active"] == 0 and st["queued"] == 0 and q < nreq:
+            continue
+        m.snn_serve_step(srv, 7)                            # retirements fall mid-chunk
+        done_ids, counts = m.snn_serve_poll(srv, N)
+        for rid, c in zip(done_ids, counts):
+            got[ids[int(rid)]] = c
+    st = m.snn_serve_status(srv)
+    assert st["slots"] == 8 and st["active"] == 0 and st["queued"] == 0
+    m.snn_serve_destroy(srv)
+    assert sum(int(c.sum()) for c in got.values()) > 0
+    for k in range(nreq):
+        want = alone_counts(p, w, wprec, rates[k], int(seeds[k]), int(lengths[k]))
+        assert np.array_equal(got[k], want), k
+
+
+def test_slots_are_counted_against_the_state_byte_cap():
+    m = snn()
+    p = synth.diehl_cook_params(100)
+    net = m.Network(p, w_init=synth.weights(784, 100))
+    per = m.snn_serve_slot_bytes(net.handle)
+    assert per > 100 * 16
+    with pytest.raises(m.SNNError) as e:
+        m.snn_serve_create(net.handle, 10, per - 1)
+    assert e.value.status == m.SNN_ERR_CAPACITY
+    srv = m.snn_serve_create(net.handle, 10, 3 * per)
+    assert m.snn_serve_status(srv)["slots"] == 3
+    m.snn_serve_destroy(srv)
