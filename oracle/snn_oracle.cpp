@@ -32,8 +32,10 @@
 //              spike = (ref was 0) && v >= thresh + (R)theta[j]; spike -> v=reset, ref=R_e.
 //   O4 inh:    the same with the inhibitory constants, I_inh and no theta.
 //   O5 traces: x_pre = x_pre*a_x + s_in; x_post = x_post*a_x + s_e.
-//   O6 STDP:   delta_b[i,j] = nu_post*x_pre[b,i]*s_e[b,j] - nu_pre*s_in[b,i]*x_post[b,j];
-//              D = red_b delta_b  (sum: ascending-b sum; mean: sum / B; max: signed max);
+//   O6 STDP:   pot_b[i,j] = nu_post*x_pre[b,i]*s_e[b,j],  dep_b[i,j] = nu_pre*s_in[b,i]*x_post[b,j];
+//              sum:  D = P - Q with P = sum_b pot_b and Q = sum_b dep_b, each in ascending b;
+//              mean: D = (P - Q) / B;
+//              max:  D = max_b (pot_b - dep_b)  (signed per-parameter maximum);
 //              W = min(max(W + D, w_min), w_max).
 //   O7 theta:  theta = theta*a_theta + theta_plus*r_j, FP64, r_j = red_b s_e[b,j].
 //   O8 constants: a_* = (R)exp(-dt/tau) from double; a_theta = exp(-dt/tau_theta)
@@ -215,7 +217,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
 
     std::vector<uint8_t> s_in((size_t)B * NI), se_new((size_t)B * N), si_new((size_t)B * N);
     std::vector<R> I_in((size_t)B * N), I_lat((size_t)B * N), I_inh((size_t)B * N);
-    std::vector<R> D((size_t)NI * N);
+    std::vector<R> D((size_t)NI * N), Q((size_t)NI * N);
     std::vector<R> Wr(P->wprec == 0 ? 0 : (size_t)NI * N);
     std::vector<double> scale(P->wprec == 2 ? (size_t)N : 0);
 
@@ -325,9 +327,10 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
 
         // O6 STDP reduced over the batch, O7 adaptive thresholds.
         if (learn) {
-            // Identity of the reduction: 0 for sum and mean, -inf for max.
+            // max: D = max over b of (pot - dep), from -inf.  sum and mean: the
+            // potentiation and depression sums P (in D) and Q, from 0.
             const R init = (reduce == 2) ? -std::numeric_limits<R>::infinity() : (R)0;
-            for (size_t k = 0; k < D.size(); ++k) D[k] = init;
+            for (size_t k = 0; k < D.size(); ++k) { D[k] = init; Q[k] = (R)0; }
             for (int b = 0; b < B; ++b) {
                 for (int i = 0; i < NI; ++i) {
                     const R xp = x_pre[(size_t)b * NI + i];
@@ -338,15 +341,20 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                         pot = pot * (R)se_new[k];
                         R dep = nu_pre * si;
                         dep = dep * x_post[k];
-                        const R delta = pot - dep;
-                        R& acc = D[(size_t)i * N + j];
-                        if (reduce == 2) acc = delta > acc ? delta : acc;
-                        else acc = acc + delta;      // ascending-b sum
+                        const size_t ij = (size_t)i * N + j;
+                        if (reduce == 2) {
+                            const R delta = pot - dep;
+                            D[ij] = delta > D[ij] ? delta : D[ij];
+                        } else {                     // ascending-b sums
+                            D[ij] = D[ij] + pot;
+                            Q[ij] = Q[ij] + dep;
+                        }
                     }
                 }
             }
             for (int k = 0; k < NI * N; ++k) {
                 R d = D[k];
+                if (reduce != 2) d = d - Q[k];
                 if (reduce == 1) d = d / (R)B;
                 R w = W[k] + d;
                 w = w < w_min ? w_min : w;
