@@ -38,7 +38,7 @@ constexpr int CAPS = 32;                   // active inputs per sample staged in
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
 constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
-constexpr int XQ = 2;                      // post samples per column whose x_pre is preloaded
+constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -525,94 +525,87 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             }
 
             // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.
-            //     The column's first XQ post samples' x_pre values are loaded
-            //     (coalesced) for several tasks before any is processed.
+            //     Potentiation runs over the column's post-spiking samples, the
+            //     same for every lane, XC at a time with their x_pre loads issued
+            //     together; depression over the lane's own (input spike and
+            //     neuron-has-fired) samples.  Both in ascending b.
             {
                 const int npc = s_nq;
                 const int nch = (NI + 31) / 32;
                 const int ntask = npc * nch;
-                for (int u0 = warp; u0 < ntask; u0 += NW * 4) {
-                    float xk[4][XQ];
-                    int jlq[4], iq[4];
+                for (int u = warp; u < ntask; u += NW) {
+                    const int jl = pcol[u / nch];
+                    const int i = (u % nch) * 32 + lane;
+                    const bool vi = i < NI;
+                    const uint32_t* Pi = preS + (vi ? i : 0) * PS;
+                    const bool is_max = c.reduce == SNN_REDUCE_MAX;
+                    float pot = is_max ? -FLT_MAX : 0.0f;   // max: running max of pot - dep
+                    int nev = 0;
+                    int w = 0;
+                    uint32_t qb = Qm[jl];
+                    for (;;) {
+                        int bs[XC];
+                        int n = 0;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int u = u0 + q * NW;
-                        jlq[q] = -1;
-                        iq[q] = 0;
-                        int bs[XQ], k = 0;
-#pragma unroll
-                        for (int z = 0; z < XQ; ++z) bs[z] = 0;
-                        if (u < ntask) {
-                            jlq[q] = pcol[u / nch];
-                            iq[q] = (u % nch) * 32 + lane;
-                            for (int w = 0; w < Bw && k < XQ; ++w) {
-                                uint32_t qb = Qm[w * nc + jlq[q]];
-                                while (qb && k < XQ) {
-                                    const int bit = __ffs(qb) - 1;
-                                    qb &= qb - 1;
-#pragma unroll
-                                    for (int z = 0; z < XQ; ++z)
-                                        if (k == z) bs[z] = w * 32 + bit;
-                                    ++k;
-                                }
+                        for (int z = 0; z < XC; ++z) {
+                            while (qb == 0u && w + 1 < Bw) qb = Qm[++w * nc + jl];
+                            bs[z] = -1;
+                            if (qb) {
+                                const int bit = __ffs(qb) - 1;
+                                qb &= qb - 1;
+                                bs[z] = w * 32 + bit;
+                                n = z + 1;
                             }
                         }
+                        if (n == 0) break;
+                        float xv[XC];
 #pragma unroll
-                        for (int z = 0; z < XQ; ++z)
-                            xk[q][z] = (z < k && iq[q] < NI) ? __ldcg(&xpre[(size_t)bs[z] * NI + iq[q]])
-                                                            : 0.0f;
+                        for (int z = 0; z < XC; ++z)
+                            xv[z] = (bs[z] >= 0 && vi) ? __ldcg(&xpre[(size_t)bs[z] * NI + i]) : 0.0f;
+#pragma unroll
+                        for (int z = 0; z < XC; ++z) {
+                            if (bs[z] < 0) continue;
+                            const float a = __fmul_rn(c.nu_post, xv[z]);
+                            if (is_max) {
+                                const int b = bs[z];
+                                const bool pre = vi && ((Pi[b >> 5] >> (b & 31)) & 1u);
+                                const float e = pre ? __fmul_rn(c.nu_pre, xps[b * nc + jl]) : 0.0f;
+                                pot = fmaxf(pot, __fsub_rn(a, e));
+                            } else {
+                                pot = __fadd_rn(pot, a);
+                            }
+                            ++nev;
+                        }
+                        if (n < XC) break;
                     }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int jl = jlq[q], i = iq[q];
-                        if (jl < 0 || i >= NI) continue;
-                        const uint32_t* Pi = preS + i * PS;
-                        float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
-                        int nev = 0, kq = 0;
-                        uint32_t words = Bw <= 32 ? (nzP[i] | nzQw[jl]) : 0xFFFFFFFFu;
-                        for (int w = 0; w < Bw; ++w) {
-                            if (Bw <= 32) {
-                                if (!words) break;
-                                w = __ffs(words) - 1;
-                                words &= words - 1;
-                            }
-                            const uint32_t p = Pi[w];
-                            const uint32_t qq = Qm[w * nc + jl];
-                            uint32_t m = (p & Sm[w * nc + jl]) | qq;
-                            while (m) {
-                                const int bit = __ffs(m) - 1;
-                                m &= m - 1;
-                                const int b = w * 32 + bit;
-                                float a = 0.0f, e = 0.0f;
-                                if ((qq >> bit) & 1u) {
-                                    float xv;
-                                    if (kq < XQ) {
-                                        xv = xk[q][0];
-#pragma unroll
-                                        for (int z = 1; z < XQ; ++z) xv = kq == z ? xk[q][z] : xv;
-                                    } else {
-                                        xv = __ldcg(&xpre[(size_t)b * NI + i]);
-                                    }
-                                    ++kq;
-                                    a = __fmul_rn(c.nu_post, xv);
-                                }
-                                if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
-                                const float dl = __fsub_rn(a, e);
-                                if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
-                                else acc = __fadd_rn(acc, dl);
-                                ++nev;
-                            }
+                    if (!vi) continue;
+                    // depression: input i fired in b, and j has fired in b this episode
+                    float dep = 0.0f;
+                    uint32_t words = Bw <= 32 ? nzP[i] : 0xFFFFFFFFu;
+                    for (int ww = 0; ww < Bw; ++ww) {
+                        if (Bw <= 32) {
+                            if (!words) break;
+                            ww = __ffs(words) - 1;
+                            words &= words - 1;
                         }
-                        if (nev > 0) {
-                            float D = acc;
-                            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
-                            if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
-                            float wv = __fadd_rn(Ws[i * nc + jl], D);
-                            wv = wv < c.w_min ? c.w_min : wv;
-                            wv = wv > c.w_max ? c.w_max : wv;
-                            Ws[i * nc + jl] = wv;
+                        uint32_t m = Pi[ww] & Sm[ww * nc + jl];
+                        if (is_max) m &= ~Qm[ww * nc + jl];     // post samples were handled above
+                        while (m) {
+                            const int bit = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int b = ww * 32 + bit;
+                            const float e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
+                            if (is_max) { pot = fmaxf(pot, __fsub_rn(0.0f, e)); ++nev; }
+                            else dep = __fadd_rn(dep, e);
                         }
                     }
+                    float D = is_max ? pot : __fsub_rn(pot, dep);
+                    if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
+                    if (is_max && nev < B) D = fmaxf(D, 0.0f);
+                    float wv = __fadd_rn(Ws[i * nc + jl], D);
+                    wv = wv < c.w_min ? c.w_min : wv;
+                    wv = wv > c.w_max ? c.w_max : wv;
+                    Ws[i * nc + jl] = wv;
                 }
             }
             __syncthreads();

@@ -265,7 +265,9 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
     const int i_end = min(c.n_in, (int)(blockIdx.y + 1) * STDP_ROWS);
     for (int i = blockIdx.y * STDP_ROWS + warp; i < i_end; i += 8) {
         const uint32_t* P = d.preT + ((size_t)(tt % 3ull) * c.n_in + i) * c.Bw;
-        float acc = (REDUCE == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
+        // max: running maximum of pot - dep; sum and mean: the potentiation and
+        // depression sums, each in ascending b, subtracted at the end.
+        float acc = (REDUCE == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f, dep_sum = 0.0f;
         int nev = 0;
         if (vj) {
             for (int w = 0; w < c.Bw; ++w) {
@@ -279,15 +281,18 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
                     if ((q >> bit) & 1u)
                         a = __fmul_rn(c.nu_post, xp_cur[(size_t)b * c.n_in + i]);
                     if ((p >> bit) & 1u) e = __fmul_rn(c.nu_pre, d.x_post[(size_t)b * c.N + j]);
-                    const float dl = __fsub_rn(a, e);
-                    if (REDUCE == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
-                    else acc = __fadd_rn(acc, dl);
+                    if (REDUCE == SNN_REDUCE_MAX) {
+                        acc = fmaxf(acc, __fsub_rn(a, e));
+                    } else {
+                        acc = __fadd_rn(acc, a);
+                        dep_sum = __fadd_rn(dep_sum, e);
+                    }
                     ++nev;
                 }
             }
         }
         if (nev > 0) {
-            float D = acc;
+            float D = REDUCE == SNN_REDUCE_MAX ? acc : __fsub_rn(acc, dep_sum);
             if (REDUCE == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
             if (REDUCE == SNN_REDUCE_MAX && nev < c.B) D = fmaxf(D, 0.0f);  // idle samples add 0
             float wv = d.W[(size_t)i * c.N + j];
