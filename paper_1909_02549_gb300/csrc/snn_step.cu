@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
         }
         if (nev > 0) {
             float D = REDUCE == SNN_REDUCE_MAX ? acc : __fsub_rn(acc, dep_sum);
-            if (REDUCE == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
+            if (REDUCE == SNN_REDUCE_MEAN) D = batch_mean(c, D);
             if (REDUCE == SNN_REDUCE_MAX && nev < c.B) D = fmaxf(D, 0.0f);  // idle samples add 0
             float wv = d.W[(size_t)i * c.N + j];
             wv = __fadd_rn(wv, D);
