@@ -38,30 +38,37 @@ constexpr int CAPS = 32;                   // active inputs per sample staged in
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
 constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
+static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
     int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
-    size_t o_ws, o_xps, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
+    int nst;                     // row stride (floats) of the weight and depression-term tiles
+    size_t o_ws, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
     // union region (phase-local)
     size_t o_cnts, o_actn, o_acts;    // neuron phase
     size_t o_pres, o_nzp, o_pcol, o_nzqw;   // STDP phase
+    size_t o_off, o_lst;              // STDP phase: per-input lists of spiking samples
     int ps;                           // row stride of the staged input-major masks
+    int lcap;                         // list entries that fit
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-Layout make_layout(const Consts& c, int G) {
+// `budget` is the dynamic shared memory one CTA may take; what the fixed parts
+// leave of it holds the per-input sample lists of the STDP phase.
+Layout make_layout(const Consts& c, int G, size_t budget) {
     Layout L{};
     L.G = G;
     L.ncmax = (c.N + G - 1) / G;
     L.spc = (c.B + G - 1) / G;
+    L.nst = (L.ncmax + 3) & ~3;                           // 16-byte rows: 4 columns per load
     size_t o = 0;
-    L.o_ws = o;  o = align16(o + (size_t)c.n_in * L.ncmax * 4);
-    L.o_xps = o; o = align16(o + (size_t)c.B * L.ncmax * 4);
+    L.o_ws = o;  o = align16(o + (size_t)c.n_in * L.nst * 4);
+    L.o_es = o;  o = align16(o + (size_t)c.B * L.nst * 4);
     L.o_sm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
     L.o_qm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
     L.o_nzq = o; o = align16(o + (size_t)L.ncmax * 4);
@@ -78,6 +85,18 @@ Layout make_layout(const Consts& c, int G) {
     L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
     L.o_pcol = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
     L.o_nzqw = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
+    L.o_off = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)(c.n_in + 1) * 4);
+    L.o_lst = o + u_stdp;
+    {
+        const size_t used = o + u_stdp;
+        size_t cap = budget > used ? (budget - used) / 2 : 0;
+        const size_t most = (size_t)c.n_in * c.B;
+        if (cap > most) cap = most;
+        if (cap > ((size_t)1 << 30)) cap = (size_t)1 << 30;
+        if (c.B > 65536) cap = 0;                         // sample indices are 16-bit
+        L.lcap = (int)(cap & ~(size_t)7);
+        u_stdp = align16(u_stdp + (size_t)L.lcap * 2);
+    }
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
     if (u_enc > u) u = u_enc;
@@ -177,14 +196,13 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
 }
 
 // One LIF update of the excitatory/inhibitory pair (b, j); same operations in
-// the same order as the per-step kernel.  Kept out of line: the batched loop
-// that calls it then fits 1024 threads without register spills.
+// the same order as the per-step kernel.
 struct Item {
     float v, vi, x;
     uint32_t st;      // packed refractory counters and this step's spike flags
 };
 
-__device__ __noinline__ Item neuron_update(const Consts* cp, Item it, float I, int C, float thj) {
+__device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I, int C, float thj) {
     const Consts& c = *cp;
     int ref_e = (int)(it.st & 0xFFu), ref_i = (int)((it.st >> 8) & 0xFFu);
     const int se_prev = (it.st & ST_SE) ? 1 : 0, si_prev = (it.st & ST_SI) ? 1 : 0;
@@ -218,14 +236,99 @@ __device__ __noinline__ Item neuron_update(const Consts* cp, Item it, float I, i
     return o;
 }
 
-constexpr int NB = 2;   // neuron items per thread whose state loads are issued together
+constexpr int NB = 1;   // neuron items per thread whose state loads are issued together
+
+// STDP for the columns without a post spike this step: depression only,
+// D_ij = sum over the samples b whose input i fired of (0 - e_bj), e_bj =
+// nu_pre x_post[b][j] (max: the largest of those terms, and 0 when some sample
+// has none).  Two input rows per warp, one per half-warp, and four adjacent
+// columns per lane (one 16-byte load of e per sample); groups of 64 columns.
+// Every sample whose input fired is visited: where neuron j has not fired in
+// the episode its trace is exactly 0 and the term is +0, which leaves a sum
+// (never -0 here) unchanged and gives the max the 0 it takes anyway.  The sum
+// subtracts e directly: acc - e equals acc + (0 - e) bit for bit.  LISTS: the
+// row's samples come from the per-input lists, else from its spike words.
+template <bool MAX, bool LISTS>
+__device__ __forceinline__ void depress_quiet_columns(
+        const Consts& c, float* Ws, const float* Es, const uint32_t* preS, const int* offs,
+        const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
+        int warp, int lane) {
+    const float init = MAX ? -FLT_MAX : 0.0f;
+    const int h = lane >> 4;
+    for (int g0 = 0; g0 < nc; g0 += 64) {
+        const int j = g0 + 4 * (lane & 15);
+        bool v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = j + q < nc && nzQ[j + q] == 0u;
+        const bool any = v[0] || v[1] || v[2] || v[3];
+        const bool all4 = v[0] && v[1] && v[2] && v[3];
+        if (!__any_sync(FULL, any)) continue;
+        const int cj = j < nst ? j : 0;              // lanes past the tile read a valid row
+        for (int i0 = 2 * warp; i0 < NI; i0 += 2 * NW) {
+            const int i = i0 + h;
+            if (i >= NI) continue;
+            float a[4] = {init, init, init, init};
+            int n = 0;
+            auto add = [&](int b) {
+                const float4 e = *(const float4*)(Es + b * nst + cj);
+                if (MAX) {
+                    a[0] = fmaxf(a[0], __fsub_rn(0.0f, e.x));
+                    a[1] = fmaxf(a[1], __fsub_rn(0.0f, e.y));
+                    a[2] = fmaxf(a[2], __fsub_rn(0.0f, e.z));
+                    a[3] = fmaxf(a[3], __fsub_rn(0.0f, e.w));
+                } else {
+                    a[0] = __fsub_rn(a[0], e.x);
+                    a[1] = __fsub_rn(a[1], e.y);
+                    a[2] = __fsub_rn(a[2], e.z);
+                    a[3] = __fsub_rn(a[3], e.w);
+                }
+            };
+            if (LISTS) {
+                const int e0 = offs[i], e1 = offs[i + 1];
+                n = e1 - e0;
+                for (int e = e0; e < e1; ++e) add((int)lst[e]);
+            } else {
+                const uint32_t* Pi = preS + i * PS;
+                for (int w = 0; w < Bw; ++w) {
+                    uint32_t m = Pi[w];
+                    while (m) {
+                        add(w * 32 + __ffs(m) - 1);
+                        m &= m - 1;
+                        ++n;
+                    }
+                }
+            }
+            if (n == 0 || !any) continue;
+            float4 wv = *(const float4*)(Ws + i * nst + cj);
+            float* wq = &wv.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float D = a[q];
+                if (!MAX && c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
+                if (MAX && n < c.B) D = fmaxf(D, 0.0f);
+                float u = __fadd_rn(wq[q], D);
+                u = u < c.w_min ? c.w_min : u;
+                u = u > c.w_max ? c.w_max : u;
+                if (v[q]) wq[q] = u;
+            }
+            // columns with a post spike belong to the other pass: store only ours
+            if (all4) {
+                *(float4*)(Ws + i * nst + cj) = wv;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (v[q]) Ws[i * nst + cj + q] = wq[q];
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(PT, 1)
 k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, const int T,
              const __grid_constant__ Layout L) {
     extern __shared__ __align__(16) unsigned char sm[];
     float* Ws = (float*)(sm + L.o_ws);
-    float* xps = (float*)(sm + L.o_xps);
+    float* Es = (float*)(sm + L.o_es);               // e_bj = nu_pre x_post[b][j] of this step
     uint32_t* Sm = (uint32_t*)(sm + L.o_sm);
     uint32_t* Qm = (uint32_t*)(sm + L.o_qm);
     uint32_t* nzQ = (uint32_t*)(sm + L.o_nzq);
@@ -236,11 +339,13 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     uint32_t* actN = (uint32_t*)(sm + L.o_actn);
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
     __shared__ int s_nq;
+    __shared__ int s_scan[NW];
 
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int G = L.G;
     const int j0 = (int)((long long)cta * c.N / G), j1 = (int)((long long)(cta + 1) * c.N / G);
     const int nc = j1 - j0;
+    const int nst = L.nst;
     const int N = c.N, B = c.B, NI = c.n_in, Bw = c.Bw;
     const int caps = CAPS < NI ? CAPS : NI;
     uint32_t* const bar = d.err + 32;             // own 128-byte line
@@ -249,15 +354,12 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     // strides of the division-free walk over (sample, column) items
     const int dq = PT / nc, dr = PT % nc;
 
-    // ---- the CTA's columns: weights, postsynaptic traces, masks, thresholds
-    for (int k = tid; k < NI * nc; k += PT) {
-        const int i = k / nc, jl = k % nc;
-        Ws[k] = d.W[(size_t)i * N + j0 + jl];
+    // ---- the CTA's columns: weights (padding columns 0), masks, thresholds
+    for (int k = tid; k < NI * nst; k += PT) {
+        const int i = k / nst, jl = k % nst;
+        Ws[k] = jl < nc ? d.W[(size_t)i * N + j0 + jl] : 0.0f;
     }
-    for (int k = tid; k < B * nc; k += PT) {
-        const int b = k / nc, jl = k % nc;
-        xps[k] = d.x_post[(size_t)b * N + j0 + jl];
-    }
+    for (int k = tid; k < B * nst; k += PT) Es[k] = 0.0f;
     for (int k = tid; k < Bw * nc; k += PT) {
         const int w = k / nc, jl = k % nc;
         Sm[k] = d.spkT[(size_t)(j0 + jl) * Bw + w];
@@ -319,7 +421,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             const int warp = tid >> 5, lane = tid & 31;
             for (int jl = warp; jl < nc; jl += NW) {
                 float m = 0.0f;
-                for (int i = lane; i < NI; i += 32) m = fmaxf(m, fabsf(Ws[i * nc + jl]));
+                for (int i = lane; i < NI; i += 32) m = fmaxf(m, fabsf(Ws[i * nst + jl]));
                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(FULL, m, o));
                 if (lane == 0) {
                     const float sc = e4m3_scale_of(m);
@@ -356,6 +458,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         it[q].st = d.st[idx];
                         it[q].v = d.v_e[idx];
                         it[q].vi = d.v_i[idx];
+                        it[q].x = d.x_post[idx];
                     }
                 }
 #pragma unroll
@@ -370,25 +473,25 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     const uint16_t* al = actS + b * CAPS;
                     const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
                     if (c.wprec == SNN_W_FP32) {
-                        for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)al[a] * nc + jl]);
-                        for (int a = caps; a < na; ++a) I = __fadd_rn(I, Ws[(int)__ldcg(&ag[a]) * nc + jl]);
+                        for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)al[a] * nst + jl]);
+                        for (int a = caps; a < na; ++a) I = __fadd_rn(I, Ws[(int)__ldcg(&ag[a]) * nst + jl]);
                     } else if (c.wprec == SNN_W_BF16) {
                         for (int a = 0; a < ns; ++a)
-                            I = __fadd_rn(I, w_read_bf16(Ws[(int)al[a] * nc + jl]));
+                            I = __fadd_rn(I, w_read_bf16(Ws[(int)al[a] * nst + jl]));
                         for (int a = caps; a < na; ++a)
-                            I = __fadd_rn(I, w_read_bf16(Ws[(int)__ldcg(&ag[a]) * nc + jl]));
+                            I = __fadd_rn(I, w_read_bf16(Ws[(int)__ldcg(&ag[a]) * nst + jl]));
                     } else {
                         const float inv = wsc[L.ncmax + jl];
                         for (int a = 0; a < ns; ++a)
-                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)al[a] * nc + jl], inv));
+                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)al[a] * nst + jl], inv));
                         for (int a = caps; a < na; ++a)
-                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)__ldcg(&ag[a]) * nc + jl], inv));
+                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)__ldcg(&ag[a]) * nst + jl], inv));
                         I = __fmul_rn(I, wsc[jl]);
                     }
-                    it[q].x = xps[b * nc + jl];
                     const Item o = neuron_update(&c, it[q], I, (int)cntS[b], thj[jl]);
                     const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
-                    xps[b * nc + jl] = o.x;
+                    Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
+                    d.x_post[idx] = o.x;
                     d.v_e[idx] = o.v;
                     d.v_i[idx] = o.vi;
                     d.st[idx] = o.st;
@@ -417,6 +520,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
             int* pcol = (int*)(sm + L.o_pcol);
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
+            int* offs = (int*)(sm + L.o_off);
+            uint16_t* lst = (uint16_t*)(sm + L.o_lst);
             const int PS = L.ps;
             for (int jl = tid; jl < nc; jl += PT) {   // theta, and which columns fired
                 int n = 0;
@@ -460,11 +565,61 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 }
             }
             __syncthreads();
-            for (int i = tid; i < NI; i += PT) {
+            // Per input i: the samples whose input i fired, ascending, in
+            // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
+            // counts.  Lists are written only while they fit; both passes walk
+            // the spike words instead when the step's total exceeds the space.
+            int n_ev = 0;
+            for (int r0 = 0; r0 < NI; r0 += PT) {
+                const int i = r0 + tid;
+                int n = 0;
                 uint32_t nz = 0;
-                for (int w = 0; w < Bw && w < 32; ++w) nz |= (preS[i * PS + w] != 0u) ? (1u << w) : 0u;
-                nzP[i] = nz;
+                if (i < NI) {
+                    for (int w = 0; w < Bw; ++w) {
+                        const uint32_t m = preS[i * PS + w];
+                        n += __popc(m);
+                        if (m && w < 32) nz |= 1u << w;
+                    }
+                    nzP[i] = nz;
+                }
+                const int wp = tid >> 5, ln = tid & 31;
+                int x = n;                                  // inclusive scan within the warp
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (ln >= o) x += y;
+                }
+                if (ln == 31) s_scan[wp] = x;
+                __syncthreads();
+                if (wp == 0) {                              // ... and over the warps
+                    int v = s_scan[ln];
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, v, o);
+                        if (ln >= o) v += y;
+                    }
+                    s_scan[ln] = v;
+                }
+                __syncthreads();
+                const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
+                if (i < NI) {
+                    offs[i] = start;
+                    if (start + n <= L.lcap) {
+                        int q = start;
+                        for (int w = 0; w < Bw; ++w) {
+                            uint32_t m = preS[i * PS + w];
+                            while (m) {
+                                lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+                                m &= m - 1;
+                            }
+                        }
+                    }
+                }
+                n_ev += s_scan[NW - 1];
+                __syncthreads();
             }
+            if (tid == 0) offs[NI] = n_ev;
+            const bool lists = n_ev <= L.lcap;
             if (tid < 32) {   // list of the columns with a post spike
                 int npc = 0;
                 for (int jl0 = 0; jl0 < nc; jl0 += 32) {
@@ -479,49 +634,17 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             __syncthreads();
             const int warp = tid >> 5, lane = tid & 31;
 
-            // (A) columns without a post spike: depression only.  Lanes walk
-            //     consecutive (row, column) pairs, so a warp shares one or a few
-            //     rows' input-spike words whatever the number of columns.
-            {
-                int i = tid / nc, jl = tid % nc;
-                for (int k = tid; k < NI * nc; k += PT) {
-                    const uint32_t nz = nzP[i];
-                    if (nzQ[jl] == 0u && (nz != 0u || Bw > 32)) {
-                        const uint32_t* Pi = preS + i * PS;
-                        float acc = (c.reduce == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f;
-                        int nev = 0;
-                        uint32_t words = Bw <= 32 ? nz : 0xFFFFFFFFu;
-                        for (int w = 0; w < Bw; ++w) {
-                            if (Bw <= 32) {
-                                if (!words) break;
-                                w = __ffs(words) - 1;
-                                words &= words - 1;
-                            }
-                            uint32_t m = Pi[w] & Sm[w * nc + jl];
-                            while (m) {
-                                const int bit = __ffs(m) - 1;
-                                m &= m - 1;
-                                const int b = w * 32 + bit;
-                                const float dl = __fsub_rn(0.0f, __fmul_rn(c.nu_pre, xps[b * nc + jl]));
-                                if (c.reduce == SNN_REDUCE_MAX) acc = fmaxf(acc, dl);
-                                else acc = __fadd_rn(acc, dl);
-                                ++nev;
-                            }
-                        }
-                        if (nev > 0) {
-                            float D = acc;
-                            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, acc);
-                            if (c.reduce == SNN_REDUCE_MAX && nev < B) D = fmaxf(D, 0.0f);
-                            float wv = __fadd_rn(Ws[k], D);
-                            wv = wv < c.w_min ? c.w_min : wv;
-                            wv = wv > c.w_max ? c.w_max : wv;
-                            Ws[k] = wv;
-                        }
-                    }
-                    i += dq;
-                    jl += dr;
-                    if (jl >= nc) { jl -= nc; ++i; }
-                }
+            // (A) columns without a post spike: depression only
+            if (c.reduce == SNN_REDUCE_MAX) {
+                if (lists)
+                    depress_quiet_columns<true, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
+                else
+                    depress_quiet_columns<true, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
+            } else {
+                if (lists)
+                    depress_quiet_columns<false, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
+                else
+                    depress_quiet_columns<false, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
             }
 
             // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.
@@ -569,7 +692,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             if (is_max) {
                                 const int b = bs[z];
                                 const bool pre = vi && ((Pi[b >> 5] >> (b & 31)) & 1u);
-                                const float e = pre ? __fmul_rn(c.nu_pre, xps[b * nc + jl]) : 0.0f;
+                                const float e = pre ? Es[b * nst + jl] : 0.0f;
                                 pot = fmaxf(pot, __fsub_rn(a, e));
                             } else {
                                 pot = __fadd_rn(pot, a);
@@ -581,8 +704,18 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     if (!vi) continue;
                     // depression: input i fired in b, and j has fired in b this episode
                     float dep = 0.0f;
-                    uint32_t words = Bw <= 32 ? nzP[i] : 0xFFFFFFFFu;
-                    for (int ww = 0; ww < Bw; ++ww) {
+                    if (lists) {   // every input-spike sample (e is 0 where j has not fired)
+                        const int e1 = offs[i + 1];
+                        for (int e = offs[i]; e < e1; ++e) {
+                            const int b = lst[e];
+                            if (is_max && ((Qm[(b >> 5) * nc + jl] >> (b & 31)) & 1u)) continue;
+                            const float ev = Es[b * nst + jl];
+                            if (is_max) { pot = fmaxf(pot, __fsub_rn(0.0f, ev)); ++nev; }
+                            else dep = __fadd_rn(dep, ev);
+                        }
+                    }
+                    uint32_t words = lists ? 0u : (Bw <= 32 ? nzP[i] : 0xFFFFFFFFu);
+                    for (int ww = 0; ww < (lists ? 0 : Bw); ++ww) {
                         if (Bw <= 32) {
                             if (!words) break;
                             ww = __ffs(words) - 1;
@@ -594,7 +727,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             const int bit = __ffs(m) - 1;
                             m &= m - 1;
                             const int b = ww * 32 + bit;
-                            const float e = __fmul_rn(c.nu_pre, xps[b * nc + jl]);
+                            const float e = Es[b * nst + jl];
                             if (is_max) { pot = fmaxf(pot, __fsub_rn(0.0f, e)); ++nev; }
                             else dep = __fadd_rn(dep, e);
                         }
@@ -602,10 +735,10 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     float D = is_max ? pot : __fsub_rn(pot, dep);
                     if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
                     if (is_max && nev < B) D = fmaxf(D, 0.0f);
-                    float wv = __fadd_rn(Ws[i * nc + jl], D);
+                    float wv = __fadd_rn(Ws[i * nst + jl], D);
                     wv = wv < c.w_min ? c.w_min : wv;
                     wv = wv > c.w_max ? c.w_max : wv;
-                    Ws[i * nc + jl] = wv;
+                    Ws[i * nst + jl] = wv;
                 }
             }
             __syncthreads();
@@ -624,13 +757,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     if (c.learn) {
         for (int k = tid; k < NI * nc; k += PT) {
             const int i = k / nc, jl = k % nc;
-            d.W[(size_t)i * N + j0 + jl] = Ws[k];
+            d.W[(size_t)i * N + j0 + jl] = Ws[i * nst + jl];
         }
         for (int jl = tid; jl < nc; jl += PT) d.theta[j0 + jl] = thS[jl];
-    }
-    for (int k = tid; k < B * nc; k += PT) {
-        const int b = k / nc, jl = k % nc;
-        d.x_post[(size_t)b * N + j0 + jl] = xps[k];
     }
     for (int k = tid; k < Bw * nc; k += PT) {
         const int w = k / nc, jl = k % nc;
@@ -666,7 +795,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     }
     const int G = su.sms < c.N ? su.sms : c.N;
     const size_t budget = su.smem_optin > 2048 ? (size_t)su.smem_optin - 2048 : 0;
-    const Layout L = make_layout(c, G);
+    const Layout L = make_layout(c, G, budget);
     if (L.bytes > budget) return cudaSuccess;
     if (su.attr_bytes < L.bytes) {
         e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
