@@ -247,9 +247,10 @@ constexpr int NB = 1;   // neuron items per thread whose state loads are issued 
 // the episode its trace is exactly 0 and the term is +0, which leaves a sum
 // (never -0 here) unchanged and gives the max the 0 it takes anyway.  The sum
 // subtracts e directly: acc - e equals acc + (0 - e) bit for bit.  LISTS: the
-// row's samples come from the per-input lists, else from its spike words.
+// row's samples come from the per-input lists, else from its spike words.  Out
+// of line, so that its loops get registers of their own inside the large kernel.
 template <bool MAX, bool LISTS>
-__device__ __forceinline__ void depress_quiet_columns(
+__device__ __noinline__ void depress_quiet_columns(
         const Consts& c, float* Ws, const float* Es, const uint32_t* preS, const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
@@ -539,86 +540,96 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 else r = n > 0 ? 1.0 : 0.0;
                 thS[jl] = __dadd_rn(__dmul_rn(thS[jl], c.a_th), __dmul_rn(c.theta_plus, r));
             }
-            {   // input-major masks of this step (written by every CTA's encode), padded rows
-                const uint32_t* src = d.preT + (size_t)p3 * NI * Bw;
-                const int n = NI * Bw;
-                if ((Bw & 3) == 0) {
-                    const uint4* s4 = (const uint4*)src;
-                    const int n4 = n >> 2;
-                    for (int k0 = tid; k0 < n4; k0 += 4 * PT) {
-                        uint4 v4[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-                            if (k0 + q * PT < n4) v4[q] = __ldcg(&s4[k0 + q * PT]);
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int k = (k0 + q * PT) << 2;
-                            if (k < n) {
-                                const int i = k / Bw, w = k % Bw;
-                                uint32_t* dst = preS + i * PS + w;
-                                dst[0] = v4[q].x; dst[1] = v4[q].y; dst[2] = v4[q].z; dst[3] = v4[q].w;
-                            }
-                        }
-                    }
-                } else {
-                    for (int k = tid; k < n; k += PT) preS[(k / Bw) * PS + (k % Bw)] = __ldcg(&src[k]);
-                }
-            }
-            __syncthreads();
             // Per input i: the samples whose input i fired, ascending, in
             // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
-            // counts.  Lists are written only while they fit; both passes walk
-            // the spike words instead when the step's total exceeds the space.
+            // counts.  One thread per row reads the row's words of this step's
+            // input-major masks (written by every CTA's encode) and keeps them
+            // in shared memory for the word walks.  Lists are written only while
+            // they fit; both passes walk the spike words instead when the step's
+            // total exceeds the space.
             int n_ev = 0;
-            for (int r0 = 0; r0 < NI; r0 += PT) {
-                const int i = r0 + tid;
-                int n = 0;
-                uint32_t nz = 0;
-                if (i < NI) {
-                    for (int w = 0; w < Bw; ++w) {
-                        const uint32_t m = preS[i * PS + w];
-                        n += __popc(m);
-                        if (m && w < 32) nz |= 1u << w;
-                    }
-                    nzP[i] = nz;
-                }
+            {
+                const uint32_t* src = d.preT + (size_t)p3 * NI * Bw;
+                const bool vec = Bw == 4 || Bw == 8;       // rows of 16 or 32 bytes, 16-byte aligned
                 const int wp = tid >> 5, ln = tid & 31;
-                int x = n;                                  // inclusive scan within the warp
+                for (int r0 = 0; r0 < NI; r0 += PT) {
+                    const int i = r0 + tid;
+                    uint32_t wr[8];                          // the row's first words
+                    int n = 0;
+                    uint32_t nz = 0;
+                    if (i < NI) {
+                        const uint32_t* row = src + (size_t)i * Bw;
+                        if (vec) {
+                            const uint4 q0 = __ldcg((const uint4*)row);
+                            const uint4 q1 = Bw == 8 ? __ldcg((const uint4*)row + 1) : make_uint4(0u, 0u, 0u, 0u);
+                            wr[0] = q0.x; wr[1] = q0.y; wr[2] = q0.z; wr[3] = q0.w;
+                            wr[4] = q1.x; wr[5] = q1.y; wr[6] = q1.z; wr[7] = q1.w;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(FULL, x, o);
-                    if (ln >= o) x += y;
-                }
-                if (ln == 31) s_scan[wp] = x;
-                __syncthreads();
-                if (wp == 0) {                              // ... and over the warps
-                    int v = s_scan[ln];
+                            for (int w = 0; w < 8; ++w) {
+                                if (w < Bw) {
+                                    preS[i * PS + w] = wr[w];
+                                    n += __popc(wr[w]);
+                                    if (wr[w]) nz |= 1u << w;
+                                }
+                            }
+                        } else {
+                            for (int w = 0; w < Bw; ++w) {
+                                const uint32_t m = __ldcg(&row[w]);
+                                preS[i * PS + w] = m;
+                                n += __popc(m);
+                                if (m && w < 32) nz |= 1u << w;
+                            }
+                        }
+                        nzP[i] = nz;
+                    }
+                    int x = n;                               // inclusive scan within the warp
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(FULL, v, o);
-                        if (ln >= o) v += y;
+                        const int y = __shfl_up_sync(FULL, x, o);
+                        if (ln >= o) x += y;
                     }
-                    s_scan[ln] = v;
-                }
-                __syncthreads();
-                const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
-                if (i < NI) {
-                    offs[i] = start;
-                    if (start + n <= L.lcap) {
-                        int q = start;
-                        for (int w = 0; w < Bw; ++w) {
-                            uint32_t m = preS[i * PS + w];
-                            while (m) {
-                                lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
-                                m &= m - 1;
+                    if (ln == 31) s_scan[wp] = x;
+                    __syncthreads();
+                    if (wp == 0) {                           // ... and over the warps
+                        int v = s_scan[ln];
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int y = __shfl_up_sync(FULL, v, o);
+                            if (ln >= o) v += y;
+                        }
+                        s_scan[ln] = v;
+                    }
+                    __syncthreads();
+                    const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
+                    if (i < NI) {
+                        offs[i] = start;
+                        if (start + n <= L.lcap) {
+                            int q = start;
+                            if (vec) {
+#pragma unroll
+                                for (int w = 0; w < 8; ++w) {
+                                    uint32_t m = w < Bw ? wr[w] : 0u;
+                                    while (m) {
+                                        lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+                                        m &= m - 1;
+                                    }
+                                }
+                            } else {
+                                for (int w = 0; w < Bw; ++w) {
+                                    uint32_t m = preS[i * PS + w];
+                                    while (m) {
+                                        lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+                                        m &= m - 1;
+                                    }
+                                }
                             }
                         }
                     }
+                    n_ev += s_scan[NW - 1];
+                    if (r0 + PT < NI) __syncthreads();       // s_scan is rewritten by the next rows
                 }
-                n_ev += s_scan[NW - 1];
-                __syncthreads();
+                if (tid == 0) offs[NI] = n_ev;
             }
-            if (tid == 0) offs[NI] = n_ev;
             const bool lists = n_ev <= L.lcap;
             if (tid < 32) {   // list of the columns with a post spike
                 int npc = 0;
