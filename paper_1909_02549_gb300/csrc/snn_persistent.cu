@@ -40,6 +40,9 @@ constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
+constexpr int QT = 16;                     // neuron items per thread that tensor memory holds
+constexpr int TMEM_COLS = 512;             // all of the SM's tensor memory: 8 warp groups x QT x 4 words
+static_assert(8 * QT * 4 == TMEM_COLS, "tensor-memory columns per warp group");
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -52,6 +55,7 @@ struct Layout {
     size_t o_off, o_lst;              // STDP phase: per-input lists of spiking samples
     int ps;                           // row stride of the staged input-major masks
     int lcap;                         // list entries that fit
+    int tstate;                       // neuron state held in tensor memory (else in global memory)
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
@@ -81,6 +85,7 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
     L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
+    L.tstate = (size_t)c.B * L.ncmax <= (size_t)QT * PT;
     L.o_pres = o;                u_stdp = align16((size_t)c.n_in * L.ps * 4);
     L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
     L.o_pcol = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
@@ -236,7 +241,29 @@ __device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I
     return o;
 }
 
-constexpr int NB = 1;   // neuron items per thread whose state loads are issued together
+// Tensor memory as per-thread storage of the neuron state.  A thread's items
+// live in its own TMEM lane (32 x (warp mod 4) + lane id: the lanes a warp may
+// access) at columns 4q .. 4q+3 of its warp group's block (warp / 4); the
+// 32x32b shape moves four consecutive columns of each lane of the warp.  The
+// wait is in the same statement as the load, so no register is read early.
+__device__ __forceinline__ void tmem_ld4(uint32_t ta, Item& it) {
+    uint32_t a, b, x, st;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(a), "=r"(b), "=r"(x), "=r"(st) : "r"(ta) : "memory");
+    it.v = __uint_as_float(a);
+    it.vi = __uint_as_float(b);
+    it.x = __uint_as_float(x);
+    it.st = st;
+}
+__device__ __forceinline__ void tmem_st4(uint32_t ta, const Item& it) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(ta), "r"(__float_as_uint(it.v)), "r"(__float_as_uint(it.vi)),
+                    "r"(__float_as_uint(it.x)), "r"(it.st) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // STDP for the columns without a post spike this step: depression only,
 // D_ij = sum over the samples b whose input i fired of (0 - e_bj), e_bj =
@@ -341,6 +368,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
     __shared__ int s_nq;
     __shared__ int s_scan[NW];
+    __shared__ uint32_t s_tmem;
 
     const int cta = blockIdx.x, tid = threadIdx.x;
     const int G = L.G;
@@ -366,6 +394,39 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         Sm[k] = d.spkT[(size_t)(j0 + jl) * Bw + w];
     }
     for (int jl = tid; jl < nc; jl += PT) thS[jl] = d.theta[j0 + jl];
+
+    // ---- neuron state of the CTA's (sample, column) items into tensor memory
+    const bool tstate = L.tstate != 0;
+    const int BN = B * nc, QN = (BN + PT - 1) / PT;   // items, and items per thread
+    uint32_t tq = 0;                                  // this thread's tensor-memory block
+    if (tstate) {
+        if (tid < 32) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"((uint32_t)__cvta_generic_to_shared(&s_tmem)), "r"(TMEM_COLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tmem_fence_before();
+        __syncthreads();
+        tmem_fence_after();
+        tq = s_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * QT * 4);
+        int b = tid / nc, jl = tid % nc;
+        for (int q = 0; q < QN; ++q) {
+            Item it{0.0f, 0.0f, 0.0f, 0u};
+            if (tid + q * PT < BN) {
+                const size_t idx = (size_t)b * N + j0 + jl;
+                it.v = d.v_e[idx];
+                it.vi = d.v_i[idx];
+                it.x = d.x_post[idx];
+                it.st = d.st[idx];
+            }
+            __syncwarp();
+            tmem_st4(tq + 4 * q, it);
+            b += dq;
+            jl += dr;
+            if (jl >= nc) { jl -= nc; ++b; }
+        }
+        tmem_wait_st();
+    }
 
     // ---- prologue: input spikes of the first step
     if (cta == 0)
@@ -434,39 +495,22 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         __syncthreads();
 
         {
-            const int BN = B * nc;
-            int b0 = tid / nc, jl0 = tid % nc;
-            for (int k0 = tid; k0 < BN; k0 += NB * PT) {
-                int bq[NB], jq[NB];
-                Item it[NB];
-                {
-                    int b = b0, jl = jl0;
-#pragma unroll
-                    for (int q = 0; q < NB; ++q) {
-                        bq[q] = b;
-                        jq[q] = jl;
-                        b += dq;
-                        jl += dr;
-                        if (jl >= nc) { jl -= nc; ++b; }
-                    }
-                    b0 = b;
-                    jl0 = jl;
+            int b = tid / nc, jl = tid % nc;
+            for (int q = 0; q < QN; ++q) {
+                const bool valid = tid + q * PT < BN;
+                const int j = j0 + jl;
+                const size_t idx = (size_t)b * N + j;
+                Item it{0.0f, 0.0f, 0.0f, 0u};
+                if (tstate) {
+                    __syncwarp();
+                    tmem_ld4(tq + 4 * q, it);
+                } else if (valid) {
+                    it.st = d.st[idx];
+                    it.v = d.v_e[idx];
+                    it.vi = d.v_i[idx];
+                    it.x = d.x_post[idx];
                 }
-#pragma unroll
-                for (int q = 0; q < NB; ++q) {          // all state loads first
-                    if (k0 + q * PT < BN) {
-                        const size_t idx = (size_t)bq[q] * N + j0 + jq[q];
-                        it[q].st = d.st[idx];
-                        it[q].v = d.v_e[idx];
-                        it[q].vi = d.v_i[idx];
-                        it[q].x = d.x_post[idx];
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < NB; ++q) {
-                    if (k0 + q * PT >= BN) break;
-                    const int b = bq[q], jl = jq[q], j = j0 + jl;
-                    const size_t idx = (size_t)b * N + j;
+                if (valid) {
                     // synaptic current: ascending active inputs of sample b
                     float I = 0.0f;
                     const int na = (int)actN[b];
@@ -489,13 +533,15 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             I = __fadd_rn(I, w_read_e4m3(Ws[(int)__ldcg(&ag[a]) * nst + jl], inv));
                         I = __fmul_rn(I, wsc[jl]);
                     }
-                    const Item o = neuron_update(&c, it[q], I, (int)cntS[b], thj[jl]);
+                    const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
                     const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
                     Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
-                    d.x_post[idx] = o.x;
-                    d.v_e[idx] = o.v;
-                    d.v_i[idx] = o.vi;
-                    d.st[idx] = o.st;
+                    if (!tstate) {
+                        d.x_post[idx] = o.x;
+                        d.v_e[idx] = o.v;
+                        d.v_i[idx] = o.vi;
+                        d.st[idx] = o.st;
+                    }
                     if (se) {
                         d.counts[idx] += 1u;
                         const uint32_t bit = 1u << (b & 31);
@@ -509,8 +555,17 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         if (c.rec_raster)
                             atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
                     }
+                    it = o;
                 }
+                if (tstate) {
+                    __syncwarp();
+                    tmem_st4(tq + 4 * q, it);
+                }
+                b += dq;
+                jl += dr;
+                if (jl >= nc) { jl -= nc; ++b; }
             }
+            if (tstate) tmem_wait_st();
         }
         __syncthreads();
 
@@ -763,8 +818,33 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
     }
 
-    // ---- write the CTA's columns back
+    // ---- write the CTA's columns back, and the neuron state held in tensor memory
     __syncthreads();
+    if (tstate) {
+        int b = tid / nc, jl = tid % nc;
+        for (int q = 0; q < QN; ++q) {
+            Item it;
+            __syncwarp();
+            tmem_ld4(tq + 4 * q, it);
+            if (tid + q * PT < BN) {
+                const size_t idx = (size_t)b * N + j0 + jl;
+                d.v_e[idx] = it.v;
+                d.v_i[idx] = it.vi;
+                d.x_post[idx] = it.x;
+                d.st[idx] = it.st;
+            }
+            b += dq;
+            jl += dr;
+            if (jl >= nc) { jl -= nc; ++b; }
+        }
+        tmem_fence_before();
+        __syncthreads();
+        if (tid < 32) {
+            tmem_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                         :: "r"(s_tmem), "r"(TMEM_COLS) : "memory");
+        }
+    }
     if (c.learn) {
         for (int k = tid; k < NI * nc; k += PT) {
             const int i = k / nc, jl = k % nc;
