@@ -181,8 +181,10 @@ SNN_API snn_status snn_read_state(snn_net* net, int field, void* dst, size_t byt
  * and resumes a simulation.  Writable: V_EXC, V_INH, X_PRE, X_POST, REF_EXC,
  * REF_INH, SPIKES_EXC, SPIKES_INH (the network must hold a batch: run once
  * with it, T may be 0), THETA, and STEP (the step counter a continuing run
- * starts from).  The library re-derives what it keeps alongside (which samples
- * have a non-zero postsynaptic trace, the previous step's inhibitory counts).
+ * starts from; the other fields keep their values, so fields and STEP may be
+ * written in either order).  The library re-derives what it keeps alongside
+ * (which samples have a non-zero postsynaptic trace, the previous step's
+ * inhibitory counts).
  * Synchronises.  Errors: SNN_ERR_ARG (unknown or read-only field, size
  * mismatch, NULL src), SNN_ERR_STATE (no batch allocated), SNN_ERR_CUDA. */
 SNN_API snn_status snn_write_state(snn_net* net, int field, const void* src, size_t bytes,

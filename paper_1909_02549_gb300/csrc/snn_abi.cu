@@ -145,9 +145,9 @@ snn_status alloc_batch(snn_net* n, int B) {
     snn::Bufs& d = n->d;
     CUDA_TRY(n, dalloc(&d.thr, (size_t)B * NI));
     CUDA_TRY(n, dalloc(&d.seeds, (size_t)B));
-    CUDA_TRY(n, dalloc(&d.x_pre, 2 * (size_t)B * NI));
+    CUDA_TRY(n, dalloc(&d.x_pre, snn::XPRE_SLOTS * (size_t)B * NI));
     CUDA_TRY(n, dalloc(&d.inb, 2 * (size_t)B * Iw));
-    CUDA_TRY(n, dalloc(&d.preT, 3 * NI * Bw));
+    CUDA_TRY(n, dalloc(&d.preT, snn::PRET_SLOTS * NI * Bw));
     CUDA_TRY(n, dalloc(&d.act_idx, 2 * (size_t)B * NI));
     CUDA_TRY(n, dalloc(&d.act_cnt, 2 * (size_t)B));
     CUDA_TRY(n, dalloc(&d.v_e, (size_t)B * N));
@@ -627,6 +627,20 @@ snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes,
         default: break;
     }
     const snn::Consts c = make_consts(n, n->B, 1.0f, 0, 0, 0);
+    if (field == SNN_FIELD_STEP && n->B > 0) {
+        // The presynaptic traces and the inhibitory counts of the last step sit
+        // in ring slots chosen by the step counter: move them with it.
+        unsigned long long old_step = 0, new_step = 0;
+        CUDA_TRY(n, cudaMemcpy(&old_step, n->d.step + 1, 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(n, cudaMemcpy(&new_step, src, 8, kind == cudaMemcpyDeviceToDevice
+                                                      ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        const size_t nx = (size_t)n->B * n->spec.n_in;
+        const unsigned long long S = snn::XPRE_SLOTS;
+        const size_t from = (size_t)((old_step + S - 1) % S), to = (size_t)((new_step + S - 1) % S);
+        if (from != to)
+            CUDA_TRY(n, cudaMemcpyAsync(n->d.x_pre + to * nx, n->d.x_pre + from * nx, nx * 4,
+                                        cudaMemcpyDeviceToDevice, st));
+    }
     if (dst) {
         CUDA_TRY(n, cudaMemcpyAsync(dst, src, want, kind, st));
     } else {   // fields stored in another layout: stage, then insert on the device
@@ -647,6 +661,8 @@ snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes,
     if (per_sample) {
         CUDA_TRY(n, snn::launch_derive(c, n->d, st));
         n->state_valid = true;
+    } else if (field == SNN_FIELD_STEP && n->B > 0) {
+        CUDA_TRY(n, snn::launch_derive(c, n->d, st));   // counts into the new step's slot
     }
     CUDA_TRY(n, cudaStreamSynchronize(st));
     return SNN_OK;

@@ -40,9 +40,9 @@ struct Bufs {
     double* theta;       // [N]        adaptive thresholds (FP64)
     uint32_t* thr;       // [B][n_in]  Poisson thresholds of this run
     uint64_t* seeds;     // [B]        per-sample Poisson seeds
-    float* x_pre;        // [2][B][n_in] presynaptic traces after step tt
+    float* x_pre;        // [XPRE_SLOTS][B][n_in] presynaptic traces after step tt (slot tt % 3)
     uint32_t* inb;       // [2][B][Iw]   input spikes of step tt, sample-major bits
-    uint32_t* preT;      // [3][n_in][Bw] input spikes of step tt, input-major bits
+    uint32_t* preT;      // [PRET_SLOTS][n_in][Bw] input spikes of step tt, input-major bits (slot tt % 4)
     uint16_t* act_idx;   // [2][B][n_in] active inputs of step tt, ascending (persistent form)
     uint32_t* act_cnt;   // [2][B]
     float* v_e;          // [B][N]
@@ -62,6 +62,13 @@ struct Bufs {
 };
 
 // Packed per-(b,j) state word.
+// Ring depths of the per-step input buffers.  In the persistent form a CTA
+// encodes step tt+1 and signals it before running the STDP of step tt, so the
+// traces and masks of step tt are still read while other CTAs run step tt+1:
+// three trace slots and four mask slots keep every overwrite behind a barrier
+// that all readers have passed.  The per-step kernels use the same slots.
+constexpr int XPRE_SLOTS = 3;
+constexpr int PRET_SLOTS = 4;
 constexpr uint32_t ST_SE = 1u << 16;
 constexpr uint32_t ST_SI = 1u << 17;
 

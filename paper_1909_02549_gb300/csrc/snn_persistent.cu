@@ -115,15 +115,22 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// Grid-wide barrier with a bounded wait.  Returns false if this or another
-// CTA gave up (device error bit 1).
-__device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target, unsigned limit) {
-    __shared__ int s_fail;
+// Grid-wide barrier in two halves.  grid_arrive: the CTA's writes so far are
+// released and counted.  grid_wait: bounded wait until every CTA has arrived
+// `target` times in all, then acquire; returns false if this or another CTA
+// gave up (device error bit 1).  Work between the halves overlaps the wait.
+__device__ void grid_arrive(uint32_t* ctr) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        int fail = 0;
         __threadfence();
         atomicAdd(ctr, 1u);
+    }
+}
+
+__device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigned limit) {
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        int fail = 0;
         unsigned spins = 0, ns = 32;
         while (ld_acquire(ctr) < target) {
             if ((++spins & 31u) == 0u && ld_acquire(err) != 0u) { fail = 1; break; }
@@ -138,12 +145,12 @@ __device__ bool grid_sync(uint32_t* ctr, uint32_t* err, unsigned target, unsigne
     return s_fail == 0;
 }
 
-// Poisson input spikes of step tt for this CTA's samples (b = cta + G*r),
-// presynaptic traces, input-major masks, and ascending active-input lists.
 __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
                              unsigned long long tt, int t_local) {
     const int cta = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cur = (int)(tt & 1ull), prv = cur ^ 1, p3 = (int)(tt % 3ull);
+    const int cur = (int)(tt & 1ull);
+    const int xc = (int)(tt % XPRE_SLOTS), xp = (int)((tt + XPRE_SLOTS - 1) % XPRE_SLOTS);
+    const int pm = (int)(tt % PRET_SLOTS);
     uint32_t* wbuf = (uint32_t*)(sm + L.o_wbuf);
     const int nmy = cta < c.B ? (c.B - cta + L.G - 1) / L.G : 0;
     const size_t nbi = (size_t)c.B * c.n_in;
@@ -161,11 +168,11 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
                 const uint32_t h = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32);
                 s = h < thr ? 1u : 0u;
             }
-            float x = __ldcg(&d.x_pre[(size_t)prv * nbi + o]);
+            float x = __ldcg(&d.x_pre[(size_t)xp * nbi + o]);
             x = __fmul_rn(x, c.a_x);
             x = __fadd_rn(x, s ? 1.0f : 0.0f);
-            d.x_pre[(size_t)cur * nbi + o] = x;
-            if (s) atomicOr(&d.preT[((size_t)p3 * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
+            d.x_pre[(size_t)xc * nbi + o] = x;
+            if (s) atomicOr(&d.preT[((size_t)pm * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
         }
         const uint32_t word = __ballot_sync(FULL, s);
         if (lane == 0) {
@@ -433,8 +440,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         for (int b = tid; b < B; b += PT) d.cnt[(size_t)(base % 3ull) * B + b] = 0u;
     encode_phase(c, d, L, sm, base, 0);
     unsigned nbar = 1;
+    grid_arrive(bar);
     // (test knob: wait for one arrival more than there are CTAs, with a short limit)
-    bool ok = grid_sync(bar, d.err, G * nbar + (c.test_timeout ? 1u : 0u),
+    bool ok = grid_wait(bar, d.err, G * nbar + (c.test_timeout ? 1u : 0u),
                         c.test_timeout ? TEST_SPIN_LIMIT : SPIN_LIMIT);
 
     for (int t = 0; t < T && ok; ++t) {
@@ -451,9 +459,10 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             thj[jl] = __fadd_rn(c.e_thresh, __double2float_rn(thS[jl]));
         if (cta == 0)   // accumulator of the next step (its last reader was step tt-1)
             for (int b = tid; b < B; b += PT) d.cnt[(size_t)((p3 + 1) % 3) * B + b] = 0u;
-        {   // input-major masks of step tt+2 (last read by the STDP phase of step tt-1)
+        {   // input-major masks of step tt+2, slot of step tt-2: every CTA has run
+            // that step's STDP before signalling its encode of step tt
             const size_t n_pre = (size_t)NI * Bw;
-            uint32_t* z = d.preT + (size_t)((p3 + 2) % 3) * n_pre;
+            uint32_t* z = d.preT + (size_t)((tt + 2ull) % PRET_SLOTS) * n_pre;
             for (size_t k = (size_t)cta * PT + tid; k < n_pre; k += (size_t)G * PT) z[k] = 0u;
         }
         {   // first entries of every sample's active-input list (in bounds: caps <= n_in)
@@ -569,9 +578,17 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
+        // ================= next step's input, signalled before this step's STDP
+        // (which needs nothing from other CTAs' next step), waited for after it
+        if (t + 1 < T) {
+            encode_phase(c, d, L, sm, tt + 1, t + 1);
+            ++nbar;
+            grid_arrive(bar);
+        }
+
         // ================= STDP phase =================
         if (c.learn) {
-            const float* xpre = d.x_pre + (size_t)cur * B * NI;
+            const float* xpre = d.x_pre + (size_t)(tt % XPRE_SLOTS) * B * NI;
             uint32_t* preS = (uint32_t*)(sm + L.o_pres);
             uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
             int* pcol = (int*)(sm + L.o_pcol);
@@ -604,7 +621,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             // total exceeds the space.
             int n_ev = 0;
             {
-                const uint32_t* src = d.preT + (size_t)p3 * NI * Bw;
+                const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
                 const bool vec = Bw == 4 || Bw == 8;       // rows of 16 or 32 bytes, 16-byte aligned
                 const int wp = tid >> 5, ln = tid & 31;
                 for (int r0 = 0; r0 < NI; r0 += PT) {
@@ -810,12 +827,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             __syncthreads();
         }
 
-        // ================= next step's input =================
-        if (t + 1 < T) {
-            encode_phase(c, d, L, sm, tt + 1, t + 1);
-            ++nbar;
-            ok = grid_sync(bar, d.err, G * nbar, SPIN_LIMIT);
-        }
+        if (t + 1 < T) ok = grid_wait(bar, d.err, G * nbar, SPIN_LIMIT);
     }
 
     // ---- write the CTA's columns back, and the neuron state held in tensor memory

@@ -44,7 +44,8 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
     const size_t n_thr = (size_t)c.B * c.n_in;
     for (size_t k = tid; k < n_thr; k += nth) {
         d.thr[k] = poisson_threshold(rates[k], c.dt);
-        if (episodic) { d.x_pre[k] = 0.0f; d.x_pre[n_thr + k] = 0.0f; }
+        if (episodic)
+            for (int s = 0; s < XPRE_SLOTS; ++s) d.x_pre[(size_t)s * n_thr + k] = 0.0f;
     }
     const size_t n_bn = (size_t)c.B * c.N;
     for (size_t k = tid; k < n_bn; k += nth) {
@@ -62,8 +63,8 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
         d.postT[k] = 0u;
         d.postT[n_nw + k] = 0u;
     }
-    const size_t n_pre = (size_t)c.n_in * c.Bw;   // input masks are per step: clear all three
-    for (size_t k = tid; k < 3 * n_pre; k += nth) d.preT[k] = 0u;
+    const size_t n_pre = (size_t)c.n_in * c.Bw;   // input masks are per step: clear every slot
+    for (size_t k = tid; k < PRET_SLOTS * n_pre; k += nth) d.preT[k] = 0u;
     if (episodic)
         for (size_t k = tid; k < 3 * (size_t)c.B; k += nth) d.cnt[k] = 0u;
     for (size_t k = tid; k < (size_t)c.B; k += nth) d.seeds[k] = seeds[k];
@@ -79,7 +80,9 @@ __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
 __global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
     const int lane = threadIdx.x & 31;
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
-    const int cur = (int)(tt & 1ull), prv = cur ^ 1, p3 = (int)(tt % 3ull);
+    const int cur = (int)(tt & 1ull), p3 = (int)(tt % 3ull);
+    const int xc = (int)(tt % XPRE_SLOTS), xp = (int)((tt + XPRE_SLOTS - 1) % XPRE_SLOTS);
+    const int pm = (int)(tt % PRET_SLOTS);
     {   // clear this step's accumulators and the next step's input-major masks;
         // their last readers ran at least one launch earlier
         const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
         uint32_t* cnt = d.cnt + (size_t)p3 * c.B;
         for (size_t k = gtid; k < (size_t)c.B; k += nth) cnt[k] = 0u;
         const size_t n_pre = (size_t)c.n_in * c.Bw;
-        uint32_t* nxt = d.preT + (size_t)((p3 + 1) % 3) * n_pre;
+        uint32_t* nxt = d.preT + (size_t)((tt + 1ull) % PRET_SLOTS) * n_pre;
         for (size_t k = gtid; k < n_pre; k += nth) nxt[k] = 0u;
     }
     const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -107,11 +110,11 @@ __global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
             s = h < thr ? 1u : 0u;
         }
         const size_t nbi = (size_t)c.B * c.n_in;
-        float x = d.x_pre[(size_t)prv * nbi + o];
+        float x = d.x_pre[(size_t)xp * nbi + o];
         x = __fmul_rn(x, c.a_x);
         x = __fadd_rn(x, s ? 1.0f : 0.0f);
-        d.x_pre[(size_t)cur * nbi + o] = x;
-        if (s) atomicOr(&d.preT[((size_t)p3 * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
+        d.x_pre[(size_t)xc * nbi + o] = x;
+        if (s) atomicOr(&d.preT[((size_t)pm * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
     }
     const uint32_t word = __ballot_sync(FULL, s);
     if (lane == 0) {
@@ -261,10 +264,10 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
         for (int w = 0; w < c.Bw; ++w) active |= (Sj[w] | Qj[w]) != 0u;
     if (!__syncthreads_or(active)) return;   // no neuron of the group has fired yet
 
-    const float* xp_cur = d.x_pre + (size_t)par * c.B * c.n_in;
+    const float* xp_cur = d.x_pre + (size_t)(tt % XPRE_SLOTS) * c.B * c.n_in;
     const int i_end = min(c.n_in, (int)(blockIdx.y + 1) * STDP_ROWS);
     for (int i = blockIdx.y * STDP_ROWS + warp; i < i_end; i += 8) {
-        const uint32_t* P = d.preT + ((size_t)(tt % 3ull) * c.n_in + i) * c.Bw;
+        const uint32_t* P = d.preT + ((size_t)(tt % PRET_SLOTS) * c.n_in + i) * c.Bw;
         // max: running maximum of pot - dep; sum and mean: the potentiation and
         // depression sums, each in ascending b, subtracted at the end.
         float acc = (REDUCE == SNN_REDUCE_MAX) ? -FLT_MAX : 0.0f, dep_sum = 0.0f;
@@ -310,7 +313,7 @@ __global__ void k_extract(Consts c, Bufs d, int field, void* out) {
     if (field == SNN_FIELD_X_PRE) {
         float* o = (float*)out;
         const size_t n = (size_t)c.B * c.n_in;
-        const int last = (int)((d.step[1] + 1ull) & 1ull);   // buffer of step end-1
+        const int last = (int)((d.step[1] + XPRE_SLOTS - 1) % XPRE_SLOTS);   // slot of step end-1
         const float* src = d.x_pre + (size_t)last * n;
         for (size_t k = tid; k < n; k += nth) o[k] = src[k];
         return;
@@ -334,7 +337,7 @@ __global__ void k_insert(Consts c, Bufs d, int field, const void* in) {
     const size_t nth = (size_t)gridDim.x * blockDim.x;
     if (field == SNN_FIELD_X_PRE) {
         const size_t n = (size_t)c.B * c.n_in;
-        const int last = (int)((d.step[1] + 1ull) & 1ull);   // buffer of step end-1
+        const int last = (int)((d.step[1] + XPRE_SLOTS - 1) % XPRE_SLOTS);   // slot of step end-1
         const float* src = (const float*)in;
         for (size_t k = tid; k < n; k += nth) d.x_pre[(size_t)last * n + k] = src[k];
         return;

@@ -205,22 +205,32 @@ def test_continuing_run_and_batch_change(modes):
     assert_parity(g3, st3, rec3)
 
 
+@pytest.mark.parametrize("step_first", [False, True])
 @pytest.mark.parametrize("mode", ["step", "persistent"])
-def test_checkpoint_and_resume_in_a_fresh_network(mode):
+def test_checkpoint_and_resume_in_a_fresh_network(mode, step_first):
     """snn_read_state + snn_write_state: a fresh network given the saved
-    state, weights, thresholds and step counter continues bit for bit."""
+    state, weights, thresholds and step counter continues bit for bit, whether
+    the step counter is written before or after the other fields."""
     m = snn()
     p, r, s, w = synth.workload(9, 100)
     a = m.Network(p, w_init=w)
     a.run(dev(r), dev(s), 100, mode=mode)
+    t0 = 100
+    while a.read("spikes_inh").sum() == 0 and t0 < 300:   # a checkpoint whose last step
+        a.run(dev(r), dev(s), 1, mode=mode, continue_=True)   # has inhibitory spikes
+        t0 += 1
     fields = ["v_exc", "v_inh", "x_pre", "x_post", "ref_exc", "ref_inh", "spikes_exc",
               "spikes_inh"]
     ck = {f: a.read(f) for f in fields}
+    assert ck["spikes_inh"].sum() > 0
     b = m.Network(p, w_init=a.weights(), theta_init=a.read("theta"))
     b.run(dev(r), dev(s), 0, mode=mode)              # holds the batch, no step taken
+    if step_first:
+        b.write("step", a.read("step"))
     for f in fields:
         b.write(f, ck[f])
-    b.write("step", a.read("step"))
+    if not step_first:
+        b.write("step", a.read("step"))
     for net in (a, b):
         net.run(dev(r), dev(s), 150, mode=mode, continue_=True, record=True, record_input=True)
     torch.cuda.synchronize()
@@ -228,7 +238,7 @@ def test_checkpoint_and_resume_in_a_fresh_network(mode):
     assert ga["raster_e"].sum() > 0
     for k in ga:
         if k == "step":
-            assert ga[k] == gb[k] == 250
+            assert ga[k] == gb[k] == t0 + 150
         else:
             assert np.array_equal(bits(ga[k]), bits(gb[k])), k
 
