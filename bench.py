@@ -25,7 +25,9 @@ the whole batch), so ``--gpus N`` runs N independent replicas (weak scaling).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -236,6 +238,37 @@ def run_reference(a):
     return 0
 
 
+KERNEL_SOURCES = ("paper_1909_02549_gb300/csrc/snn_persistent.cu",
+                  "paper_1909_02549_gb300/csrc/snn_internal.cuh")
+PERSISTENT_PROFILE = "profiles/k_persistent_784x6400_b256.md"
+
+
+def recorded_traffic(a, dom):
+    """DRAM bytes (read + write) per launch of the persistent kernel, from the
+    committed ncu summary of this exact workload, and only while the kernel
+    sources hash to the value that summary records; else None and why."""
+    if dom != "persistent":
+        return None, "no capture of k_%s on this workload" % dom
+    default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn) == (256, 6400, 250, "mean", "fp32", False)
+    if not default:
+        return None, "the capture is of the default workload only"
+    try:
+        text = open(os.path.join(ROOT, PERSISTENT_PROFILE)).read()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        want = re.search(r"source sha256: ([0-9a-f]{64})", text)
+        nbytes = re.search(r"dram bytes per launch: (\d+)", text)
+        if not want or not nbytes:
+            return None, "no traffic recorded in " + PERSISTENT_PROFILE
+        if want.group(1) != h.hexdigest():
+            return None, "kernel changed since the capture in " + PERSISTENT_PROFILE
+        return int(nbytes.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + PERSISTENT_PROFILE
+    except OSError as e:
+        return None, str(e)[:200]
+
+
 def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
     """Dominant kernel's achieved algorithmic bandwidth from an event-bracketed pass."""
     try:
@@ -255,8 +288,10 @@ def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
         pk = peaks()
         nbytes = algorithmic_bytes(dom, B, N, 784, learn, T)
         achieved = nbytes / avg_s / 1e9
+        traffic, traffic_source = recorded_traffic(a, dom)
         return {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "traffic_source": traffic_source,
                 "peak_source": pk["source"] + " hbm_gbs (burst copy), of measured",
                 "algorithmic_bytes_per_launch": nbytes, "avg_launch_us": avg_s * 1e6,
                 "share_of_device_time": dom_ms / prof_total if prof_total else None,

@@ -304,6 +304,37 @@ def test_reduction_of_two_opposite_updates(reduce):
     assert abs(st.theta[0] - float(F32(p["theta_plus"])) * theta_r) < 1e-15
 
 
+@pytest.mark.parametrize("reduce", ["sum", "mean"])
+def test_batch_sum_keeps_potentiation_and_depression_apart(reduce):
+    """R7 in FP32: D = (pot_0 + pot_1) - (dep_0 + dep_1), each sum in ascending
+    b, not the sum of per-sample differences.  Both samples see a pre and a post
+    spike in the same step; the traces are chosen so that the two groupings
+    round differently, and W starts at 0 so that W = D shows the grouping."""
+    p = params()
+    a = F32(math.exp(-1.0 / p["trace_tau"]))
+    nu_post, nu_pre = F32(p["nu_post"]), F32(p["nu_pre"])
+
+    def after(x):                                 # trace after this step's spike
+        return F32(F32(F32(x) * a) + F32(1.0))
+
+    xp, xq = (0.0, 0.0), (0.1, 0.73)              # x_pre and x_post before the step
+    pot = [F32(nu_post * after(x)) for x in xp]
+    dep = [F32(nu_pre * after(x)) for x in xq]
+    split = F32(F32(pot[0] + pot[1]) - F32(dep[0] + dep[1]))
+    paired = F32(F32(pot[0] - dep[0]) + F32(pot[1] - dep[1]))
+    assert split != paired
+    want = split if reduce == "sum" else F32(split / F32(2.0))
+    st = oracle.new_state(p, 2, np.zeros((1, 1)), dtype=np.float32)
+    st.x_pre[:, 0] = xp
+    st.x_post[:, 0] = xq
+    st.v_e[:, 0] = -40.0                          # post spike in both samples
+    rates = np.full((2, 1), 2000.0, np.float32)   # pre spike in both samples
+    rec = oracle.run(p, st, rates, np.array([1, 2], np.uint64), 1, learn=True,
+                     reduce=reduce, episodic=False)
+    assert rec.raster_e[0, :, 0].tolist() == [1, 1] and rec.raster_in[0, :, 0].tolist() == [1, 1]
+    assert st.w[0, 0] == want
+
+
 def test_max_reduction_includes_samples_without_update():
     """The per-parameter maximum runs over every sample: one depressing sample
     and one idle sample give max(delta, 0) = 0."""
