@@ -280,79 +280,98 @@ __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence
 // Every sample whose input fired is visited: where neuron j has not fired in
 // the episode its trace is exactly 0 and the term is +0, which leaves a sum
 // (never -0 here) unchanged and gives the max the 0 it takes anyway.  The sum
-// subtracts e directly: acc - e equals acc + (0 - e) bit for bit.  LISTS: the
-// row's samples come from the per-input lists, else from its spike words.  Out
-// of line, so that its loops get registers of their own inside the large kernel.
-template <bool MAX, bool LISTS>
+// subtracts e directly: acc - e equals acc + (0 - e) bit for bit.  The clip
+// min(max(u, w_min), w_max) is the comparison form's value, u being neither
+// NaN nor -0.  LISTS: the row's samples come from the per-input lists, else
+// from its spike words.  Out of line, so that its loops get registers of their
+// own inside the large kernel.
+enum { RED_SUM = 0, RED_MEAN_MUL = 1, RED_MEAN_DIV = 2, RED_MAX = 3 };
+
+template <int RED>
+__device__ __forceinline__ float deposit(float acc, float e) {
+    return RED == RED_MAX ? fmaxf(acc, __fsub_rn(0.0f, e)) : __fsub_rn(acc, e);
+}
+
+template <int RED, bool LISTS>
 __device__ __noinline__ void depress_quiet_columns(
         const Consts& c, float* Ws, const float* Es, const uint32_t* preS, const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
-    const float init = MAX ? -FLT_MAX : 0.0f;
+    const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
     const int h = lane >> 4;
     for (int g0 = 0; g0 < nc; g0 += 64) {
         const int j = g0 + 4 * (lane & 15);
-        bool v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = j + q < nc && nzQ[j + q] == 0u;
-        const bool any = v[0] || v[1] || v[2] || v[3];
-        const bool all4 = v[0] && v[1] && v[2] && v[3];
+        const bool v0 = j < nc && nzQ[j] == 0u, v1 = j + 1 < nc && nzQ[j + 1] == 0u;
+        const bool v2 = j + 2 < nc && nzQ[j + 2] == 0u, v3 = j + 3 < nc && nzQ[j + 3] == 0u;
+        const bool any = v0 || v1 || v2 || v3, all4 = v0 && v1 && v2 && v3;
         if (!__any_sync(FULL, any)) continue;
-        const int cj = j < nst ? j : 0;              // lanes past the tile read a valid row
+        const float* E = Es + (j < nst ? j : 0);     // lanes past the tile read a valid row
         for (int i0 = 2 * warp; i0 < NI; i0 += 2 * NW) {
             const int i = i0 + h;
             if (i >= NI) continue;
-            float a[4] = {init, init, init, init};
+            float a0 = init, a1 = init, a2 = init, a3 = init;
             int n = 0;
-            auto add = [&](int b) {
-                const float4 e = *(const float4*)(Es + b * nst + cj);
-                if (MAX) {
-                    a[0] = fmaxf(a[0], __fsub_rn(0.0f, e.x));
-                    a[1] = fmaxf(a[1], __fsub_rn(0.0f, e.y));
-                    a[2] = fmaxf(a[2], __fsub_rn(0.0f, e.z));
-                    a[3] = fmaxf(a[3], __fsub_rn(0.0f, e.w));
-                } else {
-                    a[0] = __fsub_rn(a[0], e.x);
-                    a[1] = __fsub_rn(a[1], e.y);
-                    a[2] = __fsub_rn(a[2], e.z);
-                    a[3] = __fsub_rn(a[3], e.w);
-                }
-            };
             if (LISTS) {
-                const int e0 = offs[i], e1 = offs[i + 1];
-                n = e1 - e0;
-                for (int e = e0; e < e1; ++e) add((int)lst[e]);
+                int e = offs[i];
+                const int e1 = offs[i + 1];
+                n = e1 - e;
+                for (; e + 1 < e1; e += 2) {             // two loads in flight, then in order
+                    const float4 x = *(const float4*)(E + (int)lst[e] * nst);
+                    const float4 y = *(const float4*)(E + (int)lst[e + 1] * nst);
+                    a0 = deposit<RED>(deposit<RED>(a0, x.x), y.x);
+                    a1 = deposit<RED>(deposit<RED>(a1, x.y), y.y);
+                    a2 = deposit<RED>(deposit<RED>(a2, x.z), y.z);
+                    a3 = deposit<RED>(deposit<RED>(a3, x.w), y.w);
+                }
+                if (e < e1) {
+                    const float4 x = *(const float4*)(E + (int)lst[e] * nst);
+                    a0 = deposit<RED>(a0, x.x);
+                    a1 = deposit<RED>(a1, x.y);
+                    a2 = deposit<RED>(a2, x.z);
+                    a3 = deposit<RED>(a3, x.w);
+                }
             } else {
                 const uint32_t* Pi = preS + i * PS;
                 for (int w = 0; w < Bw; ++w) {
                     uint32_t m = Pi[w];
                     while (m) {
-                        add(w * 32 + __ffs(m) - 1);
+                        const float4 x = *(const float4*)(E + (w * 32 + __ffs(m) - 1) * nst);
                         m &= m - 1;
+                        a0 = deposit<RED>(a0, x.x);
+                        a1 = deposit<RED>(a1, x.y);
+                        a2 = deposit<RED>(a2, x.z);
+                        a3 = deposit<RED>(a3, x.w);
                         ++n;
                     }
                 }
             }
             if (n == 0 || !any) continue;
-            float4 wv = *(const float4*)(Ws + i * nst + cj);
-            float* wq = &wv.x;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                float D = a[q];
-                if (!MAX && c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
-                if (MAX && n < c.B) D = fmaxf(D, 0.0f);
-                float u = __fadd_rn(wq[q], D);
-                u = u < c.w_min ? c.w_min : u;
-                u = u > c.w_max ? c.w_max : u;
-                if (v[q]) wq[q] = u;
+            if (RED == RED_MEAN_MUL) {
+                a0 = __fmul_rn(a0, c.inv_B); a1 = __fmul_rn(a1, c.inv_B);
+                a2 = __fmul_rn(a2, c.inv_B); a3 = __fmul_rn(a3, c.inv_B);
+            } else if (RED == RED_MEAN_DIV) {
+                const float fb = (float)c.B;
+                a0 = __fdiv_rn(a0, fb); a1 = __fdiv_rn(a1, fb);
+                a2 = __fdiv_rn(a2, fb); a3 = __fdiv_rn(a3, fb);
+            } else if (RED == RED_MAX && n < c.B) {
+                a0 = fmaxf(a0, 0.0f); a1 = fmaxf(a1, 0.0f);
+                a2 = fmaxf(a2, 0.0f); a3 = fmaxf(a3, 0.0f);
             }
+            float* wr = Ws + i * nst + (j < nst ? j : 0);
+            const float4 w = *(const float4*)wr;
+            float4 u;
+            u.x = fminf(fmaxf(__fadd_rn(w.x, a0), c.w_min), c.w_max);
+            u.y = fminf(fmaxf(__fadd_rn(w.y, a1), c.w_min), c.w_max);
+            u.z = fminf(fmaxf(__fadd_rn(w.z, a2), c.w_min), c.w_max);
+            u.w = fminf(fmaxf(__fadd_rn(w.w, a3), c.w_min), c.w_max);
             // columns with a post spike belong to the other pass: store only ours
             if (all4) {
-                *(float4*)(Ws + i * nst + cj) = wv;
+                *(float4*)wr = u;
             } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (v[q]) Ws[i * nst + cj + q] = wq[q];
+                if (v0) wr[0] = u.x;
+                if (v1) wr[1] = u.y;
+                if (v2) wr[2] = u.z;
+                if (v3) wr[3] = u.w;
             }
         }
     }
@@ -503,6 +522,64 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
+        // synaptic currents: I[b][j] = sum over the active inputs a of sample b,
+        // ascending, of W[a][j] (in the weight precision), into the e tile,
+        // which the update below reads and overwrites with e.  One sample per
+        // half-warp and four adjacent columns per lane: the active list is the
+        // same for the half-warp and each weight row is one 16-byte load.
+        {
+            const int warp = tid >> 5, lane = tid & 31, h = lane >> 4;
+            for (int g0 = 0; g0 < nc; g0 += 64) {
+                const int j = g0 + 4 * (lane & 15);
+                if (j >= nc) continue;                  // no column of the tile: idle lane
+                for (int b = 2 * warp + h; b < B; b += 2 * NW) {
+                    const int na = (int)actN[b];
+                    const int ns = na < caps ? na : caps;
+                    const uint16_t* al = actS + b * CAPS;
+                    const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+                    float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+                    if (c.wprec == SNN_W_FP32) {
+                        for (int a = 0; a < na; ++a) {
+                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                            const float4 w = *(const float4*)(Ws + r * nst + j);
+                            I0 = __fadd_rn(I0, w.x);
+                            I1 = __fadd_rn(I1, w.y);
+                            I2 = __fadd_rn(I2, w.z);
+                            I3 = __fadd_rn(I3, w.w);
+                        }
+                    } else if (c.wprec == SNN_W_BF16) {
+                        for (int a = 0; a < na; ++a) {
+                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                            const float4 w = *(const float4*)(Ws + r * nst + j);
+                            I0 = __fadd_rn(I0, w_read_bf16(w.x));
+                            I1 = __fadd_rn(I1, w_read_bf16(w.y));
+                            I2 = __fadd_rn(I2, w_read_bf16(w.z));
+                            I3 = __fadd_rn(I3, w_read_bf16(w.w));
+                        }
+                    } else {
+                        // padding columns take scale 1 (their currents are never used)
+                        const float* inv = wsc + L.ncmax;
+                        const float v0 = inv[j], v1 = j + 1 < nc ? inv[j + 1] : 1.0f;
+                        const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
+                        for (int a = 0; a < na; ++a) {
+                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                            const float4 w = *(const float4*)(Ws + r * nst + j);
+                            I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
+                            I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
+                            I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
+                            I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
+                        }
+                        I0 = __fmul_rn(I0, wsc[j]);
+                        I1 = __fmul_rn(I1, j + 1 < nc ? wsc[j + 1] : 1.0f);
+                        I2 = __fmul_rn(I2, j + 2 < nc ? wsc[j + 2] : 1.0f);
+                        I3 = __fmul_rn(I3, j + 3 < nc ? wsc[j + 3] : 1.0f);
+                    }
+                    *(float4*)(Es + b * nst + j) = make_float4(I0, I1, I2, I3);
+                }
+            }
+        }
+        __syncthreads();
+
         {
             int b = tid / nc, jl = tid % nc;
             for (int q = 0; q < QN; ++q) {
@@ -520,28 +597,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     it.x = d.x_post[idx];
                 }
                 if (valid) {
-                    // synaptic current: ascending active inputs of sample b
-                    float I = 0.0f;
-                    const int na = (int)actN[b];
-                    const int ns = na < caps ? na : caps;
-                    const uint16_t* al = actS + b * CAPS;
-                    const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
-                    if (c.wprec == SNN_W_FP32) {
-                        for (int a = 0; a < ns; ++a) I = __fadd_rn(I, Ws[(int)al[a] * nst + jl]);
-                        for (int a = caps; a < na; ++a) I = __fadd_rn(I, Ws[(int)__ldcg(&ag[a]) * nst + jl]);
-                    } else if (c.wprec == SNN_W_BF16) {
-                        for (int a = 0; a < ns; ++a)
-                            I = __fadd_rn(I, w_read_bf16(Ws[(int)al[a] * nst + jl]));
-                        for (int a = caps; a < na; ++a)
-                            I = __fadd_rn(I, w_read_bf16(Ws[(int)__ldcg(&ag[a]) * nst + jl]));
-                    } else {
-                        const float inv = wsc[L.ncmax + jl];
-                        for (int a = 0; a < ns; ++a)
-                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)al[a] * nst + jl], inv));
-                        for (int a = caps; a < na; ++a)
-                            I = __fadd_rn(I, w_read_e4m3(Ws[(int)__ldcg(&ag[a]) * nst + jl], inv));
-                        I = __fmul_rn(I, wsc[jl]);
-                    }
+                    const float I = Es[b * nst + jl];
                     const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
                     const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
                     Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
@@ -718,16 +774,15 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             const int warp = tid >> 5, lane = tid & 31;
 
             // (A) columns without a post spike: depression only
-            if (c.reduce == SNN_REDUCE_MAX) {
-                if (lists)
-                    depress_quiet_columns<true, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
-                else
-                    depress_quiet_columns<true, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
-            } else {
-                if (lists)
-                    depress_quiet_columns<false, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
-                else
-                    depress_quiet_columns<false, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane);
+            {
+#define SNN_PASS_A(R)                                                                              \
+    (lists ? depress_quiet_columns<R, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
+           : depress_quiet_columns<R, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+                if (c.reduce == SNN_REDUCE_MAX) SNN_PASS_A(RED_MAX);
+                else if (c.reduce == SNN_REDUCE_SUM) SNN_PASS_A(RED_SUM);
+                else if (c.B_pow2) SNN_PASS_A(RED_MEAN_MUL);
+                else SNN_PASS_A(RED_MEAN_DIV);
+#undef SNN_PASS_A
             }
 
             // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.

@@ -1,6 +1,9 @@
 """Host logic of bench.py that needs no GPU: the DRAM traffic it reports next
-to the roofline comes from the committed ncu summary only while the kernel
-sources are the ones that summary was taken on, and only for that workload."""
+to the roofline comes from an ncu summary only while the kernel sources are
+the ones that summary was taken on, and only for that workload.  The tests
+write their own summary and sources, so they do not depend on whether the
+committed capture is current."""
+import hashlib
 import os
 import sys
 
@@ -22,22 +25,38 @@ def args(**kw):
     return a
 
 
-def test_traffic_is_reported_for_the_captured_sources_and_workload():
+def capture(tmp_path, monkeypatch, nbytes=12345678):
+    src = [tmp_path / "kernel.cu", tmp_path / "kernel.cuh"]
+    src[0].write_bytes(b"__global__ void k() {}\n")
+    src[1].write_bytes(b"// header\n")
+    h = hashlib.sha256(src[0].read_bytes() + src[1].read_bytes()).hexdigest()
+    prof = tmp_path / "summary.md"
+    prof.write_text("source sha256: %s\ndram bytes per launch: %d\n" % (h, nbytes))
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", tuple(str(p) for p in src))
+    monkeypatch.setattr(bench, "PERSISTENT_PROFILE", str(prof))
+    return src
+
+
+def test_traffic_is_reported_for_the_captured_sources_and_workload(tmp_path, monkeypatch):
+    capture(tmp_path, monkeypatch)
     nbytes, src = bench.recorded_traffic(args(), "persistent")
-    assert isinstance(nbytes, int) and nbytes > 0
-    assert bench.PERSISTENT_PROFILE in src
+    assert nbytes == 12345678 and "summary.md" in src
 
 
-def test_traffic_is_null_for_another_workload_or_kernel():
+def test_traffic_is_null_for_another_workload_or_kernel(tmp_path, monkeypatch):
+    capture(tmp_path, monkeypatch)
     assert bench.recorded_traffic(args(batch=128), "persistent")[0] is None
     assert bench.recorded_traffic(args(reduce="max"), "persistent")[0] is None
     assert bench.recorded_traffic(args(), "stdp")[0] is None
 
 
 def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
-    changed = tmp_path / "kernel.cu"
-    with open(os.path.join(ROOT, bench.KERNEL_SOURCES[0]), "rb") as f:
-        changed.write_bytes(f.read() + b"\n// edited\n")
-    monkeypatch.setattr(bench, "KERNEL_SOURCES", (str(changed),) + bench.KERNEL_SOURCES[1:])
+    src = capture(tmp_path, monkeypatch)
+    src[0].write_bytes(src[0].read_bytes() + b"// edited\n")
     nbytes, why = bench.recorded_traffic(args(), "persistent")
     assert nbytes is None and "changed" in why
+
+
+def test_the_committed_summary_records_a_hash_and_traffic():
+    text = open(os.path.join(ROOT, bench.PERSISTENT_PROFILE)).read()
+    assert "source sha256: " in text and "dram bytes per launch: " in text
