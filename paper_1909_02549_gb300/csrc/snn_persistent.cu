@@ -49,10 +49,12 @@ struct Layout {
     int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
     int nst;                     // row stride (floats) of the weight and depression-term tiles
     size_t o_ws, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
-    // union region (phase-local)
+    // phase-local region: neuron-phase staging, encode scratch, STDP mask copy
     size_t o_cnts, o_actn, o_acts;    // neuron phase
-    size_t o_pres, o_nzp, o_pcol, o_nzqw;   // STDP phase
-    size_t o_off, o_lst;              // STDP phase: per-input lists of spiking samples
+    size_t o_pres;                    // STDP phase (max reduction, list overflow)
+    // per-step region: built before the neuron phase, read by the STDP phase
+    size_t o_nzp, o_pcol, o_nzqw;
+    size_t o_off, o_lst;              // per-input lists of spiking samples
     int ps;                           // row stride of the staged input-major masks
     int lcap;                         // list entries that fit
     int tstate;                       // neuron state held in tensor memory (else in global memory)
@@ -80,32 +82,32 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_thj = o; o = align16(o + (size_t)L.ncmax * 4);
     L.o_wsc = o; o = align16(o + (size_t)L.ncmax * 8);   // FP8 column scale and its inverse
     L.o_u = o;
-    size_t u_neuron = 0, u_stdp = 0, u_enc = 0;
+    size_t u_neuron = 0, u_enc = 0, u_pres = 0;
     L.o_cnts = o;                u_neuron = align16((size_t)c.B * 4);
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
     L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
     L.tstate = (size_t)c.B * L.ncmax <= (size_t)QT * PT;
-    L.o_pres = o;                u_stdp = align16((size_t)c.n_in * L.ps * 4);
-    L.o_nzp = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)c.n_in * 4);
-    L.o_pcol = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
-    L.o_nzqw = o + u_stdp;       u_stdp = align16(u_stdp + (size_t)L.ncmax * 4);
-    L.o_off = o + u_stdp;        u_stdp = align16(u_stdp + (size_t)(c.n_in + 1) * 4);
-    L.o_lst = o + u_stdp;
+    L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
+    L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
+    size_t u = u_neuron > u_enc ? u_neuron : u_enc;
+    if (u_pres > u) u = u_pres;
+    o += u;
+    L.o_nzp = o;                 o = align16(o + (size_t)c.n_in * 4);
+    L.o_pcol = o;                o = align16(o + (size_t)L.ncmax * 4);
+    L.o_nzqw = o;                o = align16(o + (size_t)L.ncmax * 4);
+    L.o_off = o;                 o = align16(o + (size_t)(c.n_in + 1) * 4);
+    L.o_lst = o;
     {
-        const size_t used = o + u_stdp;
-        size_t cap = budget > used ? (budget - used) / 2 : 0;
+        size_t cap = budget > o ? (budget - o) / 2 : 0;
         const size_t most = (size_t)c.n_in * c.B;
         if (cap > most) cap = most;
         if (cap > ((size_t)1 << 30)) cap = (size_t)1 << 30;
         if (c.B > 65536) cap = 0;                         // sample indices are 16-bit
         L.lcap = (int)(cap & ~(size_t)7);
-        u_stdp = align16(u_stdp + (size_t)L.lcap * 2);
+        o = align16(o + (size_t)L.lcap * 2);
     }
-    L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
-    size_t u = u_neuron > u_stdp ? u_neuron : u_stdp;
-    if (u_enc > u) u = u_enc;
-    L.bytes = o + u;
+    L.bytes = o;
     return L;
 }
 
@@ -116,15 +118,15 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 }
 
 // Grid-wide barrier in two halves.  grid_arrive: the CTA's writes so far are
-// released and counted.  grid_wait: bounded wait until every CTA has arrived
-// `target` times in all, then acquire; returns false if this or another CTA
-// gave up (device error bit 1).  Work between the halves overlaps the wait.
+// released and counted: the block barrier orders every thread's writes before
+// thread 0's release-add, which does not stall the thread.  grid_wait: bounded
+// wait until every CTA has arrived `target` times in all; the acquire load that
+// sees the count makes their writes visible, and the block barrier passes that
+// on.  Returns false if this or another CTA gave up (device error bit 1).  Work
+// between the halves overlaps the wait.
 __device__ void grid_arrive(uint32_t* ctr) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-    }
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(ctr), "r"(1u) : "memory");
 }
 
 __device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigned limit) {
@@ -138,7 +140,6 @@ __device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigne
             __nanosleep(ns);
             if (ns < 512) ns <<= 1;
         }
-        __threadfence();
         s_fail = fail;
     }
     __syncthreads();
@@ -377,6 +378,145 @@ __device__ __noinline__ void depress_quiet_columns(
     }
 }
 
+// Synaptic currents: I[b][j] = sum over the active inputs a of sample b,
+// ascending, of W[a][j] (in the weight precision), into the e tile, which the
+// neuron update then reads and overwrites with e.  One sample per half-warp and
+// four adjacent columns per lane: the active list is the same for the
+// half-warp and each weight row is one 16-byte load.
+__device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d, const float* Ws,
+                                               float* Es, const float* wsc, int ncmax,
+                                               const uint32_t* actN, const uint16_t* actS,
+                                               int caps, int nc, int nst, int cur) {
+    const int B = c.B, NI = c.n_in, tid = threadIdx.x;
+    {
+        const int warp = tid >> 5, lane = tid & 31, h = lane >> 4;
+        for (int g0 = 0; g0 < nc; g0 += 64) {
+            const int j = g0 + 4 * (lane & 15);
+            if (j >= nc) continue;                  // no column of the tile: idle lane
+            for (int b = 2 * warp + h; b < B; b += 2 * NW) {
+                const int na = (int)actN[b];
+                const int ns = na < caps ? na : caps;
+                const uint16_t* al = actS + b * CAPS;
+                const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+                float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+                if (c.wprec == SNN_W_FP32) {
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w.x);
+                        I1 = __fadd_rn(I1, w.y);
+                        I2 = __fadd_rn(I2, w.z);
+                        I3 = __fadd_rn(I3, w.w);
+                    }
+                } else if (c.wprec == SNN_W_BF16) {
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w_read_bf16(w.x));
+                        I1 = __fadd_rn(I1, w_read_bf16(w.y));
+                        I2 = __fadd_rn(I2, w_read_bf16(w.z));
+                        I3 = __fadd_rn(I3, w_read_bf16(w.w));
+                    }
+                } else {
+                    // padding columns take scale 1 (their currents are never used)
+                    const float* inv = wsc + ncmax;
+                    const float v0 = inv[j], v1 = j + 1 < nc ? inv[j + 1] : 1.0f;
+                    const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
+                        I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
+                        I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
+                        I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
+                    }
+                    I0 = __fmul_rn(I0, wsc[j]);
+                    I1 = __fmul_rn(I1, j + 1 < nc ? wsc[j + 1] : 1.0f);
+                    I2 = __fmul_rn(I2, j + 2 < nc ? wsc[j + 2] : 1.0f);
+                    I3 = __fmul_rn(I3, j + 3 < nc ? wsc[j + 3] : 1.0f);
+                }
+                *(float4*)(Es + b * nst + j) = make_float4(I0, I1, I2, I3);
+            }
+        }
+    }
+}
+
+// The neuron update of the CTA's (sample, column) items: state from tensor
+// memory (or global memory), the current from the e tile, e = nu_pre x_post
+// back into it, spikes into the masks and counters.  Inlined: a call would have
+// to save the kernel's live values around it, through L1 that the shared
+// memory leaves small, which costs more than the loop's own register pressure.
+__device__ __forceinline__ void neuron_items(const Consts& c, const Bufs& d, float* Es, uint32_t* Qm,
+                                          uint32_t* Sm, const uint32_t* cntS, const float* thj,
+                                          uint32_t tq, bool tstate, int QN, int BN, int nc, int nst,
+                                          int j0, int dq, int dr, int t, int p3) {
+    const int B = c.B, N = c.N, tid = threadIdx.x;
+    {
+        int b = tid / nc, jl = tid % nc;
+        for (int q = 0; q < QN; ++q) {
+            const bool valid = tid + q * PT < BN;
+            const int j = j0 + jl;
+            const size_t idx = (size_t)b * N + j;
+            Item it{0.0f, 0.0f, 0.0f, 0u};
+            if (tstate) {
+                __syncwarp();
+                tmem_ld4(tq + 4 * q, it);
+            } else if (valid) {
+                it.st = d.st[idx];
+                it.v = d.v_e[idx];
+                it.vi = d.v_i[idx];
+                it.x = d.x_post[idx];
+            }
+            if (valid) {
+                const float I = Es[b * nst + jl];
+                const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
+                const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
+                Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
+                if (!tstate) {
+                    d.x_post[idx] = o.x;
+                    d.v_e[idx] = o.v;
+                    d.v_i[idx] = o.vi;
+                    d.st[idx] = o.st;
+                }
+                if (se) {
+                    d.counts[idx] += 1u;
+                    const uint32_t bit = 1u << (b & 31);
+                    atomicOr(&Qm[(b >> 5) * nc + jl], bit);
+                    atomicOr(&Sm[(b >> 5) * nc + jl], bit);
+                    if (c.rec_raster)
+                        atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                }
+                if (si) {
+                    atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
+                    if (c.rec_raster)
+                        atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                }
+                it = o;
+            }
+            if (tstate) {
+                __syncwarp();
+                tmem_st4(tq + 4 * q, it);
+            }
+            b += dq;
+            jl += dr;
+            if (jl >= nc) { jl -= nc; ++b; }
+        }
+        if (tstate) tmem_wait_st();
+    }
+}
+
+// The adaptive thresholds after the STDP of a step: theta_j <- theta_j a_theta +
+// theta_plus r_j in FP64, r_j the batch reduction of column j's spike count
+// (sum: the count, mean: count / B, max: any).  n_j is the count.
+__device__ __forceinline__ double theta_next(const Consts& c, double th, int n) {
+    double r;
+    if (c.reduce == SNN_REDUCE_SUM) r = (double)n;
+    else if (c.reduce == SNN_REDUCE_MEAN)   // n / B; exactly n * 2^-k for B = 2^k
+        r = c.B_pow2 ? __dmul_rn((double)n, (double)c.inv_B) : __ddiv_rn((double)n, (double)c.B);
+    else r = n > 0 ? 1.0 : 0.0;
+    return __dadd_rn(__dmul_rn(th, c.a_th), __dmul_rn(c.theta_plus, r));
+}
+
 __global__ void __launch_bounds__(PT, 1)
 k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, const int T,
              const __grid_constant__ Layout L) {
@@ -392,6 +532,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     uint32_t* cntS = (uint32_t*)(sm + L.o_cnts);
     uint32_t* actN = (uint32_t*)(sm + L.o_actn);
     uint16_t* actS = (uint16_t*)(sm + L.o_acts);
+    uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);       // per-step input lists (see the neuron phase)
+    int* offs = (int*)(sm + L.o_off);
+    uint16_t* lst = (uint16_t*)(sm + L.o_lst);
     __shared__ int s_nq;
     __shared__ int s_scan[NW];
     __shared__ uint32_t s_tmem;
@@ -469,13 +612,24 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         const int cur = (int)(tt & 1ull), p3 = (int)(tt % 3ull);
 
         // ================= neuron phase =================
+        // (the step's input-mask rows for the lists below, loaded first so that
+        // their latency overlaps the staging)
+        const uint32_t* pre_src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
+        const bool pre_vec = Bw == 4 || Bw == 8;         // rows of 16 or 32 bytes, 16-byte aligned
+        uint4 pq0 = make_uint4(0u, 0u, 0u, 0u), pq1 = make_uint4(0u, 0u, 0u, 0u);
+        if (pre_vec && tid < NI) {
+            pq0 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw));
+            if (Bw == 8) pq1 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw) + 1);
+        }
         for (int b = tid; b < B; b += PT) {
             cntS[b] = __ldcg(&d.cnt[(size_t)((p3 + 2) % 3) * B + b]);
             actN[b] = __ldcg(&d.act_cnt[(size_t)cur * B + b]);
         }
         for (int k = tid; k < Bw * nc; k += PT) Qm[k] = 0u;
-        for (int jl = tid; jl < nc; jl += PT)
+        for (int jl = tid; jl < nc; jl += PT) {   // thresholds after the previous step's STDP
+            if (c.learn && t > 0) thS[jl] = theta_next(c, thS[jl], (int)nzQ[jl]);
             thj[jl] = __fadd_rn(c.e_thresh, __double2float_rn(thS[jl]));
+        }
         if (cta == 0)   // accumulator of the next step (its last reader was step tt-1)
             for (int b = tid; b < B; b += PT) d.cnt[(size_t)((p3 + 1) % 3) * B + b] = 0u;
         {   // input-major masks of step tt+2, slot of step tt-2: every CTA has run
@@ -507,6 +661,94 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
             }
         }
+        // Per input i: the samples whose input i fired this step, ascending, in
+        // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
+        // counts (the step's input-major masks are complete since the barrier).
+        // One thread per row reads the row's words once.  Lists are written
+        // only while they fit; the STDP passes walk the spike words instead when
+        // the step's total exceeds the space.
+        {
+            const uint32_t* src = pre_src;
+            const bool vec = pre_vec;
+            const int wp = tid >> 5, ln = tid & 31;
+            int n_ev = 0;
+            for (int r0 = 0; r0 < NI; r0 += PT) {
+                const int i = r0 + tid;
+                uint32_t wr[8];                              // the row's words
+                int n = 0;
+                uint32_t nz = 0;
+                if (i < NI) {
+                    const uint32_t* row = src + (size_t)i * Bw;
+                    if (vec) {
+                        const uint4 q0 = r0 == 0 ? pq0 : __ldcg((const uint4*)row);
+                        const uint4 q1 = r0 == 0 ? pq1 : Bw == 8 ? __ldcg((const uint4*)row + 1) : make_uint4(0u, 0u, 0u, 0u);
+                        wr[0] = q0.x; wr[1] = q0.y; wr[2] = q0.z; wr[3] = q0.w;
+                        wr[4] = q1.x; wr[5] = q1.y; wr[6] = q1.z; wr[7] = q1.w;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) {
+                            if (w < Bw) {
+                                n += __popc(wr[w]);
+                                if (wr[w]) nz |= 1u << w;
+                            }
+                        }
+                    } else {
+                        for (int w = 0; w < Bw; ++w) {
+                            const uint32_t m = __ldcg(&row[w]);
+                            n += __popc(m);
+                            if (m && w < 32) nz |= 1u << w;
+                        }
+                    }
+                    nzP[i] = nz;
+                }
+                int x = n;                                   // inclusive scan within the warp
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(FULL, x, o);
+                    if (ln >= o) x += y;
+                }
+                if (ln == 31) s_scan[wp] = x;
+                __syncthreads();
+                if (wp == 0) {                               // ... and over the warps
+                    int v = s_scan[ln];
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(FULL, v, o);
+                        if (ln >= o) v += y;
+                    }
+                    s_scan[ln] = v;
+                }
+                __syncthreads();
+                const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
+                if (i < NI) {
+                    offs[i] = start;
+                    if (start + n <= L.lcap) {
+                        int q = start;
+                        if (vec) {
+#pragma unroll
+                            for (int w = 0; w < 8; ++w) {
+                                uint32_t m = w < Bw ? wr[w] : 0u;
+                                while (m) {
+                                    lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+                                    m &= m - 1;
+                                }
+                            }
+                        } else {
+                            const uint32_t* row = src + (size_t)i * Bw;
+                            for (int w = 0; w < Bw; ++w) {
+                                uint32_t m = __ldcg(&row[w]);
+                                while (m) {
+                                    lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
+                                    m &= m - 1;
+                                }
+                            }
+                        }
+                    }
+                }
+                n_ev += s_scan[NW - 1];
+                if (r0 + PT < NI) __syncthreads();           // s_scan is rewritten by the next rows
+            }
+            if (tid == 0) offs[NI] = n_ev;
+        }
         if (c.wprec == SNN_W_FP8E4M3) {   // column scales of this step's weights
             const int warp = tid >> 5, lane = tid & 31;
             for (int jl = warp; jl < nc; jl += NW) {
@@ -522,116 +764,10 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
-        // synaptic currents: I[b][j] = sum over the active inputs a of sample b,
-        // ascending, of W[a][j] (in the weight precision), into the e tile,
-        // which the update below reads and overwrites with e.  One sample per
-        // half-warp and four adjacent columns per lane: the active list is the
-        // same for the half-warp and each weight row is one 16-byte load.
-        {
-            const int warp = tid >> 5, lane = tid & 31, h = lane >> 4;
-            for (int g0 = 0; g0 < nc; g0 += 64) {
-                const int j = g0 + 4 * (lane & 15);
-                if (j >= nc) continue;                  // no column of the tile: idle lane
-                for (int b = 2 * warp + h; b < B; b += 2 * NW) {
-                    const int na = (int)actN[b];
-                    const int ns = na < caps ? na : caps;
-                    const uint16_t* al = actS + b * CAPS;
-                    const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
-                    float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
-                    if (c.wprec == SNN_W_FP32) {
-                        for (int a = 0; a < na; ++a) {
-                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                            const float4 w = *(const float4*)(Ws + r * nst + j);
-                            I0 = __fadd_rn(I0, w.x);
-                            I1 = __fadd_rn(I1, w.y);
-                            I2 = __fadd_rn(I2, w.z);
-                            I3 = __fadd_rn(I3, w.w);
-                        }
-                    } else if (c.wprec == SNN_W_BF16) {
-                        for (int a = 0; a < na; ++a) {
-                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                            const float4 w = *(const float4*)(Ws + r * nst + j);
-                            I0 = __fadd_rn(I0, w_read_bf16(w.x));
-                            I1 = __fadd_rn(I1, w_read_bf16(w.y));
-                            I2 = __fadd_rn(I2, w_read_bf16(w.z));
-                            I3 = __fadd_rn(I3, w_read_bf16(w.w));
-                        }
-                    } else {
-                        // padding columns take scale 1 (their currents are never used)
-                        const float* inv = wsc + L.ncmax;
-                        const float v0 = inv[j], v1 = j + 1 < nc ? inv[j + 1] : 1.0f;
-                        const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
-                        for (int a = 0; a < na; ++a) {
-                            const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                            const float4 w = *(const float4*)(Ws + r * nst + j);
-                            I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
-                            I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
-                            I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
-                            I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
-                        }
-                        I0 = __fmul_rn(I0, wsc[j]);
-                        I1 = __fmul_rn(I1, j + 1 < nc ? wsc[j + 1] : 1.0f);
-                        I2 = __fmul_rn(I2, j + 2 < nc ? wsc[j + 2] : 1.0f);
-                        I3 = __fmul_rn(I3, j + 3 < nc ? wsc[j + 3] : 1.0f);
-                    }
-                    *(float4*)(Es + b * nst + j) = make_float4(I0, I1, I2, I3);
-                }
-            }
-        }
+        synaptic_currents(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
         __syncthreads();
 
-        {
-            int b = tid / nc, jl = tid % nc;
-            for (int q = 0; q < QN; ++q) {
-                const bool valid = tid + q * PT < BN;
-                const int j = j0 + jl;
-                const size_t idx = (size_t)b * N + j;
-                Item it{0.0f, 0.0f, 0.0f, 0u};
-                if (tstate) {
-                    __syncwarp();
-                    tmem_ld4(tq + 4 * q, it);
-                } else if (valid) {
-                    it.st = d.st[idx];
-                    it.v = d.v_e[idx];
-                    it.vi = d.v_i[idx];
-                    it.x = d.x_post[idx];
-                }
-                if (valid) {
-                    const float I = Es[b * nst + jl];
-                    const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
-                    const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
-                    Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
-                    if (!tstate) {
-                        d.x_post[idx] = o.x;
-                        d.v_e[idx] = o.v;
-                        d.v_i[idx] = o.vi;
-                        d.st[idx] = o.st;
-                    }
-                    if (se) {
-                        d.counts[idx] += 1u;
-                        const uint32_t bit = 1u << (b & 31);
-                        atomicOr(&Qm[(b >> 5) * nc + jl], bit);
-                        atomicOr(&Sm[(b >> 5) * nc + jl], bit);
-                        if (c.rec_raster)
-                            atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
-                    }
-                    if (si) {
-                        atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
-                        if (c.rec_raster)
-                            atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
-                    }
-                    it = o;
-                }
-                if (tstate) {
-                    __syncwarp();
-                    tmem_st4(tq + 4 * q, it);
-                }
-                b += dq;
-                jl += dr;
-                if (jl >= nc) { jl -= nc; ++b; }
-            }
-            if (tstate) tmem_wait_st();
-        }
+        neuron_items(c, d, Es, Qm, Sm, cntS, thj, tq, tstate, QN, BN, nc, nst, j0, dq, dr, t, p3);
         __syncthreads();
 
         // ================= next step's input, signalled before this step's STDP
@@ -646,129 +782,35 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         if (c.learn) {
             const float* xpre = d.x_pre + (size_t)(tt % XPRE_SLOTS) * B * NI;
             uint32_t* preS = (uint32_t*)(sm + L.o_pres);
-            uint32_t* nzP = (uint32_t*)(sm + L.o_nzp);
             int* pcol = (int*)(sm + L.o_pcol);
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
-            int* offs = (int*)(sm + L.o_off);
-            uint16_t* lst = (uint16_t*)(sm + L.o_lst);
             const int PS = L.ps;
-            for (int jl = tid; jl < nc; jl += PT) {   // theta, and which columns fired
-                int n = 0;
-                uint32_t nz = 0;
-                for (int w = 0; w < Bw; ++w) {
-                    const uint32_t q = Qm[w * nc + jl];
-                    n += __popc(q);
-                    if (q && w < 32) nz |= 1u << w;
-                }
-                nzQ[jl] = n;                          // post spikes of column jl this step
-                nzQw[jl] = nz;                        // and the batch words holding them
-                double r;
-                if (c.reduce == SNN_REDUCE_SUM) r = (double)n;
-                else if (c.reduce == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)B);
-                else r = n > 0 ? 1.0 : 0.0;
-                thS[jl] = __dadd_rn(__dmul_rn(thS[jl], c.a_th), __dmul_rn(c.theta_plus, r));
-            }
-            // Per input i: the samples whose input i fired, ascending, in
-            // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
-            // counts.  One thread per row reads the row's words of this step's
-            // input-major masks (written by every CTA's encode) and keeps them
-            // in shared memory for the word walks.  Lists are written only while
-            // they fit; both passes walk the spike words instead when the step's
-            // total exceeds the space.
-            int n_ev = 0;
-            {
-                const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
-                const bool vec = Bw == 4 || Bw == 8;       // rows of 16 or 32 bytes, 16-byte aligned
-                const int wp = tid >> 5, ln = tid & 31;
-                for (int r0 = 0; r0 < NI; r0 += PT) {
-                    const int i = r0 + tid;
-                    uint32_t wr[8];                          // the row's first words
-                    int n = 0;
-                    uint32_t nz = 0;
-                    if (i < NI) {
-                        const uint32_t* row = src + (size_t)i * Bw;
-                        if (vec) {
-                            const uint4 q0 = __ldcg((const uint4*)row);
-                            const uint4 q1 = Bw == 8 ? __ldcg((const uint4*)row + 1) : make_uint4(0u, 0u, 0u, 0u);
-                            wr[0] = q0.x; wr[1] = q0.y; wr[2] = q0.z; wr[3] = q0.w;
-                            wr[4] = q1.x; wr[5] = q1.y; wr[6] = q1.z; wr[7] = q1.w;
-#pragma unroll
-                            for (int w = 0; w < 8; ++w) {
-                                if (w < Bw) {
-                                    preS[i * PS + w] = wr[w];
-                                    n += __popc(wr[w]);
-                                    if (wr[w]) nz |= 1u << w;
-                                }
-                            }
-                        } else {
-                            for (int w = 0; w < Bw; ++w) {
-                                const uint32_t m = __ldcg(&row[w]);
-                                preS[i * PS + w] = m;
-                                n += __popc(m);
-                                if (m && w < 32) nz |= 1u << w;
-                            }
-                        }
-                        nzP[i] = nz;
-                    }
-                    int x = n;                               // inclusive scan within the warp
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(FULL, x, o);
-                        if (ln >= o) x += y;
-                    }
-                    if (ln == 31) s_scan[wp] = x;
-                    __syncthreads();
-                    if (wp == 0) {                           // ... and over the warps
-                        int v = s_scan[ln];
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(FULL, v, o);
-                            if (ln >= o) v += y;
-                        }
-                        s_scan[ln] = v;
-                    }
-                    __syncthreads();
-                    const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
-                    if (i < NI) {
-                        offs[i] = start;
-                        if (start + n <= L.lcap) {
-                            int q = start;
-                            if (vec) {
-#pragma unroll
-                                for (int w = 0; w < 8; ++w) {
-                                    uint32_t m = w < Bw ? wr[w] : 0u;
-                                    while (m) {
-                                        lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
-                                        m &= m - 1;
-                                    }
-                                }
-                            } else {
-                                for (int w = 0; w < Bw; ++w) {
-                                    uint32_t m = preS[i * PS + w];
-                                    while (m) {
-                                        lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
-                                        m &= m - 1;
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    n_ev += s_scan[NW - 1];
-                    if (r0 + PT < NI) __syncthreads();       // s_scan is rewritten by the next rows
-                }
-                if (tid == 0) offs[NI] = n_ev;
-            }
-            const bool lists = n_ev <= L.lcap;
-            if (tid < 32) {   // list of the columns with a post spike
+            const bool lists = offs[NI] <= L.lcap;
+            if (tid < 32) {   // which columns fired, and the list of those columns
                 int npc = 0;
                 for (int jl0 = 0; jl0 < nc; jl0 += 32) {
                     const int jl = jl0 + tid;
-                    const bool f = jl < nc && nzQ[jl] != 0u;
+                    int n = 0;
+                    if (jl < nc) {
+                        uint32_t nz = 0;
+                        for (int w = 0; w < Bw; ++w) {
+                            const uint32_t q = Qm[w * nc + jl];
+                            n += __popc(q);
+                            if (q && w < 32) nz |= 1u << w;
+                        }
+                        nzQ[jl] = n;                  // post spikes of column jl this step (theta
+                        nzQw[jl] = nz;                // follows at the next step's start) and the
+                    }                                 // batch words holding them
+                    const bool f = jl < nc && n != 0;
                     const uint32_t bal = __ballot_sync(FULL, f);
                     if (f) pcol[npc + __popc(bal & ((1u << tid) - 1u))] = jl;
                     npc += __popc(bal);
                 }
                 if (tid == 0) s_nq = npc;
+            }
+            if (c.reduce == SNN_REDUCE_MAX || !lists) {   // the step's masks, padded rows
+                const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
+                for (int k = tid; k < NI * Bw; k += PT) preS[(k / Bw) * PS + (k % Bw)] = __ldcg(&src[k]);
             }
             __syncthreads();
             const int warp = tid >> 5, lane = tid & 31;
@@ -884,6 +926,10 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
 
         if (t + 1 < T) ok = grid_wait(bar, d.err, G * nbar, SPIN_LIMIT);
     }
+
+    // ---- thresholds after the last step's STDP
+    if (c.learn && T > 0)
+        for (int jl = tid; jl < nc; jl += PT) thS[jl] = theta_next(c, thS[jl], (int)nzQ[jl]);
 
     // ---- write the CTA's columns back, and the neuron state held in tensor memory
     __syncthreads();

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
         for (int w = 0; w < c.Bw; ++w) n += __popc(Qj[w]);
         double r;
         if (REDUCE == SNN_REDUCE_SUM) r = (double)n;
-        else if (REDUCE == SNN_REDUCE_MEAN) r = __ddiv_rn((double)n, (double)c.B);
+        else if (REDUCE == SNN_REDUCE_MEAN)   // n / B; exactly n * 2^-k for B = 2^k
+            r = c.B_pow2 ? __dmul_rn((double)n, (double)c.inv_B) : __ddiv_rn((double)n, (double)c.B);
         else r = n > 0 ? 1.0 : 0.0;
         d.theta[j] = __dadd_rn(__dmul_rn(d.theta[j], c.a_th), __dmul_rn(c.theta_plus, r));
     }
