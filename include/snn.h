@@ -99,6 +99,17 @@ typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
 
 /* Network specification (units: mV, ms, Hz).  snn_spec_default fills the
  * 784 -> n_exc Diehl & Cook parameter set. */
+/* Learning rule of the input->excitatory weights.
+ *   SNN_RULE_PAIR:      pair-trace STDP, potentiation nu_post*x_pre at a post spike and
+ *                       depression nu_pre*x_post at a pre spike (the default).
+ *   SNN_RULE_POST_NORM: the paper's rule (Sec. "Unsupervised Learning of MNIST digits"):
+ *                       potentiation only, triggered by post-synaptic spikes; after the
+ *                       clipped update every column with a post spike in the batch is
+ *                       scaled so that its weights sum to w_norm (sum in ascending input
+ *                       order, then each weight times w_norm / sum).  Every weight is
+ *                       clipped to [w_min, w_max] at each learning step. */
+typedef enum { SNN_RULE_PAIR = 0, SNN_RULE_POST_NORM = 1 } snn_rule;
+
 typedef struct snn_spec {
     int32_t n_in, n_exc, n_inh;                  /* n_inh must equal n_exc */
     float e_rest, e_reset, e_thresh, e_tau_ms, e_refrac_ms;
@@ -107,6 +118,8 @@ typedef struct snn_spec {
     float w_ei, w_ie;                            /* exc->inh one-to-one, inh->exc all-but-self */
     float trace_tau_ms, nu_pre, nu_post, w_min, w_max;
     int32_t wprec;                               /* snn_wprec */
+    int32_t rule;                                /* snn_rule */
+    float w_norm;                                /* SNN_RULE_POST_NORM: incoming weight sum, > 0 */
     uint64_t w_seed;                             /* used when w_init == NULL */
     const float* w_init;                         /* host [n_in][n_exc], or NULL: seeded init,
                                                     uniform [0,0.3] on the 2^-12 grid */

@@ -37,6 +37,12 @@
 //              mean: D = (P - Q) / B;
 //              max:  D = max_b (pot_b - dep_b)  (signed per-parameter maximum);
 //              W = min(max(W + D, w_min), w_max).
+//   O6' the paper's own rule (Sec. "Unsupervised Learning of MNIST digits": positive
+//              updates triggered by post-synaptic spikes, incoming weights normalised
+//              to a constant sum): dep_b = 0, D and the clip as above; then every
+//              column j with a post-synaptic spike in the batch this step is scaled,
+//              S_j = sum_i W[i,j] (ascending i), W[i,j] = W[i,j] * (w_norm / S_j)
+//              (columns with S_j = 0 are left as they are).
 //   O7 theta:  theta = theta*a_theta + theta_plus*r_j, FP64, r_j = red_b s_e[b,j].
 //   O8 constants: a_* = (R)exp(-dt/tau) from double; a_theta = exp(-dt/tau_theta)
 //              in double; R_e = round(refrac_e/dt), R_i = round(refrac_i/dt).
@@ -68,6 +74,8 @@ struct oracle_params {
     float trace_tau, nu_pre, nu_post, w_min, w_max;
     float dt;
     int32_t wprec;   // storage of W read by the current: 0 FP32, 1 BF16, 2 FP8 e4m3 + column scale
+    int32_t rule;    // 0 pair-trace STDP (O6), 1 post-triggered with normalisation (O6')
+    float w_norm;    // rule 1: the incoming-weight sum of every column after its update
 };
 
 // Complete simulation state; every array is owned by the caller.
@@ -177,6 +185,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         int learn, int reduce, int episodic, oracle_state* S, oracle_record* rec) {
     if (!P || !S || B <= 0 || T < 0 || !rates || !seeds) return 1;
     if (reduce < 0 || reduce > 2) return 1;
+    if (P->rule < 0 || P->rule > 1 || (P->rule == 1 && !(P->w_norm > 0.0f))) return 1;
     if (P && (P->wprec < 0 || P->wprec > 2)) return 1;
     const int NI = P->n_in, N = P->n_exc;
     if (NI <= 0 || N <= 0 || !(P->dt > 0.0f)) return 1;
@@ -341,6 +350,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                         pot = pot * (R)se_new[k];
                         R dep = nu_pre * si;
                         dep = dep * x_post[k];
+                        if (P->rule == 1) dep = (R)0;    // O6': potentiation only
                         const size_t ij = (size_t)i * N + j;
                         if (reduce == 2) {
                             const R delta = pot - dep;
@@ -360,6 +370,19 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                 w = w < w_min ? w_min : w;
                 w = w > w_max ? w_max : w;
                 W[k] = w;
+            }
+            if (P->rule == 1) {                      // O6': normalise the updated columns
+                const R w_norm = (R)P->w_norm;
+                for (int j = 0; j < N; ++j) {
+                    int cnt = 0;
+                    for (int b = 0; b < B; ++b) cnt += se_new[(size_t)b * N + j];
+                    if (cnt == 0) continue;
+                    R S = (R)0;
+                    for (int i = 0; i < NI; ++i) S = S + W[(size_t)i * N + j];
+                    if (S == (R)0) continue;
+                    const R f = w_norm / S;
+                    for (int i = 0; i < NI; ++i) W[(size_t)i * N + j] = W[(size_t)i * N + j] * f;
+                }
             }
             for (int j = 0; j < N; ++j) {
                 int cnt = 0;

@@ -201,6 +201,8 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.rec_input = (flags & SNN_RECORD_INPUT) ? 1 : 0;
     c.test_timeout = (flags & SNN_TEST_BARRIER_TIMEOUT) ? 1 : 0;
     c.wprec = s.wprec;
+    c.rule = s.rule;
+    c.w_norm = s.w_norm;
     return c;
 }
 
@@ -273,6 +275,8 @@ void snn_spec_default(snn_spec* s, int32_t n_exc) {
     s->trace_tau_ms = 20.0f; s->nu_pre = 1e-4f; s->nu_post = 1e-2f;
     s->w_min = 0.0f; s->w_max = 1.0f;
     s->wprec = SNN_W_FP32;
+    s->rule = SNN_RULE_PAIR;
+    s->w_norm = 0.0f;
     s->w_seed = 42;
 }
 
@@ -296,6 +300,10 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
         return fail(nullptr, SNN_ERR_ARG, "snn_create: w_min must be <= w_max");
     if (s.wprec < SNN_W_FP32 || s.wprec > SNN_W_FP8E4M3)
         return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown wprec %d", (int)s.wprec);
+    if (s.rule != SNN_RULE_PAIR && s.rule != SNN_RULE_POST_NORM)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown rule %d", (int)s.rule);
+    if (s.rule == SNN_RULE_POST_NORM && !finite_pos(s.w_norm))
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: SNN_RULE_POST_NORM needs w_norm > 0");
 
     snn_net* n = new (std::nothrow) snn_net();
     if (!n) return fail(nullptr, SNN_ERR_OOM, "snn_create: host allocation failed");

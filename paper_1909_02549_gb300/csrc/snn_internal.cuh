@@ -29,6 +29,8 @@ struct Consts {
     int rec_raster, rec_input;
     int test_timeout;   // make the first grid barrier of the persistent form time out
     int wprec;          // snn_wprec of the weights read by the synaptic current
+    int rule;           // snn_rule of the weight update
+    float w_norm;       // SNN_RULE_POST_NORM: incoming weight sum of an updated column
 };
 
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.

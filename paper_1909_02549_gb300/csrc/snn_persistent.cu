@@ -53,7 +53,7 @@ struct Layout {
     size_t o_cnts, o_actn, o_acts;    // neuron phase
     size_t o_pres;                    // STDP phase (max reduction, list overflow)
     // per-step region: built before the neuron phase, read by the STDP phase
-    size_t o_nzp, o_pcol, o_nzqw;
+    size_t o_nzp, o_pcol, o_nzqw, o_nrm;
     size_t o_off, o_lst;              // per-input lists of spiking samples
     int ps;                           // row stride of the staged input-major masks
     int lcap;                         // list entries that fit
@@ -96,6 +96,7 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_nzp = o;                 o = align16(o + (size_t)c.n_in * 4);
     L.o_pcol = o;                o = align16(o + (size_t)L.ncmax * 4);
     L.o_nzqw = o;                o = align16(o + (size_t)L.ncmax * 4);
+    L.o_nrm = o;                 o = align16(o + (size_t)L.ncmax * 4);
     L.o_off = o;                 o = align16(o + (size_t)(c.n_in + 1) * 4);
     L.o_lst = o;
     {
@@ -617,7 +618,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         const uint32_t* pre_src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
         const bool pre_vec = Bw == 4 || Bw == 8;         // rows of 16 or 32 bytes, 16-byte aligned
         uint4 pq0 = make_uint4(0u, 0u, 0u, 0u), pq1 = make_uint4(0u, 0u, 0u, 0u);
-        if (pre_vec && tid < NI) {
+        if (c.learn && pre_vec && tid < NI) {
             pq0 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw));
             if (Bw == 8) pq1 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw) + 1);
         }
@@ -666,8 +667,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         // counts (the step's input-major masks are complete since the barrier).
         // One thread per row reads the row's words once.  Lists are written
         // only while they fit; the STDP passes walk the spike words instead when
-        // the step's total exceeds the space.
-        {
+        // the step's total exceeds the space.  (Learning off: nothing reads them.)
+        if (c.learn) {
             const uint32_t* src = pre_src;
             const bool vec = pre_vec;
             const int wp = tid >> 5, ln = tid & 31;
@@ -815,8 +816,15 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             __syncthreads();
             const int warp = tid >> 5, lane = tid & 31;
 
-            // (A) columns without a post spike: depression only
-            {
+            // (A) columns without a post spike: depression only (the post-triggered
+            //     rule has none; it clips every weight, and a column scaled to its
+            //     weight sum may have left the bounds)
+            if (c.rule == SNN_RULE_POST_NORM) {
+                for (int k = tid; k < NI * nc; k += PT) {
+                    const int i = k / nc, jl = k % nc;
+                    if (nzQ[jl] == 0u) Ws[i * nst + jl] = fminf(fmaxf(Ws[i * nst + jl], c.w_min), c.w_max);
+                }
+            } else {
 #define SNN_PASS_A(R)                                                                              \
     (lists ? depress_quiet_columns<R, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
            : depress_quiet_columns<R, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
@@ -836,6 +844,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 const int npc = s_nq;
                 const int nch = (NI + 31) / 32;
                 const int ntask = npc * nch;
+                const bool dep_on = c.rule != SNN_RULE_POST_NORM;   // that rule only potentiates
                 for (int u = warp; u < ntask; u += NW) {
                     const int jl = pcol[u / nch];
                     const int i = (u % nch) * 32 + lane;
@@ -871,7 +880,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             const float a = __fmul_rn(c.nu_post, xv[z]);
                             if (is_max) {
                                 const int b = bs[z];
-                                const bool pre = vi && ((Pi[b >> 5] >> (b & 31)) & 1u);
+                                const bool pre = dep_on && vi && ((Pi[b >> 5] >> (b & 31)) & 1u);
                                 const float e = pre ? Es[b * nst + jl] : 0.0f;
                                 pot = fmaxf(pot, __fsub_rn(a, e));
                             } else {
@@ -884,7 +893,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     if (!vi) continue;
                     // depression: input i fired in b, and j has fired in b this episode
                     float dep = 0.0f;
-                    if (lists) {   // every input-spike sample (e is 0 where j has not fired)
+                    if (lists && dep_on) {   // every input-spike sample (e is 0 where j has not fired)
                         const int e1 = offs[i + 1];
                         for (int e = offs[i]; e < e1; ++e) {
                             const int b = lst[e];
@@ -895,7 +904,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                         }
                     }
                     uint32_t words = lists ? 0u : (Bw <= 32 ? nzP[i] : 0xFFFFFFFFu);
-                    for (int ww = 0; ww < (lists ? 0 : Bw); ++ww) {
+                    for (int ww = 0; ww < (lists || !dep_on ? 0 : Bw); ++ww) {
                         if (Bw <= 32) {
                             if (!words) break;
                             ww = __ffs(words) - 1;
@@ -922,6 +931,26 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 }
             }
             __syncthreads();
+
+            // the post-triggered rule: each updated column back to the weight sum
+            // w_norm, S_j = sum_i W[i][j] in ascending i, W[i][j] *= w_norm / S_j
+            if (c.rule == SNN_RULE_POST_NORM) {
+                float* nrm = (float*)(sm + L.o_nrm);
+                const int npc = s_nq;
+                for (int u = tid; u < npc; u += PT) {
+                    const int jl = pcol[u];
+                    float S = 0.0f;
+                    for (int i = 0; i < NI; ++i) S = __fadd_rn(S, Ws[i * nst + jl]);
+                    nrm[u] = S == 0.0f ? 1.0f : __fdiv_rn(c.w_norm, S);   // S = 0: unchanged
+                }
+                __syncthreads();
+                for (int k = tid; k < NI * npc; k += PT) {
+                    const int i = k / npc, u = k % npc;
+                    const int jl = pcol[u];
+                    Ws[i * nst + jl] = __fmul_rn(Ws[i * nst + jl], nrm[u]);
+                }
+                __syncthreads();
+            }
         }
 
         if (t + 1 < T) ok = grid_wait(bar, d.err, G * nbar, SPIN_LIMIT);

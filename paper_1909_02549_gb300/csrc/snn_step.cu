@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
         int nev = 0;
         if (vj) {
             for (int w = 0; w < c.Bw; ++w) {
-                const uint32_t p = P[w], q = Qj[w];
+                // the post-triggered rule has no depression: only post samples count
+                const uint32_t p = c.rule == SNN_RULE_POST_NORM ? 0u : P[w], q = Qj[w];
                 uint32_t m = (p & Sj[w]) | q;
                 while (m) {
                     const int bit = __ffs(m) - 1;
@@ -306,6 +307,32 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
             d.W[(size_t)i * c.N + j] = wv;
         }
     }
+}
+
+// After the update of the post-triggered rule (Sec. "Unsupervised Learning of
+// MNIST digits"): a column that a post spike updated this step is scaled to the
+// weight sum w_norm, S_j = sum_i W[i][j] in ascending i, W[i][j] *= w_norm / S_j
+// (S_j = 0: unchanged); every other column is clipped to [w_min, w_max], as the
+// rule clips all weights each step (a scaled weight may have left the bounds).
+// One thread per column; neighbouring threads read neighbouring columns.
+__global__ void k_normalize(Consts c, Bufs d, int t_local) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c.N) return;
+    const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
+    const uint32_t* Qj = d.postT + ((size_t)(tt & 1ull) * c.N + j) * c.Bw;
+    uint32_t fired = 0u;
+    for (int w = 0; w < c.Bw; ++w) fired |= Qj[w];
+    float* Wj = d.W + j;
+    const size_t N = (size_t)c.N;
+    if (!fired) {
+        for (int i = 0; i < c.n_in; ++i) Wj[i * N] = fminf(fmaxf(Wj[i * N], c.w_min), c.w_max);
+        return;
+    }
+    float S = 0.0f;
+    for (int i = 0; i < c.n_in; ++i) S = __fadd_rn(S, Wj[i * N]);
+    if (S == 0.0f) return;
+    const float f = __fdiv_rn(c.w_norm, S);
+    for (int i = 0; i < c.n_in; ++i) Wj[i * N] = __fmul_rn(Wj[i * N], f);
 }
 
 __global__ void k_extract(Consts c, Bufs d, int field, void* out) {
@@ -436,6 +463,10 @@ cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_
         else if (c.reduce == SNN_REDUCE_MEAN) k_stdp<SNN_REDUCE_MEAN><<<g, 256, 0, s>>>(c, d, t_local);
         else k_stdp<SNN_REDUCE_MAX><<<g, 256, 0, s>>>(c, d, t_local);
         PROF_TRY(cudaGetLastError());
+        if (c.rule == SNN_RULE_POST_NORM) {
+            k_normalize<<<(c.N + 127) / 128, 128, 0, s>>>(c, d, t_local);
+            PROF_TRY(cudaGetLastError());
+        }
         PROF_TRY(prof_stop(prof, s));
     }
     return cudaSuccess;

@@ -112,6 +112,25 @@ def diehl_cook_params(n_exc: int, n_in: int = 784) -> dict:
     )
 
 
+def paper_rule_params(n_exc: int = 100, n_in: int = 784, w_norm: float | None = None) -> dict:
+    """The network of Sec. "Unsupervised Learning of MNIST digits" with the
+    paper's own learning rule: potentiation at post spikes, incoming weights
+    held at a constant sum (0.1 per input unless given), thresholds decaying
+    with a 1000 s time constant."""
+    p = diehl_cook_params(n_exc, n_in)
+    p.update(theta_tau=1e6, rule=1, w_norm=0.1 * n_in if w_norm is None else w_norm)
+    return p
+
+
+def paper_rule_workload(batch: int, n_exc: int = 100, n_in: int = 784, w_seed: int = 42,
+                        w_norm: float | None = None):
+    """(params, rates, seeds, W) for the paper's rule: rates are intensity / 2 Hz
+    as that section states."""
+    p = paper_rule_params(n_exc, n_in, w_norm)
+    r = rates_from_images(images(batch, n_in), divisor=2.0)
+    return p, r, sample_seeds(batch), weights(n_in, n_exc, w_seed)
+
+
 def workload(batch: int, n_exc: int, n_in: int = 784, w_seed: int = 42,
              bf16_grid: bool = False):
     """(params, rates[B][n_in] f32, seeds[B] u64, W[n_in][n_exc] f32)."""

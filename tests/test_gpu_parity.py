@@ -113,6 +113,28 @@ def parity_all_modes(p, r, s, w, T, *, learn=True, reduce="mean", modes=MODES, w
 
 # ------------------------------------------------------------------ cases ---
 
+@pytest.mark.parametrize("w_norm", [None, 600.0])
+@pytest.mark.parametrize("reduce", ["max", "mean", "sum"])
+def test_post_triggered_rule_with_normalisation(reduce, w_norm):
+    """The paper's own rule (potentiation at post spikes, each updated column
+    scaled to a constant weight sum): every mode bit-exact with the oracle.
+    A weight sum of 600 over 784 inputs scales weights past w_max, so the
+    clip of the columns without a post spike is exercised too."""
+    p, r, s, w = synth.paper_rule_workload(16, 100, w_norm=w_norm)
+    st, rec = parity_all_modes(p, r, s, w, 150, reduce=reduce)
+    fired = rec.raster_e.sum(axis=(0, 1)) > 0
+    assert fired.sum() > 0
+    if w_norm is None:   # columns last updated keep the constant sum (up to the clip)
+        assert np.all(np.abs(st.w[:, fired].astype(np.float64).sum(0) - p["w_norm"]) < 1e-2)
+    else:   # some step leaves scaled weights above w_max, for the next step's clip
+        st2 = oracle.new_state(p, len(s), w)
+        above = False
+        for t in range(150):
+            oracle.run(p, st2, r, s, 1, learn=True, reduce=reduce, episodic=(t == 0))
+            above = above or bool(st2.w.max() > p["w_max"])
+        assert above
+
+
 def test_784x100_single_presentation_learning():
     """B=1, 784 -> 100, T=250, pair STDP with mean reduction."""
     p, r, s, w = synth.workload(1, 100)

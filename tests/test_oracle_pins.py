@@ -350,6 +350,89 @@ def test_max_reduction_includes_samples_without_update():
     assert st.w[0, 0] < 0.5
 
 
+# ------------------------------------- O6' the paper's post-triggered rule ---
+
+def _post_rule_run(dtype, w0, t_pre, t_post, n_steps, norm, B=1, x_pre0=None, reduce="mean"):
+    """Two inputs onto one neuron; input 0 fires at t_pre (rate 2000 Hz),
+    input 1 never; the neuron is forced to fire at t_post in every sample."""
+    p = params(n_in=2, rule=1, w_norm=norm)
+    st = oracle.new_state(p, B, np.array([[w0[0]], [w0[1]]]), dtype=dtype)
+    if x_pre0 is not None:
+        st.x_pre[:, 0] = x_pre0
+    ws = []
+    for t in range(n_steps):
+        st.v_e[:] = -40.0 if t == t_post else p["e_rest"]
+        rates = np.zeros((B, 2), np.float32)
+        if t == t_pre:
+            rates[:, 0] = 2000.0
+        rec = step(p, st, rates, learn=True, reduce=reduce)
+        assert np.all(rec.raster_e[0, :, 0] == (t == t_post))
+        ws.append(st.w[:, 0].astype(np.float64).copy())
+    return p, np.array(ws)
+
+
+@pytest.mark.parametrize("delta", [1, 2, 3])
+def test_post_rule_potentiates_then_normalises_the_column(delta):
+    """Pre at t0, post at t0+delta: the update is nu_post times the trace
+    decayed delta steps (the closed form), then the column is rescaled to the
+    constant sum, which keeps the weights' ratio."""
+    w0, norm = (0.25, 0.5), 1.5
+    p, ws = _post_rule_run(np.float64, w0, 2, 2 + delta, 2 + delta + 3, norm)
+    t = 2 + delta
+    assert np.all(ws[:t] == np.array(w0))                      # nothing before the post spike
+    a = math.exp(-1.0 / p["trace_tau"])
+    dw = float(F32(p["nu_post"])) * a ** delta
+    want0 = w0[0] + dw
+    assert abs(ws[t].sum() - norm) < 1e-12                       # constant incoming sum
+    assert abs(ws[t][0] / ws[t][1] - want0 / w0[1]) < 1e-12      # ratio of the updated weights
+    assert np.all(ws[t:] == ws[t])                               # no later change
+
+
+@pytest.mark.parametrize("delta", [1, 2])
+def test_post_rule_has_no_depression(delta):
+    """Post then pre: the pair rule would depress; this rule leaves the
+    weights alone apart from the normalisation at the post spike."""
+    w0, norm = (0.25, 0.5), 0.75                                 # already at the constant sum
+    p, ws = _post_rule_run(np.float64, w0, 2 + delta, 2, 8, norm)
+    assert np.all(np.abs(ws - np.array(w0)) < 1e-15)
+
+
+def test_post_rule_leaves_columns_without_post_spikes_bit_identical():
+    p = params(n_in=2, n_exc=2, rule=1, w_norm=3.0)
+    w = np.array([[0.25, 0.3], [0.5, 0.7]])
+    st = oracle.new_state(p, 1, w, dtype=np.float32)
+    st.x_pre[:, 0] = 1.0
+    st.v_e[0, 0] = -40.0                                         # column 0 fires, column 1 does not
+    st.v_e[0, 1] = p["e_rest"]
+    rec = step(p, st, np.zeros((1, 2), np.float32), learn=True)
+    assert rec.raster_e[0, 0].tolist() == [1, 0]
+    assert np.array_equal(st.w[:, 1], w[:, 1].astype(np.float32))
+    assert abs(float(st.w[:, 0].astype(np.float64).sum()) - 3.0) < 4e-7
+
+
+@pytest.mark.parametrize("reduce", ["max", "mean", "sum"])
+def test_post_rule_batch_reductions(reduce):
+    """Two samples potentiate the same synapse from different traces: max
+    takes the larger update, mean their average, sum their total; the
+    normalisation keeps the resulting ratio."""
+    w0, norm = (0.25, 0.5), 1.0
+    xa, xb = 0.2, 0.9
+    p, ws = _post_rule_run(np.float64, w0, -1, 0, 1, norm, B=2, x_pre0=[xa, xb], reduce=reduce)
+    a = math.exp(-1.0 / p["trace_tau"])
+    nu = float(F32(p["nu_post"]))
+    da, db = nu * xa * a, nu * xb * a
+    d = {"max": max(da, db), "mean": (da + db) / 2, "sum": da + db}[reduce]
+    assert abs(ws[0][0] / ws[0][1] - (w0[0] + d) / w0[1]) < 1e-12
+    assert abs(ws[0].sum() - norm) < 1e-12
+
+
+def test_post_rule_rejects_a_missing_constant_sum():
+    p = params(n_in=2, rule=1, w_norm=0.0)
+    st = oracle.new_state(p, 1, np.full((2, 1), 0.25), dtype=np.float32)
+    with pytest.raises(Exception):
+        step(p, st, np.zeros((1, 2), np.float32), learn=True)
+
+
 # ------------------------------------------------------------ O7 theta ---
 
 def test_theta_accumulates_spikes_with_exponential_decay():
