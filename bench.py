@@ -43,6 +43,8 @@ METRIC = "sample-timesteps/s vs batch, 784→6400 STDP; % roofline; serving p50/
 UNIT = "sample-timesteps/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 WPREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+RULE_NAME = {"pair": "pair STDP",
+             "post_norm": "post-triggered STDP with incoming-weight normalisation"}
 WPREC_NAME = {"fp32": "FP32", "bf16": "BF16 (FP32 master, FP32 accumulation)",
               "fp8": "FP8 E4M3 with per-column scales (FP32 master, FP32 accumulation)"}
 
@@ -61,6 +63,9 @@ def parse():
     ap.add_argument("--wprec", default="fp32", choices=["fp32", "bf16", "fp8"],
                     help="weights read by the synaptic current (accumulation is FP32)")
     ap.add_argument("--no-learn", action="store_true")
+    ap.add_argument("--rule", default="pair", choices=["pair", "post_norm"],
+                    help="pair-trace STDP, or the paper's post-triggered rule with weight "
+                         "normalisation (inputs then at intensity/2 Hz, as that section states)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -71,14 +76,24 @@ def parse():
 
 def workload_config(a, mode):
     return {
-        "workload": "784->%d adaptive-threshold LIF + all-but-self inhibition, pair STDP, "
+        "workload": "784->%d adaptive-threshold LIF + all-but-self inhibition, %s, "
                     "%s reduction, B=%d, T=%d, dt=1 ms, %s weights" % (
-                        a.n_exc, a.reduce, a.batch, a.T, WPREC_NAME[a.wprec]),
+                        a.n_exc, RULE_NAME[a.rule], a.reduce, a.batch, a.T, WPREC_NAME[a.wprec]),
         "B": a.batch, "n_in": 784, "n_exc": a.n_exc, "n_inh": a.n_exc, "T": a.T,
         "reduce": a.reduce, "learn": not a.no_learn, "weights": WPREC_NAME[a.wprec], "mode": mode,
+        "rule": a.rule,
         "l2": "flushed by a 256 MiB write before every step",
-        "inputs": "seeded synthetic 28x28 images (70% zeros, U[0,255]), rate=intensity/4 Hz",
+        "inputs": "seeded synthetic 28x28 images (70%% zeros, U[0,255]), rate=intensity/%d Hz"
+                  % (2 if a.rule == "post_norm" else 4),
     }
+
+
+def bench_workload(a, B):
+    """(params, rates, seeds, W) of the workload the options name, B samples."""
+    from paper_1909_02549_gb300 import synth
+    if a.rule == "post_norm":
+        return synth.paper_rule_workload(B, a.n_exc)
+    return synth.workload(B, a.n_exc)
 
 
 # ------------------------------------------------------------- helpers ---
@@ -187,7 +202,7 @@ def time_oracle(a, seconds: float, max_T: int | None = None):
     from paper_1909_02549_gb300 import synth
     oracle.build()
     B = min(16, a.batch)
-    p, r, s, w = synth.workload(B, a.n_exc)
+    p, r, s, w = bench_workload(a, B)
     T = 2
     st = oracle.new_state(p, B, w)
     t0 = time.perf_counter()
@@ -211,7 +226,7 @@ def run_reference(a):
     from paper_1909_02549_gb300 import synth
     oracle.build()
     B, T = 4, 4
-    p, r, s, w = synth.workload(B, a.n_exc)
+    p, r, s, w = bench_workload(a, B)
 
     def one():
         st = oracle.new_state(p, B, w)
@@ -249,7 +264,8 @@ def recorded_traffic(a, dom):
     sources hash to the value that summary records; else None and why."""
     if dom != "persistent":
         return None, "no capture of k_%s on this workload" % dom
-    default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn) == (256, 6400, 250, "mean", "fp32", False)
+    default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn, a.rule) == (
+        256, 6400, 250, "mean", "fp32", False, "pair")
     if not default:
         return None, "the capture is of the default workload only"
     try:
@@ -397,7 +413,7 @@ def run_ours(a):
             dist.barrier()
 
     B, N, T, learn = a.batch, a.n_exc, a.T, not a.no_learn
-    p, rates, seeds, w = synth.workload(B, N)
+    p, rates, seeds, w = bench_workload(a, B)
     seeds = seeds + np.uint64(100000 * rank)     # replicas draw independent spikes
     net = snn.Network(p, w_init=w, wprec=WPREC[a.wprec])
     r_d = torch.from_numpy(rates).cuda()

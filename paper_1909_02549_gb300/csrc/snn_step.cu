@@ -314,25 +314,30 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
 // weight sum w_norm, S_j = sum_i W[i][j] in ascending i, W[i][j] *= w_norm / S_j
 // (S_j = 0: unchanged); every other column is clipped to [w_min, w_max], as the
 // rule clips all weights each step (a scaled weight may have left the bounds).
-// One thread per column; neighbouring threads read neighbouring columns.
-__global__ void k_normalize(Consts c, Bufs d, int t_local) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= c.N) return;
+// One warp per column: it loads 32 rows at a time and every lane adds them in
+// ascending order (the same sequential sum on each lane).
+__global__ void __launch_bounds__(256) k_normalize(Consts c, Bufs d, int t_local) {
+    const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= c.N) return;                                   // whole warps
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
     const uint32_t* Qj = d.postT + ((size_t)(tt & 1ull) * c.N + j) * c.Bw;
     uint32_t fired = 0u;
-    for (int w = 0; w < c.Bw; ++w) fired |= Qj[w];
+    for (int w = lane; w < c.Bw; w += 32) fired |= Qj[w];
     float* Wj = d.W + j;
     const size_t N = (size_t)c.N;
-    if (!fired) {
-        for (int i = 0; i < c.n_in; ++i) Wj[i * N] = fminf(fmaxf(Wj[i * N], c.w_min), c.w_max);
+    if (!__any_sync(FULL, fired != 0u)) {
+        for (int i = lane; i < c.n_in; i += 32) Wj[i * N] = fminf(fmaxf(Wj[i * N], c.w_min), c.w_max);
         return;
     }
     float S = 0.0f;
-    for (int i = 0; i < c.n_in; ++i) S = __fadd_rn(S, Wj[i * N]);
+    for (int i0 = 0; i0 < c.n_in; i0 += 32) {
+        const float v = i0 + lane < c.n_in ? Wj[(i0 + lane) * N] : 0.0f;
+        const int n = c.n_in - i0 < 32 ? c.n_in - i0 : 32;
+        for (int k = 0; k < n; ++k) S = __fadd_rn(S, __shfl_sync(FULL, v, k));
+    }
     if (S == 0.0f) return;
     const float f = __fdiv_rn(c.w_norm, S);
-    for (int i = 0; i < c.n_in; ++i) Wj[i * N] = __fmul_rn(Wj[i * N], f);
+    for (int i = lane; i < c.n_in; i += 32) Wj[i * N] = __fmul_rn(Wj[i * N], f);
 }
 
 __global__ void k_extract(Consts c, Bufs d, int field, void* out) {
@@ -464,7 +469,7 @@ cudaError_t launch_step(const Consts& c, const Bufs& d, int t_local, cudaStream_
         else k_stdp<SNN_REDUCE_MAX><<<g, 256, 0, s>>>(c, d, t_local);
         PROF_TRY(cudaGetLastError());
         if (c.rule == SNN_RULE_POST_NORM) {
-            k_normalize<<<(c.N + 127) / 128, 128, 0, s>>>(c, d, t_local);
+            k_normalize<<<(c.N + 7) / 8, 256, 0, s>>>(c, d, t_local);   // a warp per column
             PROF_TRY(cudaGetLastError());
         }
         PROF_TRY(prof_stop(prof, s));
