@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--fig1", action="store_true",
+                    help="run the two-layer scaling experiment instead (one JSON line)")
     return ap.parse_args()
 
 
@@ -514,8 +516,50 @@ def run_ours(a):
     return 0
 
 
+def fig1_leg(a):
+    """Sec. "Scaling a Two Layer Network": device time of 1 s of simulated time
+    (T = 1000 at dt = 1 ms) against batch size, output layer size and STDP,
+    over 10 independent trials (weights, rates and seeds drawn anew); run
+    mode AUTO (the persistent form where it fits, else the graph form)."""
+    import torch
+    from paper_1909_02549_gb300 import build, snn, synth
+    build.build()
+    rows = []
+    for n_out in (100, 1000, 10000):
+        for B in (1, 16, 256, 1024):
+            for learn in (False, True):
+                ms = []
+                net = None
+                for trial in range(10):
+                    p, r, s, w = synth.fig1_workload(B, n_out, trial=trial)
+                    rd = torch.from_numpy(r).cuda()
+                    sd = torch.from_numpy(s.view(np.int64)).cuda()
+                    if net is None:   # one network per point: allocation and graph capture once
+                        net = snn.Network(p, w_init=w)
+                        net.run(rd, sd, 1000, learn=learn, mode="auto")
+                    net.set_weights(w)   # this trial's weights (theta stays 0: no adaptation)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    net.run(rd, sd, 1000, learn=learn, mode="auto")
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                net.close()
+                rows.append({"n_out": n_out, "B": B, "stdp": learn, "ms_mean": statistics.mean(ms),
+                             "ms_std": statistics.stdev(ms),
+                             "sample_timesteps_per_s": B * 1000 / (statistics.mean(ms) * 1e-3)})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "two-layer scaling (100 Poisson inputs U[0,120] Hz, "
+                                    "W ~ N(0.1, 0.01^2), LIF layer, 1 s simulated, 10 trials)",
+                      "rows": rows}), flush=True)
+
+
 def main():
     a = parse()
+    if a.fig1:
+        fig1_leg(a)
+        return
     if a.impl == "reference":
         return run_reference(a)
     return run_ours(a)

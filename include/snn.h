@@ -110,6 +110,15 @@ typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
  *                       clipped to [w_min, w_max] at each learning step. */
 typedef enum { SNN_RULE_PAIR = 0, SNN_RULE_POST_NORM = 1 } snn_rule;
 
+/* Excitatory neuron model.
+ *   SNN_NEURON_LIF:    leaky integrate-and-fire with adaptive threshold, reset to e_reset
+ *                      (the default).
+ *   SNN_NEURON_IF_SUB: non-leaky integrate-and-fire with reset by subtraction (Sec. "ANN to
+ *                      SNN conversion"): v <- v + I while not refractory; a spike at
+ *                      v >= th = e_thresh + theta subtracts th - e_reset from v, so the
+ *                      excess over the threshold is kept.  e_tau_ms is not used. */
+typedef enum { SNN_NEURON_LIF = 0, SNN_NEURON_IF_SUB = 1 } snn_neuron;
+
 typedef struct snn_spec {
     int32_t n_in, n_exc, n_inh;                  /* n_inh must equal n_exc */
     float e_rest, e_reset, e_thresh, e_tau_ms, e_refrac_ms;
@@ -120,6 +129,7 @@ typedef struct snn_spec {
     int32_t wprec;                               /* snn_wprec */
     int32_t rule;                                /* snn_rule */
     float w_norm;                                /* SNN_RULE_POST_NORM: incoming weight sum, > 0 */
+    int32_t neuron;                              /* snn_neuron of the excitatory population */
     uint64_t w_seed;                             /* used when w_init == NULL */
     const float* w_init;                         /* host [n_in][n_exc], or NULL: seeded init,
                                                     uniform [0,0.3] on the 2^-12 grid */

@@ -41,7 +41,7 @@ class _Params(C.Structure):
             "e_rest", "e_reset", "e_thresh", "e_tau", "e_refrac", "theta_plus", "theta_tau",
             "i_rest", "i_reset", "i_thresh", "i_tau", "i_refrac", "w_ei", "w_ie",
             "trace_tau", "nu_pre", "nu_post", "w_min", "w_max", "dt")] + [
-        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float)]
+        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32)]
 
 
 class _State(C.Structure):
@@ -133,8 +133,10 @@ def run(params: dict, state: State, rates: np.ndarray, seeds: np.ndarray, T: int
     assert rates.shape == (B, NI) and seeds.shape == (B,)
     rates = np.ascontiguousarray(rates, np.float32)
     seeds = np.ascontiguousarray(seeds, np.uint64)
-    P = _Params(**{k: params[k] for k, _ in _Params._fields_ if k not in ("dt", "wprec", "rule", "w_norm")},
-                dt=dt, wprec=wprec, rule=int(params.get("rule", 0)), w_norm=float(params.get("w_norm", 0.0)))
+    P = _Params(**{k: params[k] for k, _ in _Params._fields_
+                   if k not in ("dt", "wprec", "rule", "w_norm", "neuron")},
+                dt=dt, wprec=wprec, rule=int(params.get("rule", 0)), w_norm=float(params.get("w_norm", 0.0)),
+                neuron=int(params.get("neuron", 0)))
     arrs = {k: getattr(state, k) for k in ("v_e", "v_i", "ref_e", "ref_i", "s_e", "s_i",
                                             "x_pre", "x_post", "w", "theta")}
     for k, a in arrs.items():

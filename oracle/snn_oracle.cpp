@@ -30,6 +30,10 @@
 //              I_inh[b,j] = w_ei*s_e'[b,j]   (' = previous step).
 //   O3 exc:    d=v-rest; d=d*a_e; v=rest+d; if ref>0 { ref-- } else { v=v+(I_in+I_lat) };
 //              spike = (ref was 0) && v >= thresh + (R)theta[j]; spike -> v=reset, ref=R_e.
+//   O3' the non-leaky integrate-and-fire neuron with reset by subtraction
+//              (Sec. "ANN to SNN conversion"), neuron = 1:  if ref>0 { ref-- } else
+//              { v=v+(I_in+I_lat) }; spike = (ref was 0) && v >= th, th = thresh +
+//              (R)theta[j]; spike -> v = v - (th - reset), ref = R_e.
 //   O4 inh:    the same with the inhibitory constants, I_inh and no theta.
 //   O5 traces: x_pre = x_pre*a_x + s_in; x_post = x_post*a_x + s_e.
 //   O6 STDP:   pot_b[i,j] = nu_post*x_pre[b,i]*s_e[b,j],  dep_b[i,j] = nu_pre*s_in[b,i]*x_post[b,j];
@@ -76,6 +80,8 @@ struct oracle_params {
     int32_t wprec;   // storage of W read by the current: 0 FP32, 1 BF16, 2 FP8 e4m3 + column scale
     int32_t rule;    // 0 pair-trace STDP (O6), 1 post-triggered with normalisation (O6')
     float w_norm;    // rule 1: the incoming-weight sum of every column after its update
+    int32_t neuron;  // excitatory neuron: 0 leaky with reset to a value (O3), 1 IF with
+                     // reset by subtraction (O3')
 };
 
 // Complete simulation state; every array is owned by the caller.
@@ -186,6 +192,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
     if (!P || !S || B <= 0 || T < 0 || !rates || !seeds) return 1;
     if (reduce < 0 || reduce > 2) return 1;
     if (P->rule < 0 || P->rule > 1 || (P->rule == 1 && !(P->w_norm > 0.0f))) return 1;
+    if (P->neuron < 0 || P->neuron > 1) return 1;
     if (P && (P->wprec < 0 || P->wprec > 2)) return 1;
     const int NI = P->n_in, N = P->n_exc;
     if (NI <= 0 || N <= 0 || !(P->dt > 0.0f)) return 1;
@@ -293,9 +300,12 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                 const size_t k = (size_t)b * N + j;
                 // excitatory, adaptive threshold
                 {
-                    R d = v_e[k] - e_rest;
-                    d = d * a_e;
-                    R v = e_rest + d;
+                    R v = v_e[k];
+                    if (P->neuron == 0) {               // O3: leak towards rest
+                        R d = v - e_rest;
+                        d = d * a_e;
+                        v = e_rest + d;
+                    }
                     const bool free_ = ref_e[k] == 0;
                     if (!free_) {
                         ref_e[k] = ref_e[k] - 1;
@@ -305,7 +315,15 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                     }
                     const R th = e_thresh + (R)theta[j];
                     const bool spk = free_ && v >= th;
-                    if (spk) { v = e_reset; ref_e[k] = R_e; }
+                    if (spk) {
+                        if (P->neuron == 0) {
+                            v = e_reset;
+                        } else {                        // O3': subtract threshold - baseline
+                            const R gap = th - e_reset;
+                            v = v - gap;
+                        }
+                        ref_e[k] = R_e;
+                    }
                     v_e[k] = v;
                     se_new[k] = spk ? 1 : 0;
                 }

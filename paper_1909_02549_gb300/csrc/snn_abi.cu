@@ -203,6 +203,7 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.wprec = s.wprec;
     c.rule = s.rule;
     c.w_norm = s.w_norm;
+    c.neuron = s.neuron;
     return c;
 }
 
@@ -277,6 +278,7 @@ void snn_spec_default(snn_spec* s, int32_t n_exc) {
     s->wprec = SNN_W_FP32;
     s->rule = SNN_RULE_PAIR;
     s->w_norm = 0.0f;
+    s->neuron = SNN_NEURON_LIF;
     s->w_seed = 42;
 }
 
@@ -304,6 +306,8 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
         return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown rule %d", (int)s.rule);
     if (s.rule == SNN_RULE_POST_NORM && !finite_pos(s.w_norm))
         return fail(nullptr, SNN_ERR_ARG, "snn_create: SNN_RULE_POST_NORM needs w_norm > 0");
+    if (s.neuron != SNN_NEURON_LIF && s.neuron != SNN_NEURON_IF_SUB)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown neuron %d", (int)s.neuron);
 
     snn_net* n = new (std::nothrow) snn_net();
     if (!n) return fail(nullptr, SNN_ERR_OOM, "snn_create: host allocation failed");

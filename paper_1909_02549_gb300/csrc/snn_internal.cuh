@@ -31,7 +31,33 @@ struct Consts {
     int wprec;          // snn_wprec of the weights read by the synaptic current
     int rule;           // snn_rule of the weight update
     float w_norm;       // SNN_RULE_POST_NORM: incoming weight sum of an updated column
+    int neuron;         // snn_neuron of the excitatory population
 };
+
+// One step of an excitatory membrane (every run form uses it): the leaky
+// neuron decays towards rest, d = v - rest; d = d*a; v = rest + d, then
+// integrates `drive` unless refractory and resets to e_reset at a spike; the
+// non-leaky IF neuron (Sec. "ANN to SNN conversion") integrates without decay
+// and at a spike subtracts th - e_reset, keeping the excess over the
+// threshold.  th is the threshold with theta; se returns the spike.
+__device__ __forceinline__ float exc_membrane(int neuron, float v, float drive, float th,
+                                              float e_rest, float a_e, float e_reset, int R_e,
+                                              int& ref_e, bool& se) {
+    if (neuron == SNN_NEURON_LIF) {
+        float dv = __fsub_rn(v, e_rest);
+        dv = __fmul_rn(dv, a_e);
+        v = __fadd_rn(e_rest, dv);
+    }
+    const bool free_e = ref_e == 0;
+    if (!free_e) ref_e -= 1;
+    else v = __fadd_rn(v, drive);
+    se = free_e && v >= th;
+    if (se) {
+        v = neuron == SNN_NEURON_LIF ? e_reset : __fsub_rn(v, __fsub_rn(th, e_reset));
+        ref_e = R_e;
+    }
+    return v;
+}
 
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.
 // Buffers indexed by the absolute step tt rotate so that one step's writers

@@ -40,6 +40,7 @@ struct NaConsts {
     float i_rest, i_reset, i_thresh, a_i;
     float w_ei, w_ie, dt;
     int R_e, R_i;
+    int neuron;            // snn_neuron of the excitatory population
 };
 
 struct NaBufs {
@@ -132,18 +133,13 @@ __global__ void __launch_bounds__(256) k_na_neuron(NaConsts c, NaBufs d, int t) 
     const int C = (int)d.cnt[(size_t)((t + 2) % 3) * c.B + b];
     const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
     const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-    float v = d.v_e[idx];
-    float dv = __fsub_rn(v, c.e_rest);
-    dv = __fmul_rn(dv, c.a_e);
-    v = __fadd_rn(c.e_rest, dv);
-    const bool free_e = ref_e == 0;
-    if (!free_e) ref_e -= 1;
-    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
-    const bool se = free_e && v >= __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j]));
-    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    bool se;
+    const float v = snn::exc_membrane(c.neuron, d.v_e[idx], __fadd_rn(I, I_lat),
+                                      __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j])), c.e_rest,
+                                      c.a_e, c.e_reset, c.R_e, ref_e, se);
     d.v_e[idx] = v;
     float vi = d.v_i[idx];
-    dv = __fsub_rn(vi, c.i_rest);
+    float dv = __fsub_rn(vi, c.i_rest);
     dv = __fmul_rn(dv, c.a_i);
     vi = __fadd_rn(c.i_rest, dv);
     const bool free_i = ref_i == 0;
@@ -209,6 +205,7 @@ extern "C" snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, co
     c.a_i = (float)std::exp(-(double)dt_ms / (double)s.i_tau_ms);
     c.w_ei = s.w_ei; c.w_ie = s.w_ie; c.dt = dt_ms;
     c.R_e = R_e; c.R_i = R_i;
+    c.neuron = s.neuron;
 
     const size_t BN = (size_t)B * s.n_exc, BI = (size_t)B * s.n_in;
     unsigned char* p = (unsigned char*)base;

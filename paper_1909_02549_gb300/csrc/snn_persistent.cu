@@ -222,17 +222,11 @@ __device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I
     const int se_prev = (it.st & ST_SE) ? 1 : 0, si_prev = (it.st & ST_SI) ? 1 : 0;
     const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
     const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-    float v = it.v;
-    float dv = __fsub_rn(v, c.e_rest);
-    dv = __fmul_rn(dv, c.a_e);
-    v = __fadd_rn(c.e_rest, dv);
-    const bool free_e = ref_e == 0;
-    if (!free_e) ref_e -= 1;
-    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
-    const bool se = free_e && v >= thj;
-    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    bool se;
+    const float v = exc_membrane(c.neuron, it.v, __fadd_rn(I, I_lat), thj, c.e_rest, c.a_e,
+                                 c.e_reset, c.R_e, ref_e, se);
     float vi = it.vi;
-    dv = __fsub_rn(vi, c.i_rest);
+    float dv = __fsub_rn(vi, c.i_rest);
     dv = __fmul_rn(dv, c.a_i);
     vi = __fadd_rn(c.i_rest, dv);
     const bool free_i = ref_i == 0;

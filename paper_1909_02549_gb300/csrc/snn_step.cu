@@ -177,21 +177,15 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
     const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);         // one-to-one
 
     // Excitatory, adaptive threshold.
-    float v = d.v_e[idx];
-    float dv = __fsub_rn(v, c.e_rest);
-    dv = __fmul_rn(dv, c.a_e);
-    v = __fadd_rn(c.e_rest, dv);
-    const bool free_e = ref_e == 0;
-    if (!free_e) ref_e -= 1;
-    else v = __fadd_rn(v, __fadd_rn(I, I_lat));
     const float th = __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j]));
-    const bool se = free_e && v >= th;
-    if (se) { v = c.e_reset; ref_e = c.R_e; }
+    bool se;
+    const float v = exc_membrane(c.neuron, d.v_e[idx], __fadd_rn(I, I_lat), th, c.e_rest, c.a_e,
+                                 c.e_reset, c.R_e, ref_e, se);
     d.v_e[idx] = v;
 
     // Inhibitory.
     float vi = d.v_i[idx];
-    dv = __fsub_rn(vi, c.i_rest);
+    float dv = __fsub_rn(vi, c.i_rest);
     dv = __fmul_rn(dv, c.a_i);
     vi = __fadd_rn(c.i_rest, dv);
     const bool free_i = ref_i == 0;

@@ -22,6 +22,7 @@ SNN_REDUCE_SUM, SNN_REDUCE_MEAN, SNN_REDUCE_MAX = 0, 1, 2
 REDUCE = {"sum": SNN_REDUCE_SUM, "mean": SNN_REDUCE_MEAN, "max": SNN_REDUCE_MAX}
 SNN_W_FP32, SNN_W_BF16, SNN_W_FP8E4M3 = 0, 1, 2
 SNN_RULE_PAIR, SNN_RULE_POST_NORM = 0, 1
+SNN_NEURON_LIF, SNN_NEURON_IF_SUB = 0, 1
 SNN_CONTINUE = 1 << 0
 SNN_RECORD_RASTER = 1 << 1
 SNN_RECORD_INPUT = 1 << 2
@@ -69,7 +70,7 @@ class snn_spec(C.Structure):
             "e_rest", "e_reset", "e_thresh", "e_tau_ms", "e_refrac_ms", "theta_plus",
             "theta_tau_ms", "i_rest", "i_reset", "i_thresh", "i_tau_ms", "i_refrac_ms",
             "w_ei", "w_ie", "trace_tau_ms", "nu_pre", "nu_post", "w_min", "w_max")] + [
-        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float),
+        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32),
         ("w_seed", C.c_uint64), ("w_init", C.c_void_p),
         ("theta_init", C.c_void_p)]
 

@@ -98,6 +98,48 @@ def weights(n_in: int, n_exc: int, w_seed: int = 42, bf16_grid: bool = False) ->
     return w.astype(np.float32).reshape(n_in, n_exc)
 
 
+def _units(seed: int, n: int) -> np.ndarray:
+    """n uniform doubles in [0, 1) from one SplitMix64 stream (seed)."""
+    with np.errstate(over="ignore"):
+        states = np.uint64(seed) + np.arange(1, n + 1, dtype=np.uint64) * GOLDEN_GAMMA
+        return (_mix64(states) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def normal_weights(n_in: int, n_out: int, mean: float, std: float, seed: int) -> np.ndarray:
+    """``[n_in][n_out]`` float32 weights N(mean, std^2), Box-Muller on a
+    SplitMix64 stream (pairs of draws)."""
+    n = n_in * n_out
+    u = _units(seed, 2 * n).reshape(n, 2)
+    z = np.sqrt(-2.0 * np.log1p(-u[:, 0])) * np.cos(2.0 * np.pi * u[:, 1])
+    return (mean + std * z).astype(np.float32).reshape(n_in, n_out)
+
+
+def fig1_params(n_out: int, n_in: int = 100, neuron: int = 0) -> dict:
+    """The two-layer network of Sec. "Scaling a Two Layer Network": Poisson
+    inputs onto a layer of LIF neurons (rest -65, reset -65, threshold -52 mV,
+    tau 100 ms, refractory 5 ms), no adaptive threshold and no inhibition (the
+    inhibitory population gets no drive and gives none), pair STDP when
+    learning.  neuron=1: non-leaky IF neurons with reset by subtraction,
+    threshold 1 and baseline 0 (Sec. "ANN to SNN conversion")."""
+    p = diehl_cook_params(n_out, n_in)
+    p.update(e_rest=-65.0, e_reset=-65.0, e_thresh=-52.0, e_tau=100.0, e_refrac=5.0,
+             theta_plus=0.0, w_ei=0.0, w_ie=0.0)
+    if neuron == 1:
+        p.update(neuron=1, e_rest=0.0, e_reset=0.0, e_thresh=1.0, e_refrac=0.0)
+    return p
+
+
+def fig1_workload(batch: int, n_out: int, n_in: int = 100, trial: int = 0, neuron: int = 0):
+    """(params, rates, seeds, W) for Sec. "Scaling a Two Layer Network": rates
+    uniform in [0, 120] Hz per sample and input, weights N(0.1, 0.01^2);
+    `trial` selects an independent draw of all three."""
+    p = fig1_params(n_out, n_in, neuron)
+    rates = (120.0 * _units(7000 + 31 * trial, batch * n_in)).astype(np.float32).reshape(batch, n_in)
+    seeds = sample_seeds(batch, first=20000 + 100000 * trial)
+    w = normal_weights(n_in, n_out, 0.1, 0.01, seed=9000 + trial)
+    return p, rates, seeds, w
+
+
 def diehl_cook_params(n_exc: int, n_in: int = 784) -> dict:
     """Network parameters of the adaptive-threshold LIF network with lateral
     inhibition (784 Poisson inputs -> n_exc excitatory -> n_exc inhibitory),

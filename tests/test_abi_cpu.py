@@ -50,6 +50,7 @@ def test_spec_default_matches_workload_parameters(lib):
     assert s.n_inh == 400 and s.wprec == snn.SNN_W_FP32 and s.w_init is None
     # the fields after the rule read back where the library wrote them
     assert s.rule == snn.SNN_RULE_PAIR and s.w_norm == 0.0 and s.w_seed == 42
+    assert s.neuron == snn.SNN_NEURON_LIF
 
 
 def test_calls_on_null_network_return_status(lib):
@@ -83,6 +84,10 @@ def test_create_rejects_bad_specs(lib):
     s.rule = snn.SNN_RULE_POST_NORM                     # needs a positive weight sum
     assert lib.snn_create(C.byref(s), C.byref(out)) == snn.SNN_ERR_ARG
     assert "w_norm" in snn.snn_last_error(None)
+    s = snn.snn_spec_default(10)
+    s.neuron = 4
+    assert lib.snn_create(C.byref(s), C.byref(out)) == snn.SNN_ERR_ARG
+    assert "neuron" in snn.snn_last_error(None)
 
 
 def test_create_without_gpu_fails_cleanly(lib):

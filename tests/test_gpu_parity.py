@@ -113,6 +113,19 @@ def parity_all_modes(p, r, s, w, T, *, learn=True, reduce="mean", modes=MODES, w
 
 # ------------------------------------------------------------------ cases ---
 
+@pytest.mark.parametrize("learn", [True, False])
+@pytest.mark.parametrize("neuron", [0, 1])
+def test_two_layer_scaling_network_lif_and_if(neuron, learn):
+    """The network of the scaling experiment (100 inputs at U[0,120] Hz,
+    N(0.1, 0.01^2) weights, a layer without inhibition or adaptation), with
+    leaky neurons and with IF neurons reset by subtraction: every mode
+    bit-exact with the oracle.  100 inputs also take the unaligned staging
+    paths of the persistent form."""
+    p, r, s, w = synth.fig1_workload(8, 300, neuron=neuron)
+    st, rec = parity_all_modes(p, r, s, w, 200, learn=learn)
+    assert rec.raster_e.sum() > 0 and rec.raster_i.sum() == 0
+
+
 @pytest.mark.parametrize("w_norm", [None, 600.0])
 @pytest.mark.parametrize("reduce", ["max", "mean", "sum"])
 def test_post_triggered_rule_with_normalisation(reduce, w_norm):

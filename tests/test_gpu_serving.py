@@ -33,11 +33,13 @@ def alone_counts(p, w, wprec, rates, seed, T):
     return out
 
 
-@pytest.mark.parametrize("wprec", [0, 2])
-def test_each_request_equals_its_alone_run_in_the_mix(wprec):
+@pytest.mark.parametrize("wprec,neuron", [(0, 0), (2, 0), (0, 1)])
+def test_each_request_equals_its_alone_run_in_the_mix(wprec, neuron):
     m = snn()
     N, nreq = 400, 36
     p = synth.diehl_cook_params(N)
+    if neuron == 1:   # IF neurons with reset by subtraction
+        p.update(neuron=1, e_rest=0.0, e_reset=0.0, e_thresh=1.0, e_refrac=0.0)
     w = synth.weights(784, N)
     net = m.Network(p, w_init=w, wprec=wprec)
     srv = m.snn_serve_create(net.handle, 8, 1 << 30)

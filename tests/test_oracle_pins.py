@@ -350,6 +350,70 @@ def test_max_reduction_includes_samples_without_update():
     assert st.w[0, 0] < 0.5
 
 
+# -------------------------------- O3' IF neuron with reset by subtraction ---
+
+def _if_params(**kw):
+    q = dict(neuron=1, e_rest=0.0, e_thresh=1.0, e_reset=0.0, e_refrac=0.0, w_ie=0.0,
+             w_ei=0.0, theta_plus=0.0)
+    q.update(kw)
+    return params(**q)
+
+
+def _if_run(p, drive, T, v0=None):
+    """One always-firing input (2000 Hz) with weight `drive` onto one IF neuron."""
+    st = oracle.new_state(p, 1, np.full((1, 1), drive), dtype=np.float32)
+    if v0 is not None:
+        st.v_e[:] = v0
+    vs, spikes = [], []
+    for _ in range(T):
+        rec = step(p, st, 2000.0 if drive != 0.0 else 0.0)
+        spikes.append(int(rec.raster_e[0, 0, 0]))
+        vs.append(float(st.v_e[0, 0]))
+    return np.array(vs), np.array(spikes)
+
+
+def test_if_neuron_does_not_leak():
+    vs, spikes = _if_run(_if_params(), 0.0, 50, v0=0.625)
+    assert np.all(vs == np.float32(0.625)) and spikes.sum() == 0
+
+
+@pytest.mark.parametrize("drive", [0.25, 0.375, 0.5625, 0.8125])
+def test_if_neuron_rate_is_drive_over_threshold(drive):
+    """Constant drive I (dyadic, so every sum is exact): after t steps the
+    neuron has fired k = floor(t I / theta) times and holds t I - k theta."""
+    T = 64
+    vs, spikes = _if_run(_if_params(), drive, T)
+    for t in range(1, T + 1):
+        k = math.floor(t * drive)                      # theta = 1
+        assert spikes[:t].sum() == k, t
+        assert vs[t - 1] == t * drive - k, t
+
+
+def test_if_reset_keeps_the_excess_above_threshold():
+    """Drive 1.5 with threshold 1: one spike per step, and the 0.5 over the
+    threshold of each step stays in the voltage (a reset to a value would
+    lose it)."""
+    vs, spikes = _if_run(_if_params(), 1.5, 6)
+    assert spikes.tolist() == [1] * 6
+    assert vs.tolist() == [0.5 * t for t in range(1, 7)]
+
+
+def test_if_reset_subtracts_threshold_minus_baseline():
+    p = _if_params(e_reset=-0.5, e_rest=-0.5)           # baseline -0.5: a spike removes 1.5
+    vs, spikes = _if_run(p, 0.75, 4, v0=-0.5)
+    # from -0.5: 0.25, 1.0 (spike: 1.0 - 1.5), 0.25, 1.0 (spike)
+    assert spikes.tolist() == [0, 1, 0, 1]
+    assert vs.tolist() == [0.25, -0.5, 0.25, -0.5]
+
+
+def test_if_neuron_refractory_blocks_input():
+    p = _if_params(e_refrac=2.0)                         # two steps
+    vs, spikes = _if_run(p, 0.5, 8)
+    # 0.5, 1.0 (spike -> 0, 2 steps blocked), 0, 0, 0.5, 1.0 (spike), 0, 0
+    assert spikes.tolist() == [0, 1, 0, 0, 0, 1, 0, 0]
+    assert vs.tolist() == [0.5, 0.0, 0.0, 0.0, 0.5, 0.0, 0.0, 0.0]
+
+
 # ------------------------------------- O6' the paper's post-triggered rule ---
 
 def _post_rule_run(dtype, w0, t_pre, t_post, n_steps, norm, B=1, x_pre0=None, reduce="mean"):

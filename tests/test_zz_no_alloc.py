@@ -55,9 +55,12 @@ def counts_from_noalloc(p, w_d, theta_d, rates, seeds, T):
     return out.cpu().numpy().view(np.uint32).reshape(B, N)
 
 
-def test_noalloc_matches_the_allocating_path_on_two_calls_in_a_row():
+@pytest.mark.parametrize("neuron", [0, 1])
+def test_noalloc_matches_the_allocating_path_on_two_calls_in_a_row(neuron):
     N, T = 400, 250
     p, rates, seeds, w = synth.workload(24, N)
+    if neuron == 1:   # IF neurons with reset by subtraction
+        p.update(neuron=1, e_rest=0.0, e_reset=0.0, e_thresh=1.0, e_refrac=0.0)
     theta = np.linspace(0.0, 1.5, N)              # exercises the adaptive threshold
     w_d = torch.from_numpy(w).cuda()
     theta_d = torch.from_numpy(theta).cuda()
