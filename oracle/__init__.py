@@ -2,10 +2,12 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``snn_oracle.cpp`` (plain C++,
-float and double instantiations) through ctypes and shares nothing with the
-CUDA library: no code, header, constant or helper.
+float and double instantiations) and ``rec_oracle.cpp`` (the recurrent
+inference network) through ctypes and shares nothing with the CUDA library:
+no code, header, constant or helper.
 
-See ``snn_oracle.cpp`` for the update equations (readings O1-O8) and the paper
+See ``snn_oracle.cpp`` for the update equations (readings O1-O8) and
+``rec_oracle.cpp`` for the recurrent network's (R1-R5), with the paper
 passages they follow.
 """
 from __future__ import annotations
@@ -19,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "snn_oracle.cpp")
+_SRC_REC = os.path.join(_HERE, "rec_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "libsnn_oracle.so")
 
 REDUCE = {"sum": 0, "mean": 1, "max": 2}
@@ -27,10 +30,11 @@ REDUCE = {"sum": 0, "mean": 1, "max": 2}
 def build(force: bool = False) -> str:
     """Compile the oracle (g++, -O2 -ffp-contract=off, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_REC))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC])
+                               "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_REC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -194,3 +198,69 @@ def poisson_thresholds(rates, dt: float = 1.0) -> np.ndarray:
     out = np.empty(r.shape, np.uint32)
     lib().oracle_poisson_thresholds(r.ctypes.data, C.c_float(dt), out.ctypes.data, r.size)
     return out
+
+
+# ----------------------------------------------- recurrent inference network ---
+
+class _RecParams(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hid", C.c_int32), ("n_out", C.c_int32)] + [
+        (n, C.c_float) for n in ("tau_mem", "tau_syn", "v_thresh", "v_reset", "dt")]
+
+
+class _RecState(C.Structure):
+    _fields_ = [("v", C.c_void_p), ("i_syn", C.c_void_p), ("s_h", C.c_void_p),
+                ("v_out", C.c_void_p), ("counts", C.c_void_p), ("step", C.c_uint64)]
+
+
+class _RecRecord(C.Structure):
+    _fields_ = [("raster_h", C.c_void_p), ("raster_in", C.c_void_p)]
+
+
+@dataclass
+class RecState:
+    """Per-sample state of the recurrent network (numpy arrays, FP32)."""
+    v: np.ndarray
+    i_syn: np.ndarray
+    s_h: np.ndarray
+    v_out: np.ndarray
+    counts: np.ndarray
+    step: int = 0
+
+
+def rec_new_state(params: dict, B: int) -> RecState:
+    N, NO = params["n_hid"], params["n_out"]
+    return RecState(v=np.zeros((B, N), np.float32), i_syn=np.zeros((B, N), np.float32),
+                    s_h=np.zeros((B, N), np.uint8), v_out=np.zeros((B, NO), np.float32),
+                    counts=np.zeros((B, N), np.uint32))
+
+
+def rec_run(params: dict, st: RecState, rates, seeds, T: int, w_ff, w_rec, w_out, *,
+            dt: float = 1.0, episodic: bool = True, record: bool = True):
+    """T steps of the recurrent network; the weights are float arrays holding
+    BF16 values.  Returns (raster_h [T][B][n_hid], raster_in [T][B][n_in]) as
+    uint8, or (None, None) without recording."""
+    f = lib().rec_oracle_run
+    f.restype = C.c_int
+    f.argtypes = [C.POINTER(_RecParams), C.c_int, C.c_int] + [C.c_void_p] * 5 + [
+        C.c_int, C.POINTER(_RecState), C.POINTER(_RecRecord)]
+    B = st.v.shape[0]
+    P = _RecParams(n_in=params["n_in"], n_hid=params["n_hid"], n_out=params["n_out"],
+                   tau_mem=params["tau_mem"], tau_syn=params["tau_syn"],
+                   v_thresh=params["v_thresh"], v_reset=params["v_reset"], dt=dt)
+    arrs = [np.ascontiguousarray(x, np.float32) for x in (w_ff, w_rec, w_out)]
+    rates = np.ascontiguousarray(rates, np.float32)
+    seeds = np.ascontiguousarray(seeds, np.uint64)
+    S = _RecState(v=_ptr(st.v), i_syn=_ptr(st.i_syn), s_h=_ptr(st.s_h), v_out=_ptr(st.v_out),
+                  counts=_ptr(st.counts), step=st.step)
+    rh = ri = None
+    if record:
+        rh = np.zeros((T, B, params["n_hid"]), np.uint8)
+        ri = np.zeros((T, B, params["n_in"]), np.uint8)
+    R = _RecRecord(raster_h=_ptr(rh) if rh is not None else None,
+                   raster_in=_ptr(ri) if ri is not None else None)
+    rc = f(C.byref(P), B, T, _ptr(rates), _ptr(seeds), _ptr(arrs[0]), _ptr(arrs[1]),
+           _ptr(arrs[2]), 1 if episodic else 0, C.byref(S), C.byref(R))
+    if rc != 0:
+        raise ValueError("rec_oracle_run: bad arguments")
+    st.step = int(S.step)
+    return rh, ri

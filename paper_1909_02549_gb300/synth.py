@@ -140,6 +140,42 @@ def fig1_workload(batch: int, n_out: int, n_in: int = 100, trial: int = 0, neuro
     return p, rates, seeds, w
 
 
+def to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """float32 -> bfloat16 bit patterns (uint16), round to nearest even (the
+    storage format of the recurrent network's weights)."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+
+
+def bf16_bits_to_float(b: np.ndarray) -> np.ndarray:
+    """bfloat16 bit patterns -> the float32 values they hold (exact)."""
+    return (np.ascontiguousarray(b, np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+def rec_params(n_in: int = 1024, n_hid: int = 4096, n_out: int = 10) -> dict:
+    """The recurrent inference network: current-based LIF neurons with
+    exponential synapses (tau_mem 20 ms, tau_syn 5 ms, threshold 1, reset 0)."""
+    return dict(n_in=n_in, n_hid=n_hid, n_out=n_out, tau_mem=20.0, tau_syn=5.0,
+                v_thresh=1.0, v_reset=0.0)
+
+
+def rec_workload(batch: int, n_in: int = 1024, n_hid: int = 4096, n_out: int = 10,
+                 seed: int = 0):
+    """(params, rates [B][n_in] f32, seeds [B] u64, w_ff, w_rec, w_out) with the
+    weights as bfloat16 bit patterns: rates uniform in [0, 50] Hz, W_ff dense
+    N(0, 0.05^2), W_rec a 10 % Bernoulli mask times N(0, 0.02^2) (exact zeros
+    elsewhere), W_out N(0, 0.05^2)."""
+    p = rec_params(n_in, n_hid, n_out)
+    rates = (50.0 * _units(31000 + seed, batch * n_in)).astype(np.float32).reshape(batch, n_in)
+    seeds = sample_seeds(batch, first=40000 + 100000 * seed)
+    w_ff = to_bf16_bits(normal_weights(n_in, n_hid, 0.0, 0.05, 32000 + seed))
+    mask = _units(33000 + seed, n_hid * n_hid).reshape(n_hid, n_hid) < 0.1
+    w_rec = to_bf16_bits(np.where(mask, normal_weights(n_hid, n_hid, 0.0, 0.02, 34000 + seed),
+                                  np.float32(0.0)))
+    w_out = to_bf16_bits(normal_weights(n_hid, n_out, 0.0, 0.05, 35000 + seed))
+    return p, rates, seeds, w_ff, w_rec, w_out
+
+
 def diehl_cook_params(n_exc: int, n_in: int = 784) -> dict:
     """Network parameters of the adaptive-threshold LIF network with lateral
     inhibition (784 Poisson inputs -> n_exc excitatory -> n_exc inhibitory),
