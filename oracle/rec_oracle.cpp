@@ -38,7 +38,7 @@ struct rec_state {
     float* i_syn;      // [B][n_hid]
     uint8_t* s_h;      // [B][n_hid] hidden spikes of the previous step
     float* v_out;      // [B][n_out]
-    uint32_t* counts;  // [B][n_hid] hidden spike counts
+    uint32_t* counts;  // [B][n_hid] hidden spike counts of the last run
     uint64_t step;     // step counter of the next step within the episode
 };
 
@@ -76,11 +76,12 @@ int rec_oracle_run(const rec_params* P, int B, int T, const float* rates, const 
     const float a_syn = (float)std::exp(-(double)P->dt / (double)P->tau_syn);
     if (episodic) {
         for (size_t k = 0; k < (size_t)B * N; ++k) {
-            S->v[k] = 0.0f; S->i_syn[k] = 0.0f; S->s_h[k] = 0; S->counts[k] = 0;
+            S->v[k] = 0.0f; S->i_syn[k] = 0.0f; S->s_h[k] = 0;
         }
         for (size_t k = 0; k < (size_t)B * NO; ++k) S->v_out[k] = 0.0f;
         S->step = 0;
     }
+    for (size_t k = 0; k < (size_t)B * N; ++k) S->counts[k] = 0;   // counts of this run
     std::vector<uint32_t> thr((size_t)B * NI);
     for (size_t k = 0; k < thr.size(); ++k) thr[k] = threshold_of(rates[k], P->dt);
     std::vector<uint8_t> s_in((size_t)B * NI), s_new((size_t)B * N);
