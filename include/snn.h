@@ -313,6 +313,66 @@ SNN_API snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, const
  * the last failed snn_create on this thread. */
 SNN_API const char* snn_last_error(const snn_net* net);
 
+/* ------------------------------------------------------------------------
+ * Recurrent inference network (no plasticity): n_in Poisson inputs onto n_hid
+ * current-based LIF neurons with exponential synapses and a recurrent
+ * connection, read out by summing the inputs to n_out output units (Sec.
+ * "Implementation": per-sample state duplicated B times; Sec. "ANN to SNN
+ * conversion": inference networks read out by the summed input to the last
+ * layer).  Per step t and sample b, with s_h' the previous step's spikes:
+ *   x     = sum over active inputs a of W_ff[a][j] (ascending a), then over
+ *           k with s_h'[k] of W_rec[k][j] (ascending k), one FP32 sum;
+ *   I     = a_syn*I + x;   v = a_mem*v + I;   spike at v >= v_thresh, v = v_reset;
+ *   v_out[c] += (sum over k with s_h(t)[k] of W_out[k][c]), ascending k,
+ * a_* = (float)exp(-dt/tau_*).  Inputs use the main network's Poisson draw.
+ * Weights are bfloat16 bit patterns; sums and state are FP32.
+ * ------------------------------------------------------------------------ */
+typedef struct snn_rec snn_rec;
+
+typedef struct snn_rec_spec {
+    int32_t n_in, n_hid, n_out;
+    float tau_mem_ms, tau_syn_ms, v_thresh, v_reset;
+    const uint16_t* w_ff;    /* host [n_in][n_hid] bfloat16, copied at create */
+    const uint16_t* w_rec;   /* host [n_hid][n_hid] bfloat16, 0 where there is no synapse */
+    const uint16_t* w_out;   /* host [n_hid][n_out] bfloat16 */
+} snn_rec_spec;
+
+enum {
+    SNN_REC_V = 0,            /* [B][n_hid] float, membrane voltage */
+    SNN_REC_I_SYN = 1,        /* [B][n_hid] float, synaptic current */
+    SNN_REC_SPIKES = 2,       /* [B][n_hid] uint8, spikes of the last step */
+    SNN_REC_COUNTS = 3,       /* [B][n_hid] uint32, spike counts of the last run */
+    SNN_REC_V_OUT = 4,        /* [B][n_out] float, accumulated readout */
+    SNN_REC_RASTER = 5,       /* [T][B][n_hid] uint8 (SNN_RECORD_RASTER) */
+    SNN_REC_RASTER_INPUT = 6, /* [T][B][n_in] uint8 (SNN_RECORD_INPUT) */
+    SNN_REC_STEP = 7,         /* [1] uint64, step counter after the last run */
+    SNN_REC_FIELD_COUNT = 8
+};
+
+/* Create the network on the current device; the weights are copied.  Errors:
+ * SNN_ERR_ARG (sizes, time constants, missing weights), SNN_ERR_OOM,
+ * SNN_ERR_CUDA; the reason is in snn_rec_last_error(NULL). */
+SNN_API snn_status snn_rec_create(const snn_rec_spec* spec, snn_rec** out);
+/* Free the network (synchronises its last stream).  NULL is a no-op. */
+SNN_API snn_status snn_rec_destroy(snn_rec* net);
+/* Enqueue T steps for B samples on `stream`.  rates [B][n_in] (Hz) and seeds
+ * [B] are device pointers, or host pointers with SNN_HOST_INPUTS (staged by the
+ * library); they must stay valid until the stream reaches the end of the run.
+ * Flags: SNN_CONTINUE (keep the state and step counter; same B),
+ * SNN_RECORD_RASTER, SNN_RECORD_INPUT, SNN_HOST_INPUTS.  A new B re-allocates
+ * the per-sample state.  Errors: SNN_ERR_ARG, SNN_ERR_STATE, SNN_ERR_OOM,
+ * SNN_ERR_CUDA. */
+SNN_API snn_status snn_rec_run(snn_rec* net, const float* rates, const uint64_t* seeds, int32_t B,
+                               int32_t T, float dt_ms, uint32_t flags, void* stream);
+/* Bytes of a field for the current batch (0 if absent or not recorded). */
+SNN_API size_t snn_rec_field_bytes(const snn_rec* net, int field);
+/* Copy a field into dst (device memory if dst_on_device); synchronises.
+ * Errors: SNN_ERR_ARG (field, size, NULL), SNN_ERR_STATE (no run, not
+ * recorded), SNN_ERR_CUDA. */
+SNN_API snn_status snn_rec_read(snn_rec* net, int field, void* dst, size_t bytes, int dst_on_device);
+/* One-line reason for the last error of net (NULL: of the last failed create). */
+SNN_API const char* snn_rec_last_error(const snn_rec* net);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,8 @@ EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_fie
             "snn_profile",
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
+            "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
+            "snn_rec_read", "snn_rec_last_error",
             "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -73,6 +75,22 @@ class snn_spec(C.Structure):
         ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32),
         ("w_seed", C.c_uint64), ("w_init", C.c_void_p),
         ("theta_init", C.c_void_p)]
+
+
+class snn_rec_spec(C.Structure):
+    _fields_ = [("n_in", C.c_int32), ("n_hid", C.c_int32), ("n_out", C.c_int32)] + [
+        (n, C.c_float) for n in ("tau_mem_ms", "tau_syn_ms", "v_thresh", "v_reset")] + [
+        ("w_ff", C.c_void_p), ("w_rec", C.c_void_p), ("w_out", C.c_void_p)]
+
+
+(SNN_REC_V, SNN_REC_I_SYN, SNN_REC_SPIKES, SNN_REC_COUNTS, SNN_REC_V_OUT, SNN_REC_RASTER,
+ SNN_REC_RASTER_INPUT, SNN_REC_STEP) = range(8)
+REC_FIELDS = {"v": SNN_REC_V, "i_syn": SNN_REC_I_SYN, "spikes": SNN_REC_SPIKES,
+              "counts": SNN_REC_COUNTS, "v_out": SNN_REC_V_OUT, "raster": SNN_REC_RASTER,
+              "raster_input": SNN_REC_RASTER_INPUT, "step": SNN_REC_STEP}
+REC_DTYPE = {SNN_REC_V: np.float32, SNN_REC_I_SYN: np.float32, SNN_REC_SPIKES: np.uint8,
+             SNN_REC_COUNTS: np.uint32, SNN_REC_V_OUT: np.float32, SNN_REC_RASTER: np.uint8,
+             SNN_REC_RASTER_INPUT: np.uint8, SNN_REC_STEP: np.uint64}
 
 
 class SNNError(RuntimeError):
@@ -129,6 +147,17 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
+        L.snn_rec_create.argtypes = [C.POINTER(snn_rec_spec), C.POINTER(C.c_void_p)]
+        L.snn_rec_destroy.argtypes = [C.c_void_p]
+        L.snn_rec_run.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                  C.c_float, C.c_uint32, C.c_void_p]
+        L.snn_rec_field_bytes.argtypes = [C.c_void_p, C.c_int]
+        L.snn_rec_field_bytes.restype = C.c_size_t
+        L.snn_rec_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_rec_last_error.argtypes = [C.c_void_p]
+        L.snn_rec_last_error.restype = C.c_char_p
+        for name in ("snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_read"):
+            getattr(L, name).restype = C.c_int
         for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state", "snn_write_state",
                      "snn_read_weights", "snn_write_weights", "snn_profile"):
             getattr(L, name).restype = C.c_int
@@ -386,6 +415,88 @@ class Network:
     def close(self) -> None:
         if self.handle:
             snn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------- recurrent inference network ---
+
+def snn_rec_create(params: dict, w_ff, w_rec, w_out):
+    """snn_rec handle from rec parameters (``synth.rec_params`` keys) and
+    bfloat16 weight bit patterns (uint16 arrays)."""
+    arrs = [np.ascontiguousarray(x, np.uint16) for x in (w_ff, w_rec, w_out)]
+    spec = snn_rec_spec(n_in=params["n_in"], n_hid=params["n_hid"], n_out=params["n_out"],
+                        tau_mem_ms=params["tau_mem"], tau_syn_ms=params["tau_syn"],
+                        v_thresh=params["v_thresh"], v_reset=params["v_reset"],
+                        w_ff=arrs[0].ctypes.data, w_rec=arrs[1].ctypes.data,
+                        w_out=arrs[2].ctypes.data)
+    out = C.c_void_p()
+    rc = lib().snn_rec_create(C.byref(spec), C.byref(out))
+    if rc != SNN_OK:
+        raise SNNError(rc, lib().snn_rec_last_error(None).decode())
+    return out.value
+
+
+def _rec_check(net, rc):
+    if rc != SNN_OK:
+        raise SNNError(rc, lib().snn_rec_last_error(net).decode())
+
+
+def snn_rec_run(net, rates, seeds, B: int, T: int, dt: float = 1.0, flags: int = 0,
+                stream=None) -> None:
+    rp, _, rd = _buf(rates)
+    sp, _, sd = _buf(seeds)
+    if not rd or not sd:
+        flags |= SNN_HOST_INPUTS
+    _rec_check(net, lib().snn_rec_run(net, rp, sp, B, T, dt, flags, _stream(stream)))
+
+
+def snn_rec_read(net, field: int) -> np.ndarray:
+    n = lib().snn_rec_field_bytes(net, field)
+    dt = REC_DTYPE[field]
+    out = np.empty(n // np.dtype(dt).itemsize, dt)
+    _rec_check(net, lib().snn_rec_read(net, field, out.ctypes.data, out.nbytes, 0))
+    return out
+
+
+class RecNetwork:
+    """Owns one ``snn_rec``; thin object wrapper over the C calls."""
+
+    def __init__(self, params: dict, w_ff, w_rec, w_out):
+        self.params = dict(params)
+        self.handle = snn_rec_create(params, w_ff, w_rec, w_out)
+        self.B = 0
+
+    def run(self, rates, seeds, T: int, *, dt: float = 1.0, continue_: bool = False,
+            record: bool = False, record_input: bool = False, stream=None) -> None:
+        B = rates.shape[0]
+        flags = (SNN_CONTINUE if continue_ else 0) | (SNN_RECORD_RASTER if record else 0) | (
+            SNN_RECORD_INPUT if record_input else 0)
+        snn_rec_run(self.handle, rates, seeds, B, T, dt, flags, stream)
+        self.B = B
+
+    def read(self, name: str) -> np.ndarray:
+        f = REC_FIELDS[name]
+        a = snn_rec_read(self.handle, f)
+        N, NI, NO = self.params["n_hid"], self.params["n_in"], self.params["n_out"]
+        if f in (SNN_REC_V, SNN_REC_I_SYN, SNN_REC_SPIKES, SNN_REC_COUNTS):
+            return a.reshape(self.B, N)
+        if f == SNN_REC_V_OUT:
+            return a.reshape(self.B, NO)
+        if f == SNN_REC_RASTER:
+            return a.reshape(-1, self.B, N)
+        if f == SNN_REC_RASTER_INPUT:
+            return a.reshape(-1, self.B, NI)
+        return a
+
+    def close(self) -> None:
+        if self.handle:
+            lib().snn_rec_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
