@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=3.0)
     ap.add_argument("--fig1", action="store_true",
                     help="run the two-layer scaling experiment instead (one JSON line)")
+    ap.add_argument("--rec", action="store_true",
+                    help="the recurrent inference network (1024 -> 4096 -> 10, B=4096, T=500) "
+                         "instead (one JSON line)")
     return ap.parse_args()
 
 
@@ -555,8 +558,85 @@ def fig1_leg(a):
                       "rows": rows}), flush=True)
 
 
+def rec_leg(a):
+    """The recurrent inference network at its full size: B = 4096 samples,
+    T = 500 steps of 1 ms, bfloat16 weights.  Both forms of the drive: the
+    tensor-core form (the default choice at this density) timed over the
+    presentations, the exact gather form over one; sample-timesteps/s with
+    inputs resident and L2 flushed before each presentation, the dense
+    product's FLOP rate per step against the bf16 peak, the measured hidden
+    firing fraction, and the oracle on one sample as CPU baseline."""
+    import torch
+    from paper_1909_02549_gb300 import build, snn, synth
+    build.build()
+    B, T = 4096, 500
+    steps = max(1, min(a.steps, 5))
+    p, r, s, wf, wr, wo = synth.rec_workload(B)
+    net = snn.RecNetwork(p, wf, wr, wo)
+    rd = torch.from_numpy(r).cuda()
+    sd = torch.from_numpy(s.view(np.int64)).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(form, n):
+        ms = []
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.run(rd, sd, T, form=form)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    timed("tensor", max(1, a.warmup))                            # warm-up, allocation
+    ms = timed("tensor", steps)
+    density = float(net.read("counts").astype(np.float64).mean() / T)
+    ms_gather = timed("gather", 1)
+    density_gather = float(net.read("counts").astype(np.float64).mean() / T)
+    net.close()
+    value = B * T * steps / (sum(ms) * 1e-3)
+    K = p["n_in"] + p["n_hid"]
+    flop_step = 2.0 * B * p["n_hid"] * K
+    step_s = statistics.mean(ms) * 1e-3 / T
+    pk = peaks()
+    line = {"metric": "sample-timesteps/s, recurrent inference network", "value": value,
+            "unit": UNIT, "ms_per_presentation": statistics.mean(ms), "steps": steps,
+            "form": "tensor",
+            "config": {"workload": "1024 Poisson inputs (U[0,50] Hz) -> 4096 current-based LIF "
+                                   "(tau_mem 20 ms, tau_syn 5 ms, exponential synapses, 10 % "
+                                   "recurrence) -> 10 summed readout, B=4096, T=500, dt=1 ms",
+                       "weights": "bfloat16; drive as one [4096 x 5120] x [5120 x 4096] "
+                                  "tcgen05 product per step, FP32 accumulation",
+                       "l2": "flushed by a 256 MiB write before every presentation"},
+            "step_roofline": {"bound": "tensor", "achieved": flop_step / step_s / 1e12,
+                              "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                              "frac": flop_step / step_s / 1e12 / pk["bf16_tflops"],
+                              "note": "whole step (encode, product with fused neuron update, "
+                                      "readout) against the product's FLOPs; of measured peak"},
+            "gather": {"value": B * T / (ms_gather[0] * 1e-3), "unit": UNIT,
+                       "ms_per_presentation": ms_gather[0],
+                       "note": "exact form: FP32 sums in input order, bit-exact with the oracle"},
+            "hidden_firing_fraction": density, "hidden_firing_fraction_gather": density_gather}
+    if not a.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        st = oracle.rec_new_state(p, 1)
+        Tc = 5
+        t0 = time.perf_counter()
+        oracle.rec_run(p, st, r[:1], s[:1], Tc, *(synth.bf16_bits_to_float(x) for x in (wf, wr, wo)),
+                       record=False)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": Tc / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "1 of the 4096 samples for %d steps, %.1f s" % (Tc, el)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
+    if a.rec:
+        rec_leg(a)
+        return
     if a.fig1:
         fig1_leg(a)
         return

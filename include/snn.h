@@ -326,7 +326,27 @@ SNN_API const char* snn_last_error(const snn_net* net);
  *   v_out[c] += (sum over k with s_h(t)[k] of W_out[k][c]), ascending k,
  * a_* = (float)exp(-dt/tau_*).  Inputs use the main network's Poisson draw.
  * Weights are bfloat16 bit patterns; sums and state are FP32.
+ *
+ * Two forms compute x (both keep the same state, so runs may alternate):
+ *   SNN_REC_GATHER  sums the active rows in the order above: bit-exact with
+ *                   the definition for any weights;
+ *   SNN_REC_TENSOR  one dense tensor-core product per step, [B][K] spikes
+ *                   (0/1) times the stacked [K][n_hid] weights, K = n_in +
+ *                   n_hid, FP32 accumulation in the tensor cores' order: equal
+ *                   to the definition when every partial sum is exact in FP32
+ *                   (e.g. weights that are multiples of 2^-8 below 1 in
+ *                   magnitude), otherwise within FP32 rounding of x.
+ * With neither flag the run picks by the spike density measured on an
+ * earlier run (hidden spikes per sample and step over n_in + n_hid, read back
+ * without synchronising): the gather below SNN_REC_GATHER_MAX_DENSITY, else
+ * the tensor form, which is also the choice of a network's first run.  The
+ * gather's cost grows with the active rows, the product's with n_in + n_hid.
  * ------------------------------------------------------------------------ */
+#define SNN_REC_GATHER  (1u << 8)
+#define SNN_REC_TENSOR  (1u << 9)
+/* Crossover of the automatic choice (measured with 1024 inputs, 4096 neurons,
+ * B = 4096). */
+#define SNN_REC_GATHER_MAX_DENSITY 0.0035
 typedef struct snn_rec snn_rec;
 
 typedef struct snn_rec_spec {
@@ -359,9 +379,9 @@ SNN_API snn_status snn_rec_destroy(snn_rec* net);
  * [B] are device pointers, or host pointers with SNN_HOST_INPUTS (staged by the
  * library); they must stay valid until the stream reaches the end of the run.
  * Flags: SNN_CONTINUE (keep the state and step counter; same B),
- * SNN_RECORD_RASTER, SNN_RECORD_INPUT, SNN_HOST_INPUTS.  A new B re-allocates
- * the per-sample state.  Errors: SNN_ERR_ARG, SNN_ERR_STATE, SNN_ERR_OOM,
- * SNN_ERR_CUDA. */
+ * SNN_RECORD_RASTER, SNN_RECORD_INPUT, SNN_HOST_INPUTS, SNN_REC_GATHER or
+ * SNN_REC_TENSOR (not both).  A new B re-allocates the per-sample state.
+ * Errors: SNN_ERR_ARG, SNN_ERR_STATE, SNN_ERR_OOM, SNN_ERR_CUDA. */
 SNN_API snn_status snn_rec_run(snn_rec* net, const float* rates, const uint64_t* seeds, int32_t B,
                                int32_t T, float dt_ms, uint32_t flags, void* stream);
 /* Bytes of a field for the current batch (0 if absent or not recorded). */
@@ -370,7 +390,21 @@ SNN_API size_t snn_rec_field_bytes(const snn_rec* net, int field);
  * Errors: SNN_ERR_ARG (field, size, NULL), SNN_ERR_STATE (no run, not
  * recorded), SNN_ERR_CUDA. */
 SNN_API snn_status snn_rec_read(snn_rec* net, int field, void* dst, size_t bytes, int dst_on_device);
-/* One-line reason for the last error of net (NULL: of the last failed create). */
+/* Overwrite a field of the current batch's state from src (device memory if
+ * src_on_device), e.g. to resume from a checkpoint: SNN_REC_V, SNN_REC_I_SYN,
+ * SNN_REC_SPIKES (the previous step's hidden spikes, bytes 0/1), SNN_REC_COUNTS,
+ * SNN_REC_V_OUT and SNN_REC_STEP (the counter of the next step), in any order.
+ * The batch must exist (a run with T = 0 allocates one); a later run with
+ * SNN_CONTINUE starts from the written state.  Synchronises.  Errors:
+ * SNN_ERR_ARG (field, size, NULL, spike bytes other than 0/1), SNN_ERR_STATE
+ * (no batch), SNN_ERR_CUDA. */
+SNN_API snn_status snn_rec_write(snn_rec* net, int field, const void* src, size_t bytes, int src_on_device);
+/* The form the last run took: SNN_REC_GATHER or SNN_REC_TENSOR (0 before any
+ * run or for NULL). */
+SNN_API uint32_t snn_rec_form(const snn_rec* net);
+/* One-line reason for the last error of net (NULL: of the last failed create).
+ * snn_rec_read reports, as SNN_ERR_TIMEOUT, a tensor-form step whose pipeline
+ * wait gave up after 2 s (that run's results are undefined). */
 SNN_API const char* snn_rec_last_error(const snn_rec* net);
 
 #ifdef __cplusplus

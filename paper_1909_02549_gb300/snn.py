@@ -61,7 +61,7 @@ EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_fie
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
             "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
-            "snn_rec_read", "snn_rec_last_error",
+            "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_last_error",
             "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -85,6 +85,9 @@ class snn_rec_spec(C.Structure):
 
 (SNN_REC_V, SNN_REC_I_SYN, SNN_REC_SPIKES, SNN_REC_COUNTS, SNN_REC_V_OUT, SNN_REC_RASTER,
  SNN_REC_RASTER_INPUT, SNN_REC_STEP) = range(8)
+SNN_REC_GATHER = 1 << 8      # exact gather form of the drive
+SNN_REC_TENSOR = 1 << 9      # dense tensor-core form
+REC_FORMS = {"auto": 0, "gather": SNN_REC_GATHER, "tensor": SNN_REC_TENSOR}
 REC_FIELDS = {"v": SNN_REC_V, "i_syn": SNN_REC_I_SYN, "spikes": SNN_REC_SPIKES,
               "counts": SNN_REC_COUNTS, "v_out": SNN_REC_V_OUT, "raster": SNN_REC_RASTER,
               "raster_input": SNN_REC_RASTER_INPUT, "step": SNN_REC_STEP}
@@ -154,9 +157,13 @@ def lib():
         L.snn_rec_field_bytes.argtypes = [C.c_void_p, C.c_int]
         L.snn_rec_field_bytes.restype = C.c_size_t
         L.snn_rec_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_rec_write.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_rec_form.argtypes = [C.c_void_p]
+        L.snn_rec_form.restype = C.c_uint32
         L.snn_rec_last_error.argtypes = [C.c_void_p]
         L.snn_rec_last_error.restype = C.c_char_p
-        for name in ("snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_read"):
+        for name in ("snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_read",
+                     "snn_rec_write"):
             getattr(L, name).restype = C.c_int
         for name in ("snn_create", "snn_destroy", "snn_run", "snn_read_state", "snn_write_state",
                      "snn_read_weights", "snn_write_weights", "snn_profile"):
@@ -464,6 +471,12 @@ def snn_rec_read(net, field: int) -> np.ndarray:
     return out
 
 
+def snn_rec_write(net, field: int, src) -> None:
+    """Overwrite a state field from a host array or a device tensor."""
+    p, n, on_dev = _buf(src)
+    _rec_check(net, lib().snn_rec_write(net, field, p, n, 1 if on_dev else 0))
+
+
 class RecNetwork:
     """Owns one ``snn_rec``; thin object wrapper over the C calls."""
 
@@ -473,10 +486,12 @@ class RecNetwork:
         self.B = 0
 
     def run(self, rates, seeds, T: int, *, dt: float = 1.0, continue_: bool = False,
-            record: bool = False, record_input: bool = False, stream=None) -> None:
+            record: bool = False, record_input: bool = False, form: str = "auto",
+            stream=None) -> None:
+        """``form``: "gather" (exact), "tensor" (dense tensor cores) or "auto"."""
         B = rates.shape[0]
         flags = (SNN_CONTINUE if continue_ else 0) | (SNN_RECORD_RASTER if record else 0) | (
-            SNN_RECORD_INPUT if record_input else 0)
+            SNN_RECORD_INPUT if record_input else 0) | REC_FORMS[form]
         snn_rec_run(self.handle, rates, seeds, B, T, dt, flags, stream)
         self.B = B
 
@@ -493,6 +508,15 @@ class RecNetwork:
         if f == SNN_REC_RASTER_INPUT:
             return a.reshape(-1, self.B, NI)
         return a
+
+    def write(self, name: str, src) -> None:
+        snn_rec_write(self.handle, REC_FIELDS[name], src)
+
+    @property
+    def form(self) -> str:
+        """"gather" or "tensor": the form of the last run ("" before any)."""
+        f = lib().snn_rec_form(self.handle)
+        return {SNN_REC_GATHER: "gather", SNN_REC_TENSOR: "tensor"}.get(f, "")
 
     def close(self) -> None:
         if self.handle:

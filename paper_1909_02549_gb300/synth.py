@@ -28,6 +28,8 @@ each output is the 64-bit finaliser applied to the new state.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 GOLDEN_GAMMA = np.uint64(0x9E3779B97F4A7C15)
@@ -174,6 +176,31 @@ def rec_workload(batch: int, n_in: int = 1024, n_hid: int = 4096, n_out: int = 1
                                   np.float32(0.0)))
     w_out = to_bf16_bits(normal_weights(n_hid, n_out, 0.0, 0.05, 35000 + seed))
     return p, rates, seeds, w_ff, w_rec, w_out
+
+
+def dyadic(w, frac_bits: int = 10, k_max: int = 255) -> np.ndarray:
+    """Weights rounded to k * 2^-frac_bits with |k| <= k_max (float32).  With
+    k_max = 255 they have at most eight significant bits, so bfloat16 holds them
+    exactly, and any sum of them whose partial sums stay below
+    2^(24 - frac_bits) in magnitude is exact in FP32, in any order."""
+    w = np.asarray(w, np.float64)
+    k = np.clip(np.rint(w * 2.0 ** frac_bits), -k_max, k_max)
+    return (k * 2.0 ** -frac_bits).astype(np.float32)
+
+
+def rec_workload_dyadic(batch: int, n_in: int = 1024, n_hid: int = 4096, n_out: int = 10,
+                        seed: int = 0, ff_gain: float = 1.0):
+    """``rec_workload`` with every weight matrix rounded by ``dyadic`` (W_ff
+    after a power-of-two gain, on a grid coarser by the same factor): all
+    weights are multiples of 2^-10, so every drive is exact in FP32 in any
+    summation order while its partial sums stay below 2^14 in magnitude."""
+    g = int(round(math.log2(ff_gain)))
+    assert 2.0 ** g == ff_gain and 0 <= g <= 10
+    p, rates, seeds, wf, wr, wo = rec_workload(batch, n_in, n_hid, n_out, seed)
+    wf = to_bf16_bits(dyadic(bf16_bits_to_float(wf) * np.float32(ff_gain), 10 - g))
+    wr = to_bf16_bits(dyadic(bf16_bits_to_float(wr), 10))
+    wo = to_bf16_bits(dyadic(bf16_bits_to_float(wo), 10))
+    return p, rates, seeds, wf, wr, wo
 
 
 def diehl_cook_params(n_exc: int, n_in: int = 784) -> dict:

@@ -143,3 +143,28 @@ def test_batch_equals_single_sample_runs():
         rhb, rib = run(p, sb, r[b:b + 1], s[b:b + 1], 40, w_ff, w_rec, w_out, episodic=True)
         assert np.array_equal(rhb[:, 0], rh[:, b]) and np.array_equal(rib[:, 0], ri[:, b])
         assert np.array_equal(sb.v[0], st.v[b]) and np.array_equal(sb.v_out[0], st.v_out[b])
+
+
+def test_dyadic_weights_are_exact_in_bfloat16():
+    w = synth.dyadic(np.random.default_rng(7).normal(0, 0.3, 10000), 10)
+    assert np.array_equal(synth.bf16_bits_to_float(synth.to_bf16_bits(w)), w)
+    assert np.abs(w).max() <= 255 * 2.0 ** -10
+    assert np.array_equal(w * 1024, np.rint(w * 1024))
+
+
+def test_dyadic_drive_equals_the_exact_product():
+    """With dyadic weights the oracle's FP32 drive from rest is the exact
+    (FP64) product s_in W_ff + s_h' W_rec, with no rounding at all: the premise
+    under which any summation order gives the same bits."""
+    B, NI, N = 4, 64, 96
+    p, r, s, wf, wr, wo = synth.rec_workload_dyadic(B, NI, N, 10, seed=3, ff_gain=8.0)
+    p["v_thresh"] = 1e9
+    w_ff, w_rec, w_out = (synth.bf16_bits_to_float(x) for x in (wf, wr, wo))
+    assert np.abs(w_ff).max() > 0.5                          # the gain is kept, not clipped
+    st = oracle.rec_new_state(p, B)
+    st.s_h[:] = (np.random.default_rng(1).random((B, N)) < 0.3).astype(np.uint8)
+    s_h0 = st.s_h.astype(np.float64).copy()
+    _, rin = run(p, st, r, s, 1, w_ff, w_rec, w_out)
+    x = rin[0].astype(np.float64) @ w_ff.astype(np.float64) + s_h0 @ w_rec.astype(np.float64)
+    assert rin[0].sum() > 0 and np.abs(x).max() > 1.0
+    assert np.array_equal(st.i_syn.astype(np.float64), x)
