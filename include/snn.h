@@ -379,8 +379,8 @@ SNN_API snn_status snn_rec_destroy(snn_rec* net);
  * [B] are device pointers, or host pointers with SNN_HOST_INPUTS (staged by the
  * library); they must stay valid until the stream reaches the end of the run.
  * Flags: SNN_CONTINUE (keep the state and step counter; same B),
- * SNN_RECORD_RASTER, SNN_RECORD_INPUT, SNN_HOST_INPUTS, SNN_REC_GATHER or
- * SNN_REC_TENSOR (not both).  A new B re-allocates the per-sample state.
+ * SNN_RECORD_RASTER, SNN_RECORD_INPUT, SNN_HOST_INPUTS, SNN_PROFILE,
+ * SNN_REC_GATHER or SNN_REC_TENSOR (not both).  A new B re-allocates the per-sample state.
  * Errors: SNN_ERR_ARG, SNN_ERR_STATE, SNN_ERR_OOM, SNN_ERR_CUDA. */
 SNN_API snn_status snn_rec_run(snn_rec* net, const float* rates, const uint64_t* seeds, int32_t B,
                                int32_t T, float dt_ms, uint32_t flags, void* stream);
@@ -402,6 +402,18 @@ SNN_API snn_status snn_rec_write(snn_rec* net, int field, const void* src, size_
 /* The form the last run took: SNN_REC_GATHER or SNN_REC_TENSOR (0 before any
  * run or for NULL). */
 SNN_API uint32_t snn_rec_form(const snn_rec* net);
+/* Kernel classes reported by snn_rec_profile. */
+enum {
+    SNN_REC_KERNEL_ENCODE = 0,   /* Poisson input spikes */
+    SNN_REC_KERNEL_DRIVE = 1,    /* drive and neuron update (gather or tensor form) */
+    SNN_REC_KERNEL_READOUT = 2,  /* summed readout */
+    SNN_REC_KERNEL_COUNT = 3
+};
+/* Device time of the last run made with SNN_PROFILE (every step's launches
+ * bracketed by CUDA events), per kernel class: ms[k] summed milliseconds,
+ * launches[k] launches, k < count <= SNN_REC_KERNEL_COUNT.  Synchronises.
+ * Errors: SNN_ERR_ARG, SNN_ERR_STATE (last run not profiled), SNN_ERR_CUDA. */
+SNN_API snn_status snn_rec_profile(snn_rec* net, double* ms, int* launches, int count);
 /* One-line reason for the last error of net (NULL: of the last failed create).
  * snn_rec_read reports, as SNN_ERR_TIMEOUT, a tensor-form step whose pipeline
  * wait gave up after 2 s (that run's results are undefined). */

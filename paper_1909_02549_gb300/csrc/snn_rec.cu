@@ -32,8 +32,12 @@
 //           in their own order, so this form agrees with the oracle to FP32
 //           rounding of the drive, not bit for bit.
 // Both forms keep the hidden spikes as words (readout, counts) and as the
-// bfloat16 operand, so a network may change form between runs; readout
-// (thread = sample x output unit) is shared.
+// bfloat16 operand, so a network may change form between runs; the readout
+// (warp = sample) is shared.  v, I and the counts are stored sample-interleaved,
+// [ceil(B/32)][N][32]: the dense epilogue, whose lanes are 32 consecutive
+// samples of one neuron, then reads and writes whole 128-byte lines; reads and
+// writes through the API convert from and to [B][N].
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -41,6 +45,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -69,26 +74,40 @@ struct RecBufs {
     uint64_t* seeds;         // [B]
     uint32_t* inb;           // [B][Iw]     input spikes of the step
     uint32_t* sh;            // [2][B][Nw]  hidden spikes, slot = step parity
-    float* v;                // [B][N]
-    float* i_syn;            // [B][N]
+    float* v;                // [Bp/32][N][32], Bp = B rounded up to 32 (sidx)
+    float* i_syn;            // [Bp/32][N][32]
     float* v_out;            // [B][n_out]
-    uint32_t* counts;        // [B][N]
+    uint32_t* counts;        // [Bp/32][N][32]
     uint8_t* raster_h;       // [T][B][N]
     uint8_t* raster_in;      // [T][B][n_in]
     unsigned long long* step;   // [2]: first step of the run, step after it
 };
 
 __device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+// element (b, j) of the sample-interleaved state arrays
+__host__ __device__ __forceinline__ size_t sidx(int b, int j, int N) {
+    return ((size_t)(b >> 5) * (size_t)N + (size_t)j) * 32u + (size_t)(b & 31);
+}
+__host__ __device__ __forceinline__ size_t state_elems(int B, int N) { return (size_t)((B + 31) & ~31) * (size_t)N; }
 constexpr uint16_t BF16_ONE = 0x3F80;
 
 // ---- dense form: tcgen05 GEMM with the neuron update in the epilogue -------
 constexpr int GBM = 128, GBN = 256, GBK = 64, GSTAGES = 4;
 constexpr int GA_BYTES = GBM * GBK * 2, GB_BYTES = GBN * GBK * 2, GSTAGE = GA_BYTES + GB_BYTES;
 constexpr int GSMEM = GSTAGES * GSTAGE + 1024 + 256;
+constexpr int GEPI_WARPS = 8, GTHREADS = 64 + 32 * GEPI_WARPS;
 constexpr unsigned long long GWAIT_NS = 2000000000ull;   // bounded waits: 2 s, then the error flag
 // instruction descriptor: FP32 accumulator, bfloat16 A and B, both K-major, M=128, N=256
-constexpr uint32_t GIDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GBN >> 3) << 17) |
-                            ((uint32_t)(GBM >> 4) << 24);
+__host__ __device__ constexpr uint32_t gidesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(GBM >> 4) << 24);
+}
+
+// Tiles of the dense form: ntn_drive neuron tiles of GBN columns per 128 samples,
+// then, when the readout is fused (n_out <= GBN), one readout tile whose
+// weight rows start at R0 = ntn_drive * GBN and whose MMAs are n_ro wide.
+struct DenseGeom {
+    int ntn_drive, ntn, ntiles, fused, n_ro;
+};
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -158,7 +177,7 @@ __global__ void k_rec_begin(RecConsts c, RecBufs d, const float* __restrict__ ra
     for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth) d.thr[k] = poisson_threshold(rates[k], c.dt);
     for (size_t k = tid; k < (size_t)c.B; k += nth) d.seeds[k] = seeds[k];
     if (episodic) {
-        for (size_t k = tid; k < (size_t)c.B * c.N; k += nth) {
+        for (size_t k = tid; k < state_elems(c.B, c.N); k += nth) {
             d.v[k] = 0.0f;
             d.i_syn[k] = 0.0f;
         }
@@ -169,7 +188,7 @@ __global__ void k_rec_begin(RecConsts c, RecBufs d, const float* __restrict__ ra
         }
         for (size_t k = tid; k < (size_t)c.B * c.n_out; k += nth) d.v_out[k] = 0.0f;
     }
-    for (size_t k = tid; k < (size_t)c.B * c.N; k += nth) d.counts[k] = 0u;
+    for (size_t k = tid; k < state_elems(c.B, c.N); k += nth) d.counts[k] = 0u;
     if (tid == 0) {
         const unsigned long long base = episodic ? 0ull : d.step[1];
         d.step[0] = base;
@@ -230,7 +249,7 @@ __global__ void __launch_bounds__(256) k_rec_hidden(RecConsts c, RecBufs d, int 
             x = __fadd_rn(x, bf16_value(d.w_rec[(size_t)k * c.N + jc]));
         }
     }
-    const size_t q = (size_t)b * c.N + jc;
+    const size_t q = sidx(b, jc, c.N);
     bool spk = false;
     if (vj) {
         float I = __fmul_rn(c.a_syn, d.i_syn[q]);
@@ -249,29 +268,124 @@ __global__ void __launch_bounds__(256) k_rec_hidden(RecConsts c, RecBufs d, int 
     if (vj) d.S[((size_t)prv * c.B + b) * d.K + c.n_in + j] = spk ? BF16_ONE : 0;   // next step's operand
 }
 
-// dense form: one CTA = 128 samples x 256 neurons; warp 0 lane 0 loads, warp 1
-// lane 0 issues the MMAs, all four warps run the epilogue (warp w: samples
-// 32w..32w+31 of the tile, one per lane, 32 neurons per tensor-memory load)
-__global__ void __launch_bounds__(128, 1) k_rec_dense(const __grid_constant__ CUtensorMap tmS0,
-                                                      const __grid_constant__ CUtensorMap tmS1,
-                                                      const __grid_constant__ CUtensorMap tmW,
-                                                      RecConsts c, RecBufs d, int t_local, uint32_t* err) {
+// dense form, epilogue of 32 consecutive samples (lanes, live when b < B) x 32
+// neurons j0.. (j0 < N): the synapse and membrane update from the accumulated
+// drive r[u] of neuron j0 + u, the spike words, the next step's operand and
+// the optional raster.  State accesses are one 128-byte line per warp.
+__device__ __forceinline__ void dense_epilogue_chunk(const RecConsts& c, const RecBufs& d, const uint32_t (&r)[32],
+                                                     int b, bool live, int j0, int cur, int nxt, int t_local) {
+    const int lane = threadIdx.x & 31;
+    const int nu = min(32, c.N - j0);
+    uint32_t word = 0u;
+    if (live) {
+        const size_t q0 = sidx(b, j0, c.N);
+        if (nu == 32) {
+            float I[32], v[32];
+            uint32_t cn[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) { I[u] = d.i_syn[q0 + 32 * u]; v[u] = d.v[q0 + 32 * u]; }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                float x = __fmul_rn(c.a_syn, I[u]);
+                x = __fadd_rn(x, __uint_as_float(r[u]));
+                I[u] = x;
+                float y = __fmul_rn(c.a_mem, v[u]);
+                y = __fadd_rn(y, x);
+                const bool spk = y >= c.v_thresh;
+                v[u] = spk ? c.v_reset : y;
+                word |= (spk ? 1u : 0u) << u;
+            }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) { d.i_syn[q0 + 32 * u] = I[u]; d.v[q0 + 32 * u] = v[u]; }
+#pragma unroll
+            for (int u = 0; u < 32; ++u) cn[u] = d.counts[q0 + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) d.counts[q0 + 32 * u] = cn[u] + ((word >> u) & 1u);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 32; ++u) {
+                if (u >= nu) continue;
+                const size_t q = q0 + 32 * u;
+                float x = __fmul_rn(c.a_syn, d.i_syn[q]);
+                x = __fadd_rn(x, __uint_as_float(r[u]));
+                d.i_syn[q] = x;
+                float y = __fmul_rn(c.a_mem, d.v[q]);
+                y = __fadd_rn(y, x);
+                const bool spk = y >= c.v_thresh;
+                d.v[q] = spk ? c.v_reset : y;
+                if (spk) d.counts[q] += 1u;
+                word |= (spk ? 1u : 0u) << u;
+            }
+        }
+        d.sh[((size_t)cur * c.B + b) * c.Nw + (j0 >> 5)] = word;
+        if (c.rec_raster) {
+            uint8_t* rp = d.raster_h + ((size_t)t_local * c.B + b) * c.N + j0;
+            for (int u = 0; u < nu; ++u) rp[u] = (uint8_t)((word >> u) & 1u);
+        }
+    }
+    // next step's operand, rows of the warp's samples: two rows per store, lanes
+    // 0-15 and 16-31 each writing a pair of neurons of one row
+    const int b0 = b - lane;
+    const int half = lane >> 4, pr = lane & 15;
+    if (nu == 32 && (c.n_in & 1) == 0) {
+#pragma unroll 4
+        for (int rr = 0; rr < 32; rr += 2) {
+            const uint32_t wr = __shfl_sync(FULL, word, rr + half);
+            const int row = b0 + rr + half;
+            if (row < c.B) {
+                const uint32_t bits2 = (wr >> (2 * pr)) & 3u;
+                const uint32_t val = ((bits2 & 1u) ? (uint32_t)BF16_ONE : 0u) | ((bits2 & 2u) ? ((uint32_t)BF16_ONE << 16) : 0u);
+                uint16_t* dst = d.S + ((size_t)nxt * c.B + row) * d.K + c.n_in + j0 + 2 * pr;
+                *reinterpret_cast<uint32_t*>(dst) = val;
+            }
+        }
+    } else if (live) {
+        uint16_t* snext = d.S + ((size_t)nxt * c.B + b) * d.K + c.n_in + j0;
+        for (int u = 0; u < nu; ++u) snext[u] = ((word >> u) & 1u) ? BF16_ONE : 0;
+    }
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr) : "memory");
+}
+
+// Dense form, persistent: one CTA per SM walks the 128-sample x 256-neuron
+// tiles (tile = blockIdx.x + i * gridDim.x, neuron tiles fastest).  Warp 0
+// lane 0 streams the operand tiles with TMA through GSTAGES stages; warp 1
+// owns the tensor memory (two 256-column accumulators) and one lane issues
+// the MMAs; warps 2..9 run the epilogue of the previous tile while the next
+// one accumulates (warp w reads tensor-memory lanes 32*(w%4).., half
+// (w-2)/4 of the tile's columns).
+__global__ void __launch_bounds__(GTHREADS, 1) k_rec_dense(const __grid_constant__ CUtensorMap tmS0,
+                                                           const __grid_constant__ CUtensorMap tmS1,
+                                                           const __grid_constant__ CUtensorMap tmW,
+                                                           RecConsts c, RecBufs d, int t_local, DenseGeom g,
+                                                           uint32_t* err) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = (uint64_t*)(smem + GSTAGES * GSTAGE);
     uint64_t* empty = full + GSTAGES;
-    uint64_t* done = empty + GSTAGES;
+    uint64_t* accf = empty + GSTAGES;      // [2] accumulator ready (MMA commit)
+    uint64_t* acce = accf + 2;             // [2] accumulator drained (epilogue warps)
+    uint64_t* drain = acce + 2;            // the MMA thread's last commit
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tm = blockIdx.x, tn = blockIdx.y;
     if (tid == 0) {
         for (int s = 0; s < GSTAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        mbar_init(done, 1);
+        for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], GEPI_WARPS); }
+        mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(su32(&s_tmem)), "r"(GBN) : "memory");
+                     :: "r"(su32(&s_tmem)), "r"(2 * GBN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -282,157 +396,146 @@ __global__ void __launch_bounds__(128, 1) k_rec_dense(const __grid_constant__ CU
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
     const int cur = (int)(tt & 1ull), nxt = cur ^ 1;
     const CUtensorMap* tmS = cur ? &tmS1 : &tmS0;
-    bool ok = true;
-    if (warp == 0 && lane == 0) {                       // TMA producer
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % GSTAGES, round = kb / GSTAGES;
-            if (kb >= GSTAGES) ok = mbar_wait(&empty[s], (round - 1) & 1);
-            if (!ok) break;
-            uint8_t* st = smem + s * GSTAGE;
-            mbar_expect_tx(&full[s], GSTAGE);
-            tma_2d(st, tmS, kb * GBK, tm * GBM, &full[s]);
-            tma_2d(st + GA_BYTES, &tmW, kb * GBK, tn * GBN, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0) {                // MMA issuer
-        for (int kb = 0; kb < nk && ok; ++kb) {
-            const int s = kb % GSTAGES, round = kb / GSTAGES;
-            ok = mbar_wait(&full[s], round & 1);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = su32(smem + s * GSTAGE), b0 = a0 + GA_BYTES;
-#pragma unroll
-            for (int k = 0; k < GBK / 16; ++k) {            // K = 16 per MMA: +32 bytes in the swizzled row
-                const uint64_t ad = sdesc(a0) + (uint64_t)(2 * k), bd = sdesc(b0) + (uint64_t)(2 * k);
-                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                             :: "r"(tmem), "l"(ad), "l"(bd), "r"(GIDESC), "r"(acc) : "memory");
+    if (warp == 0) {
+        if (lane == 0) {                                  // TMA producer
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < g.ntiles && ok; tile += gridDim.x) {
+                const int tm = tile / g.ntn, tn = tile % g.ntn;
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % GSTAGES, round = it / GSTAGES;
+                    if (it >= GSTAGES && !(ok = mbar_wait(&empty[s], (round - 1) & 1))) break;
+                    uint8_t* st = smem + s * GSTAGE;
+                    mbar_expect_tx(&full[s], GSTAGE);
+                    tma_2d(st, tmS, kb * GBK, tm * GBM, &full[s]);
+                    tma_2d(st + GA_BYTES, &tmW, kb * GBK, tn * GBN, &full[s]);
+                }
             }
+            if (!ok) atomicOr(err, 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {                                  // MMA issuer
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < g.ntiles && ok; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1, use = lt >> 1;
+                if (lt >= 2 && !(ok = mbar_wait(&acce[buf], (use - 1) & 1))) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_addr = tmem + (uint32_t)(buf * GBN);
+                const bool ro = g.fused && tile % g.ntn == g.ntn_drive;
+                const uint32_t idesc = ro ? gidesc(g.n_ro) : gidesc(GBN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = it % GSTAGES, round = it / GSTAGES;
+                    if (!(ok = mbar_wait(&full[s], round & 1))) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = su32(smem + s * GSTAGE), b0 = a0 + GA_BYTES;
+#pragma unroll
+                    for (int k = 0; k < GBK / 16; ++k) {      // K = 16 per MMA: +32 bytes in the swizzled row
+                        const uint64_t ad = sdesc(a0) + (uint64_t)(2 * k), bd = sdesc(b0) + (uint64_t)(2 * k);
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                     :: "r"(acc_addr), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(su32(&empty[s])) : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(su32(&accf[buf])) : "memory");
+            }
+            // every MMA issued has completed before the tensor memory is freed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(su32(&empty[s])) : "memory");
+                         :: "r"(su32(drain)) : "memory");
+            if (!mbar_wait(drain, 0)) ok = false;
+            if (!ok) atomicOr(err, 1u);
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                     :: "r"(su32(done)) : "memory");
-    }
-    __syncwarp();
-    if (!ok) atomicOr(err, 1u);
-    // the tensor-memory loads below are warp-collective: every lane takes them,
-    // lanes past the batch discard their row
-    const bool got = __all_sync(FULL, mbar_wait(done, 0) ? 1 : 0) != 0;
-    if (!got && lane == 0) atomicOr(err, 1u);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int b = tm * GBM + warp * 32 + lane;
-    if (got) {
-        for (int ch = 0; ch < GBN / 32; ++ch) {
-            const int j0 = tn * GBN + ch * 32;          // uniform over the warp
-            if (j0 >= c.N) break;
-            uint32_t r[32];
-            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
-                         "tcgen05.wait::ld.sync.aligned;"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                         : "r"(ta) : "memory");
-            if (b >= c.B) continue;
-            const size_t q0 = (size_t)b * c.N + j0;
-            uint32_t word = 0u;
-            uint16_t* snext = d.S + ((size_t)nxt * c.B + b) * d.K + c.n_in + j0;
-            if (((c.N & 3) == 0) && j0 + 32 <= c.N) {
-                // each lane owns 32 consecutive neurons of its sample: 128-byte rows
-                float4* ip = reinterpret_cast<float4*>(d.i_syn + q0);
-                float4* vp = reinterpret_cast<float4*>(d.v + q0);
-                uint4* cp = reinterpret_cast<uint4*>(d.counts + q0);
-#pragma unroll
-                for (int g = 0; g < 8; ++g) {
-                    float4 I4 = ip[g], v4 = vp[g];
-                    uint4 c4 = cp[g];
-                    float* Ie = &I4.x;
-                    float* ve = &v4.x;
-                    uint32_t* ce = &c4.x;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int u = 4 * g + e;
-                        float I = __fmul_rn(c.a_syn, Ie[e]);
-                        I = __fadd_rn(I, __uint_as_float(r[u]));
-                        Ie[e] = I;
-                        float v = __fmul_rn(c.a_mem, ve[e]);
-                        v = __fadd_rn(v, I);
-                        const bool spk = v >= c.v_thresh;
-                        ve[e] = spk ? c.v_reset : v;
-                        ce[e] += spk ? 1u : 0u;
-                        word |= (spk ? 1u : 0u) << u;
-                    }
-                    ip[g] = I4;
-                    vp[g] = v4;
-                    cp[g] = c4;
+    } else {                                              // epilogue warps
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        int lt = 0;
+        for (int tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++lt) {
+            const int tm = tile / g.ntn, tn = tile % g.ntn;
+            const bool ro = g.fused && tn == g.ntn_drive;
+            const int ncols = ro ? c.n_out : c.N - tn * GBN;   // live columns of the tile
+            const int buf = lt & 1, use = lt >> 1;
+            const bool got = __all_sync(FULL, mbar_wait(&accf[buf], use & 1) ? 1 : 0) != 0;
+            if (!got) {
+                if (lane == 0) atomicOr(err, 1u);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int b = tm * GBM + quarter * 32 + lane;
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * GBN);
+            constexpr int CH = GBN / 32 / 2;               // chunks of 32 columns per warp
+            for (int q = 0; q < CH; ++q) {
+                const int col = (half * CH + q) * 32;       // uniform over the warp
+                uint32_t r[32];
+                if (col < ncols) tmem_ld32(tbase + (uint32_t)col, r);
+                if (q == CH - 1) {                          // this warp is done with the accumulator
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(&acce[buf])) : "memory");
                 }
-            } else {
+                if (col >= ncols) continue;
+                if (!ro) {
+                    dense_epilogue_chunk(c, d, r, b, b < c.B, tn * GBN + col, cur, nxt, t_local);
+                } else if (t_local > 0 && b < c.B) {
+                    // the readout of the previous step: its hidden spikes are this
+                    // step's operand (the run's first step skips it: the run before
+                    // added it)
+                    float* vo = d.v_out + (size_t)b * c.n_out;
 #pragma unroll
-                for (int u = 0; u < 32; ++u) {
-                    if (j0 + u >= c.N) continue;
-                    float I = __fmul_rn(c.a_syn, d.i_syn[q0 + u]);
-                    I = __fadd_rn(I, __uint_as_float(r[u]));
-                    d.i_syn[q0 + u] = I;
-                    float v = __fmul_rn(c.a_mem, d.v[q0 + u]);
-                    v = __fadd_rn(v, I);
-                    const bool spk = v >= c.v_thresh;
-                    d.v[q0 + u] = spk ? c.v_reset : v;
-                    if (spk) d.counts[q0 + u] += 1u;
-                    word |= (spk ? 1u : 0u) << u;
+                    for (int u = 0; u < 32; ++u)
+                        if (col + u < c.n_out) vo[col + u] = __fadd_rn(vo[col + u], __uint_as_float(r[u]));
                 }
             }
-            const int nu = min(32, c.N - j0);
-            if (((c.n_in & 7) == 0) && nu == 32) {
-                uint4* sp = reinterpret_cast<uint4*>(snext);
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    uint32_t h[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int u = 8 * g + 2 * e;
-                        h[e] = (((word >> u) & 1u) ? (uint32_t)BF16_ONE : 0u) |
-                               ((((word >> (u + 1)) & 1u) ? (uint32_t)BF16_ONE : 0u) << 16);
-                    }
-                    sp[g] = make_uint4(h[0], h[1], h[2], h[3]);
-                }
-            } else {
-                for (int u = 0; u < nu; ++u) snext[u] = ((word >> u) & 1u) ? BF16_ONE : 0;
-            }
-            if (c.rec_raster) {
-                uint8_t* rp = d.raster_h + ((size_t)t_local * c.B + b) * c.N + j0;
-                for (int u = 0; u < nu; ++u) rp[u] = (uint8_t)((word >> u) & 1u);
-            }
-            d.sh[((size_t)cur * c.B + b) * c.Nw + (j0 >> 5)] = word;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(GBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(2 * GBN) : "memory");
     }
 }
 
-// thread = one sample x one output unit
+// warp = one sample, lane = one output unit (n_out > 32 in rounds of 32): every
+// lane walks the same spike words, so the warp does not diverge, and each
+// output's sum keeps ascending k; four weights are fetched before they are
+// added, in order
 __global__ void __launch_bounds__(256) k_rec_readout(RecConsts c, RecBufs d, int t_local) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)c.B * c.n_out) return;
+    const int lane = threadIdx.x & 31;
+    const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (size_t)c.B) return;
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
-    const int b = (int)(idx / c.n_out), o = (int)(idx % c.n_out);
+    const int b = (int)gw;
     const uint32_t* hb = d.sh + ((size_t)(tt & 1ull) * c.B + b) * c.Nw;
-    float y = 0.0f;
-    for (int w = 0; w < c.Nw; ++w) {
-        uint32_t m = hb[w];
-        while (m) {
-            const int k = w * 32 + __ffs(m) - 1;
-            m &= m - 1;
-            y = __fadd_rn(y, bf16_value(d.w_out[(size_t)k * c.n_out + o]));
+    for (int o0 = 0; o0 < c.n_out; o0 += 32) {
+        const int o = o0 + lane;
+        const int oc = o < c.n_out ? o : c.n_out - 1;
+        float y = 0.0f;
+        for (int w = 0; w < c.Nw; ++w) {
+            uint32_t m = hb[w];
+            while (m) {
+                int k[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    k[q] = m ? w * 32 + __ffs(m) - 1 : -1;
+                    m &= m - 1;
+                }
+                float wv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) wv[q] = k[q] >= 0 ? bf16_value(d.w_out[(size_t)k[q] * c.n_out + oc]) : 0.0f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (k[q] >= 0) y = __fadd_rn(y, wv[q]);
+            }
+        }
+        if (o < c.n_out) {
+            const size_t idx = (size_t)b * c.n_out + o;
+            d.v_out[idx] = __fadd_rn(d.v_out[idx], y);
         }
     }
-    d.v_out[idx] = __fadd_rn(d.v_out[idx], y);
 }
 
 // field extraction: the last step's hidden spikes as bytes
@@ -442,6 +545,17 @@ __global__ void k_rec_spikes(RecConsts c, RecBufs d, uint8_t* out) {
     const int b = (int)(idx / c.N), j = (int)(idx % c.N);
     const int last = (int)((d.step[1] + 1ull) & 1ull);   // slot of step end-1
     out[idx] = (uint8_t)((d.sh[((size_t)last * c.B + b) * c.Nw + (j >> 5)] >> (j & 31)) & 1u);
+}
+
+// [B][N] <-> sample-interleaved, 32-bit elements
+__global__ void k_rec_relayout(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, int B, int N,
+                               int to_interleaved) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)B * N) return;
+    const int b = (int)(idx / N), j = (int)(idx % N);
+    const size_t q = sidx(b, j, N);
+    if (to_interleaved) dst[q] = src[idx];
+    else dst[idx] = src[q];
 }
 
 // total hidden spikes of the run (the automatic form choice of the next run)
@@ -474,15 +588,22 @@ __global__ void k_rec_put_spikes(RecConsts c, RecBufs d, const uint8_t* __restri
         for (int slot = 0; slot < 2; ++slot) d.sh[((size_t)slot * c.B + b) * c.Nw + jw] = word;
 }
 
-// Wt[j][k] = W_ff[k][j] for k < n_in, W_rec[k - n_in][j] for k < n_in + N, else 0
+// Wt[j][k], rows < rows: for j < N, W_ff[k][j] (k < n_in) then W_rec[k - n_in][j]
+// (k < n_in + N); for R0 <= j < R0 + n_out (the fused readout), W_out[k - n_in][j - R0]
+// on the hidden columns; 0 elsewhere
 __global__ void k_rec_pack(const uint16_t* __restrict__ w_ff, const uint16_t* __restrict__ w_rec,
-                           uint16_t* __restrict__ wt, int n_in, int N, int K) {
+                           const uint16_t* __restrict__ w_out, uint16_t* __restrict__ wt, int n_in, int N,
+                           int n_out, int K, int R0, int rows) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)N * K) return;
+    if (idx >= (size_t)rows * K) return;
     const int j = (int)(idx / K), k = (int)(idx % K);
     uint16_t w = 0;
-    if (k < n_in) w = w_ff[(size_t)k * N + j];
-    else if (k < n_in + N) w = w_rec[(size_t)(k - n_in) * N + j];
+    if (j < N) {
+        if (k < n_in) w = w_ff[(size_t)k * N + j];
+        else if (k < n_in + N) w = w_rec[(size_t)(k - n_in) * N + j];
+    } else if (j >= R0 && j < R0 + n_out && k >= n_in && k < n_in + N) {
+        w = w_out[(size_t)(k - n_in) * n_out + (j - R0)];
+    }
     wt[idx] = w;
 }
 
@@ -522,8 +643,10 @@ struct snn_rec {
     uint16_t* w_ff = nullptr;
     uint16_t* w_rec = nullptr;
     uint16_t* w_out = nullptr;
-    uint16_t* wt = nullptr;            // [n_hid][K] stacked transposed weights of the dense form
+    uint16_t* wt = nullptr;            // [wt_rows][K] stacked transposed weights of the dense form
     int K = 0;
+    DenseGeom geom{};                  // per batch: ntiles depends on B
+    int wt_rows = 0;
     CUtensorMap map_w{}, map_s[2]{};
     uint32_t* dev_err = nullptr;       // [2]: a dense step's pipeline wait timed out; bad spike bytes
     unsigned long long* act_dev = nullptr;   // hidden spikes of the last run
@@ -533,6 +656,11 @@ struct snn_rec {
     double activity = -1.0;            // hidden spikes per sample and step, last measurement
     long long act_div = 0;             // B * T of the measured run
     int last_form = 0;                 // SNN_REC_GATHER or SNN_REC_TENSOR of the last run
+    int num_sms = 1;
+    std::vector<cudaEvent_t> prof_ev;   // SNN_PROFILE: a start and an end event per launch
+    std::vector<int> prof_cls;
+    int prof_n = 0;
+    bool last_profiled = false;
     unsigned long long* step = nullptr;
     RecBufs d{};
     int B = 0;
@@ -589,6 +717,16 @@ cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
 }
 
+cudaError_t ensure_scratch(snn_rec* r, size_t bytes) {
+    if (r->scratch_bytes >= bytes) return cudaSuccess;
+    if (r->scratch) cudaFree(r->scratch);
+    r->scratch = nullptr;
+    r->scratch_bytes = 0;
+    const cudaError_t e = cudaMalloc(&r->scratch, bytes);
+    if (e == cudaSuccess) r->scratch_bytes = bytes;
+    return e;
+}
+
 snn_status alloc_batch(snn_rec* r, int B) {
     free_batch(r);
     const size_t NI = r->spec.n_in, N = r->spec.n_hid, NO = r->spec.n_out;
@@ -597,10 +735,12 @@ snn_status alloc_batch(snn_rec* r, int B) {
     REC_TRY(r, dalloc(&r->d.seeds, (size_t)B));
     REC_TRY(r, dalloc(&r->d.inb, (size_t)B * Iw));
     REC_TRY(r, dalloc(&r->d.sh, 2 * (size_t)B * Nw));
-    REC_TRY(r, dalloc(&r->d.v, (size_t)B * N));
-    REC_TRY(r, dalloc(&r->d.i_syn, (size_t)B * N));
+    const size_t ns = state_elems(B, (int)N);
+    REC_TRY(r, dalloc(&r->d.v, ns));
+    REC_TRY(r, dalloc(&r->d.i_syn, ns));
     REC_TRY(r, dalloc(&r->d.v_out, (size_t)B * NO));
-    REC_TRY(r, dalloc(&r->d.counts, (size_t)B * N));
+    REC_TRY(r, dalloc(&r->d.counts, ns));
+    REC_TRY(r, cudaMemset(r->d.counts, 0, ns * 4));   // padding samples stay 0
     REC_TRY(r, dalloc(&r->rates_stage, (size_t)B * NI));
     REC_TRY(r, dalloc(&r->seeds_stage, (size_t)B));
     REC_TRY(r, dalloc(&r->d.S, 2 * (size_t)B * r->K));
@@ -656,7 +796,12 @@ snn_status snn_rec_create(const snn_rec_spec* spec, snn_rec** out) {
     if (e == cudaSuccess) e = dalloc(&r->w_out, nout);
     r->K = (s.n_in + s.n_hid + GBK - 1) / GBK * GBK;
     if (e == cudaSuccess) e = dalloc(&r->step, 2);
-    if (e == cudaSuccess) e = dalloc(&r->wt, (size_t)s.n_hid * r->K);
+    r->geom.ntn_drive = (s.n_hid + GBN - 1) / GBN;
+    r->geom.fused = s.n_out <= GBN ? 1 : 0;
+    r->geom.ntn = r->geom.ntn_drive + r->geom.fused;
+    r->geom.n_ro = r->geom.fused ? (s.n_out + 15) / 16 * 16 : 0;
+    r->wt_rows = r->geom.fused ? r->geom.ntn_drive * GBN + s.n_out : s.n_hid;
+    if (e == cudaSuccess) e = dalloc(&r->wt, (size_t)r->wt_rows * r->K);
     if (e == cudaSuccess) e = dalloc(&r->dev_err, 2);
     if (e == cudaSuccess) e = cudaMemset(r->dev_err, 0, 8);
     if (e == cudaSuccess) e = dalloc(&r->act_dev, 1);
@@ -667,16 +812,18 @@ snn_status snn_rec_create(const snn_rec_spec* spec, snn_rec** out) {
     if (e == cudaSuccess) e = cudaMemcpy(r->w_out, s.w_out, nout * 2, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(r->step, 0, 16);
     if (e == cudaSuccess) {
-        const size_t n = (size_t)s.n_hid * r->K;
-        k_rec_pack<<<(unsigned)((n + 255) / 256), 256>>>(r->w_ff, r->w_rec, r->wt, s.n_in, s.n_hid, r->K);
+        const size_t n = (size_t)r->wt_rows * r->K;
+        k_rec_pack<<<(unsigned)((n + 255) / 256), 256>>>(r->w_ff, r->w_rec, r->w_out, r->wt, s.n_in, s.n_hid,
+                                                         s.n_out, r->K, r->geom.ntn_drive * GBN, r->wt_rows);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e == cudaSuccess && !encode_map(&r->map_w, r->wt, s.n_hid, r->K, GBN)) {
+    if (e == cudaSuccess && !encode_map(&r->map_w, r->wt, r->wt_rows, r->K, GBN)) {
         snn_rec_destroy(r);
         return rec_fail(nullptr, SNN_ERR_CUDA, "snn_rec_create: cannot encode the weight tensor map");
     }
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rec_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, GSMEM);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&r->num_sms, cudaDevAttrMultiProcessorCount, r->device);
     if (e != cudaSuccess) {
         snn_rec_destroy(r);
         return rec_fail(nullptr, e == cudaErrorMemoryAllocation ? SNN_ERR_OOM : SNN_ERR_CUDA,
@@ -702,6 +849,7 @@ snn_status snn_rec_destroy(snn_rec* r) {
     if (r->act_dev) cudaFree(r->act_dev);
     if (r->act_host) cudaFreeHost(r->act_host);
     if (r->act_ev) cudaEventDestroy(r->act_ev);
+    for (cudaEvent_t e : r->prof_ev) cudaEventDestroy(e);
     if (r->scratch) cudaFree(r->scratch);
     delete r;
     return SNN_OK;
@@ -765,23 +913,55 @@ snn_status snn_rec_run(snn_rec* r, const float* rates, const uint64_t* seeds, in
         form = (r->activity >= 0.0 && r->activity < SNN_REC_GATHER_MAX_DENSITY * (double)(c.n_in + c.N))
                    ? SNN_REC_GATHER : SNN_REC_TENSOR;
     const int dense = form == SNN_REC_TENSOR ? 1 : 0;
+    const bool profile = (flags & SNN_PROFILE) != 0;
+    r->last_profiled = false;
+    r->prof_n = 0;
+    if (profile) {
+        const size_t need = (size_t)T * SNN_REC_KERNEL_COUNT * 2;
+        while (r->prof_ev.size() < need) {
+            cudaEvent_t e;
+            REC_TRY(r, cudaEventCreate(&e));
+            r->prof_ev.push_back(e);
+        }
+        r->prof_cls.resize(need / 2);
+    }
+    auto mark = [&](int cls, bool start) {
+        if (!profile) return;
+        if (start) r->prof_cls[r->prof_n] = cls;
+        cudaEventRecord(r->prof_ev[2 * r->prof_n + (start ? 0 : 1)], st);
+        if (!start) ++r->prof_n;
+    };
     RecBufs d = r->d;
     k_rec_begin<<<296, 256, 0, st>>>(c, d, rdev, sdev, cont ? 0 : 1, T);
     REC_TRY(r, cudaGetLastError());
-    const size_t enc_warps = (size_t)B * c.Iw, hid_warps = (size_t)B * c.Nw, outs = (size_t)B * c.n_out;
-    const dim3 dgrid((unsigned)((B + GBM - 1) / GBM), (unsigned)((c.N + GBN - 1) / GBN));
+    const size_t enc_warps = (size_t)B * c.Iw, hid_warps = (size_t)B * c.Nw;
+    DenseGeom geom = r->geom;
+    geom.ntiles = ((B + GBM - 1) / GBM) * geom.ntn;
+    const unsigned dgrid = (unsigned)std::min(geom.ntiles, r->num_sms);
     for (int t = 0; t < T; ++t) {
+        mark(SNN_REC_KERNEL_ENCODE, true);
         k_rec_encode<<<(unsigned)((enc_warps + 7) / 8), 256, 0, st>>>(c, d, t, dense);
+        mark(SNN_REC_KERNEL_ENCODE, false);
+        mark(SNN_REC_KERNEL_DRIVE, true);
         if (dense)
-            k_rec_dense<<<dgrid, 128, GSMEM, st>>>(r->map_s[0], r->map_s[1], r->map_w, c, d, t, r->dev_err);
+            k_rec_dense<<<dgrid, GTHREADS, GSMEM, st>>>(r->map_s[0], r->map_s[1], r->map_w, c, d, t, geom,
+                                                         r->dev_err);
         else
             k_rec_hidden<<<(unsigned)((hid_warps + 7) / 8), 256, 0, st>>>(c, d, t);
-        k_rec_readout<<<(unsigned)((outs + 255) / 256), 256, 0, st>>>(c, d, t);
+        mark(SNN_REC_KERNEL_DRIVE, false);
+        // the tensor form's product adds each step's readout one step later;
+        // the run's last step is read out here
+        if (!dense || !geom.fused || t == T - 1) {
+            mark(SNN_REC_KERNEL_READOUT, true);
+            k_rec_readout<<<(unsigned)((B + 7) / 8), 256, 0, st>>>(c, d, t);
+            mark(SNN_REC_KERNEL_READOUT, false);
+        }
     }
     REC_TRY(r, cudaGetLastError());
+    r->last_profiled = profile;
     if (T > 0 && !r->act_pending) {   // measure this run's activity for the next automatic choice
         REC_TRY(r, cudaMemsetAsync(r->act_dev, 0, sizeof(unsigned long long), st));
-        k_rec_activity<<<152, 256, 0, st>>>(d.counts, (size_t)B * c.N, r->act_dev);
+        k_rec_activity<<<(unsigned)(8 * r->num_sms), 256, 0, st>>>(d.counts, state_elems(B, c.N), r->act_dev);
         REC_TRY(r, cudaGetLastError());
         REC_TRY(r, cudaMemcpyAsync(r->act_host, r->act_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
         REC_TRY(r, cudaEventRecord(r->act_ev, st));
@@ -833,24 +1013,26 @@ snn_status snn_rec_read(snn_rec* r, int field, void* dst, size_t bytes, int dst_
         return rec_fail(r, SNN_ERR_TIMEOUT, "snn_rec_read: a tensor-form step's pipeline wait gave up");
     const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const void* src = nullptr;
+    const void* interleaved = nullptr;
     switch (field) {
-        case SNN_REC_V: src = r->d.v; break;
-        case SNN_REC_I_SYN: src = r->d.i_syn; break;
-        case SNN_REC_COUNTS: src = r->d.counts; break;
+        case SNN_REC_V: interleaved = r->d.v; break;
+        case SNN_REC_I_SYN: interleaved = r->d.i_syn; break;
+        case SNN_REC_COUNTS: interleaved = r->d.counts; break;
         case SNN_REC_V_OUT: src = r->d.v_out; break;
         case SNN_REC_RASTER: src = r->d.raster_h; break;
         case SNN_REC_RASTER_INPUT: src = r->d.raster_in; break;
         case SNN_REC_STEP: src = r->step + 1; break;
         default: break;
     }
-    if (!src) {   // the last step's spikes, unpacked on the device
-        if (r->scratch_bytes < want) {
-            if (r->scratch) cudaFree(r->scratch);
-            r->scratch = nullptr;
-            r->scratch_bytes = 0;
-            REC_TRY(r, cudaMalloc(&r->scratch, want));
-            r->scratch_bytes = want;
-        }
+    if (interleaved) {   // state arrays, back to [B][N] on the device
+        REC_TRY(r, ensure_scratch(r, want));
+        const size_t n = want / 4;
+        k_rec_relayout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const uint32_t*)interleaved,
+                                                                     (uint32_t*)r->scratch, r->B, r->spec.n_hid, 0);
+        REC_TRY(r, cudaGetLastError());
+        src = r->scratch;
+    } else if (!src) {   // the last step's spikes, unpacked on the device
+        REC_TRY(r, ensure_scratch(r, want));
         const RecConsts c = make_consts(r, r->B, 1.0f, 0);
         k_rec_spikes<<<(unsigned)((want + 255) / 256), 256, 0, st>>>(c, r->d, (uint8_t*)r->scratch);
         REC_TRY(r, cudaGetLastError());
@@ -877,13 +1059,25 @@ snn_status snn_rec_write(snn_rec* r, int field, const void* src, size_t bytes, i
     REC_TRY(r, cudaStreamSynchronize(st));
     const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     void* dst = nullptr;
+    void* interleaved = nullptr;
     switch (field) {
-        case SNN_REC_V: dst = r->d.v; break;
-        case SNN_REC_I_SYN: dst = r->d.i_syn; break;
-        case SNN_REC_COUNTS: dst = r->d.counts; break;
+        case SNN_REC_V: interleaved = r->d.v; break;
+        case SNN_REC_I_SYN: interleaved = r->d.i_syn; break;
+        case SNN_REC_COUNTS: interleaved = r->d.counts; break;
         case SNN_REC_V_OUT: dst = r->d.v_out; break;
         case SNN_REC_STEP: dst = r->step + 1; break;
         default: break;
+    }
+    if (interleaved) {
+        REC_TRY(r, ensure_scratch(r, want));
+        REC_TRY(r, cudaMemcpyAsync(r->scratch, src, want, kind, st));
+        const size_t n = want / 4;
+        k_rec_relayout<<<(unsigned)((n + 255) / 256), 256, 0, st>>>((const uint32_t*)r->scratch,
+                                                                     (uint32_t*)interleaved, r->B, r->spec.n_hid, 1);
+        REC_TRY(r, cudaGetLastError());
+        REC_TRY(r, cudaStreamSynchronize(st));
+        r->state_valid = true;
+        return SNN_OK;
     }
     if (dst) {
         REC_TRY(r, cudaMemcpyAsync(dst, src, want, kind, st));
@@ -891,13 +1085,7 @@ snn_status snn_rec_write(snn_rec* r, int field, const void* src, size_t bytes, i
         r->state_valid = true;
         return SNN_OK;
     }
-    if (r->scratch_bytes < want) {   // spikes: staged, then packed on the device
-        if (r->scratch) cudaFree(r->scratch);
-        r->scratch = nullptr;
-        r->scratch_bytes = 0;
-        REC_TRY(r, cudaMalloc(&r->scratch, want));
-        r->scratch_bytes = want;
-    }
+    REC_TRY(r, ensure_scratch(r, want));   // spikes: staged, then packed on the device
     REC_TRY(r, cudaMemcpyAsync(r->scratch, src, want, kind, st));
     REC_TRY(r, cudaMemsetAsync(r->dev_err + 1, 0, 4, st));
     const RecConsts c = make_consts(r, r->B, 1.0f, 0);
@@ -913,6 +1101,25 @@ snn_status snn_rec_write(snn_rec* r, int field, const void* src, size_t bytes, i
 }
 
 uint32_t snn_rec_form(const snn_rec* r) { return r ? (uint32_t)r->last_form : 0u; }
+
+snn_status snn_rec_profile(snn_rec* r, double* ms, int* launches, int count) {
+    if (!r) return rec_fail(nullptr, SNN_ERR_ARG, "snn_rec_profile: net is NULL");
+    r->err.clear();
+    if (!ms || !launches || count <= 0 || count > SNN_REC_KERNEL_COUNT)
+        return rec_fail(r, SNN_ERR_ARG, "snn_rec_profile: need ms, launches and 0 < count <= %d",
+                        SNN_REC_KERNEL_COUNT);
+    if (!r->last_profiled) return rec_fail(r, SNN_ERR_STATE, "snn_rec_profile: the last run was not profiled");
+    REC_TRY(r, cudaSetDevice(r->device));
+    REC_TRY(r, cudaStreamSynchronize(r->last));
+    for (int k = 0; k < count; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (int i = 0; i < r->prof_n; ++i) {
+        float t = 0.0f;
+        REC_TRY(r, cudaEventElapsedTime(&t, r->prof_ev[2 * i], r->prof_ev[2 * i + 1]));
+        const int k = r->prof_cls[i];
+        if (k < count) { ms[k] += t; launches[k] += 1; }
+    }
+    return SNN_OK;
+}
 
 const char* snn_rec_last_error(const snn_rec* r) {
     return r ? r->err.c_str() : g_rec_create_error.c_str();

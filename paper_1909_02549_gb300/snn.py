@@ -61,7 +61,8 @@ EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_fie
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
             "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
-            "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_last_error",
+            "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_profile",
+            "snn_rec_last_error",
             "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -88,6 +89,7 @@ class snn_rec_spec(C.Structure):
 SNN_REC_GATHER = 1 << 8      # exact gather form of the drive
 SNN_REC_TENSOR = 1 << 9      # dense tensor-core form
 REC_FORMS = {"auto": 0, "gather": SNN_REC_GATHER, "tensor": SNN_REC_TENSOR}
+REC_KERNELS = ("encode", "drive", "readout")
 REC_FIELDS = {"v": SNN_REC_V, "i_syn": SNN_REC_I_SYN, "spikes": SNN_REC_SPIKES,
               "counts": SNN_REC_COUNTS, "v_out": SNN_REC_V_OUT, "raster": SNN_REC_RASTER,
               "raster_input": SNN_REC_RASTER_INPUT, "step": SNN_REC_STEP}
@@ -158,6 +160,8 @@ def lib():
         L.snn_rec_field_bytes.restype = C.c_size_t
         L.snn_rec_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_rec_write.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
+        L.snn_rec_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
+        L.snn_rec_profile.restype = C.c_int
         L.snn_rec_form.argtypes = [C.c_void_p]
         L.snn_rec_form.restype = C.c_uint32
         L.snn_rec_last_error.argtypes = [C.c_void_p]
@@ -487,11 +491,12 @@ class RecNetwork:
 
     def run(self, rates, seeds, T: int, *, dt: float = 1.0, continue_: bool = False,
             record: bool = False, record_input: bool = False, form: str = "auto",
-            stream=None) -> None:
+            profile: bool = False, stream=None) -> None:
         """``form``: "gather" (exact), "tensor" (dense tensor cores) or "auto"."""
         B = rates.shape[0]
         flags = (SNN_CONTINUE if continue_ else 0) | (SNN_RECORD_RASTER if record else 0) | (
-            SNN_RECORD_INPUT if record_input else 0) | REC_FORMS[form]
+            SNN_RECORD_INPUT if record_input else 0) | REC_FORMS[form] | (
+            SNN_PROFILE if profile else 0)
         snn_rec_run(self.handle, rates, seeds, B, T, dt, flags, stream)
         self.B = B
 
@@ -511,6 +516,14 @@ class RecNetwork:
 
     def write(self, name: str, src) -> None:
         snn_rec_write(self.handle, REC_FIELDS[name], src)
+
+    def profile(self) -> dict:
+        """{kernel class: (ms, launches)} of the last run made with profile=True."""
+        n = len(REC_KERNELS)
+        ms = (C.c_double * n)()
+        cnt = (C.c_int * n)()
+        _rec_check(self.handle, lib().snn_rec_profile(self.handle, ms, cnt, n))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(REC_KERNELS)}
 
     @property
     def form(self) -> str:

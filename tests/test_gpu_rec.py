@@ -284,3 +284,20 @@ def test_rec_automatic_form_follows_the_measured_activity():
     net.run(dev(r), dev(s), 5, form="gather")
     assert net.form == "gather"
     net.close()
+
+
+def test_rec_profile_counts_every_launch():
+    m = snn()
+    p, r, s, wf, wr, wo = dyadic_workload(4, 64, 96, 10, seed=23)
+    net = m.RecNetwork(p, wf, wr, wo)
+    net.run(dev(r), dev(s), 12, form="tensor")
+    with pytest.raises(m.SNNError) as e:
+        net.profile()                                          # not profiled
+    assert e.value.status == m.SNN_ERR_STATE
+    for form in ("tensor", "gather"):
+        net.run(dev(r), dev(s), 12, form=form, profile=True)
+        prof = net.profile()
+        assert all(prof[k][1] == 12 and prof[k][0] > 0 for k in ("encode", "drive")), prof
+        # the tensor form's product carries the readout; only the last step has its own
+        assert prof["readout"][1] == (1 if form == "tensor" else 12) and prof["readout"][0] > 0
+    net.close()
