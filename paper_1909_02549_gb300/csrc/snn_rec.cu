@@ -70,7 +70,7 @@ struct RecBufs {
     const uint16_t* w_ff;    // [n_in][N] bfloat16
     const uint16_t* w_rec;   // [N][N]
     const uint16_t* w_out;   // [N][n_out]
-    uint32_t* thr;           // [B][n_in]
+    uint32_t* thr;           // [Bp/32][n_in][32] Poisson thresholds (sidx)
     uint64_t* seeds;         // [B]
     uint32_t* inb;           // [B][Iw]     input spikes of the step
     uint32_t* sh;            // [2][B][Nw]  hidden spikes, slot = step parity
@@ -105,8 +105,10 @@ __host__ __device__ constexpr uint32_t gidesc(int n) {
 // Tiles of the dense form: ntn_drive neuron tiles of GBN columns per 128 samples,
 // then, when the readout is fused (n_out <= GBN), one readout tile whose
 // weight rows start at R0 = ntn_drive * GBN and whose MMAs are n_ro wide.
+// With enc_next, drive tile (tm, tn) also draws the next step's input spikes of
+// its samples for inputs [tn * a_per, (tn + 1) * a_per), a_per a multiple of 32.
 struct DenseGeom {
-    int ntn_drive, ntn, ntiles, fused, n_ro;
+    int ntn_drive, ntn, ntiles, fused, n_ro, a_per, enc_next;
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -174,7 +176,8 @@ __global__ void k_rec_begin(RecConsts c, RecBufs d, const float* __restrict__ ra
                             const uint64_t* __restrict__ seeds, int episodic, int T) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
-    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth) d.thr[k] = poisson_threshold(rates[k], c.dt);
+    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth)
+        d.thr[sidx((int)(k / c.n_in), (int)(k % c.n_in), c.n_in)] = poisson_threshold(rates[k], c.dt);
     for (size_t k = tid; k < (size_t)c.B; k += nth) d.seeds[k] = seeds[k];
     if (episodic) {
         for (size_t k = tid; k < state_elems(c.B, c.N); k += nth) {
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(256) k_rec_encode(RecConsts c, RecBufs d, int 
     const int a = iw * 32 + lane;
     uint32_t s = 0;
     if (a < c.n_in) {
-        const uint32_t thr = d.thr[(size_t)b * c.n_in + a];
+        const uint32_t thr = d.thr[sidx(b, a, c.n_in)];
         if (thr != 0u) {
             const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)a;
             s = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32) < thr ? 1u : 0u;
@@ -268,6 +271,57 @@ __global__ void __launch_bounds__(256) k_rec_hidden(RecConsts c, RecBufs d, int 
     if (vj) d.S[((size_t)prv * c.B + b) * d.K + c.n_in + j] = spk ? BF16_ONE : 0;   // next step's operand
 }
 
+// 32 consecutive columns col0.. (nu of them live) of the spike operand of slot
+// `slot` from each lane's spike word (lanes = 32 consecutive samples, live when
+// b < B; every lane takes part): with col0 even and nu = 32, two rows per
+// store, lanes 0-15 and 16-31 each writing a pair of columns of one row
+__device__ __forceinline__ void store_operand_word(const RecConsts& c, const RecBufs& d, int b, bool live,
+                                                   uint32_t word, int slot, int col0, int nu) {
+    const int lane = threadIdx.x & 31;
+    const int b0 = b - lane;
+    const int half = lane >> 4, pr = lane & 15;
+    if (nu == 32 && (col0 & 1) == 0) {
+#pragma unroll 4
+        for (int rr = 0; rr < 32; rr += 2) {
+            const uint32_t wr = __shfl_sync(FULL, word, rr + half);
+            const int row = b0 + rr + half;
+            if (row < c.B) {
+                const uint32_t bits2 = (wr >> (2 * pr)) & 3u;
+                const uint32_t val = ((bits2 & 1u) ? (uint32_t)BF16_ONE : 0u) |
+                                     ((bits2 & 2u) ? ((uint32_t)BF16_ONE << 16) : 0u);
+                uint16_t* dst = d.S + ((size_t)slot * c.B + row) * d.K + col0 + 2 * pr;
+                *reinterpret_cast<uint32_t*>(dst) = val;
+            }
+        }
+    } else if (live) {
+        uint16_t* dst = d.S + ((size_t)slot * c.B + b) * d.K + col0;
+        for (int u = 0; u < nu; ++u) dst[u] = ((word >> u) & 1u) ? BF16_ONE : 0;
+    }
+}
+
+// dense form: the input spikes of step tt of 32 consecutive samples (lanes) for
+// inputs a0 .. a0 + 31 (the same draw as k_rec_encode), into the operand slot
+// of that step
+__device__ __forceinline__ void dense_encode_group(const RecConsts& c, const RecBufs& d, int b, bool live,
+                                                   unsigned long long tt, int a0) {
+    const int nu = min(32, c.n_in - a0);
+    uint32_t word = 0u;
+    if (live) {
+        const uint64_t seed = d.seeds[b];
+        const size_t q0 = sidx(b, a0, c.n_in);
+#pragma unroll 4
+        for (int u = 0; u < 32; ++u) {
+            if (u >= nu) break;
+            const uint32_t thr = d.thr[q0 + 32 * u];
+            if (thr != 0u) {
+                const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)(a0 + u);
+                if ((uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32) < thr) word |= 1u << u;
+            }
+        }
+    }
+    store_operand_word(c, d, b, live, word, (int)(tt & 1ull), a0, nu);
+}
+
 // dense form, epilogue of 32 consecutive samples (lanes, live when b < B) x 32
 // neurons j0.. (j0 < N): the synapse and membrane update from the accumulated
 // drive r[u] of neuron j0 + u, the spike words, the next step's operand and
@@ -323,26 +377,7 @@ __device__ __forceinline__ void dense_epilogue_chunk(const RecConsts& c, const R
             for (int u = 0; u < nu; ++u) rp[u] = (uint8_t)((word >> u) & 1u);
         }
     }
-    // next step's operand, rows of the warp's samples: two rows per store, lanes
-    // 0-15 and 16-31 each writing a pair of neurons of one row
-    const int b0 = b - lane;
-    const int half = lane >> 4, pr = lane & 15;
-    if (nu == 32 && (c.n_in & 1) == 0) {
-#pragma unroll 4
-        for (int rr = 0; rr < 32; rr += 2) {
-            const uint32_t wr = __shfl_sync(FULL, word, rr + half);
-            const int row = b0 + rr + half;
-            if (row < c.B) {
-                const uint32_t bits2 = (wr >> (2 * pr)) & 3u;
-                const uint32_t val = ((bits2 & 1u) ? (uint32_t)BF16_ONE : 0u) | ((bits2 & 2u) ? ((uint32_t)BF16_ONE << 16) : 0u);
-                uint16_t* dst = d.S + ((size_t)nxt * c.B + row) * d.K + c.n_in + j0 + 2 * pr;
-                *reinterpret_cast<uint32_t*>(dst) = val;
-            }
-        }
-    } else if (live) {
-        uint16_t* snext = d.S + ((size_t)nxt * c.B + b) * d.K + c.n_in + j0;
-        for (int u = 0; u < nu; ++u) snext[u] = ((word >> u) & 1u) ? BF16_ONE : 0;
-    }
+    store_operand_word(c, d, b, live, word, nxt, c.n_in + j0, nu);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
@@ -489,6 +524,11 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_rec_dense(const __grid_constant
                         if (col + u < c.n_out) vo[col + u] = __fadd_rn(vo[col + u], __uint_as_float(r[u]));
                 }
             }
+            // this warp's share of the next step's input draws: groups of 32 inputs,
+            // alternating between the two column halves
+            if (!ro && g.enc_next)
+                for (int a0 = tn * g.a_per + half * 32; a0 < min(c.n_in, (tn + 1) * g.a_per); a0 += 64)
+                    dense_encode_group(c, d, b, b < c.B, tt + 1ull, a0);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -731,7 +771,7 @@ snn_status alloc_batch(snn_rec* r, int B) {
     free_batch(r);
     const size_t NI = r->spec.n_in, N = r->spec.n_hid, NO = r->spec.n_out;
     const size_t Iw = (NI + 31) / 32, Nw = (N + 31) / 32;
-    REC_TRY(r, dalloc(&r->d.thr, (size_t)B * NI));
+    REC_TRY(r, dalloc(&r->d.thr, state_elems(B, (int)NI)));
     REC_TRY(r, dalloc(&r->d.seeds, (size_t)B));
     REC_TRY(r, dalloc(&r->d.inb, (size_t)B * Iw));
     REC_TRY(r, dalloc(&r->d.sh, 2 * (size_t)B * Nw));
@@ -800,6 +840,7 @@ snn_status snn_rec_create(const snn_rec_spec* spec, snn_rec** out) {
     r->geom.fused = s.n_out <= GBN ? 1 : 0;
     r->geom.ntn = r->geom.ntn_drive + r->geom.fused;
     r->geom.n_ro = r->geom.fused ? (s.n_out + 15) / 16 * 16 : 0;
+    r->geom.a_per = ((s.n_in + r->geom.ntn_drive - 1) / r->geom.ntn_drive + 31) / 32 * 32;
     r->wt_rows = r->geom.fused ? r->geom.ntn_drive * GBN + s.n_out : s.n_hid;
     if (e == cudaSuccess) e = dalloc(&r->wt, (size_t)r->wt_rows * r->K);
     if (e == cudaSuccess) e = dalloc(&r->dev_err, 2);
@@ -938,10 +979,16 @@ snn_status snn_rec_run(snn_rec* r, const float* rates, const uint64_t* seeds, in
     DenseGeom geom = r->geom;
     geom.ntiles = ((B + GBM - 1) / GBM) * geom.ntn;
     const unsigned dgrid = (unsigned)std::min(geom.ntiles, r->num_sms);
+    // the tensor form draws each next step's inputs in the product's epilogue,
+    // unless the input raster is recorded
+    const bool fuse_enc = dense && !c.rec_input;
     for (int t = 0; t < T; ++t) {
-        mark(SNN_REC_KERNEL_ENCODE, true);
-        k_rec_encode<<<(unsigned)((enc_warps + 7) / 8), 256, 0, st>>>(c, d, t, dense);
-        mark(SNN_REC_KERNEL_ENCODE, false);
+        if (!fuse_enc || t == 0) {
+            mark(SNN_REC_KERNEL_ENCODE, true);
+            k_rec_encode<<<(unsigned)((enc_warps + 7) / 8), 256, 0, st>>>(c, d, t, dense);
+            mark(SNN_REC_KERNEL_ENCODE, false);
+        }
+        geom.enc_next = fuse_enc && t + 1 < T ? 1 : 0;
         mark(SNN_REC_KERNEL_DRIVE, true);
         if (dense)
             k_rec_dense<<<dgrid, GTHREADS, GSMEM, st>>>(r->map_s[0], r->map_s[1], r->map_w, c, d, t, geom,
