@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sample-timesteps/s vs batch, 784→6400 STDP; % roofline; serving p50/p99 ms"
 UNIT = "sample-timesteps/s"
-FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 WPREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 RULE_NAME = {"pair": "pair STDP",
              "post_norm": "post-triggered STDP with incoming-weight normalisation"}
@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--rec", action="store_true",
                     help="the recurrent inference network (1024 -> 4096 -> 10, B=4096, T=500) "
                          "instead (one JSON line)")
+    ap.add_argument("--no-gather", action="store_true",
+                    help="with --rec: skip the exact gather form's presentation")
     return ap.parse_args()
 
 
@@ -109,6 +111,7 @@ def peaks():
         with open(path) as f:
             d = json.load(f)
         return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
                 "source": "measured"}
     except Exception:
         return dict(FALLBACK_PEAKS, source="fallback")
@@ -592,13 +595,21 @@ def rec_leg(a):
     timed("tensor", max(1, a.warmup))                            # warm-up, allocation
     ms = timed("tensor", steps)
     density = float(net.read("counts").astype(np.float64).mean() / T)
-    ms_gather = timed("gather", 1)
-    density_gather = float(net.read("counts").astype(np.float64).mean() / T)
+    flush.zero_()
+    net.run(rd, sd, T, form="tensor", profile=True)              # per-kernel device times
+    prof = net.profile()
+    ms_gather, density_gather = None, None
+    if not a.no_gather:
+        ms_gather = timed("gather", 1)
+        density_gather = float(net.read("counts").astype(np.float64).mean() / T)
     net.close()
     value = B * T * steps / (sum(ms) * 1e-3)
     K = p["n_in"] + p["n_hid"]
-    flop_step = 2.0 * B * p["n_hid"] * K
-    step_s = statistics.mean(ms) * 1e-3 / T
+    # algorithmic FLOPs of one product launch: the drive of every (sample,
+    # neuron) over all n_in + n_hid inputs, and the readout over the hidden ones
+    flop_launch = 2.0 * B * p["n_hid"] * K + 2.0 * B * p["n_out"] * p["n_hid"]
+    drive_ms, drive_n = prof["drive"]
+    drive_tflops = flop_launch / (drive_ms * 1e-3 / drive_n) / 1e12
     pk = peaks()
     line = {"metric": "sample-timesteps/s, recurrent inference network", "value": value,
             "unit": UNIT, "ms_per_presentation": statistics.mean(ms), "steps": steps,
@@ -609,14 +620,20 @@ def rec_leg(a):
                        "weights": "bfloat16; drive as one [4096 x 5120] x [5120 x 4096] "
                                   "tcgen05 product per step, FP32 accumulation",
                        "l2": "flushed by a 256 MiB write before every presentation"},
-            "step_roofline": {"bound": "tensor", "achieved": flop_step / step_s / 1e12,
-                              "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                              "frac": flop_step / step_s / 1e12 / pk["bf16_tflops"],
-                              "note": "whole step (encode, product with fused neuron update, "
-                                      "readout) against the product's FLOPs; of measured peak"},
-            "gather": {"value": B * T / (ms_gather[0] * 1e-3), "unit": UNIT,
-                       "ms_per_presentation": ms_gather[0],
-                       "note": "exact form: FP32 sums in input order, bit-exact with the oracle"},
+            "roofline": {"bound": "tensor", "kernel": "k_rec_dense",
+                         "achieved": drive_tflops, "peak": pk["bf16_tflops_sustained"],
+                         "unit": "TFLOP/s", "frac": drive_tflops / pk["bf16_tflops_sustained"],
+                         "traffic": None,
+                         "note": "%.3g GFLOP per launch / %.1f us (CUDA events around each of "
+                                 "the %d launches of a profiled presentation); peak: measured "
+                                 "sustained bf16" % (flop_launch / 1e9, 1000 * drive_ms / drive_n,
+                                                    drive_n)},
+            "kernels_us_per_launch": {k: 1000 * v[0] / max(1, v[1]) for k, v in prof.items()},
+            "launches_per_presentation": {k: v[1] for k, v in prof.items()},
+            "gather": None if ms_gather is None else {
+                "value": B * T / (ms_gather[0] * 1e-3), "unit": UNIT,
+                "ms_per_presentation": ms_gather[0],
+                "note": "exact form: FP32 sums in input order, bit-exact with the oracle"},
             "hidden_firing_fraction": density, "hidden_firing_fraction_gather": density_gather}
     if not a.no_cpu_baseline:
         import oracle
