@@ -264,33 +264,41 @@ def run_reference(a):
 KERNEL_SOURCES = ("paper_1909_02549_gb300/csrc/snn_persistent.cu",
                   "paper_1909_02549_gb300/csrc/snn_internal.cuh")
 PERSISTENT_PROFILE = "profiles/k_persistent_784x6400_b256.md"
+REC_SOURCES = ("paper_1909_02549_gb300/csrc/snn_rec.cu",)
+REC_PROFILE = "profiles/k_rec_dense_1024x4096_b4096.md"
+
+
+def profile_traffic(profile, sources):
+    """DRAM bytes (read + write) per launch from a committed ncu summary, only
+    while the kernel sources hash to the value that summary records; else
+    None and why."""
+    try:
+        text = open(os.path.join(ROOT, profile)).read()
+        h = hashlib.sha256()
+        for f in sources:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        want = re.search(r"source sha256: ([0-9a-f]{64})", text)
+        nbytes = re.search(r"dram bytes per launch: (\d+)", text)
+        if not want or not nbytes:
+            return None, "no traffic recorded in " + profile
+        if want.group(1) != h.hexdigest():
+            return None, "kernel changed since the capture in " + profile
+        return int(nbytes.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + profile
+    except OSError as e:
+        return None, str(e)[:200]
 
 
 def recorded_traffic(a, dom):
-    """DRAM bytes (read + write) per launch of the persistent kernel, from the
-    committed ncu summary of this exact workload, and only while the kernel
-    sources hash to the value that summary records; else None and why."""
+    """Traffic of the persistent kernel on the default workload (see
+    ``profile_traffic``)."""
     if dom != "persistent":
         return None, "no capture of k_%s on this workload" % dom
     default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn, a.rule) == (
         256, 6400, 250, "mean", "fp32", False, "pair")
     if not default:
         return None, "the capture is of the default workload only"
-    try:
-        text = open(os.path.join(ROOT, PERSISTENT_PROFILE)).read()
-        h = hashlib.sha256()
-        for f in KERNEL_SOURCES:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        want = re.search(r"source sha256: ([0-9a-f]{64})", text)
-        nbytes = re.search(r"dram bytes per launch: (\d+)", text)
-        if not want or not nbytes:
-            return None, "no traffic recorded in " + PERSISTENT_PROFILE
-        if want.group(1) != h.hexdigest():
-            return None, "kernel changed since the capture in " + PERSISTENT_PROFILE
-        return int(nbytes.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + PERSISTENT_PROFILE
-    except OSError as e:
-        return None, str(e)[:200]
+    return profile_traffic(PERSISTENT_PROFILE, KERNEL_SOURCES)
 
 
 def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
@@ -610,6 +618,7 @@ def rec_leg(a):
     flop_launch = 2.0 * B * p["n_hid"] * K + 2.0 * B * p["n_out"] * p["n_hid"]
     drive_ms, drive_n = prof["drive"]
     drive_tflops = flop_launch / (drive_ms * 1e-3 / drive_n) / 1e12
+    traffic, traffic_src = profile_traffic(REC_PROFILE, REC_SOURCES)
     pk = peaks()
     line = {"metric": "sample-timesteps/s, recurrent inference network", "value": value,
             "unit": UNIT, "ms_per_presentation": statistics.mean(ms), "steps": steps,
@@ -623,7 +632,7 @@ def rec_leg(a):
             "roofline": {"bound": "tensor", "kernel": "k_rec_dense",
                          "achieved": drive_tflops, "peak": pk["bf16_tflops_sustained"],
                          "unit": "TFLOP/s", "frac": drive_tflops / pk["bf16_tflops_sustained"],
-                         "traffic": None,
+                         "traffic": traffic, "traffic_source": traffic_src,
                          "note": "%.3g GFLOP per launch / %.1f us (CUDA events around each of "
                                  "the %d launches of a profiled presentation); peak: measured "
                                  "sustained bf16" % (flop_launch / 1e9, 1000 * drive_ms / drive_n,
