@@ -309,13 +309,14 @@ __device__ __forceinline__ void dense_encode_group(const RecConsts& c, const Rec
     if (live) {
         const uint64_t seed = d.seeds[b];
         const size_t q0 = sidx(b, a0, c.n_in);
-#pragma unroll 4
+        uint32_t thr[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) thr[u] = u < nu ? d.thr[q0 + 32 * u] : 0u;   // all in flight
+#pragma unroll
         for (int u = 0; u < 32; ++u) {
-            if (u >= nu) break;
-            const uint32_t thr = d.thr[q0 + 32 * u];
-            if (thr != 0u) {
+            if (thr[u] != 0u) {
                 const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)(a0 + u);
-                if ((uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32) < thr) word |= 1u << u;
+                if ((uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32) < thr[u]) word |= 1u << u;
             }
         }
     }
@@ -328,16 +329,20 @@ __device__ __forceinline__ void dense_encode_group(const RecConsts& c, const Rec
 // the optional raster.  State accesses are one 128-byte line per warp.
 __device__ __forceinline__ void dense_epilogue_chunk(const RecConsts& c, const RecBufs& d, const uint32_t (&r)[32],
                                                      int b, bool live, int j0, int cur, int nxt, int t_local) {
-    const int lane = threadIdx.x & 31;
     const int nu = min(32, c.N - j0);
     uint32_t word = 0u;
     if (live) {
         const size_t q0 = sidx(b, j0, c.N);
         if (nu == 32) {
+            // every load of the chunk in flight at once: one DRAM round trip
             float I[32], v[32];
             uint32_t cn[32];
 #pragma unroll
-            for (int u = 0; u < 32; ++u) { I[u] = d.i_syn[q0 + 32 * u]; v[u] = d.v[q0 + 32 * u]; }
+            for (int u = 0; u < 32; ++u) {
+                I[u] = d.i_syn[q0 + 32 * u];
+                v[u] = d.v[q0 + 32 * u];
+                cn[u] = d.counts[q0 + 32 * u];
+            }
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
                 float x = __fmul_rn(c.a_syn, I[u]);
@@ -350,11 +355,11 @@ __device__ __forceinline__ void dense_epilogue_chunk(const RecConsts& c, const R
                 word |= (spk ? 1u : 0u) << u;
             }
 #pragma unroll
-            for (int u = 0; u < 32; ++u) { d.i_syn[q0 + 32 * u] = I[u]; d.v[q0 + 32 * u] = v[u]; }
-#pragma unroll
-            for (int u = 0; u < 32; ++u) cn[u] = d.counts[q0 + 32 * u];
-#pragma unroll
-            for (int u = 0; u < 32; ++u) d.counts[q0 + 32 * u] = cn[u] + ((word >> u) & 1u);
+            for (int u = 0; u < 32; ++u) {
+                d.i_syn[q0 + 32 * u] = I[u];
+                d.v[q0 + 32 * u] = v[u];
+                d.counts[q0 + 32 * u] = cn[u] + ((word >> u) & 1u);
+            }
         } else {
 #pragma unroll
             for (int u = 0; u < 32; ++u) {
@@ -493,15 +498,16 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_rec_dense(const __grid_constant
             const bool ro = g.fused && tn == g.ntn_drive;
             const int ncols = ro ? c.n_out : c.N - tn * GBN;   // live columns of the tile
             const int buf = lt & 1, use = lt >> 1;
+            constexpr int CH = GBN / 32 / 2;               // chunks of 32 columns per warp
+            const int b0 = tm * GBM + quarter * 32;        // the warp's first sample
             const bool got = __all_sync(FULL, mbar_wait(&accf[buf], use & 1) ? 1 : 0) != 0;
             if (!got) {
                 if (lane == 0) atomicOr(err, 1u);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int b = tm * GBM + quarter * 32 + lane;
+            const int b = b0 + lane;
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * GBN);
-            constexpr int CH = GBN / 32 / 2;               // chunks of 32 columns per warp
             for (int q = 0; q < CH; ++q) {
                 const int col = (half * CH + q) * 32;       // uniform over the warp
                 uint32_t r[32];
