@@ -638,6 +638,7 @@ def rec_leg(a):
             ms.append(e0.elapsed_time(e1))
         return ms
 
+    crossover = net.tune(rd, sd, 20)                             # measured dense-vs-gather switch
     timed("tensor", max(1, a.warmup))                            # warm-up, allocation
     ms = timed("tensor", steps)
     density = float(net.read("counts").astype(np.float64).mean() / T)
@@ -681,7 +682,9 @@ def rec_leg(a):
                 "value": B * T / (ms_gather[0] * 1e-3), "unit": UNIT,
                 "ms_per_presentation": ms_gather[0],
                 "note": "exact form: FP32 sums in input order, bit-exact with the oracle"},
-            "hidden_firing_fraction": density, "hidden_firing_fraction_gather": density_gather}
+            "hidden_firing_fraction": density, "hidden_firing_fraction_gather": density_gather,
+            "tuned_crossover_density": crossover,
+            "automatic_form": "tensor" if density * p["n_hid"] >= crossover * K else "gather"}
     if not a.no_cpu_baseline:
         import oracle
         oracle.build()

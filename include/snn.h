@@ -338,8 +338,9 @@ SNN_API const char* snn_last_error(const snn_net* net);
  *                   magnitude), otherwise within FP32 rounding of x.
  * With neither flag the run picks by the spike density measured on an
  * earlier run (hidden spikes per sample and step over n_in + n_hid, read back
- * without synchronising): the gather below SNN_REC_GATHER_MAX_DENSITY, else
- * the tensor form, which is also the choice of a network's first run.  The
+ * without synchronising): the gather below the crossover that snn_rec_tune
+ * measured (SNN_REC_GATHER_MAX_DENSITY before any tuning), else the tensor
+ * form, which is also the choice of a network's first run.  The
  * gather's cost grows with the active rows, the product's with n_in + n_hid.
  * ------------------------------------------------------------------------ */
 #define SNN_REC_GATHER  (1u << 8)
@@ -399,6 +400,18 @@ SNN_API snn_status snn_rec_read(snn_rec* net, int field, void* dst, size_t bytes
  * SNN_ERR_ARG (field, size, NULL, spike bytes other than 0/1), SNN_ERR_STATE
  * (no batch), SNN_ERR_CUDA. */
 SNN_API snn_status snn_rec_write(snn_rec* net, int field, const void* src, size_t bytes, int src_on_device);
+/* Tune the automatic choice on this network and batch: runs T steps in each form
+ * (two episodic runs from rates and seeds; flags may hold SNN_HOST_INPUTS) and
+ * synchronises the stream.  The gather form's cost is taken as proportional to
+ * the active rows per sample-step (hidden spikes measured on its run, plus the
+ * inputs' expected spikes); from the two measured step times follows the
+ * hidden activity below which the gather form is faster.  Later runs without a
+ * form flag compare the measured activity with it instead of
+ * SNN_REC_GATHER_MAX_DENSITY.  *crossover (may be NULL) receives it as a
+ * density (over n_in + n_hid).  Afterwards the batch holds the tensor run's
+ * state.  Errors: those of snn_rec_run, SNN_ERR_ARG for T <= 0. */
+SNN_API snn_status snn_rec_tune(snn_rec* net, const float* rates, const uint64_t* seeds, int32_t B,
+                                int32_t T, float dt_ms, uint32_t flags, void* stream, double* crossover);
 /* The form the last run took: SNN_REC_GATHER or SNN_REC_TENSOR (0 before any
  * run or for NULL). */
 SNN_API uint32_t snn_rec_form(const snn_rec* net);

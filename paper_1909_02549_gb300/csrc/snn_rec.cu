@@ -613,6 +613,17 @@ __global__ void k_rec_activity(const uint32_t* __restrict__ counts, size_t n, un
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(total, s);
 }
 
+// expected input spikes of the batch per step: the sum of the Poisson
+// probabilities thr / 2^32
+__global__ void k_rec_input_rate(const uint32_t* __restrict__ thr, int B, int n_in, double* total) {
+    double s = 0.0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < (size_t)B * n_in;
+         k += (size_t)gridDim.x * blockDim.x)
+        s += (double)thr[sidx((int)(k / n_in), (int)(k % n_in), n_in)];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(total, s * 0x1p-32);
+}
+
 // written spikes (bytes 0/1) into both slots of the words and of the operand,
 // so the step that follows reads them whatever the step counter; a byte above
 // 1 sets *bad and is stored as 1
@@ -702,6 +713,7 @@ struct snn_rec {
     double activity = -1.0;            // hidden spikes per sample and step, last measurement
     long long act_div = 0;             // B * T of the measured run
     int last_form = 0;                 // SNN_REC_GATHER or SNN_REC_TENSOR of the last run
+    double crossover = -1.0;           // tuned: hidden spikes per sample-step below which the gather wins
     int num_sms = 1;
     std::vector<cudaEvent_t> prof_ev;   // SNN_PROFILE: a start and an end event per launch
     std::vector<int> prof_cls;
@@ -956,9 +968,11 @@ snn_status snn_rec_run(snn_rec* r, const float* rates, const uint64_t* seeds, in
         r->act_pending = false;
     }
     int form = (int)(flags & (SNN_REC_GATHER | SNN_REC_TENSOR));
-    if (!form)
-        form = (r->activity >= 0.0 && r->activity < SNN_REC_GATHER_MAX_DENSITY * (double)(c.n_in + c.N))
-                   ? SNN_REC_GATHER : SNN_REC_TENSOR;
+    if (!form) {
+        const double cut = r->crossover >= 0.0 ? r->crossover
+                                               : SNN_REC_GATHER_MAX_DENSITY * (double)(c.n_in + c.N);
+        form = (r->activity >= 0.0 && r->activity < cut) ? SNN_REC_GATHER : SNN_REC_TENSOR;
+    }
     const int dense = form == SNN_REC_TENSOR ? 1 : 0;
     const bool profile = (flags & SNN_PROFILE) != 0;
     r->last_profiled = false;
@@ -1027,6 +1041,69 @@ snn_status snn_rec_run(snn_rec* r, const float* rates, const uint64_t* seeds, in
     r->last_T = T;
     r->last_raster = c.rec_raster != 0;
     r->last_input = c.rec_input != 0;
+    return SNN_OK;
+}
+
+snn_status snn_rec_tune(snn_rec* r, const float* rates, const uint64_t* seeds, int32_t B, int32_t T,
+                        float dt_ms, uint32_t flags, void* stream, double* crossover) {
+    if (!r) return rec_fail(nullptr, SNN_ERR_ARG, "snn_rec_tune: net is NULL");
+    if (T <= 0) return rec_fail(r, SNN_ERR_ARG, "snn_rec_tune: need T > 0");
+    const uint32_t base = flags & SNN_HOST_INPUTS;      // episodic runs, nothing recorded
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* dsum = nullptr;                             // [0] expected input spikes, [1] hidden spikes (integer)
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (dsum) cudaFree(dsum);
+    };
+    REC_TRY(r, cudaSetDevice(r->device));
+    for (cudaEvent_t& e : ev) {
+        const cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) { cleanup(); return rec_fail(r, SNN_ERR_CUDA, "snn_rec_tune: %s", cudaGetErrorString(err)); }
+    }
+    snn_status q = SNN_OK;
+    double t_gather = 0.0, t_tensor = 0.0, hidden = 0.0, input = 0.0;
+    do {
+        cudaEventRecord(ev[0], st);
+        if ((q = snn_rec_run(r, rates, seeds, B, T, dt_ms, base | SNN_REC_GATHER, stream)) != SNN_OK) break;
+        cudaEventRecord(ev[1], st);
+        // the gather run's hidden spikes and the inputs' expected spikes
+        unsigned long long spikes = 0;
+        if (cudaMalloc(&dsum, 2 * sizeof(double)) != cudaSuccess ||
+            cudaMemsetAsync(dsum, 0, 2 * sizeof(double), st) != cudaSuccess) {
+            q = rec_fail(r, SNN_ERR_CUDA, "snn_rec_tune: scratch");
+            break;
+        }
+        k_rec_activity<<<(unsigned)(8 * r->num_sms), 256, 0, st>>>(r->d.counts, state_elems(B, r->spec.n_hid),
+                                                                   (unsigned long long*)(dsum + 1));
+        k_rec_input_rate<<<(unsigned)(8 * r->num_sms), 256, 0, st>>>(r->d.thr, B, r->spec.n_in, dsum);
+        cudaEventRecord(ev[2], st);
+        if ((q = snn_rec_run(r, rates, seeds, B, T, dt_ms, base | SNN_REC_TENSOR, stream)) != SNN_OK) break;
+        cudaEventRecord(ev[3], st);
+        cudaError_t e = cudaEventSynchronize(ev[3]);
+        float ms_g = 0.0f, ms_t = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_g, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_t, ev[2], ev[3]);
+        if (e == cudaSuccess) e = cudaMemcpy(&spikes, dsum + 1, sizeof spikes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(&input, dsum, sizeof input, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) { q = rec_fail(r, SNN_ERR_CUDA, "snn_rec_tune: %s", cudaGetErrorString(e)); break; }
+        t_gather = ms_g / T;
+        t_tensor = ms_t / T;
+        hidden = (double)spikes / ((double)B * T);
+        input /= (double)B;
+    } while (false);
+    cleanup();
+    if (q != SNN_OK) return q;
+    // gather cost taken as proportional to the active rows per sample-step
+    // (input and hidden spikes); equal to the tensor form's at
+    // rows = (hidden + input) * t_tensor / t_gather
+    const double rows = hidden + input;
+    double cut = rows > 0.0 && t_gather > 0.0 ? rows * t_tensor / t_gather - input : 0.0;
+    if (cut < 0.0) cut = 0.0;
+    r->crossover = cut;
+    r->activity = hidden;
+    if (crossover) *crossover = cut / (double)(r->spec.n_in + r->spec.n_hid);
     return SNN_OK;
 }
 

@@ -61,7 +61,7 @@ EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_fie
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
             "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
-            "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_profile",
+            "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_profile", "snn_rec_tune",
             "snn_rec_last_error",
             "snn_last_error"]
 SNN_NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -161,6 +161,9 @@ def lib():
         L.snn_rec_read.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_rec_write.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_rec_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
+        L.snn_rec_tune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float,
+                                   C.c_uint32, C.c_void_p, C.POINTER(C.c_double)]
+        L.snn_rec_tune.restype = C.c_int
         L.snn_rec_profile.restype = C.c_int
         L.snn_rec_form.argtypes = [C.c_void_p]
         L.snn_rec_form.restype = C.c_uint32
@@ -516,6 +519,19 @@ class RecNetwork:
 
     def write(self, name: str, src) -> None:
         snn_rec_write(self.handle, REC_FIELDS[name], src)
+
+    def tune(self, rates, seeds, T: int = 20, *, dt: float = 1.0, stream=None) -> float:
+        """Time both forms on this batch (two episodic T-step runs) and set the
+        automatic choice's crossover; returns it as a density."""
+        B = rates.shape[0]
+        rp, _, rd = _buf(rates)
+        sp, _, sd = _buf(seeds)
+        flags = 0 if (rd and sd) else SNN_HOST_INPUTS
+        out = C.c_double(-1.0)
+        _rec_check(self.handle, lib().snn_rec_tune(self.handle, rp, sp, B, T, dt, flags, _stream(stream),
+                                                   C.byref(out)))
+        self.B = B
+        return out.value
 
     def profile(self) -> dict:
         """{kernel class: (ms, launches)} of the last run made with profile=True."""

@@ -310,3 +310,25 @@ def test_rec_profile_counts_every_launch():
         assert prof["readout"][1] == n and prof["encode"][1] == n, prof
         assert prof["readout"][0] > 0 and prof["encode"][0] > 0, prof
     net.close()
+
+
+def test_rec_tune_sets_the_automatic_crossover():
+    """snn_rec_tune times both forms; the crossover it sets decides later
+    automatic runs: a run after an active run takes the gather form exactly
+    when the measured activity is below the crossover.  The tuned runs leave
+    a valid batch (the tensor run's state) that continues exactly."""
+    m = snn()
+    p, r, s, wf, wr, wo = dyadic_workload(8, 64, 256, 10, seed=29)
+    net = m.RecNetwork(p, wf, wr, wo)
+    dens = net.tune(dev(r), dev(s), 30)
+    assert np.isfinite(dens) and dens >= 0.0
+    st, _, _ = oracle_run(p, r, s, wf, wr, wo, 30)              # the tensor run: exact (dyadic)
+    assert np.array_equal(net.read("counts"), st.counts)
+    activity = st.counts.sum() / (8 * 30)                     # hidden spikes per sample-step
+    net.run(dev(r), dev(s), 10)
+    want = "gather" if activity < dens * (64 + 256) else "tensor"
+    assert net.form == want, (activity, dens)
+    with pytest.raises(m.SNNError) as e:
+        net.tune(dev(r), dev(s), 0)
+    assert e.value.status == m.SNN_ERR_ARG
+    net.close()
