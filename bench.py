@@ -196,10 +196,10 @@ def algorithmic_bytes(kernel: str, B: int, N: int, NI: int, learn: bool, T: int 
     return 0.0
 
 
-def survey_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool) -> float:
-    """Algorithmic bytes per sample-step as the scope table's measurement
-    section defines them: the per-step streaming form, per-sample state read
-    and written once per step plus the shared W's bytes shared by the batch.
+def streaming_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool) -> float:
+    """Algorithmic bytes per sample-step of the per-step streaming form:
+    per-sample state read and written once per step, plus the shared W's
+    bytes divided over the batch.
 
     per sample, learning on : v_exc, v_inh FP32 r/w (16 N), the two u8
         refractory counters r/w (4 N), x_pre r/w (8 n_in), x_post r/w (8 N),
@@ -212,7 +212,7 @@ def survey_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool) -> float:
         weight; other learning-on workloads an FP32 read and write (8 B);
         learning off one FP32 read (4 B).
     784 -> 400 at B=1024: 23.4 KB; at B=256: 30.8 KB.  784 -> 6400 at B=256:
-    587 KB (quoted there as about 584 KB)."""
+    587 KB."""
     if learn:
         per = 29.0 * N + 12.0 * NI
         wb = 20.0 if (NI, N) == (784, 6400) else 8.0
@@ -346,14 +346,14 @@ def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
         pk = peaks()
         own = algorithmic_bytes(dom, B, N, 784, learn, T)
         if dom == "persistent":
-            # one launch is every step of the presentation: the scope table's
+            # one launch is every step of the presentation: the streaming form's
             # per-sample-step bytes times the B*T sample-steps it processes
-            per = survey_bytes_per_sample_step(B, N, 784, learn)
+            per = streaming_bytes_per_sample_step(B, N, 784, learn)
             nbytes = per * B * T
-            definition = ("scope-table per-sample-step bytes (%.1f KB) x B x T sample-steps" % (per / 1e3))
+            definition = ("per-step streaming bytes per sample-step (%.1f KB) x B x T sample-steps" % (per / 1e3))
         else:
             nbytes = own
-            definition = "the kernel's own minimum bytes (the scope table defines only whole steps)"
+            definition = "the kernel's own minimum bytes (the streaming bytes are defined per whole step)"
         achieved = nbytes / avg_s / 1e9
         traffic, traffic_source = recorded_traffic(a, dom)
         return {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk["hbm_gbs"],

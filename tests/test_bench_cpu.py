@@ -62,13 +62,14 @@ def test_the_committed_summary_records_a_hash_and_traffic():
     assert "source sha256: " in text and "dram bytes per launch: " in text
 
 
-def test_survey_bytes_reproduce_the_scope_tables_figures():
-    """The roofline's per-sample-step bytes against the figures the scope
-    table quotes: 21.0 KB per sample (784->400, learning on), 23.4 KB at
-    B=1024 and 30.8 KB at B=256, 11.5 KB per sample without learning, and
-    about 584 KB at 784->6400, B=256 (195 KB state + 392 KB of W)."""
+def test_streaming_bytes_reproduce_the_stated_figures():
+    """The roofline's per-sample-step bytes against the figures the
+    measurement definition states: 21.0 KB per sample (784->400, learning on),
+    23.4 KB at B=1024 and 30.8 KB at B=256, 11.5 KB per sample without
+    learning, and about 584 KB at 784->6400, B=256 (195 KB of state and
+    392 KB of W)."""
     import bench
-    f = bench.survey_bytes_per_sample_step
+    f = bench.streaming_bytes_per_sample_step
     per_on = f(10 ** 12, 400, 784, True)                 # B -> inf: the per-sample part
     assert abs(per_on - 21008) < 1 and round(per_on / 1e3, 1) == 21.0
     assert 23.4e3 < f(1024, 400, 784, True) < 23.5e3

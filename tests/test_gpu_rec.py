@@ -355,7 +355,7 @@ def test_rec_tensor_form_raster_agreement_at_full_size():
     agree = float((rg == rt).mean())
     assert agree >= 0.999, agree
     # samples whose whole raster agrees: their voltages and readouts differ by the
-    # drive's rounding only (the benchmark spec's 1e-4 relative voltage tolerance)
+    # drive's rounding only (within the stated 1e-4 relative voltage tolerance)
     same = (rg == rt).reshape(T, B, -1).all(axis=(0, 2))
     assert same.any(), "no sample agrees over the whole run"
     rel = np.abs(vt[same] - vg[same]) / np.maximum(1.0, np.abs(vg[same]))
