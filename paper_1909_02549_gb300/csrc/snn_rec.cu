@@ -323,77 +323,104 @@ __device__ __forceinline__ void dense_encode_group(const RecConsts& c, const Rec
     store_operand_word(c, d, b, live, word, (int)(tt & 1ull), a0, nu);
 }
 
-// dense form, epilogue of 32 consecutive samples (lanes, live when b < B) x 32
-// neurons j0.. (j0 < N): the synapse and membrane update from the accumulated
-// drive r[u] of neuron j0 + u, the spike words, the next step's operand and
-// the optional raster.  State accesses are one 128-byte line per warp.
-__device__ __forceinline__ void dense_epilogue_chunk(const RecConsts& c, const RecBufs& d, const uint32_t (&r)[32],
-                                                     int b, bool live, int j0, int cur, int nxt, int t_local) {
-    const int nu = min(32, c.N - j0);
-    uint32_t word = 0u;
-    if (live) {
-        const size_t q0 = sidx(b, j0, c.N);
-        if (nu == 32) {
-            // every load of the chunk in flight at once: one DRAM round trip
-            float I[32], v[32];
-            uint32_t cn[32];
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                I[u] = d.i_syn[q0 + 32 * u];
-                v[u] = d.v[q0 + 32 * u];
-                cn[u] = d.counts[q0 + 32 * u];
-            }
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                float x = __fmul_rn(c.a_syn, I[u]);
-                x = __fadd_rn(x, __uint_as_float(r[u]));
-                I[u] = x;
-                float y = __fmul_rn(c.a_mem, v[u]);
-                y = __fadd_rn(y, x);
-                const bool spk = y >= c.v_thresh;
-                v[u] = spk ? c.v_reset : y;
-                word |= (spk ? 1u : 0u) << u;
-            }
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                d.i_syn[q0 + 32 * u] = I[u];
-                d.v[q0 + 32 * u] = v[u];
-                d.counts[q0 + 32 * u] = cn[u] + ((word >> u) & 1u);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 32; ++u) {
-                if (u >= nu) continue;
-                const size_t q = q0 + 32 * u;
-                float x = __fmul_rn(c.a_syn, d.i_syn[q]);
-                x = __fadd_rn(x, __uint_as_float(r[u]));
-                d.i_syn[q] = x;
-                float y = __fmul_rn(c.a_mem, d.v[q]);
-                y = __fadd_rn(y, x);
-                const bool spk = y >= c.v_thresh;
-                d.v[q] = spk ? c.v_reset : y;
-                if (spk) d.counts[q] += 1u;
-                word |= (spk ? 1u : 0u) << u;
-            }
-        }
-        d.sh[((size_t)cur * c.B + b) * c.Nw + (j0 >> 5)] = word;
-        if (c.rec_raster) {
-            uint8_t* rp = d.raster_h + ((size_t)t_local * c.B + b) * c.N + j0;
-            for (int u = 0; u < nu; ++u) rp[u] = (uint8_t)((word >> u) & 1u);
-        }
-    }
-    store_operand_word(c, d, b, live, word, nxt, c.n_in + j0, nu);
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
                  "tcgen05.wait::ld.sync.aligned;"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                   "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                   "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr) : "memory");
+}
+
+// Dense form, epilogue of one warp's half tile (32 samples x 128 neurons j0..,
+// all < N) as a 2-deep pipeline over 16-neuron steps: the state loads of step
+// k+1 are in flight while step k is computed and stored, so the loads of
+// consecutive steps leave no gap.  (A third slot would not fit the 168
+// registers a thread has at this block size.)  The warp's accumulator is
+// released (acce) after its last tensor-memory load.  Each pipeline slot is a
+// template argument, so every register index is a compile-time constant.
+constexpr int EPD = 2, EPH = 8;   // pipeline depth, 16-neuron steps per half tile
+struct EpiSlot {
+    float I[16], V[16];
+    uint32_t CN[16];
+};
+
+__device__ __forceinline__ void epi_load(const RecConsts& c, const RecBufs& d, EpiSlot& sl, int b, int j) {
+    const size_t q0 = sidx(b, j, c.N);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        sl.I[u] = d.i_syn[q0 + 32 * u];
+        sl.V[u] = d.v[q0 + 32 * u];
+        sl.CN[u] = d.counts[q0 + 32 * u];
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void epi_step(const RecConsts& c, const RecBufs& d, const EpiSlot& sl, uint32_t tcol,
+                                         int b, bool live, int j0, int cur, int nxt, int t_local,
+                                         uint64_t* acce_bar, uint32_t& word) {
+    const int lane = threadIdx.x & 31;
+    uint32_t r[16];
+    tmem_ld16(tcol + (uint32_t)(16 * K), r);
+    if (K == EPH - 1) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(acce_bar)) : "memory");
+    }
+    uint32_t w16 = 0u;
+    if (live) {
+        const size_t q0 = sidx(b, j0 + 16 * K, c.N);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            float x = __fmul_rn(c.a_syn, sl.I[u]);
+            x = __fadd_rn(x, __uint_as_float(r[u]));
+            float y = __fmul_rn(c.a_mem, sl.V[u]);
+            y = __fadd_rn(y, x);
+            const bool spk = y >= c.v_thresh;
+            d.i_syn[q0 + 32 * u] = x;
+            d.v[q0 + 32 * u] = spk ? c.v_reset : y;
+            d.counts[q0 + 32 * u] = sl.CN[u] + (spk ? 1u : 0u);
+            w16 |= (spk ? 1u : 0u) << u;
+        }
+        if (c.rec_raster) {
+            uint8_t* rp = d.raster_h + ((size_t)t_local * c.B + b) * c.N + j0 + 16 * K;
+            for (int u = 0; u < 16; ++u) rp[u] = (uint8_t)((w16 >> u) & 1u);
+        }
+    }
+    word |= w16 << (16 * (K & 1));
+    if (K & 1) {                                          // a full 32-neuron word
+        const int jw0 = j0 + 16 * (K - 1);
+        if (live) d.sh[((size_t)cur * c.B + b) * c.Nw + (jw0 >> 5)] = word;
+        store_operand_word(c, d, b, live, word, nxt, c.n_in + jw0, 32);
+        word = 0u;
+    }
+}
+
+// one pipeline iteration H: load step H (into slot H % EPD), then compute step H - (EPD - 1)
+template <int H>
+__device__ __forceinline__ void epi_iter(const RecConsts& c, const RecBufs& d, EpiSlot (&sl)[EPD], uint32_t tcol,
+                                         int b, bool live, int j0, int cur, int nxt, int t_local,
+                                         uint64_t* acce_bar, uint32_t& word) {
+    if (H < EPH && live) epi_load(c, d, sl[H % EPD], b, j0 + 16 * H);
+    if (H >= EPD - 1)
+        epi_step<(H >= EPD - 1 ? H - (EPD - 1) : 0)>(c, d, sl[(H >= EPD - 1 ? H - (EPD - 1) : 0) % EPD], tcol, b, live,
+                                                     j0, cur, nxt, t_local, acce_bar, word);
+}
+
+__device__ __forceinline__ void dense_epilogue_half_pipelined(const RecConsts& c, const RecBufs& d, uint32_t tcol,
+                                                              int b, bool live, int j0, int cur, int nxt,
+                                                              int t_local, uint64_t* acce_bar) {
+    static_assert(EPD == 2 && EPH == 8, "the iterations below are written out for these sizes");
+    EpiSlot sl[EPD];
+    uint32_t word = 0u;
+    epi_iter<0>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<1>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<2>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<3>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<4>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<5>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<6>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<7>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
+    epi_iter<8>(c, d, sl, tcol, b, live, j0, cur, nxt, t_local, acce_bar, word);
 }
 
 // Dense form, persistent: one CTA per SM walks the 128-sample x 256-neuron
@@ -508,25 +535,61 @@ __global__ void __launch_bounds__(GTHREADS, 1) k_rec_dense(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int b = b0 + lane;
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * GBN);
-            for (int q = 0; q < CH; ++q) {
-                const int col = (half * CH + q) * 32;       // uniform over the warp
-                uint32_t r[32];
-                if (col < ncols) tmem_ld32(tbase + (uint32_t)col, r);
-                if (q == CH - 1) {                          // this warp is done with the accumulator
+            const bool piped = !ro && (half + 1) * CH * 32 <= ncols && (c.n_in & 1) == 0;
+            if (piped)
+                dense_epilogue_half_pipelined(c, d, tbase + (uint32_t)(half * CH * 32), b, b < c.B,
+                                              tn * GBN + half * CH * 32, cur, nxt, t_local, &acce[buf]);
+            // otherwise (a half tile past the layer's end, or the readout tile):
+            // 16-column steps, each neuron guarded
+            uint32_t word = 0u;
+            for (int q = 0; q < (piped ? 0 : 2 * CH); ++q) {
+                const int col = half * CH * 32 + 16 * q;    // uniform over the warp
+                uint32_t r[16];
+                if (col < ncols) tmem_ld16(tbase + (uint32_t)col, r);
+                if (q == 2 * CH - 1) {                      // this warp is done with the accumulator
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(su32(&acce[buf])) : "memory");
                 }
                 if (col >= ncols) continue;
                 if (!ro) {
-                    dense_epilogue_chunk(c, d, r, b, b < c.B, tn * GBN + col, cur, nxt, t_local);
+                    const int j = tn * GBN + col, nu = min(16, c.N - j);
+                    uint32_t w16 = 0u;
+                    if (b < c.B) {
+                        const size_t q0 = sidx(b, j, c.N);
+#pragma unroll 4
+                        for (int u = 0; u < 16; ++u) {
+                            if (u >= nu) break;
+                            const size_t qq = q0 + 32 * u;
+                            float x = __fmul_rn(c.a_syn, d.i_syn[qq]);
+                            x = __fadd_rn(x, __uint_as_float(r[u]));
+                            d.i_syn[qq] = x;
+                            float y = __fmul_rn(c.a_mem, d.v[qq]);
+                            y = __fadd_rn(y, x);
+                            const bool spk = y >= c.v_thresh;
+                            d.v[qq] = spk ? c.v_reset : y;
+                            if (spk) d.counts[qq] += 1u;
+                            w16 |= (spk ? 1u : 0u) << u;
+                        }
+                        if (c.rec_raster) {
+                            uint8_t* rp = d.raster_h + ((size_t)t_local * c.B + b) * c.N + j;
+                            for (int u = 0; u < nu; ++u) rp[u] = (uint8_t)((w16 >> u) & 1u);
+                        }
+                    }
+                    word |= w16 << (16 * (q & 1));
+                    if ((q & 1) || col + 16 >= ncols) {     // the 32-neuron word is complete
+                        const int jw0 = j - 16 * (q & 1), nu32 = min(32, c.N - jw0);
+                        if (b < c.B) d.sh[((size_t)cur * c.B + b) * c.Nw + (jw0 >> 5)] = word;
+                        store_operand_word(c, d, b, b < c.B, word, nxt, c.n_in + jw0, nu32);
+                        word = 0u;
+                    }
                 } else if (t_local > 0 && b < c.B) {
                     // the readout of the previous step: its hidden spikes are this
                     // step's operand (the run's first step skips it: the run before
                     // added it)
                     float* vo = d.v_out + (size_t)b * c.n_out;
 #pragma unroll
-                    for (int u = 0; u < 32; ++u)
+                    for (int u = 0; u < 16; ++u)
                         if (col + u < c.n_out) vo[col + u] = __fadd_rn(vo[col + u], __uint_as_float(r[u]));
                 }
             }
