@@ -40,6 +40,7 @@ constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
+constexpr int LW = 4;                      // input-mask words per round trip when building the lists
 constexpr int QT = 16;                     // neuron items per thread that tensor memory holds
 constexpr int TMEM_COLS = 512;             // all of the SM's tensor memory: 8 warp groups x QT x 4 words
 static_assert(8 * QT * 4 == TMEM_COLS, "tensor-memory columns per warp group");
@@ -206,6 +207,72 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
             running += __shfl_sync(FULL, incl, 31);
         }
         if (lane == 0) d.act_cnt[(size_t)cur * c.B + b] = running;
+    }
+}
+
+// Rows of the step's input-major masks wider than 8 words (B > 256), for the
+// per-input sample lists: out of line, so that their load batches do not add to
+// the kernel's registers on the narrow rows the inline path reads.
+// wide_row_count: the row's spike count (high half) and its nonzero words
+// (first 32; low half), LW words per round trip (16-byte loads when Bw is a
+// multiple of 4).
+__device__ __noinline__ unsigned long long wide_row_count(const uint32_t* row, int Bw) {
+    int n = 0;
+    uint32_t nz = 0u;
+    if ((Bw & 3) == 0) {
+        for (int w0 = 0; w0 < Bw; w0 += LW) {
+            uint4 q[LW / 4];
+#pragma unroll
+            for (int k = 0; k < LW / 4; ++k)
+                q[k] = w0 + 4 * k < Bw ? __ldcg((const uint4*)(row + w0) + k) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int k = 0; k < LW / 4; ++k) {
+                const uint32_t m4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int w = w0 + 4 * k + e;
+                    n += __popc(m4[e]);
+                    if (m4[e] && w < 32) nz |= 1u << w;
+                }
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int w = 0; w < Bw; ++w) {
+            const uint32_t m = __ldcg(&row[w]);
+            n += __popc(m);
+            if (m && w < 32) nz |= 1u << w;
+        }
+    }
+    return ((unsigned long long)(unsigned)n << 32) | nz;   // count, nonzero words
+}
+
+// wide_row_list: the row's samples in ascending order into out, reading only its
+// nonzero words (nz; every word when Bw > 32), LW of them per round trip
+__device__ __noinline__ void wide_row_list(const uint32_t* row, int Bw, uint32_t nz, uint16_t* out) {
+    uint32_t left = Bw <= 32 ? nz : 0xFFFFFFFFu;
+    int wnext = 0, q = 0;
+    while (Bw <= 32 ? left != 0u : wnext < Bw) {
+        int ws[LW];
+        uint32_t ms[LW];
+#pragma unroll
+        for (int k = 0; k < LW; ++k) {
+            ws[k] = -1;
+            if (Bw <= 32) {
+                if (left) { ws[k] = __ffs(left) - 1; left &= left - 1; }
+            } else if (wnext < Bw) {
+                ws[k] = wnext++;
+            }
+            ms[k] = ws[k] >= 0 ? __ldcg(&row[ws[k]]) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < LW; ++k) {
+            uint32_t m = ms[k];
+            while (m) {
+                out[q++] = (uint16_t)(ws[k] * 32 + __ffs(m) - 1);
+                m &= m - 1;
+            }
+        }
     }
 }
 
@@ -687,11 +754,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             }
                         }
                     } else {
-                        for (int w = 0; w < Bw; ++w) {
-                            const uint32_t m = __ldcg(&row[w]);
-                            n += __popc(m);
-                            if (m && w < 32) nz |= 1u << w;
-                        }
+                        const unsigned long long cz = wide_row_count(row, Bw);
+                        n = (int)(cz >> 32);
+                        nz = (uint32_t)cz;
                     }
                     nzP[i] = nz;
                 }
@@ -728,14 +793,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                                 }
                             }
                         } else {
-                            const uint32_t* row = src + (size_t)i * Bw;
-                            for (int w = 0; w < Bw; ++w) {
-                                uint32_t m = __ldcg(&row[w]);
-                                while (m) {
-                                    lst[q++] = (uint16_t)(w * 32 + __ffs(m) - 1);
-                                    m &= m - 1;
-                                }
-                            }
+                            wide_row_list(src + (size_t)i * Bw, Bw, nz, lst + q);
                         }
                     }
                 }
