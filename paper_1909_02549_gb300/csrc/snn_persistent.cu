@@ -355,22 +355,24 @@ __device__ __forceinline__ float deposit(float acc, float e) {
     return RED == RED_MAX ? fmaxf(acc, __fsub_rn(0.0f, e)) : __fsub_rn(acc, e);
 }
 
-template <int RED, bool LISTS>
+template <int RED, bool LISTS, bool NARROW>
 __device__ __noinline__ void depress_quiet_columns(
         const Consts& c, float* Ws, const float* Es, const uint32_t* preS, const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
     const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
     const int h = lane >> 4;
-    for (int g0 = 0; g0 < nc; g0 += 64) {
-        const int j = g0 + 4 * (lane & 15);
+    // NARROW (at most four columns): one row per lane and the one 16-byte column
+    // group, instead of two rows per warp and 16 groups (15 of them idle)
+    for (int g0 = 0; g0 < nc; g0 += NARROW ? 4 : 64) {
+        const int j = NARROW ? g0 : g0 + 4 * (lane & 15);
         const bool v0 = j < nc && nzQ[j] == 0u, v1 = j + 1 < nc && nzQ[j + 1] == 0u;
         const bool v2 = j + 2 < nc && nzQ[j + 2] == 0u, v3 = j + 3 < nc && nzQ[j + 3] == 0u;
         const bool any = v0 || v1 || v2 || v3, all4 = v0 && v1 && v2 && v3;
         if (!__any_sync(FULL, any)) continue;
         const float* E = Es + (j < nst ? j : 0);     // lanes past the tile read a valid row
-        for (int i0 = 2 * warp; i0 < NI; i0 += 2 * NW) {
-            const int i = i0 + h;
+        for (int i0 = (NARROW ? 32 : 2) * warp; i0 < NI; i0 += (NARROW ? 32 : 2) * NW) {
+            const int i = i0 + (NARROW ? lane : h);
             if (i >= NI) continue;
             float a0 = init, a1 = init, a2 = init, a3 = init;
             int n = 0;
@@ -503,6 +505,60 @@ __device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d
     }
 }
 
+// The synaptic currents when the CTA has at most four columns (narrow layers):
+// one sample per lane, its columns in one 16-byte load per active input, the
+// same sums in the same order as synaptic_currents (which would leave 15 of 16
+// lanes idle here).
+__device__ __forceinline__ void synaptic_currents_narrow(const Consts& c, const Bufs& d, const float* Ws,
+                                                      float* Es, const float* wsc, int ncmax,
+                                                      const uint32_t* actN, const uint16_t* actS,
+                                                      int caps, int nc, int nst, int cur) {
+    const int B = c.B, NI = c.n_in;
+    for (int b = threadIdx.x; b < B; b += PT) {
+        const int na = (int)actN[b];
+        const int ns = na < caps ? na : caps;
+        const uint16_t* al = actS + b * CAPS;
+        const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+        float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+        if (c.wprec == SNN_W_FP32) {
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w.x);
+                I1 = __fadd_rn(I1, w.y);
+                I2 = __fadd_rn(I2, w.z);
+                I3 = __fadd_rn(I3, w.w);
+            }
+        } else if (c.wprec == SNN_W_BF16) {
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w_read_bf16(w.x));
+                I1 = __fadd_rn(I1, w_read_bf16(w.y));
+                I2 = __fadd_rn(I2, w_read_bf16(w.z));
+                I3 = __fadd_rn(I3, w_read_bf16(w.w));
+            }
+        } else {
+            const float* inv = wsc + ncmax;
+            const float v0 = inv[0], v1 = 1 < nc ? inv[1] : 1.0f;
+            const float v2 = 2 < nc ? inv[2] : 1.0f, v3 = 3 < nc ? inv[3] : 1.0f;
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
+                I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
+                I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
+                I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
+            }
+            I0 = __fmul_rn(I0, wsc[0]);
+            I1 = __fmul_rn(I1, 1 < nc ? wsc[1] : 1.0f);
+            I2 = __fmul_rn(I2, 2 < nc ? wsc[2] : 1.0f);
+            I3 = __fmul_rn(I3, 3 < nc ? wsc[3] : 1.0f);
+        }
+        *(float4*)(Es + b * nst) = make_float4(I0, I1, I2, I3);
+    }
+}
+
 // The neuron update of the CTA's (sample, column) items: state from tensor
 // memory (or global memory), the current from the e tile, e = nu_pre x_post
 // back into it, spikes into the masks and counters.  Inlined: a call would have
@@ -579,6 +635,10 @@ __device__ __forceinline__ double theta_next(const Consts& c, double th, int n) 
     return __dadd_rn(__dmul_rn(th, c.a_th), __dmul_rn(c.theta_plus, r));
 }
 
+// NARROW: the CTAs own at most four columns each (narrow layers); the currents
+// and the quiet-column pass then map a lane to a sample or a row.  Two
+// instantiations, so that wide layers run code without the narrow paths.
+template <bool NARROW>
 __global__ void __launch_bounds__(PT, 1)
 k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, const int T,
              const __grid_constant__ Layout L) {
@@ -817,7 +877,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
-        synaptic_currents(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
+        if (NARROW) synaptic_currents_narrow(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
+        else synaptic_currents(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
         __syncthreads();
 
         neuron_items(c, d, Es, Qm, Sm, cntS, thj, tq, tstate, QN, BN, nc, nst, j0, dq, dr, t, p3);
@@ -877,14 +938,16 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     if (nzQ[jl] == 0u) Ws[i * nst + jl] = fminf(fmaxf(Ws[i * nst + jl], c.w_min), c.w_max);
                 }
             } else {
-#define SNN_PASS_A(R)                                                                              \
-    (lists ? depress_quiet_columns<R, true>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
-           : depress_quiet_columns<R, false>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+#define SNN_PASS_A_N(R, NR)                                                                        \
+    (lists ? depress_quiet_columns<R, true, NR>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
+           : depress_quiet_columns<R, false, NR>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+#define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)
                 if (c.reduce == SNN_REDUCE_MAX) SNN_PASS_A(RED_MAX);
                 else if (c.reduce == SNN_REDUCE_SUM) SNN_PASS_A(RED_SUM);
                 else if (c.B_pow2) SNN_PASS_A(RED_MEAN_MUL);
                 else SNN_PASS_A(RED_MEAN_DIV);
 #undef SNN_PASS_A
+#undef SNN_PASS_A_N
             }
 
             // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.
@@ -1065,7 +1128,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     }
     // Device properties and the kernel's shared-memory opt-in are looked up
     // once per device and layout size, not on every run.
-    struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes = 0; };
+    struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes = 0, attr_narrow = 0; };
     static Setup setup[64];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1082,15 +1145,17 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     const size_t budget = su.smem_optin > 2048 ? (size_t)su.smem_optin - 2048 : 0;
     const Layout L = make_layout(c, G, budget);
     if (L.bytes > budget) return cudaSuccess;
-    if (su.attr_bytes < L.bytes) {
-        e = cudaFuncSetAttribute(k_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)L.bytes);
+    const bool narrow = L.ncmax <= 4;
+    const void* kern = narrow ? (const void*)k_persistent<true> : (const void*)k_persistent<false>;
+    size_t& attr = narrow ? su.attr_narrow : su.attr_bytes;
+    if (attr < L.bytes) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent, PT, L.bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PT, L.bytes);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaSuccess;
-        su.attr_bytes = L.bytes;
+        attr = L.bytes;
     }
     Consts cc = c;
     Bufs dd = d;
@@ -1099,7 +1164,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     void* args[] = {&cc, &dd, &TT, &LL};
     e = prof_start(prof, SNN_KERNEL_PERSISTENT, s);
     if (e != cudaSuccess) return e;
-    e = cudaLaunchCooperativeKernel((const void*)k_persistent, dim3(G), dim3(PT), args, L.bytes, s);
+    e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(PT), args, L.bytes, s);
     if (e != cudaSuccess) return e;
     e = prof_stop(prof, s);
     if (e != cudaSuccess) return e;

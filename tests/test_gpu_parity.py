@@ -162,10 +162,12 @@ def test_784x400_batch16_learning(reduce):
 
 
 @pytest.mark.parametrize("B,N", [(37, 100), (33, 70), (1, 1), (5, 31), (64, 32), (40, 500),
-                                 (384, 40), (1100, 20)])
+                                 (24, 1000), (384, 40), (1100, 20)])
 def test_ragged_shapes_learning(B, N):
     """Batches and layers that are not multiples of 32 (ragged warps and words),
-    and layers narrower or wider than one column per SM.  384 and 1100 samples
+    and layers narrower or wider than one column per SM (up to four columns per
+    SM the persistent form maps a lane to a sample or a row; 1000 neurons give
+    six or seven, the wide mapping with idle lanes).  384 and 1100 samples
     take the persistent form's wide-batch list building (rows of 12 and 35
     mask words: 16-byte loads, and more words than a 32-bit word mask holds)."""
     p, r, s, w = synth.workload(B, N)
