@@ -40,7 +40,8 @@ constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
-constexpr int LW = 4;                      // input-mask words per round trip when building the lists
+constexpr int LW = 16;                     // input-mask words per round trip, counting a list's row
+constexpr int LWL = 8;                     // nonzero words per round trip, writing a list
 constexpr int QT = 16;                     // neuron items per thread that tensor memory holds
 constexpr int TMEM_COLS = 512;             // all of the SM's tensor memory: 8 warp groups x QT x 4 words
 static_assert(8 * QT * 4 == TMEM_COLS, "tensor-memory columns per warp group");
@@ -248,15 +249,15 @@ __device__ __noinline__ unsigned long long wide_row_count(const uint32_t* row, i
 }
 
 // wide_row_list: the row's samples in ascending order into out, reading only its
-// nonzero words (nz; every word when Bw > 32), LW of them per round trip
+// nonzero words (nz; every word when Bw > 32), LWL of them per round trip
 __device__ __noinline__ void wide_row_list(const uint32_t* row, int Bw, uint32_t nz, uint16_t* out) {
     uint32_t left = Bw <= 32 ? nz : 0xFFFFFFFFu;
     int wnext = 0, q = 0;
     while (Bw <= 32 ? left != 0u : wnext < Bw) {
-        int ws[LW];
-        uint32_t ms[LW];
+        int ws[LWL];
+        uint32_t ms[LWL];
 #pragma unroll
-        for (int k = 0; k < LW; ++k) {
+        for (int k = 0; k < LWL; ++k) {
             ws[k] = -1;
             if (Bw <= 32) {
                 if (left) { ws[k] = __ffs(left) - 1; left &= left - 1; }
@@ -266,7 +267,7 @@ __device__ __noinline__ void wide_row_list(const uint32_t* row, int Bw, uint32_t
             ms[k] = ws[k] >= 0 ? __ldcg(&row[ws[k]]) : 0u;
         }
 #pragma unroll
-        for (int k = 0; k < LW; ++k) {
+        for (int k = 0; k < LWL; ++k) {
             uint32_t m = ms[k];
             while (m) {
                 out[q++] = (uint16_t)(ws[k] * 32 + __ffs(m) - 1);
