@@ -447,6 +447,27 @@ def serving_leg(a, torch, snn, synth):
 
 # ------------------------------------------------------------ our arm ---
 
+def replica_seeds(seeds: np.ndarray, rank: int) -> np.ndarray:
+    """Per-sample seeds of replica `rank`: distinct Poisson draws on every rank."""
+    return seeds + np.uint64(100000 * rank)
+
+
+def max_over_ranks(ms: float, world: int, dist, device) -> float:
+    """The slowest rank's time (max all-reduce); the time itself at one rank."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(world: int, B: int, T: int, steps: int, ms: float) -> float:
+    """Whole-job sample-timesteps/s: every rank's B*T*steps over the slowest
+    rank's time."""
+    return world * B * T * steps / (ms * 1e-3)
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -468,7 +489,7 @@ def run_ours(a):
 
     B, N, T, learn = a.batch, a.n_exc, a.T, not a.no_learn
     p, rates, seeds, w = bench_workload(a, B)
-    seeds = seeds + np.uint64(100000 * rank)     # replicas draw independent spikes
+    seeds = replica_seeds(seeds, rank)            # replicas draw independent spikes
     net = snn.Network(p, w_init=w, wprec=WPREC[a.wprec])
     r_d = torch.from_numpy(rates).cuda()
     s_d = torch.from_numpy(seeds.view(np.int64)).cuda()
@@ -510,12 +531,8 @@ def run_ours(a):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B * T * a.steps / (ms * 1e-3)
+    ms = max_over_ranks(sum(e0.elapsed_time(e1) for e0, e1 in ev), world, dist, "cuda")
+    value = replicas_value(world, B, T, a.steps, ms)
 
     # ---- per-kernel device time (same workload, every launch bracketed by events)
     roofline = profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn)

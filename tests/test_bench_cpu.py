@@ -78,3 +78,43 @@ def test_streaming_bytes_reproduce_the_stated_figures():
     big = f(256, 6400, 784, True)
     assert abs(big - (29 * 6400 + 12 * 784) - 20 * 784 * 6400 / 256) < 1e-6
     assert 580e3 < big < 590e3
+
+
+def _replica_rank(rank, world, port, out):
+    import os
+    import numpy as np
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 100.0 + 50.0 * rank                       # rank 1 is the slowest
+    slowest = bench.max_over_ranks(ms, world, dist, "cpu")
+    seeds = bench.replica_seeds(np.arange(4, dtype=np.uint64), rank)
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, slowest, bench.replicas_value(world, 256, 250, 10, slowest), seeds.tolist()))
+
+
+def test_replicas_aggregate_over_two_gloo_ranks():
+    """The multi-GPU bench path on the CPU: two gloo ranks agree on the slowest
+    rank's time, the value counts both ranks' work over it, and each rank draws
+    with its own seeds."""
+    import socket
+    import torch.multiprocessing as mp
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_replica_rank, args=(r, 2, port, q)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    (r0, s0, v0, seeds0), (r1, s1, v1, seeds1) = res
+    assert (r0, r1) == (0, 1) and s0 == s1 == 150.0
+    assert v0 == v1 == 2 * 256 * 250 * 10 / 0.150
+    assert seeds0 != seeds1 and [b - a for a, b in zip(seeds0, seeds1)] == [100000] * 4
