@@ -429,3 +429,28 @@ def test_784x6400_batch256_learning_first_steps():
     for mode in ("persistent", "graph"):
         _, g = gpu_run(p, r, s, w, 12, mode=mode)
         assert_parity(g, st, rec)
+
+
+def test_784x400_batch1024_learning_off_sampled():
+    """The 784 -> 400 sweep's largest batch (B = 1024) in the persistent form:
+    the narrow-layer instantiation and the wide-batch input lists.  Sampled
+    samples against the oracle's single-sample runs (learning off, T = 250)."""
+    p, r, s, w = synth.workload(1024, 400)
+    _, g = gpu_run(p, r, s, w, 250, learn=False, mode="persistent")
+    for b in (0, 517, 1023):
+        st, rec = oracle_run(p, r[b:b + 1], s[b:b + 1], w, 250, learn=False)
+        assert np.array_equal(g["raster_e"][:, b:b + 1], rec.raster_e), b
+        assert np.array_equal(bits(g["v_e"][b:b + 1]), bits(st.v_e)), b
+        assert np.array_equal(bits(g["x_post"][b:b + 1]), bits(st.x_post)), b
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum"])
+def test_784x400_batch1024_learning_first_steps(reduce):
+    """Learning on at B = 1024 for the first 10 steps against the whole-batch
+    oracle: the batch reduction over 1024 samples, in both reductions the
+    sweep measures."""
+    p, r, s, w = synth.workload(1024, 400)
+    st, rec = oracle_run(p, r, s, w, 10, reduce=reduce)
+    assert rec.raster_e.sum() > 0 and not np.array_equal(st.w, w)
+    _, g = gpu_run(p, r, s, w, 10, reduce=reduce, mode="persistent")
+    assert_parity(g, st, rec)

@@ -362,3 +362,23 @@ def test_rec_tensor_form_raster_agreement_at_full_size():
     assert rel.max() < 1e-4, float(rel.max())
     relo = np.abs(ot[same] - og[same]) / np.maximum(1.0, np.abs(og[same]))
     assert relo.max() < 1e-4, float(relo.max())
+
+
+@pytest.mark.parametrize("form", ["gather", "tensor"])
+def test_rec_bench_batch_on_samples_the_oracle_runs_alone(form):
+    """The benchmark's launch configuration, B = 4096 at 1024 -> 4096 -> 10,
+    for 40 steps; samples 0 and 4095 against oracle runs of that sample alone
+    (the tensor form on the dyadic rounding of the same weights)."""
+    B, T = 4096, 40
+    make = synth.rec_workload if form == "gather" else synth.rec_workload_dyadic
+    p, r, s, wf, wr, wo = make(B)
+    net = snn().RecNetwork(p, wf, wr, wo)
+    net.run(dev(r), dev(s), T, record=True, form=form)
+    raster, v, v_out = net.read("raster"), net.read("v"), net.read("v_out")
+    for b in (0, 4095):
+        st, rh, _ = oracle_run(p, r[b:b + 1], s[b:b + 1], wf, wr, wo, T)
+        assert rh.sum() > 0
+        assert np.array_equal(raster[:, b], rh[:, 0]), b
+        assert np.array_equal(bits(v[b]), bits(st.v[0])), b
+        assert np.array_equal(bits(v_out[b]), bits(st.v_out[0])), b
+    net.close()
