@@ -24,13 +24,17 @@
 //   dense   the drive of every (sample, neuron) as one tcgen05 GEMM per step,
 //           X[B][N] = S[B][K] * Wt[N][K]^T with S = (input spikes | previous
 //           hidden spikes) as bfloat16 0/1 and Wt = (W_ff ; W_rec) transposed,
-//           K = n_in + n_hid: TMA loads of 128x64 and 256x64 bfloat16 tiles
-//           (128-byte swizzle) through a 4-stage mbarrier pipeline, one thread
-//           issuing the MMAs into a 128x256 FP32 accumulator in tensor memory,
-//           and the synapse and neuron update fused into the epilogue, which
-//           also writes the next step's spike operand.  The tensor cores sum
-//           in their own order, so this form agrees with the oracle to FP32
-//           rounding of the drive, not bit for bit.
+//           K = n_in + n_hid: a persistent kernel streams 128x64 and 256x64
+//           bfloat16 tiles with TMA (128-byte swizzle) through a 4-stage
+//           mbarrier pipeline, one thread issues the MMAs into two 128x256
+//           FP32 accumulators in tensor memory, and eight epilogue warps apply
+//           the synapse and neuron update, write the next step's spike operand
+//           and draw the next step's inputs.  W_out rides along as a 16-wide
+//           extra tile, so each product also yields the previous step's
+//           readout (the run's last step has its own readout launch).  The
+//           tensor cores sum in their own order, so this form agrees with the
+//           oracle to FP32 rounding of the drive, and bit for bit whenever
+//           every partial sum is exact (e.g. weights on a 2^-10 grid).
 // Both forms keep the hidden spikes as words (readout, counts) and as the
 // bfloat16 operand, so a network may change form between runs; the readout
 // (warp = sample) is shared.  v, I and the counts are stored sample-interleaved,

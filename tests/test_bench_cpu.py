@@ -1,9 +1,8 @@
 """Host logic of bench.py that needs no GPU: the DRAM traffic it reports next
-to the roofline comes from an ncu summary only while the kernel sources are
-the ones that summary was taken on, and only for that workload.  The tests
-write their own summary and sources, so they do not depend on whether the
-committed capture is current."""
-import hashlib
+to the roofline comes from an ncu summary only while the kernel code is the
+code that summary was taken on (comments aside), and only for that workload.
+The tests write their own summary and sources, so they do not depend on
+whether the committed capture is current."""
 import os
 import sys
 
@@ -29,9 +28,9 @@ def capture(tmp_path, monkeypatch, nbytes=12345678):
     src = [tmp_path / "kernel.cu", tmp_path / "kernel.cuh"]
     src[0].write_bytes(b"__global__ void k() {}\n")
     src[1].write_bytes(b"// header\n")
-    h = hashlib.sha256(src[0].read_bytes() + src[1].read_bytes()).hexdigest()
+    h = bench.code_digest(tuple(str(p) for p in src))
     prof = tmp_path / "summary.md"
-    prof.write_text("source sha256: %s\ndram bytes per launch: %d\n" % (h, nbytes))
+    prof.write_text("code sha256: %s\ndram bytes per launch: %d\n" % (h, nbytes))
     monkeypatch.setattr(bench, "KERNEL_SOURCES", tuple(str(p) for p in src))
     monkeypatch.setattr(bench, "PERSISTENT_PROFILE", str(prof))
     return src
@@ -52,14 +51,21 @@ def test_traffic_is_null_for_another_workload_or_kernel(tmp_path, monkeypatch):
 
 def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
     src = capture(tmp_path, monkeypatch)
-    src[0].write_bytes(src[0].read_bytes() + b"// edited\n")
+    src[0].write_bytes(src[0].read_bytes() + b"__device__ int x;\n")
     nbytes, why = bench.recorded_traffic(args(), "persistent")
     assert nbytes is None and "changed" in why
 
 
+def test_traffic_survives_an_edit_of_comments_only(tmp_path, monkeypatch):
+    src = capture(tmp_path, monkeypatch)
+    src[0].write_bytes(b"// what k does\n__global__ void   k() { /* nothing */ }\n")
+    src[1].write_bytes(b"// another header comment\n")
+    assert bench.recorded_traffic(args(), "persistent")[0] == 12345678
+
+
 def test_the_committed_summary_records_a_hash_and_traffic():
     text = open(os.path.join(ROOT, bench.PERSISTENT_PROFILE)).read()
-    assert "source sha256: " in text and "dram bytes per launch: " in text
+    assert "code sha256: " in text and "dram bytes per launch: " in text
 
 
 def test_streaming_bytes_reproduce_the_stated_figures():
