@@ -423,13 +423,15 @@ enum {
     SNN_REC_KERNEL_COUNT = 3
 };
 /* Device time of the last run made with SNN_PROFILE (every step's launches
- * bracketed by CUDA events), per kernel class: ms[k] summed milliseconds,
+ * bracketed by CUDA events: up to 6*T events, created once and kept by the
+ * network), per kernel class: ms[k] summed milliseconds,
  * launches[k] launches, k < count <= SNN_REC_KERNEL_COUNT.  Synchronises.
  * Errors: SNN_ERR_ARG, SNN_ERR_STATE (last run not profiled), SNN_ERR_CUDA. */
 SNN_API snn_status snn_rec_profile(snn_rec* net, double* ms, int* launches, int count);
 /* One-line reason for the last error of net (NULL: of the last failed create).
  * snn_rec_read reports, as SNN_ERR_TIMEOUT, a tensor-form step whose pipeline
- * wait gave up after 2 s (that run's results are undefined). */
+ * wait gave up after 2 s (that run's results are undefined), until the next
+ * run starts. */
 SNN_API const char* snn_rec_last_error(const snn_rec* net);
 
 #ifdef __cplusplus

@@ -1060,6 +1060,8 @@ snn_status snn_rec_run(snn_rec* r, const float* rates, const uint64_t* seeds, in
         if (!start) ++r->prof_n;
     };
     RecBufs d = r->d;
+    // a timed-out tensor step of an earlier run is reported until this run starts
+    REC_TRY(r, cudaMemsetAsync(r->dev_err, 0, sizeof(uint32_t), st));
     k_rec_begin<<<296, 256, 0, st>>>(c, d, rdev, sdev, cont ? 0 : 1, T);
     REC_TRY(r, cudaGetLastError());
     const size_t enc_warps = (size_t)B * c.Iw, hid_warps = (size_t)B * c.Nw;
