@@ -667,7 +667,9 @@ def rec_leg(a):
 
     crossover = net.tune(rd, sd, 20)                             # measured dense-vs-gather switch
     timed("tensor", max(1, a.warmup))                            # warm-up, allocation
-    ms = timed("tensor", steps)
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    with ClockSampler(visible.split(",")[0] if visible else "0") as clk:
+        ms = timed("tensor", steps)
     density = float(net.read("counts").astype(np.float64).mean() / T)
     flush.zero_()
     net.run(rd, sd, T, form="tensor", profile=True)              # per-kernel device times
@@ -711,7 +713,8 @@ def rec_leg(a):
                 "note": "exact form: FP32 sums in input order, bit-exact with the oracle"},
             "hidden_firing_fraction": density, "hidden_firing_fraction_gather": density_gather,
             "tuned_crossover_density": crossover,
-            "automatic_form": "tensor" if density * p["n_hid"] >= crossover * K else "gather"}
+            "automatic_form": "tensor" if density * p["n_hid"] >= crossover * K else "gather",
+            "clocks": clk.summary()}
     if not a.no_cpu_baseline:
         import oracle
         oracle.build()

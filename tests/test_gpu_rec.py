@@ -382,3 +382,26 @@ def test_rec_bench_batch_on_samples_the_oracle_runs_alone(form):
         assert np.array_equal(bits(v[b]), bits(st.v[0])), b
         assert np.array_equal(bits(v_out[b]), bits(st.v_out[0])), b
     net.close()
+
+
+@pytest.mark.parametrize("B,NI,N", [(3072, 64, 1700), (3072, 64, 1300)])
+def test_rec_tensor_form_several_tiles_per_cta_on_samples_the_oracle_runs_alone(B, NI, N):
+    """Batches large enough that the CTAs walk more than one tile (24 sample
+    tiles x 8 or 7 tiles of 256 neurons and the readout: 192 and 168 tiles on
+    152 SMs), with a ragged last neuron tile (164 and 20 columns) that leaves
+    the epilogue's second column half partly or wholly empty.  Dyadic weights:
+    samples from the first, a middle and the last sample tile against oracle
+    runs of that sample alone, raster, v, I, readout and counts bit for bit."""
+    T = 20
+    p, r, s, wf, wr, wo = dyadic_workload(B, NI, N, 10, seed=N)
+    net = snn().RecNetwork(p, wf, wr, wo)
+    net.run(dev(r), dev(s), T, record=True, form="tensor")
+    raster = net.read("raster")
+    got = {name: net.read(name) for name in ("v", "i_syn", "v_out", "counts")}
+    net.close()
+    for b in (5, 2600, B - 1):
+        st, rh, _ = oracle_run(p, r[b:b + 1], s[b:b + 1], wf, wr, wo, T)
+        assert rh.sum() > 0
+        assert np.array_equal(raster[:, b], rh[:, 0]), b
+        for name, ref in (("v", st.v), ("i_syn", st.i_syn), ("v_out", st.v_out), ("counts", st.counts)):
+            assert np.array_equal(bits(got[name][b]), bits(ref[0])), (b, name)
