@@ -40,6 +40,7 @@ constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
+constexpr int PG = 4;                      // post columns that share a walk over their samples
 constexpr int LW = 16;                     // input-mask words per round trip, counting a list's row
 constexpr int LWL = 8;                     // nonzero words per round trip, writing a list
 constexpr int QT = 16;                     // neuron items per thread that tensor memory holds
@@ -439,6 +440,93 @@ __device__ __noinline__ void depress_quiet_columns(
                 if (v2) wr[2] = u.z;
                 if (v3) wr[3] = u.w;
             }
+        }
+    }
+}
+
+// Pass B for the sum and mean reductions with per-input sample lists: task =
+// (PG post columns, 32 rows), lanes = rows.  The union of the columns' post
+// samples is walked once in ascending b, XC at a time with their x_pre loads
+// issued together, so each x_pre value is loaded once for the PG columns, and
+// each column adds only its own samples (its potentiation sum keeps ascending
+// b).  The depression walks the lane's input list once for the PG columns (e
+// is 0 where a column has not fired).  Wide layers only: with at most four
+// columns a CTA has too few groups to keep its warps busy.
+__device__ __forceinline__ void update_post_column_groups(
+        const Consts& c, float* Ws, const float* Es, const uint32_t* Qm, const int* pcol, const int* offs,
+        const uint16_t* lst, const float* xpre, int npc, int NI, int nc, int nst, int Bw, bool dep_on,
+        int warp, int lane) {
+    const int nch = (NI + 31) / 32, ngr = (npc + PG - 1) / PG;
+    for (int u = warp; u < ngr * nch; u += NW) {
+        const int k0 = (u / nch) * PG, kn = min(PG, npc - k0);
+        const int i = (u % nch) * 32 + lane;
+        const bool vi = i < NI;
+        int jls[PG];
+        float pot[PG], dep[PG];
+#pragma unroll
+        for (int k = 0; k < PG; ++k) {
+            jls[k] = pcol[k0 + (k < kn ? k : 0)];   // padding repeats a live column
+            pot[k] = 0.0f;
+            dep[k] = 0.0f;
+        }
+        int w = 0;
+        uint32_t un = 0u;
+#pragma unroll
+        for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[jls[k]] : 0u;
+        for (;;) {
+            int bs[XC];
+            int n = 0;
+#pragma unroll
+            for (int z = 0; z < XC; ++z) {
+                while (un == 0u && w + 1 < Bw) {
+                    ++w;
+#pragma unroll
+                    for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[w * nc + jls[k]] : 0u;
+                }
+                bs[z] = -1;
+                if (un) {
+                    const int bit = __ffs(un) - 1;
+                    un &= un - 1;
+                    bs[z] = w * 32 + bit;
+                    n = z + 1;
+                }
+            }
+            if (n == 0) break;
+            float xv[XC];
+#pragma unroll
+            for (int z = 0; z < XC; ++z)
+                xv[z] = (bs[z] >= 0 && vi) ? __ldcg(&xpre[(size_t)bs[z] * NI + i]) : 0.0f;
+#pragma unroll
+            for (int z = 0; z < XC; ++z) {
+                if (bs[z] < 0) continue;
+                const float a = __fmul_rn(c.nu_post, xv[z]);
+                const uint32_t* qw = Qm + (bs[z] >> 5) * nc;
+                const int bit = bs[z] & 31;
+#pragma unroll
+                for (int k = 0; k < PG; ++k)
+                    if ((qw[jls[k]] >> bit) & 1u) pot[k] = __fadd_rn(pot[k], a);
+            }
+            if (n < XC) break;
+        }
+        if (!vi) continue;
+        if (dep_on) {   // every input-spike sample (e is 0 where j has not fired)
+            const int e1 = offs[i + 1];
+            for (int e = offs[i]; e < e1; ++e) {
+                const float* er = Es + (int)lst[e] * nst;
+#pragma unroll
+                for (int k = 0; k < PG; ++k) dep[k] = __fadd_rn(dep[k], er[jls[k]]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PG; ++k) {
+            if (k >= kn) break;
+            float D = __fsub_rn(pot[k], dep[k]);
+            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
+            float* wp = Ws + i * nst + jls[k];
+            float wv = __fadd_rn(*wp, D);
+            wv = wv < c.w_min ? c.w_min : wv;
+            wv = wv > c.w_max ? c.w_max : wv;
+            *wp = wv;
         }
     }
 }
@@ -951,17 +1039,23 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
 #undef SNN_PASS_A_N
             }
 
-            // (B) columns with a post spike: task = (column, 32 rows), lanes = rows.
-            //     Potentiation runs over the column's post-spiking samples, the
-            //     same for every lane, XC at a time with their x_pre loads issued
-            //     together; depression over the lane's own (input spike and
-            //     neuron-has-fired) samples.  Both in ascending b.
+            // (B) columns with a post spike, lanes = rows, every sum in ascending b.
             {
                 const int npc = s_nq;
                 const int nch = (NI + 31) / 32;
                 const int ntask = npc * nch;
                 const bool dep_on = c.rule != SNN_RULE_POST_NORM;   // that rule only potentiates
-                for (int u = warp; u < ntask; u += NW) {
+                // Sum and mean with input lists, wide layers: groups of PG post columns
+                const bool grouped = !NARROW && lists && c.reduce != SNN_REDUCE_MAX;
+                if constexpr (!NARROW)
+                    if (grouped)
+                        update_post_column_groups(c, Ws, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw,
+                                                  dep_on, warp, lane);
+                // Otherwise task = (column, 32 rows): potentiation over the column's
+                // post-spiking samples, the same for every lane, XC at a time with
+                // their x_pre loads issued together; depression over the lane's own
+                // (input spike and neuron-has-fired) samples.
+                for (int u = warp; u < (grouped ? 0 : ntask); u += NW) {
                     const int jl = pcol[u / nch];
                     const int i = (u % nch) * 32 + lane;
                     const bool vi = i < NI;

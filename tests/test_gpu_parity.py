@@ -174,6 +174,17 @@ def test_ragged_shapes_learning(B, N):
     parity_all_modes(p, r, s, w, 80, reduce="sum")
 
 
+def test_wide_layer_mean_learning():
+    """A wide layer (1500 neurons: ten columns per SM) with the mean reduction,
+    80 steps in every run mode: in the persistent form the columns with a post
+    spike take their STDP update in groups of four (one walk over the group's
+    post samples, groups padded where the column count is not a multiple of
+    four), in bursts where dozens of columns fire in one step."""
+    p, r, s, w = synth.workload(32, 1500)
+    _, rec = parity_all_modes(p, r, s, w, 80, reduce="mean")
+    assert rec.raster_e.sum() > 1000
+
+
 def test_small_input_layer_and_saturated_rates():
     """n_in = 40 (two words, ragged); some rates >= 1000 Hz (always spike), so
     samples carry more active inputs than the persistent form stages."""
