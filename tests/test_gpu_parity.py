@@ -174,14 +174,16 @@ def test_ragged_shapes_learning(B, N):
     parity_all_modes(p, r, s, w, 80, reduce="sum")
 
 
-def test_wide_layer_mean_learning():
-    """A wide layer (1500 neurons: ten columns per SM) with the mean reduction,
-    80 steps in every run mode: in the persistent form the columns with a post
-    spike take their STDP update in groups of four (one walk over the group's
-    post samples, groups padded where the column count is not a multiple of
-    four), in bursts where dozens of columns fire in one step."""
+@pytest.mark.parametrize("reduce", ["mean", "max"])
+def test_wide_layer_learning(reduce):
+    """A wide layer (1500 neurons: ten columns per SM), 80 steps in every run
+    mode: in the persistent form the columns with a post spike take their STDP
+    update in groups of four (one walk over the group's post samples, groups
+    padded where the column count is not a multiple of four), in bursts where
+    dozens of columns fire in one step; the max reduction's running maximum
+    per synapse as well as the mean's sums."""
     p, r, s, w = synth.workload(32, 1500)
-    _, rec = parity_all_modes(p, r, s, w, 80, reduce="mean")
+    _, rec = parity_all_modes(p, r, s, w, 80, reduce=reduce)
     assert rec.raster_e.sum() > 1000
 
 
