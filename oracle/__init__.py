@@ -64,9 +64,12 @@ _lib = None
 
 
 def lib():
+    """The oracle library: the in-tree build, or the file that the environment
+    variable SNN_ORACLE_LIB names (the mutation test loads planted-bug builds
+    of the same sources that way)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(os.environ.get("SNN_ORACLE_LIB") or build())
         for name in ("oracle_run_f32", "oracle_run_f64"):
             fn = getattr(_lib, name)
             fn.restype = C.c_int

@@ -607,6 +607,25 @@ def test_episodic_reset_restores_initial_state():
     assert np.array_equal(r1.raster_e, r2.raster_e) and np.array_equal(r1.raster_in, r2.raster_in)
 
 
+def test_episodic_reset_with_learning_equals_a_fresh_state():
+    """Sec. "Episodic vs. continuing simulation": after a learning run, an
+    episodic run starts every per-sample variable (voltages, refractory
+    counters, previous spikes and both traces) from its initial value while W
+    and theta carry over.  The reference is a state built from the initial
+    values (R10) with the carried W and theta, run without the reset: every
+    array must agree bit for bit after 60 more learning steps."""
+    p, r, s, w = synth.workload(3, 100)
+    st = oracle.new_state(p, 3, w)
+    oracle.run(p, st, r, s, 90, learn=True)
+    assert st.x_post.any() and st.x_pre.any()          # the episode left traces behind
+    ref = oracle.new_state(p, 3, st.w, theta=st.theta)
+    ra = oracle.run(p, st, r, s, 60, learn=True)                   # episodic
+    rb = oracle.run(p, ref, r, s, 60, learn=True, episodic=False)  # fresh values, no reset
+    assert np.array_equal(ra.raster_e, rb.raster_e)
+    for name in ("v_e", "v_i", "ref_e", "ref_i", "s_e", "s_i", "x_pre", "x_post", "w", "theta"):
+        assert np.array_equal(getattr(st, name), getattr(ref, name)), name
+
+
 # ---------------------------------------------- O9 weight precision ---
 
 def _e4m3_values():
