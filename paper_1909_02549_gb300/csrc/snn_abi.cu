@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "snn_internal.cuh"
+#include "snn_nvtx.cuh"
 
 namespace snn {
 cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s);
@@ -363,6 +364,7 @@ snn_status snn_destroy(snn_net* n) {
 
 snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B, int T,
                    float dt, int learn, int reduce, unsigned flags, void* stream_) {
+    const snn::NvtxRange range("snn_run");
     if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_run: net is NULL");
     n->err.clear();
     if (B <= 0) return fail(n, SNN_ERR_ARG, "snn_run: B must be > 0 (got %d)", B);

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "snn_internal.cuh"
+#include "snn_nvtx.cuh"
 
 namespace snn {
 const snn_spec& net_spec(const snn_net* n);
@@ -360,6 +361,7 @@ snn_status snn_serve_submit(snn_server* s, const float* rates_hz, uint64_t seed,
 }
 
 snn_status snn_serve_step(snn_server* s, int k, void* stream_, int* steps_run) {
+    const snn::NvtxRange range("snn_serve_step");
     if (!s || k <= 0) return sfail(s, SNN_ERR_ARG, "snn_serve_step: NULL server or k <= 0");
     if (steps_run) *steps_run = 0;
     cudaStream_t st = (cudaStream_t)stream_;
