@@ -124,3 +124,26 @@ def test_replicas_aggregate_over_two_gloo_ranks():
     assert (r0, r1) == (0, 1) and s0 == s1 == 150.0
     assert v0 == v1 == 2 * 256 * 250 * 10 / 0.150
     assert seeds0 != seeds1 and [b - a for a, b in zip(seeds0, seeds1)] == [100000] * 4
+
+
+def test_reference_arm_prints_the_contract_line():
+    """``bench.py --impl reference`` (the oracle on the host cores) prints one
+    JSON line with the keys the driver reads: the same metric, unit and
+    direction as the GPU arm, ``impl``, a ``cpu_baseline`` describing its run
+    and an ``e2e`` object that copies nothing between host and device."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "3"], cwd=ROOT, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1 and d["value"] > 0
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
