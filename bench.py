@@ -78,6 +78,9 @@ def parse():
                          "instead (one JSON line)")
     ap.add_argument("--no-gather", action="store_true",
                     help="with --rec: skip the exact gather form's presentation")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="the CPU oracle against batch size (784->100 and 784->400) instead "
+                         "(one JSON line; needs no GPU)")
     return ap.parse_args()
 
 
@@ -196,7 +199,8 @@ def algorithmic_bytes(kernel: str, B: int, N: int, NI: int, learn: bool, T: int 
     return 0.0
 
 
-def streaming_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool) -> float:
+def streaming_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool,
+                                    master: str = "fp32") -> float:
     """Algorithmic bytes per sample-step of the per-step streaming form:
     per-sample state read and written once per step, plus the shared W's
     bytes divided over the batch.
@@ -207,15 +211,14 @@ def streaming_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool) -> flo
         (21.0 KB at 784 -> 400; 195.0 KB at 784 -> 6400)
     per sample, learning off: 16 N + 4 N + 4 n_in + N  ->  21 N + 4 n_in
         (11.5 KB at 784 -> 400)
-    shared W per step: learning on, 784 -> 6400 (the precision workload):
-        compensated master hi+lo r/w (16 B) and the BF16 copy w+r (4 B) per
-        weight; other learning-on workloads an FP32 read and write (8 B);
-        learning off one FP32 read (4 B).
-    784 -> 400 at B=1024: 23.4 KB; at B=256: 30.8 KB.  784 -> 6400 at B=256:
-    587 KB."""
+    shared W per step, charged for the master the timed form keeps: an FP32
+        master is read and written once (8 B per weight), a compensated
+        (hi, lo) FP32 pair twice that (16 B); learning off reads W once (4 B).
+    784 -> 400 at B=1024: 23.4 KB; at B=256: 30.8 KB.  784 -> 6400 at B=256,
+    FP32 master: 351.8 KB (compensated master: 508.6 KB)."""
     if learn:
         per = 29.0 * N + 12.0 * NI
-        wb = 20.0 if (NI, N) == (784, 6400) else 8.0
+        wb = 16.0 if master == "compensated" else 8.0
     else:
         per = 21.0 * N + 4.0 * NI
         wb = 4.0
@@ -230,26 +233,67 @@ def launches_per_run(mode: str, T: int, learn: bool) -> int:
 
 # ------------------------------------------------------- reference arm ---
 
-def time_oracle(a, seconds: float, max_T: int | None = None):
-    """CPU oracle (FP32 instantiation, one thread) on a bounded sample of the workload."""
+def host_cores() -> int:
+    """Host cores this process may run on (nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def _oracle_rate(a, B: int, seconds: float, threads: int, max_T: int | None = None):
+    """sample-timesteps/s of the CPU oracle (FP32) on the first steps of B
+    samples of the workload, about `seconds` of CPU time; (rate, steps, s)."""
     import oracle
-    from paper_1909_02549_gb300 import synth
     oracle.build()
-    B = min(16, a.batch)
+    oracle.set_threads(threads)
     p, r, s, w = bench_workload(a, B)
-    T = 2
     st = oracle.new_state(p, B, w)
     t0 = time.perf_counter()
-    oracle.run(p, st, r, s, T, learn=not a.no_learn, reduce=a.reduce, record=False)
+    oracle.run(p, st, r, s, 2, learn=not a.no_learn, reduce=a.reduce, record=False)
     dt = time.perf_counter() - t0
-    T2 = max(1, min(max_T or a.T, int(seconds / max(dt / T, 1e-9))))
+    T2 = max(1, min(max_T or a.T, int(seconds / max(dt / 2, 1e-9))))
     st = oracle.new_state(p, B, w)
     t0 = time.perf_counter()
     oracle.run(p, st, r, s, T2, learn=not a.no_learn, reduce=a.reduce, record=False)
     el = time.perf_counter() - t0
-    return {"value": B * T2 / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "first %d of %d steps of %d of the %d samples (784->%d, learning on, %s), "
-                      "FP32 oracle, 1 thread, %.1f s" % (T2, a.T, B, a.batch, a.n_exc, a.reduce, el)}
+    oracle.set_threads(1)
+    return B * T2 / el, T2, el
+
+
+def time_oracle(a, seconds: float, max_T: int | None = None):
+    """CPU oracle (FP32) on a bounded sample of the workload, on every host
+    core (OpenMP over samples and input rows), and on one core beside it."""
+    cores = host_cores()
+    B = min(16, a.batch)
+    v, T2, el = _oracle_rate(a, B, 0.7 * seconds, cores, max_T)
+    v1, T1, el1 = _oracle_rate(a, B, 0.3 * seconds, 1, max_T)
+    return {"value": v, "unit": UNIT, "cores": cores, "nproc": cores, "kind": "oracle",
+            "sample": "first %d of %d steps of %d of the %d samples (784->%d, %s, %s), FP32 oracle, "
+                      "%d threads, %.1f s" % (T2, a.T, B, a.batch, a.n_exc,
+                                               "learning off" if a.no_learn else "learning on",
+                                               a.reduce, cores, el),
+            "single_thread": {"value": v1, "sample": "first %d steps, %.1f s" % (T1, el1)}}
+
+
+def cpu_sweep_leg(a):
+    """The CPU oracle against batch size on the 784 -> 100 and 784 -> 400
+    workloads (pair STDP, mean reduction, learning on and off), one thread and
+    every host core, each point a bounded sample of its first steps."""
+    cores = host_cores()
+    rows = []
+    for n_exc in (100, 400):
+        for learn in (True, False):
+            for B in (1, 4, 16, 64, 256, 1024):
+                aa = argparse.Namespace(**vars(a))
+                aa.n_exc, aa.no_learn, aa.batch = n_exc, not learn, B
+                for th in (1, cores):
+                    v, T2, el = _oracle_rate(aa, B, a.cpu_seconds / 8.0, th, max_T=250)
+                    rows.append({"n_exc": n_exc, "learn": learn, "B": B, "threads": th,
+                                 "value": v, "steps": T2, "seconds": el})
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "CPU oracle sample-timesteps/s vs batch (FP32, T<=250 sampled)",
+                      "nproc": cores, "unit": UNIT, "rows": rows}), flush=True)
 
 
 def run_reference(a):
@@ -259,6 +303,8 @@ def run_reference(a):
     import oracle
     from paper_1909_02549_gb300 import synth
     oracle.build()
+    cores = host_cores()
+    oracle.set_threads(cores)
     B, T = 4, 4
     p, r, s, w = bench_workload(a, B)
 
@@ -274,14 +320,14 @@ def run_reference(a):
     tot = sum(times)
     value = B * T * a.steps / tot
     sample = ("each step: %d samples x %d time steps of the 784->%d workload (learning on, %s), "
-              "FP32 oracle, 1 thread" % (B, T, a.n_exc, a.reduce))
+              "FP32 oracle, %d threads" % (B, T, a.n_exc, a.reduce, cores))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(a, "cpu-oracle"),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "nproc": cores,
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -308,10 +354,11 @@ def code_digest(sources) -> str:
     return h.hexdigest()
 
 
-def profile_traffic(profile, sources):
-    """DRAM bytes (read + write) per launch from a committed ncu summary, only
-    while the kernel sources' code digest matches the one that summary
-    records; else None and why."""
+def profile_record(profile, sources):
+    """The machine-readable lines of a committed ncu summary ("dram bytes per
+    launch", and where recorded "issue active pct" and "warp instructions per
+    launch"), only while the kernel sources' code digest matches the one that
+    summary records; else None and why."""
     try:
         text = open(os.path.join(ROOT, profile)).read()
         want = re.search(r"code sha256: ([0-9a-f]{64})", text)
@@ -320,21 +367,37 @@ def profile_traffic(profile, sources):
             return None, "no traffic recorded in " + profile
         if want.group(1) != code_digest(sources):
             return None, "kernel changed since the capture in " + profile
-        return int(nbytes.group(1)), "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + profile
+        rec = {"traffic": int(nbytes.group(1))}
+        issue = re.search(r"issue active pct: ([0-9.]+)", text)
+        inst = re.search(r"warp instructions per launch: (\d+)", text)
+        if issue:
+            rec["issue_active_pct"] = float(issue.group(1))
+        if inst:
+            rec["warp_instructions_per_launch"] = int(inst.group(1))
+        return rec, "ncu, " + profile
     except OSError as e:
         return None, str(e)[:200]
 
 
-def recorded_traffic(a, dom):
-    """Traffic of the persistent kernel on the default workload (see
-    ``profile_traffic``)."""
+def profile_traffic(profile, sources):
+    """DRAM bytes (read + write) per launch from a committed ncu summary (see
+    ``profile_record``); else None and why."""
+    rec, why = profile_record(profile, sources)
+    if rec is None:
+        return None, why
+    return rec["traffic"], "ncu dram__bytes_read.sum + dram__bytes_write.sum, " + why[5:]
+
+
+def recorded_profile(a, dom):
+    """ncu record of the persistent kernel on the default workload (see
+    ``profile_record``)."""
     if dom != "persistent":
         return None, "no capture of k_%s on this workload" % dom
-    default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn, a.rule) == (
-        256, 6400, 250, "mean", "fp32", False, "pair")
+    default = (a.batch, a.n_exc, a.T, a.reduce, a.wprec, a.no_learn, a.rule,
+               getattr(a, "master", "fp32")) == (256, 6400, 250, "mean", "fp32", False, "pair", "fp32")
     if not default:
         return None, "the capture is of the default workload only"
-    return profile_traffic(PERSISTENT_PROFILE, KERNEL_SOURCES)
+    return profile_record(PERSISTENT_PROFILE, KERNEL_SOURCES)
 
 
 def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
@@ -355,20 +418,33 @@ def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
         avg_s = dom_ms / dom_launches * 1e-3
         pk = peaks()
         own = algorithmic_bytes(dom, B, N, 784, learn, T)
+        master = getattr(a, "master", "fp32")
         if dom == "persistent":
             # one launch is every step of the presentation: the streaming form's
-            # per-sample-step bytes times the B*T sample-steps it processes
-            per = streaming_bytes_per_sample_step(B, N, 784, learn)
+            # per-sample-step bytes (W charged for the master this form keeps)
+            # times the B*T sample-steps it processes
+            per = streaming_bytes_per_sample_step(B, N, 784, learn, master)
             nbytes = per * B * T
-            definition = ("per-step streaming bytes per sample-step (%.1f KB) x B x T sample-steps" % (per / 1e3))
+            definition = ("per-step streaming bytes per sample-step (%.1f KB, W as a%s master: "
+                          "%d B per weight per step) x B x T sample-steps" % (
+                              per / 1e3, " compensated FP32" if master == "compensated" else "n FP32",
+                              (16 if master == "compensated" else 8) if learn else 4))
         else:
             nbytes = own
             definition = "the kernel's own minimum bytes (the streaming bytes are defined per whole step)"
         achieved = nbytes / avg_s / 1e9
-        traffic, traffic_source = recorded_traffic(a, dom)
+        rec, rec_source = recorded_profile(a, dom)
+        traffic = rec["traffic"] if rec else None
+        limiter = None
+        if rec and "issue_active_pct" in rec:
+            limiter = {"kind": "instruction issue", "issue_active_pct": rec["issue_active_pct"],
+                       "warp_instructions_per_launch": rec.get("warp_instructions_per_launch"),
+                       "note": "the DRAM traffic is a small fraction of the algorithmic bytes "
+                               "(the state stays on chip); issue slots and latency bound the "
+                               "kernel", "source": rec_source}
         return {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                "traffic_source": traffic_source,
+                "traffic_source": rec_source, "limiter": limiter,
                 "peak_source": pk["source"] + " hbm_gbs (burst copy), of measured",
                 "algorithmic_bytes_per_launch": nbytes, "bytes_definition": definition,
                 "design_bytes_per_launch": own,
@@ -731,6 +807,9 @@ def rec_leg(a):
 
 def main():
     a = parse()
+    if a.cpu_sweep:
+        cpu_sweep_leg(a)
+        return
     if a.rec:
         rec_leg(a)
         return

@@ -28,13 +28,13 @@ REDUCE = {"sum": 0, "mean": 1, "max": 2}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (g++, -O2 -ffp-contract=off, no fast-math)."""
+    """Compile the oracle (g++, -O2 -ffp-contract=off, no fast-math, OpenMP)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_REC))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_REC])
+                               "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_REC])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -75,11 +75,17 @@ def lib():
             fn.restype = C.c_int
             fn.argtypes = [C.POINTER(_Params), C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                            C.c_int, C.c_int, C.c_int, C.POINTER(_State), C.POINTER(_Record)]
+        _lib.oracle_set_threads.argtypes = [C.c_int]
         _lib.oracle_splitmix64.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
         _lib.oracle_poisson_thresholds.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int64]
         for name in ("oracle_round_bf16", "oracle_round_e4m3", "oracle_e4m3_column_scale"):
             getattr(_lib, name).argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle runs (the results do not depend on it)."""
+    lib().oracle_set_threads(int(n))
 
 
 def _ptr(a):

@@ -58,12 +58,21 @@
 // the file is compiled with -ffp-contract=off and without -ffast-math so the
 // float instantiation is the bit-exact reference and the double instantiation
 // the error reference.
+//
+// Threads (oracle_set_threads, default 1): the loops over independent elements
+// -- samples for the input, currents and neurons, input rows for the weight
+// update, neurons for theta -- are split over OpenMP threads.  Every element
+// is computed by one thread with the same operations in the same order (each
+// synapse still sums its batch terms in ascending b), so the result does not
+// depend on the thread count.
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <limits>
 #include <vector>
+
+#include <omp.h>
 
 extern "C" {
 
@@ -113,6 +122,8 @@ struct oracle_record {
 }  // extern "C"
 
 namespace {
+
+int g_threads = 1;   // OpenMP threads of a run (oracle_set_threads)
 
 // SplitMix64 (Steele, Lea & Flood 2014): the first output of a generator whose
 // state is x -- advance by the golden-ratio increment, then finalise.
@@ -216,6 +227,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
     const R nu_pre = (R)P->nu_pre, nu_post = (R)P->nu_post;
     const R w_min = (R)P->w_min, w_max = (R)P->w_max;
     const double theta_plus = (double)P->theta_plus;
+    const int nth = g_threads;
 
     // Episodic reset (Sec. "Episodic vs. continuing simulation"): every
     // per-sample variable back to its common initial value; W and theta persist.
@@ -241,12 +253,14 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         const uint64_t t = S->step;
 
         // O1 Poisson input spikes of this step.
+#pragma omp parallel for num_threads(nth)
         for (int b = 0; b < B; ++b)
             for (int i = 0; i < NI; ++i)
                 s_in[(size_t)b * NI + i] =
                     poisson_draw(seeds[b], t, NI, i) < thr[(size_t)b * NI + i] ? 1 : 0;
 
         // O5 presynaptic traces (after this step's input spikes).
+#pragma omp parallel for num_threads(nth)
         for (int k = 0; k < B * NI; ++k) {
             R m = x_pre[k] * a_x;
             x_pre[k] = m + (R)s_in[k];
@@ -272,6 +286,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
 
         // O2 currents.  I_in: for every (b, j) the sum runs over ascending i
         // (FP8: the sum of the scaled codes, times the column scale).
+#pragma omp parallel for num_threads(nth)
         for (int b = 0; b < B; ++b) {
             R* Ib = &I_in[(size_t)b * N];
             for (int j = 0; j < N; ++j) Ib[j] = (R)0;
@@ -295,6 +310,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         }
 
         // O3 excitatory and O4 inhibitory neurons (both read previous spikes).
+#pragma omp parallel for num_threads(nth)
         for (int b = 0; b < B; ++b) {
             for (int j = 0; j < N; ++j) {
                 const size_t k = (size_t)b * N + j;
@@ -347,6 +363,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         }
 
         // O5 postsynaptic traces.
+#pragma omp parallel for num_threads(nth)
         for (int k = 0; k < B * N; ++k) {
             R m = x_post[k] * a_x;
             x_post[k] = m + (R)se_new[k];
@@ -356,10 +373,16 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
         if (learn) {
             // max: D = max over b of (pot - dep), from -inf.  sum and mean: the
             // potentiation and depression sums P (in D) and Q, from 0.
+            // (rows i are independent: each synapse (i, j) takes its batch terms
+            // in ascending b whichever thread owns row i)
             const R init = (reduce == 2) ? -std::numeric_limits<R>::infinity() : (R)0;
-            for (size_t k = 0; k < D.size(); ++k) { D[k] = init; Q[k] = (R)0; }
-            for (int b = 0; b < B; ++b) {
-                for (int i = 0; i < NI; ++i) {
+#pragma omp parallel for num_threads(nth)
+            for (int i = 0; i < NI; ++i) {
+                for (int j = 0; j < N; ++j) {
+                    D[(size_t)i * N + j] = init;
+                    Q[(size_t)i * N + j] = (R)0;
+                }
+                for (int b = 0; b < B; ++b) {
                     const R xp = x_pre[(size_t)b * NI + i];
                     const R si = (R)s_in[(size_t)b * NI + i];
                     for (int j = 0; j < N; ++j) {
@@ -380,6 +403,7 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                     }
                 }
             }
+#pragma omp parallel for num_threads(nth)
             for (int k = 0; k < NI * N; ++k) {
                 R d = D[k];
                 if (reduce != 2) d = d - Q[k];
@@ -451,6 +475,9 @@ int oracle_run_f64(const oracle_params* P, int B, int T, const float* rates,
                    oracle_state* S, oracle_record* rec) {
     return run<double>(P, B, T, rates, seeds, learn, reduce, episodic, S, rec);
 }
+
+// Number of OpenMP threads of later runs (n >= 1).
+void oracle_set_threads(int n) { g_threads = n > 0 ? n : 1; }
 
 // Exposed so the tests can pin the generator against its published outputs.
 void oracle_splitmix64(const uint64_t* x, uint64_t* out, int64_t n) {

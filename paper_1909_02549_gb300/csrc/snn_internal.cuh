@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "snn.h"
+#include "snn_draw.cuh"
 
 namespace snn {
 
@@ -59,6 +60,44 @@ __device__ __forceinline__ float exc_membrane(int neuron, float v, float drive, 
     return v;
 }
 
+// One step of an inhibitory membrane (every run form uses it): decay towards
+// rest, d = v - rest; d = d*a; v = rest + d, integrate `drive` unless
+// refractory, spike at v >= i_thresh, then reset and refractory.
+__device__ __forceinline__ float inh_membrane(float vi, float drive, float i_rest, float a_i,
+                                              float i_thresh, float i_reset, int R_i, int& ref_i,
+                                              bool& si) {
+    float dv = __fsub_rn(vi, i_rest);
+    dv = __fmul_rn(dv, a_i);
+    vi = __fadd_rn(i_rest, dv);
+    const bool free_i = ref_i == 0;
+    if (!free_i) ref_i -= 1;
+    else vi = __fadd_rn(vi, drive);
+    si = free_i && vi >= i_thresh;
+    if (si) { vi = i_reset; ref_i = R_i; }
+    return vi;
+}
+
+constexpr uint32_t ST_SE = 1u << 16;
+constexpr uint32_t ST_SI = 1u << 17;
+
+// One step of the excitatory/inhibitory pair (b, j), shared by every run form:
+// the all-but-self inhibition from the previous step's inhibitory count C of
+// the sample (C - s_i'), the one-to-one drive w_ei * s_e', both membranes, and
+// the packed word st = ref_e | ref_i << 8 | s_e << 16 | s_i << 17 of this step.
+// I is the synaptic current and th the excitatory threshold with theta.
+__device__ __forceinline__ uint32_t pair_update(const Consts& c, float& v, float& vi, uint32_t st,
+                                                float I, int C, float th) {
+    int ref_e = (int)(st & 0xFFu), ref_i = (int)((st >> 8) & 0xFFu);
+    const int se_prev = (st & ST_SE) ? 1 : 0, si_prev = (st & ST_SI) ? 1 : 0;
+    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));   // all-but-self
+    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);         // one-to-one
+    bool se, si;
+    v = exc_membrane(c.neuron, v, __fadd_rn(I, I_lat), th, c.e_rest, c.a_e, c.e_reset, c.R_e,
+                     ref_e, se);
+    vi = inh_membrane(vi, I_inh, c.i_rest, c.a_i, c.i_thresh, c.i_reset, c.R_i, ref_i, si);
+    return (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+}
+
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.
 // Buffers indexed by the absolute step tt rotate so that one step's writers
 // never overwrite what the previous step's readers may still use:
@@ -89,7 +128,6 @@ struct Bufs {
     float* wscale;       // [N] per-column power-of-two scale of the FP8 weights (this step)
 };
 
-// Packed per-(b,j) state word.
 // Ring depths of the per-step input buffers.  In the persistent form a CTA
 // encodes step tt+1 and signals it before running the STDP of step tt, so the
 // traces and masks of step tt are still read while other CTAs run step tt+1:
@@ -97,17 +135,6 @@ struct Bufs {
 // that all readers have passed.  The per-step kernels use the same slots.
 constexpr int XPRE_SLOTS = 3;
 constexpr int PRET_SLOTS = 4;
-constexpr uint32_t ST_SE = 1u << 16;
-constexpr uint32_t ST_SI = 1u << 17;
-
-// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the first output of a
-// generator whose state is x.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 // Weight as read by the synaptic current.  BF16: round to nearest even.
 // FP8: the E4M3 code (nearest, ties to even, saturating) of W / s_j, with the

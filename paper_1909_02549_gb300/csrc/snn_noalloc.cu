@@ -12,6 +12,8 @@
 // contents; each call re-initialises what must start at zero.  Two calls whose
 // work overlaps on the GPU (different streams, no ordering between them) race
 // on the array.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -30,18 +32,30 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch, looked up once per device with that
-// device current.
+// device current, and again when the device's context is no longer the one
+// of the lookup (after cudaDeviceReset the runtime creates a new primary
+// context and loads the module anew, possibly elsewhere).
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[MAX_DEVICES] = {nullptr};
+CUcontext g_scratch_ctx[MAX_DEVICES] = {nullptr};
 
-struct NaConsts {
-    int n_in, N, B, Iw;
-    float e_rest, e_reset, e_thresh, a_e;
-    float i_rest, i_reset, i_thresh, a_i;
-    float w_ei, w_ie, dt;
-    int R_e, R_i;
-    int neuron;            // snn_neuron of the excitatory population
-};
+// The calling thread's current driver context (NULL if none or unavailable),
+// through the runtime's entry-point query so the library need not link libcuda.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (Fn)f;
+    });
+    CUcontext ctx = nullptr;
+    if (fn && fn(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    return ctx;
+}
 
 struct NaBufs {
     const float* W;        // [n_in][N]  caller's weights
@@ -61,24 +75,11 @@ size_t scratch_bytes(size_t B, size_t N, size_t n_in) {
     return 12 * B * N + 4 * B * n_in + 4 * B * Iw + 12 * B;
 }
 
-__device__ __forceinline__ uint64_t sm64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__global__ void k_na_init(NaConsts c, NaBufs d, const float* __restrict__ rates) {
+__global__ void k_na_init(snn::Consts c, NaBufs d, const float* __restrict__ rates) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
-    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth) {
-        double p = __dmul_rn((double)rates[k], (double)c.dt);
-        p = __dmul_rn(p, 1e-3);
-        const double x = __dmul_rn(p, 4294967296.0);
-        uint32_t thr = 0u;
-        if (x > 0.0) thr = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(x);
-        d.thr[k] = thr;
-    }
+    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth)
+        d.thr[k] = snn::poisson_threshold(rates[k], c.dt);
     for (size_t k = tid; k < (size_t)c.B * c.N; k += nth) {
         d.v_e[k] = c.e_rest;
         d.v_i[k] = c.i_rest;
@@ -89,7 +90,7 @@ __global__ void k_na_init(NaConsts c, NaBufs d, const float* __restrict__ rates)
 }
 
 // warp = one sample x one 32-input word
-__global__ void __launch_bounds__(256) k_na_encode(NaConsts c, NaBufs d, int t) {
+__global__ void __launch_bounds__(256) k_na_encode(snn::Consts c, NaBufs d, int t) {
     const int lane = threadIdx.x & 31;
     const size_t gtid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
@@ -100,20 +101,15 @@ __global__ void __launch_bounds__(256) k_na_encode(NaConsts c, NaBufs d, int t) 
     const int b = (int)(gw / c.Iw), iw = (int)(gw % c.Iw);
     const int i = iw * 32 + lane;
     uint32_t s = 0;
-    if (i < c.n_in) {
-        const uint32_t thr = d.thr[(size_t)b * c.n_in + i];
-        if (thr != 0u) {
-            const uint64_t ctr = (uint64_t)t * (uint64_t)c.n_in + (uint64_t)i;
-            const uint32_t h = (uint32_t)(sm64(d.seeds[b] ^ sm64(ctr)) >> 32);
-            s = h < thr ? 1u : 0u;
-        }
-    }
+    if (i < c.n_in)
+        s = snn::poisson_spike(d.seeds[b], (unsigned long long)t, c.n_in, i,
+                               d.thr[(size_t)b * c.n_in + i]) ? 1u : 0u;
     const uint32_t word = __ballot_sync(FULL, s);
     if (lane == 0) d.inb[(size_t)b * c.Iw + iw] = word;
 }
 
 // one thread per (b, j)
-__global__ void __launch_bounds__(256) k_na_neuron(NaConsts c, NaBufs d, int t) {
+__global__ void __launch_bounds__(256) k_na_neuron(snn::Consts c, NaBufs d, int t) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)c.B * c.N) return;
     const int b = (int)(idx / c.N), j = (int)(idx % c.N);
@@ -127,30 +123,15 @@ __global__ void __launch_bounds__(256) k_na_neuron(NaConsts c, NaBufs d, int t) 
             I = __fadd_rn(I, d.W[(size_t)(w * 32 + k) * c.N + j]);
         }
     }
-    const uint32_t s = d.st[idx];
-    int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
-    const int se_prev = (s >> 16) & 1, si_prev = (s >> 17) & 1;
     const int C = (int)d.cnt[(size_t)((t + 2) % 3) * c.B + b];
-    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
-    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-    bool se;
-    const float v = snn::exc_membrane(c.neuron, d.v_e[idx], __fadd_rn(I, I_lat),
-                                      __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j])), c.e_rest,
-                                      c.a_e, c.e_reset, c.R_e, ref_e, se);
+    float v = d.v_e[idx], vi = d.v_i[idx];
+    const uint32_t st = snn::pair_update(c, v, vi, d.st[idx], I, C,
+                                         __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j])));
     d.v_e[idx] = v;
-    float vi = d.v_i[idx];
-    float dv = __fsub_rn(vi, c.i_rest);
-    dv = __fmul_rn(dv, c.a_i);
-    vi = __fadd_rn(c.i_rest, dv);
-    const bool free_i = ref_i == 0;
-    if (!free_i) ref_i -= 1;
-    else vi = __fadd_rn(vi, I_inh);
-    const bool si = free_i && vi >= c.i_thresh;
-    if (si) { vi = c.i_reset; ref_i = c.R_i; }
     d.v_i[idx] = vi;
-    d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? 1u << 16 : 0u) | (si ? 1u << 17 : 0u);
-    if (se) d.counts[idx] += 1u;
-    if (si) atomicAdd(&d.cnt[(size_t)(t % 3) * c.B + b], 1u);
+    d.st[idx] = st;
+    if (st & snn::ST_SE) d.counts[idx] += 1u;
+    if (st & snn::ST_SI) atomicAdd(&d.cnt[(size_t)(t % 3) * c.B + b], 1u);
 }
 
 snn_status na_fail(snn_status code, const char* msg) {
@@ -167,9 +148,14 @@ extern "C" snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, co
         return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: NULL pointer argument");
     const snn_spec& s = *spec;
     if (s.n_in <= 0 || s.n_exc <= 0 || s.n_inh != s.n_exc || B <= 0 || T < 0 ||
-        !(dt_ms > 0.0f) || !(s.e_tau_ms > 0.0f) || !(s.i_tau_ms > 0.0f) ||
+        !std::isfinite(dt_ms) || !(dt_ms > 0.0f) || !std::isfinite(s.e_tau_ms) ||
+        !(s.e_tau_ms > 0.0f) || !std::isfinite(s.i_tau_ms) || !(s.i_tau_ms > 0.0f) ||
         !(s.e_refrac_ms >= 0.0f) || !(s.i_refrac_ms >= 0.0f))
         return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: invalid sizes or parameters");
+    if (s.neuron != SNN_NEURON_LIF && s.neuron != SNN_NEURON_IF_SUB)
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: unknown neuron model");
+    if ((size_t)B * (size_t)s.n_exc > ((size_t)1 << 31) || (size_t)B * (size_t)s.n_in > ((size_t)1 << 31))
+        return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: B*n_exc or B*n_in exceeds 2^31");
     if (s.wprec != SNN_W_FP32)
         return na_fail(SNN_ERR_ARG, "snn_infer_noalloc: only FP32 weights (wprec 0)");
     const int R_e = (int)std::lround((double)s.e_refrac_ms / (double)dt_ms);
@@ -187,17 +173,19 @@ extern "C" snn_status snn_infer_noalloc(const snn_spec* spec, const float* w, co
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_ptr[dev]) {
+        const CUcontext ctx = current_context();
+        if (!g_scratch_ptr[dev] || ctx != g_scratch_ctx[dev]) {
             void* p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess || !p)
                 return na_fail(SNN_ERR_CUDA, "snn_infer_noalloc: cudaGetSymbolAddress failed");
             g_scratch_ptr[dev] = p;
+            g_scratch_ctx[dev] = current_context();   // the lookup made the context current
         }
         base = g_scratch_ptr[dev];
     }
 
-    NaConsts c{};
+    snn::Consts c{};
     c.n_in = s.n_in; c.N = s.n_exc; c.B = B; c.Iw = (s.n_in + 31) / 32;
     c.e_rest = s.e_rest; c.e_reset = s.e_reset; c.e_thresh = s.e_thresh;
     c.a_e = (float)std::exp(-(double)dt_ms / (double)s.e_tau_ms);

@@ -27,6 +27,7 @@
 // The arithmetic is the per-step kernels' (same intrinsics, same order), so the
 // three run modes give bit-identical results.
 #include <cfloat>
+#include <mutex>
 
 #include "snn_internal.cuh"
 
@@ -167,12 +168,7 @@ __device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, un
         uint32_t s = 0;
         if (i < c.n_in) {
             const size_t o = (size_t)b * c.n_in + i;
-            const uint32_t thr = d.thr[o];
-            if (thr != 0u) {
-                const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)i;
-                const uint32_t h = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32);
-                s = h < thr ? 1u : 0u;
-            }
+            s = poisson_spike(d.seeds[b], tt, c.n_in, i, d.thr[o]) ? 1u : 0u;
             float x = __ldcg(&d.x_pre[(size_t)xp * nbi + o]);
             x = __fmul_rn(x, c.a_x);
             x = __fadd_rn(x, s ? 1.0f : 0.0f);
@@ -287,29 +283,12 @@ struct Item {
 
 __device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I, int C, float thj) {
     const Consts& c = *cp;
-    int ref_e = (int)(it.st & 0xFFu), ref_i = (int)((it.st >> 8) & 0xFFu);
-    const int se_prev = (it.st & ST_SE) ? 1 : 0, si_prev = (it.st & ST_SI) ? 1 : 0;
-    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
-    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-    bool se;
-    const float v = exc_membrane(c.neuron, it.v, __fadd_rn(I, I_lat), thj, c.e_rest, c.a_e,
-                                 c.e_reset, c.R_e, ref_e, se);
-    float vi = it.vi;
-    float dv = __fsub_rn(vi, c.i_rest);
-    dv = __fmul_rn(dv, c.a_i);
-    vi = __fadd_rn(c.i_rest, dv);
-    const bool free_i = ref_i == 0;
-    if (!free_i) ref_i -= 1;
-    else vi = __fadd_rn(vi, I_inh);
-    const bool si = free_i && vi >= c.i_thresh;
-    if (si) { vi = c.i_reset; ref_i = c.R_i; }
-    float x = __fmul_rn(it.x, c.a_x);
-    x = __fadd_rn(x, se ? 1.0f : 0.0f);
     Item o;
-    o.v = v;
-    o.vi = vi;
-    o.x = x;
-    o.st = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+    o.v = it.v;
+    o.vi = it.vi;
+    o.st = pair_update(c, o.v, o.vi, it.st, I, C, thj);
+    float x = __fmul_rn(it.x, c.a_x);
+    o.x = __fadd_rn(x, (o.st & ST_SE) ? 1.0f : 0.0f);
     return o;
 }
 
@@ -1222,13 +1201,16 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
         return cudaSuccess;
     }
     // Device properties and the kernel's shared-memory opt-in are looked up
-    // once per device and layout size, not on every run.
+    // once per device and layout size, not on every run; the cache is shared
+    // by every host thread, so its reads and writes hold a lock.
     struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes = 0, attr_narrow = 0; };
     static Setup setup[64];
+    static std::mutex setup_mutex;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::unique_lock<std::mutex> lock(setup_mutex);
     Setup& su = setup[dev];
     if (su.sms == 0) {
         e = cudaDeviceGetAttribute(&su.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1252,6 +1234,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
         if (per_sm < 1) return cudaSuccess;
         attr = L.bytes;
     }
+    lock.unlock();
     Consts cc = c;
     Bufs dd = d;
     int TT = T;

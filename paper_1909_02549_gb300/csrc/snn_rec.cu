@@ -55,8 +55,12 @@
 #include <cuda_runtime.h>
 
 #include "snn.h"
+#include "snn_draw.cuh"
 
 namespace {
+
+using snn::poisson_threshold;
+using snn::splitmix64;
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -158,22 +162,6 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)1 << 46;
     d |= (uint64_t)2 << 61;
     return d;
-}
-
-__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ uint32_t poisson_threshold(float rate, float dt) {
-    double p = __dmul_rn((double)rate, (double)dt);
-    p = __dmul_rn(p, 1e-3);
-    const double x = __dmul_rn(p, 4294967296.0);
-    if (!(x > 0.0)) return 0u;
-    if (x >= 4294967295.0) return 0xFFFFFFFFu;
-    return (uint32_t)floor(x);
 }
 
 __global__ void k_rec_begin(RecConsts c, RecBufs d, const float* __restrict__ rates,

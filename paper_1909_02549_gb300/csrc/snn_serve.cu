@@ -59,26 +59,13 @@ struct SlotBufs {
     uint32_t* fin_counts;  // [S][N] their spike counts, gathered
 };
 
-__device__ __forceinline__ uint64_t sm64(uint64_t x) {
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 // Admitted slot a: thresholds from its rates, state reset, counters.
 __global__ void k_serve_admit(snn::Consts c, SlotBufs d, int n_adm, int S) {
     const int a = blockIdx.x;
     if (a >= n_adm) return;
     const int s = d.adm[a];
-    for (int i = threadIdx.x; i < c.n_in; i += blockDim.x) {
-        double p = __dmul_rn((double)d.stage[(size_t)a * c.n_in + i], (double)c.dt);
-        p = __dmul_rn(p, 1e-3);
-        const double x = __dmul_rn(p, 4294967296.0);
-        uint32_t thr = 0u;
-        if (x > 0.0) thr = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)floor(x);
-        d.thr[(size_t)s * c.n_in + i] = thr;
-    }
+    for (int i = threadIdx.x; i < c.n_in; i += blockDim.x)
+        d.thr[(size_t)s * c.n_in + i] = snn::poisson_threshold(d.stage[(size_t)a * c.n_in + i], c.dt);
     for (int j = threadIdx.x; j < c.N; j += blockDim.x) {
         const size_t k = (size_t)s * c.N + j;
         d.v_e[k] = c.e_rest;
@@ -108,14 +95,9 @@ __global__ void __launch_bounds__(256) k_serve_encode(snn::Consts c, SlotBufs d,
     const bool live = t < d.t_len[s];
     const int i = iw * 32 + lane;
     uint32_t sp = 0;
-    if (live && i < c.n_in) {
-        const uint32_t thr = d.thr[(size_t)s * c.n_in + i];
-        if (thr != 0u) {
-            const uint64_t ctr = (uint64_t)t * (uint64_t)c.n_in + (uint64_t)i;
-            const uint32_t h = (uint32_t)(sm64(d.seeds[s] ^ sm64(ctr)) >> 32);
-            sp = h < thr ? 1u : 0u;
-        }
-    }
+    if (live && i < c.n_in)
+        sp = snn::poisson_spike(d.seeds[s], (unsigned long long)t, c.n_in, i,
+                                d.thr[(size_t)s * c.n_in + i]) ? 1u : 0u;
     const uint32_t word = __ballot_sync(FULL, sp);
     if (lane == 0) {
         d.inb[(size_t)s * c.Iw + iw] = word;
@@ -147,31 +129,15 @@ __global__ void __launch_bounds__(256) k_serve_neuron(snn::Consts c, SlotBufs d,
         }
     }
     if (c.wprec == SNN_W_FP8E4M3) I = __fmul_rn(I, sc);
-    const uint32_t st = d.st[idx];
-    int ref_e = (int)(st & 0xFFu), ref_i = (int)((st >> 8) & 0xFFu);
-    const int se_prev = (st & snn::ST_SE) ? 1 : 0, si_prev = (st & snn::ST_SI) ? 1 : 0;
     const int C = (int)d.cnt[(size_t)((g + 2) % 3) * S + s];
-    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));
-    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);
-    bool se;
-    const float v = snn::exc_membrane(c.neuron, d.v_e[idx], __fadd_rn(I, I_lat),
-                                 __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j])), c.e_rest,
-                                 c.a_e, c.e_reset, c.R_e, ref_e, se);
+    float v = d.v_e[idx], vi = d.v_i[idx];
+    const uint32_t st = snn::pair_update(c, v, vi, d.st[idx], I, C,
+                                         __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j])));
     d.v_e[idx] = v;
-    float vi = d.v_i[idx];
-    float dv = __fsub_rn(vi, c.i_rest);
-    dv = __fmul_rn(dv, c.a_i);
-    vi = __fadd_rn(c.i_rest, dv);
-    const bool free_i = ref_i == 0;
-    if (!free_i) ref_i -= 1;
-    else vi = __fadd_rn(vi, I_inh);
-    const bool si = free_i && vi >= c.i_thresh;
-    if (si) { vi = c.i_reset; ref_i = c.R_i; }
     d.v_i[idx] = vi;
-    d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? snn::ST_SE : 0u) |
-                (si ? snn::ST_SI : 0u);
-    if (se) d.counts[idx] += 1u;
-    if (si) atomicAdd(&d.cnt[(size_t)(g % 3) * S + s], 1u);
+    d.st[idx] = st;
+    if (st & snn::ST_SE) d.counts[idx] += 1u;
+    if (st & snn::ST_SI) atomicAdd(&d.cnt[(size_t)(g % 3) * S + s], 1u);
     if (j == 0) d.t_loc[s] += 1;
 }
 

@@ -26,17 +26,6 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr int STDP_ROWS = 64;   // input rows per k_stdp block
 
-// Bernoulli threshold of one time bin: p = rate * dt / 1000 scaled to 2^32,
-// computed in FP64 (Sec. "Scaling a Two Layer Network": Poisson spike trains).
-__device__ __forceinline__ uint32_t poisson_threshold(float rate, float dt) {
-    double p = __dmul_rn((double)rate, (double)dt);
-    p = __dmul_rn(p, 1e-3);
-    const double x = __dmul_rn(p, 4294967296.0);
-    if (!(x > 0.0)) return 0u;
-    if (x >= 4294967295.0) return 0xFFFFFFFFu;
-    return (uint32_t)floor(x);
-}
-
 __global__ void k_begin_run(Consts c, Bufs d, const float* __restrict__ rates,
                             const uint64_t* __restrict__ seeds, int episodic, int T) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,12 +92,7 @@ __global__ void __launch_bounds__(256) k_encode(Consts c, Bufs d, int t_local) {
     uint32_t s = 0;
     if (i < c.n_in) {
         const size_t o = (size_t)b * c.n_in + i;
-        const uint32_t thr = d.thr[o];
-        if (thr != 0u) {
-            const uint64_t ctr = tt * (uint64_t)c.n_in + (uint64_t)i;
-            const uint32_t h = (uint32_t)(splitmix64(d.seeds[b] ^ splitmix64(ctr)) >> 32);
-            s = h < thr ? 1u : 0u;
-        }
+        s = poisson_spike(d.seeds[b], tt, c.n_in, i, d.thr[o]) ? 1u : 0u;
         const size_t nbi = (size_t)c.B * c.n_in;
         float x = d.x_pre[(size_t)xp * nbi + o];
         x = __fmul_rn(x, c.a_x);
@@ -168,31 +152,13 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
         }
         I = __fmul_rn(I, sc);
     }
-    const uint32_t s = d.st[idx];
-    int ref_e = (int)(s & 0xFFu), ref_i = (int)((s >> 8) & 0xFFu);
-    const int se_prev = (s & ST_SE) ? 1 : 0, si_prev = (s & ST_SI) ? 1 : 0;
     const int p3 = (int)(tt % 3ull);
     const int C = (int)d.cnt[(size_t)((p3 + 2) % 3) * c.B + b];
-    const float I_lat = __fmul_rn(c.w_ie, (float)(C - si_prev));   // all-but-self
-    const float I_inh = __fmul_rn(c.w_ei, (float)se_prev);         // one-to-one
-
-    // Excitatory, adaptive threshold.
     const float th = __fadd_rn(c.e_thresh, __double2float_rn(d.theta[j]));
-    bool se;
-    const float v = exc_membrane(c.neuron, d.v_e[idx], __fadd_rn(I, I_lat), th, c.e_rest, c.a_e,
-                                 c.e_reset, c.R_e, ref_e, se);
+    float v = d.v_e[idx], vi = d.v_i[idx];
+    const uint32_t st = pair_update(c, v, vi, d.st[idx], I, C, th);
+    const bool se = (st & ST_SE) != 0u, si = (st & ST_SI) != 0u;
     d.v_e[idx] = v;
-
-    // Inhibitory.
-    float vi = d.v_i[idx];
-    float dv = __fsub_rn(vi, c.i_rest);
-    dv = __fmul_rn(dv, c.a_i);
-    vi = __fadd_rn(c.i_rest, dv);
-    const bool free_i = ref_i == 0;
-    if (!free_i) ref_i -= 1;
-    else vi = __fadd_rn(vi, I_inh);
-    const bool si = free_i && vi >= c.i_thresh;
-    if (si) { vi = c.i_reset; ref_i = c.R_i; }
     d.v_i[idx] = vi;
 
     // Postsynaptic trace.
@@ -201,7 +167,7 @@ __global__ void __launch_bounds__(256) k_neuron(Consts c, Bufs d, int t_local) {
     x = __fadd_rn(x, se ? 1.0f : 0.0f);
     d.x_post[idx] = x;
 
-    d.st[idx] = (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
+    d.st[idx] = st;
     if (se) {
         d.counts[idx] += 1u;
         const uint32_t bit = 1u << (b & 31);

@@ -24,6 +24,11 @@ def args(**kw):
     return a
 
 
+def recorded_traffic(a, dom):
+    rec, why = bench.recorded_profile(a, dom)
+    return (rec["traffic"] if rec else None), why
+
+
 def capture(tmp_path, monkeypatch, nbytes=12345678):
     src = [tmp_path / "kernel.cu", tmp_path / "kernel.cuh"]
     src[0].write_bytes(b"__global__ void k() {}\n")
@@ -38,21 +43,21 @@ def capture(tmp_path, monkeypatch, nbytes=12345678):
 
 def test_traffic_is_reported_for_the_captured_sources_and_workload(tmp_path, monkeypatch):
     capture(tmp_path, monkeypatch)
-    nbytes, src = bench.recorded_traffic(args(), "persistent")
+    nbytes, src = recorded_traffic(args(), "persistent")
     assert nbytes == 12345678 and "summary.md" in src
 
 
 def test_traffic_is_null_for_another_workload_or_kernel(tmp_path, monkeypatch):
     capture(tmp_path, monkeypatch)
-    assert bench.recorded_traffic(args(batch=128), "persistent")[0] is None
-    assert bench.recorded_traffic(args(reduce="max"), "persistent")[0] is None
-    assert bench.recorded_traffic(args(), "stdp")[0] is None
+    assert recorded_traffic(args(batch=128), "persistent")[0] is None
+    assert recorded_traffic(args(reduce="max"), "persistent")[0] is None
+    assert recorded_traffic(args(), "stdp")[0] is None
 
 
 def test_traffic_is_null_once_the_kernel_changes(tmp_path, monkeypatch):
     src = capture(tmp_path, monkeypatch)
     src[0].write_bytes(src[0].read_bytes() + b"__device__ int x;\n")
-    nbytes, why = bench.recorded_traffic(args(), "persistent")
+    nbytes, why = recorded_traffic(args(), "persistent")
     assert nbytes is None and "changed" in why
 
 
@@ -60,7 +65,7 @@ def test_traffic_survives_an_edit_of_comments_only(tmp_path, monkeypatch):
     src = capture(tmp_path, monkeypatch)
     src[0].write_bytes(b"// what k does\n__global__ void   k() { /* nothing */ }\n")
     src[1].write_bytes(b"// another header comment\n")
-    assert bench.recorded_traffic(args(), "persistent")[0] == 12345678
+    assert recorded_traffic(args(), "persistent")[0] == 12345678
 
 
 def test_the_committed_summary_records_a_hash_and_traffic():
@@ -72,8 +77,9 @@ def test_streaming_bytes_reproduce_the_stated_figures():
     """The roofline's per-sample-step bytes against the figures the
     measurement definition states: 21.0 KB per sample (784->400, learning on),
     23.4 KB at B=1024 and 30.8 KB at B=256, 11.5 KB per sample without
-    learning, and about 584 KB at 784->6400, B=256 (195 KB of state and
-    392 KB of W)."""
+    learning; at 784->6400, B=256 the 195 KB of state plus W charged for the
+    master the timed form keeps: 8 B per weight for an FP32 master
+    (351.8 KB), 16 B for a compensated (hi, lo) pair."""
     import bench
     f = bench.streaming_bytes_per_sample_step
     per_on = f(10 ** 12, 400, 784, True)                 # B -> inf: the per-sample part
@@ -82,8 +88,23 @@ def test_streaming_bytes_reproduce_the_stated_figures():
     assert round(f(256, 400, 784, True) / 1e3, 1) == 30.8
     assert round(f(10 ** 12, 400, 784, False) / 1e3, 1) == 11.5
     big = f(256, 6400, 784, True)
-    assert abs(big - (29 * 6400 + 12 * 784) - 20 * 784 * 6400 / 256) < 1e-6
-    assert 580e3 < big < 590e3
+    assert abs(big - (29 * 6400 + 12 * 784) - 8 * 784 * 6400 / 256) < 1e-6
+    assert round(big / 1e3, 1) == 351.8
+    comp = f(256, 6400, 784, True, "compensated")
+    assert abs(comp - big - 8 * 784 * 6400 / 256) < 1e-6
+
+
+def test_issue_figures_come_with_the_traffic(tmp_path, monkeypatch):
+    """The limiter figures of the summary (issue slots, warp instructions) are
+    reported with its traffic and dropped with it once the kernel changes."""
+    src = capture(tmp_path, monkeypatch)
+    prof = tmp_path / "summary.md"
+    prof.write_text(prof.read_text() + "issue active pct: 67.6\nwarp instructions per launch: 6680000000\n")
+    rec, _ = bench.recorded_profile(args(), "persistent")
+    assert rec == {"traffic": 12345678, "issue_active_pct": 67.6,
+                   "warp_instructions_per_launch": 6680000000}
+    src[0].write_bytes(src[0].read_bytes() + b"__device__ int y;\n")
+    assert bench.recorded_profile(args(), "persistent")[0] is None
 
 
 def _replica_rank(rank, world, port, out):

@@ -6,6 +6,8 @@ the batch reduction of the STDP updates), so rasters, voltages, traces,
 refractory counters, weights and thresholds must agree bit for bit, with
 learning on or off, for every reduction and run mode.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -24,6 +26,9 @@ def _built():
     from paper_1909_02549_gb300 import build
     build.build()
     oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)    # same bits at any thread count
+    yield
+    oracle.set_threads(1)
 
 
 def snn():
@@ -442,6 +447,19 @@ def test_784x6400_batch256_learning_first_steps():
     for mode in ("persistent", "graph"):
         _, g = gpu_run(p, r, s, w, 12, mode=mode)
         assert_parity(g, st, rec)
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+def test_784x6400_batch32_learning_whole_presentation(reduce):
+    """The 784 -> 6400 layer with learning on for a whole presentation (T =
+    250), in every run mode and reduction, element by element against the
+    whole-batch oracle.  The run passes through the burst steps in which most
+    columns fire at once (the persistent form's grouped post-column pass, and
+    the max reduction's column-at-a-time pass, at their heaviest)."""
+    p, r, s, w = synth.workload(32, 6400)
+    st, rec = parity_all_modes(p, r, s, w, 250, reduce=reduce)
+    per_step = rec.raster_e.reshape(250, -1).sum(1)
+    assert per_step.max() > 1000 and not np.array_equal(st.w, w)
 
 
 def test_784x400_batch1024_learning_off_sampled():

@@ -1,10 +1,11 @@
 """Serving with continuous batching: requests of different lengths arrive while
 others run, are admitted as slots free up, retire mid-run and are backfilled.
-Each result must equal the request run alone (snn_run, B = 1, learning off),
-bit for bit like every parity check here."""
+Each result must equal the CPU oracle's run of that request alone (B = 1,
+learning off), bit for bit like every parity check here."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1909_02549_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -17,6 +18,7 @@ def _built():
         pytest.skip("no GPU")
     from paper_1909_02549_gb300 import build
     build.build()
+    oracle.build()
 
 
 def snn():
@@ -25,12 +27,11 @@ def snn():
 
 
 def alone_counts(p, w, wprec, rates, seed, T):
-    m = snn()
-    net = m.Network(p, w_init=w, wprec=wprec)
-    net.run(rates[None, :].copy(), np.array([seed], np.uint64), T, learn=False, mode="step")
-    out = net.read("spike_counts")[0]
-    net.close()
-    return out
+    """The oracle's excitatory spike counts of the request run alone."""
+    st = oracle.new_state(p, 1, w)
+    rec = oracle.run(p, st, rates[None, :].copy(), np.array([seed], np.uint64), T, learn=False,
+                     wprec=wprec)
+    return rec.counts_e[0]
 
 
 @pytest.mark.parametrize("wprec,neuron", [(0, 0), (2, 0), (0, 1)])

@@ -98,8 +98,8 @@ def _plant(name, tmp):
         open(os.path.join(d, f), "w").write(code)
         files.append(os.path.join(d, f))
     so = os.path.join(d, "liboracle.so")
-    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", so, *files])
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math",
+                           "-fopenmp", "-fPIC", "-shared", "-o", so, *files])
     env = dict(os.environ, SNN_ORACLE_LIB=so)
     r = subprocess.run([sys.executable, "-m", "pytest", pins, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True)

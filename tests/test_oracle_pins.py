@@ -712,3 +712,21 @@ def test_fp8_current_is_within_the_format_error_of_fp32():
     bound = ra.raster_in[0].astype(np.float64) @ (np.abs(w).astype(np.float64) * 2.0 ** -4)
     diff = np.abs(ra.cur_in[0].astype(np.float64) - rb.cur_in[0].astype(np.float64))
     assert np.all(diff <= bound + 1e-6) and diff.max() > 0
+
+
+@pytest.mark.parametrize("reduce", ["mean", "max"])
+def test_thread_count_does_not_change_the_result(reduce):
+    """The oracle splits independent elements over OpenMP threads; each element
+    keeps its operations and its ascending-b order, so 1 and 5 threads give the
+    same bits (learning on: the batch reduction runs per input row)."""
+    p, r, s, w = synth.workload(7, 90)
+    out = []
+    for n in (1, 5):
+        oracle.set_threads(n)
+        st = oracle.new_state(p, 7, w)
+        rec = oracle.run(p, st, r, s, 120, learn=True, reduce=reduce)
+        out.append((rec.raster_e, st.v_e, st.w, st.theta, st.x_post))
+    oracle.set_threads(1)
+    assert out[0][0].sum() > 0
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)

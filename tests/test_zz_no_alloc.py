@@ -3,13 +3,15 @@ allocate device memory (plug-ins inside runtimes that own all device memory,
 latency-critical loops that cannot pay for an allocation's synchronisation).
 
 Its spike counts must equal those of the allocating path (snn_create +
-snn_run with learning off + snn_read_state), bit for bit like every parity
-check in this suite, on two calls in a row that reuse the same fixed scratch
-array.  This file is named so that pytest collects it last.
+snn_run with learning off + snn_read_state) and those of the CPU oracle, bit
+for bit like every parity check in this suite, on two calls in a row that
+reuse the same fixed scratch array.  This file is named so that pytest
+collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1909_02549_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -23,6 +25,7 @@ def _built():
         pytest.skip("no GPU")
     from paper_1909_02549_gb300 import build
     build.build()
+    oracle.build()
 
 
 def snn():
@@ -71,6 +74,29 @@ def test_noalloc_matches_the_allocating_path_on_two_calls_in_a_row(neuron):
         want = counts_from_snn_run(p, w, theta, r, s, T)
         assert want.sum() > 0
         assert np.array_equal(got, want)
+        st = oracle.new_state(p, len(s), w, theta=theta)
+        rec = oracle.run(p, st, r, s, T, learn=False)
+        assert np.array_equal(got, rec.counts_e)
+
+
+def test_noalloc_rejects_what_snn_run_refuses():
+    """An unknown neuron model and a non-finite time step are refused, as
+    snn_create and snn_run refuse them, before any launch."""
+    m = snn()
+    p, rates, seeds, w = synth.workload(2, 20)
+    w_d = torch.from_numpy(w).cuda()
+    th_d = torch.zeros(20, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2 * 20, dtype=torch.int32, device="cuda")
+    spec, _ = m.spec_from_params(p)
+    spec.neuron = 7
+    with pytest.raises(m.SNNError) as e:
+        m.snn_infer_noalloc(spec, w_d, th_d, dev(rates), dev(seeds), 2, 5, 1.0, out)
+    assert e.value.status == m.SNN_ERR_ARG
+    spec, _ = m.spec_from_params(p)
+    for dt in (float("inf"), float("nan")):
+        with pytest.raises(m.SNNError) as e:
+            m.snn_infer_noalloc(spec, w_d, th_d, dev(rates), dev(seeds), 2, 5, dt, out)
+        assert e.value.status == m.SNN_ERR_ARG
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
