@@ -334,9 +334,12 @@ def run_reference(a):
 
 
 KERNEL_SOURCES = ("paper_1909_02549_gb300/csrc/snn_persistent.cu",
-                  "paper_1909_02549_gb300/csrc/snn_internal.cuh")
+                  "paper_1909_02549_gb300/csrc/snn_internal.cuh",
+                  "paper_1909_02549_gb300/csrc/snn_draw.cuh")
 PERSISTENT_PROFILE = "profiles/k_persistent_784x6400_b256.md"
-REC_SOURCES = ("paper_1909_02549_gb300/csrc/snn_rec.cu",)
+REC_SOURCES = ("paper_1909_02549_gb300/csrc/snn_rec.cu",
+               "paper_1909_02549_gb300/csrc/snn_draw.cuh",
+               "paper_1909_02549_gb300/csrc/snn_tc.cuh")
 REC_PROFILE = "profiles/k_rec_dense_1024x4096_b4096.md"
 
 

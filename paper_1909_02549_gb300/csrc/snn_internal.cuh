@@ -1,6 +1,7 @@
 // Internal declarations shared by the kernels and the C ABI implementation.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -192,6 +193,46 @@ inline cudaError_t prof_stop(Prof* p, cudaStream_t s) {
     if (!p) return cudaSuccess;
     return prof_record(p, s);
 }
+
+// Tensor form (snn_tensor.cu): per-step launches whose synaptic current and
+// batch-reduced STDP update are tcgen05 products.  Operands are bfloat16
+// matrices with K contiguous; FP32 values enter as a sum of bfloat16 terms
+// (three terms hold every FP32 value exactly).
+//   current  I[j][b] = sum_s WT_s[j][:] . SIN[b][:]          (M = neurons, N = samples)
+//   update   DW[i][j] = sum_s XPRE_s[i][:] . SPOST[j][:] + sum_q SINT[i][:] . XPOST_q[j][:]
+//            (M = inputs, N = neurons, K = samples), XPRE = nu_post * x_pre and
+//            XPOST = -(nu_pre * x_post), split over KS slices of the batch whose
+//            partial sums are added in slice order before the weight update.
+struct TBufs {
+    int NW, NXP, NXQ;       // bfloat16 terms of W, of XPRE and of XPOST
+    int Np, Kp, Bp;         // neurons padded to 128, inputs to 64, samples to 64
+    int TB;                 // samples per tile of the current
+    int TNJ, ntj, mti, KS;  // update: neurons per tile, neuron tiles, input tiles, batch slices
+    int dense;              // 1: the current is the tcgen05 product; 0: the ordered gather
+    uint16_t* wt;           // [NW][Np][Kp]   W transposed, split
+    uint16_t* sin;          // [Bp][Kp]       input spikes of the step (0/1)
+    uint16_t* sint;         // [n_in][Bp]     the same, transposed
+    uint16_t* xpre;         // [NXP][n_in][Bp] nu_post * x_pre, split
+    uint16_t* spost;        // [Np][Bp]       excitatory spikes of the step (0/1)
+    uint16_t* xpost;        // [NXQ][Np][Bp]  -(nu_pre * x_post), split
+    float* part;            // [KS][n_in][N]  the update's per-slice sums
+    uint32_t* colcnt;       // [N]            excitatory spikes of column j in the step
+    CUtensorMap m_wt, m_sin, m_xpre, m_sint, m_spost, m_xpost;
+};
+
+// Sizes and tiles of the tensor form for a batch of B (dense: tcgen05 current).
+TBufs tensor_plan(const Consts& c, int dense, int sms);
+size_t tensor_bytes(const TBufs& t, const Consts& c);
+// Carve the buffers out of `base` (tensor_bytes bytes, zeroed by the caller)
+// and encode the tensor maps; false if the driver refuses a map.
+bool tensor_bind(TBufs& t, const Consts& c, void* base);
+// Whether the tensor form computes this run (reduction, rule, weight precision).
+bool tensor_supports(const Consts& c);
+// At the start of a run: W's transposed split from the master, column counters.
+cudaError_t launch_tensor_begin(const Consts& c, const Bufs& d, const TBufs& t, cudaStream_t s, Prof* prof);
+// One time step: encode, current and neurons, and (learning) the update.
+cudaError_t launch_tensor_step(const Consts& c, const Bufs& d, const TBufs& t, int t_local, cudaStream_t s,
+                               Prof* prof);
 
 // Launchers (snn_step.cu).
 cudaError_t launch_begin_run(const Consts& c, const Bufs& d, const float* rates,

@@ -56,11 +56,18 @@
 
 #include "snn.h"
 #include "snn_draw.cuh"
+#include "snn_tc.cuh"
 
 namespace {
 
 using snn::poisson_threshold;
 using snn::splitmix64;
+using snn::tc::mbar_expect_tx;
+using snn::tc::mbar_init;
+using snn::tc::sdesc;
+using snn::tc::su32;
+using snn::tc::tma_2d;
+using snn::tc::tmem_ld16;
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
@@ -105,10 +112,9 @@ constexpr int GA_BYTES = GBM * GBK * 2, GB_BYTES = GBN * GBK * 2, GSTAGE = GA_BY
 constexpr int GSMEM = GSTAGES * GSTAGE + 1024 + 256;
 constexpr int GEPI_WARPS = 8, GTHREADS = 64 + 32 * GEPI_WARPS;
 constexpr unsigned long long GWAIT_NS = 2000000000ull;   // bounded waits: 2 s, then the error flag
-// instruction descriptor: FP32 accumulator, bfloat16 A and B, both K-major, M=128, N=256
-__host__ __device__ constexpr uint32_t gidesc(int n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(GBM >> 4) << 24);
-}
+// instruction descriptor: FP32 accumulator, bfloat16 A and B, both K-major, M=128
+__host__ __device__ constexpr uint32_t gidesc(int n) { return snn::tc::idesc_bf16(n); }
+static_assert(GBM == 128, "the instruction descriptor is for M = 128");
 
 // Tiles of the dense form: ntn_drive neuron tiles of GBN columns per 128 samples,
 // then, when the readout is fused (n_out <= GBN), one readout tile whose
@@ -119,49 +125,9 @@ struct DenseGeom {
     int ntn_drive, ntn, ntiles, fused, n_ro, a_per, enc_next;
 };
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ unsigned long long now_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
-    return ok != 0;
-}
 // waits for the phase with the given parity to complete; false after GWAIT_NS
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-    if (mbar_try(b, parity)) return true;
-    const unsigned long long t0 = now_ns();
-    for (;;) {
-        for (int i = 0; i < 64; ++i)
-            if (mbar_try(b, parity)) return true;
-        if (now_ns() - t0 > GWAIT_NS) return false;
-    }
-}
-__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* tm, int c0, int c1, uint64_t* bar) {
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-                 "[%0], [%1, {%2, %3}], [%4];"
-                 :: "r"(su32(dst)), "l"((uint64_t)tm), "r"(c0), "r"(c1), "r"(su32(bar)) : "memory");
-}
-// shared-memory matrix descriptor: K-major rows of 128 bytes, 128-byte swizzle,
-// groups of 8 rows 1024 bytes apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
+    return snn::tc::mbar_wait(b, parity, GWAIT_NS);
 }
 
 __global__ void k_rec_begin(RecConsts c, RecBufs d, const float* __restrict__ rates,
@@ -313,14 +279,6 @@ __device__ __forceinline__ void dense_encode_group(const RecConsts& c, const Rec
         }
     }
     store_operand_word(c, d, b, live, word, (int)(tt & 1ull), a0, nu);
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
-                 "tcgen05.wait::ld.sync.aligned;"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr) : "memory");
 }
 
 // Dense form, epilogue of one warp's half tile (32 samples x 128 neurons j0..,
@@ -719,30 +677,11 @@ __global__ void k_rec_pack(const uint16_t* __restrict__ w_ff, const uint16_t* __
     wt[idx] = w;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
-                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                  CUtensorMapFloatOOBfill);
-
 // a [rows][K] bfloat16 matrix in tiles of 64 x box_rows with the 128-byte swizzle
 // (rows past the end read as zero)
 bool encode_map(CUtensorMap* m, void* base, int rows, int K, int box_rows) {
-    static EncodeTiledFn enc = nullptr;
-    if (!enc) {
-        void* fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return false;
-        enc = (EncodeTiledFn)fn;
-    }
-    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)GBK, (cuuint32_t)box_rows};
-    const cuuint32_t es[2] = {1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    static_assert(GBK == snn::tc::KB, "tiles are 64 K-elements wide");
+    return snn::tc::encode_bf16_map(m, base, rows, K, box_rows);
 }
 
 bool finite_pos(float x) { return std::isfinite(x) && x > 0.0f; }
