@@ -90,12 +90,25 @@ typedef enum { SNN_W_FP32 = 0, SNN_W_BF16 = 1, SNN_W_FP8E4M3 = 2 } snn_wprec;
                                          barrier waits for an arrival that never comes, so
                                          its bounded wait (a few ms here) runs out and the run
                                          reports SNN_ERR_TIMEOUT; no real hang occurs */
+#define SNN_TENSOR_GATHER   (1u << 6) /* with SNN_MODE_TENSOR: sum the synaptic current over
+                                         the active inputs in ascending order (exact) instead
+                                         of the tensor-core product; the update stays a product */
 #define SNN_MODE_STEP       (0u << 8) /* one kernel launch per phase per time step */
 #define SNN_MODE_GRAPH      (1u << 8) /* the T-step launch sequence captured once as a
                                          CUDA graph and replayed */
 #define SNN_MODE_PERSISTENT (2u << 8) /* one persistent cooperative kernel for all T steps */
-#define SNN_MODE_AUTO       (3u << 8) /* library picks the mode */
-#define SNN_MODE_MASK       (3u << 8)
+#define SNN_MODE_AUTO       (3u << 8) /* library picks the mode (see snn_tune) */
+#define SNN_MODE_TENSOR     (4u << 8) /* per-step launches, captured as a CUDA graph, in which
+                                         the synaptic current (Sec. "Implementation": the
+                                         current as a matrix multiplication) and the STDP
+                                         update reduced over the batch (Sec. "Reduction
+                                         methods") are tcgen05 tensor-core products of
+                                         bfloat16 operands with FP32 accumulation; FP32
+                                         values enter as three bfloat16 terms, so every
+                                         product term is exact and only the order of the
+                                         FP32 sums differs from the definition.  Pair rule,
+                                         sum or mean reduction, FP32 or BF16 weights. */
+#define SNN_MODE_MASK       (7u << 8)
 
 /* Network specification (units: mV, ms, Hz).  snn_spec_default fills the
  * 784 -> n_exc Diehl & Cook parameter set. */

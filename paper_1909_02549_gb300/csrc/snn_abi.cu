@@ -28,12 +28,13 @@ thread_local std::string g_create_error;
 
 struct GraphKey {
     int B = -1, T = -1, learn = -1, reduce = -1, rec_raster = -1, rec_input = -1, profile = -1;
+    int form = -1;             // 0 per-step kernels, 1 tensor form (product), 2 tensor form (gather)
     uint32_t dt_bits = 0;
     uint64_t generation = 0;
     bool operator==(const GraphKey& o) const {
         return B == o.B && T == o.T && learn == o.learn && reduce == o.reduce &&
                rec_raster == o.rec_raster && rec_input == o.rec_input && profile == o.profile &&
-               dt_bits == o.dt_bits &&
+               form == o.form && dt_bits == o.dt_bits &&
                generation == o.generation;
     }
 };
@@ -58,6 +59,11 @@ struct snn_net {
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
     cudaStream_t last = nullptr;
+    // tensor form: buffers of the current batch (one allocation)
+    snn::TBufs tb{};
+    void* tb_mem = nullptr;
+    int tb_B = 0, tb_dense = -1, tb_wprec = -1;
+    int num_sms = 0;
     // graph cache
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -124,6 +130,10 @@ void free_batch(snn_net* n) {
                     d.x_post, d.st, d.cnt, d.postT, d.spkT, d.counts, n->rates_stage,
                     n->seeds_stage};
     for (void* p : ptrs) if (p) cudaFree(p);
+    if (n->tb_mem) cudaFree(n->tb_mem);
+    n->tb_mem = nullptr;
+    n->tb_B = 0;
+    n->tb_dense = -1;
     d.thr = nullptr; d.seeds = nullptr; d.x_pre = nullptr; d.inb = nullptr; d.preT = nullptr;
     d.act_idx = nullptr; d.act_cnt = nullptr;
     d.v_e = nullptr; d.v_i = nullptr; d.x_post = nullptr; d.st = nullptr; d.cnt = nullptr;
@@ -176,6 +186,30 @@ snn_status ensure_raster(snn_net* n, uint32_t** buf, size_t* cap, size_t words) 
     return SNN_OK;
 }
 
+// The tensor form's buffers for this batch, product or gather current (one
+// zeroed allocation; the tensor maps are encoded against it).
+snn_status ensure_tensor(snn_net* n, const snn::Consts& c, int dense) {
+    if (n->tb_mem && n->tb_B == c.B && n->tb_dense == dense && n->tb_wprec == c.wprec) return SNN_OK;
+    if (n->tb_mem) {
+        cudaFree(n->tb_mem);
+        n->tb_mem = nullptr;
+    }
+    if (n->num_sms == 0)
+        CUDA_TRY(n, cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, n->device));
+    snn::TBufs t = snn::tensor_plan(c, dense, n->num_sms);
+    const size_t bytes = snn::tensor_bytes(t, c);
+    CUDA_TRY(n, cudaMalloc(&n->tb_mem, bytes));
+    CUDA_TRY(n, cudaMemset(n->tb_mem, 0, bytes));
+    if (!snn::tensor_bind(t, c, n->tb_mem))
+        return fail(n, SNN_ERR_CUDA, "snn_run: the driver refused a tensor map of the tensor form");
+    n->tb = t;
+    n->tb_B = c.B;
+    n->tb_dense = dense;
+    n->tb_wprec = c.wprec;
+    n->generation++;
+    return SNN_OK;
+}
+
 snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce, unsigned flags) {
     const snn_spec& s = n->spec;
     snn::Consts c{};
@@ -221,8 +255,9 @@ snn_status check_device_error(snn_net* n) {
         cudaMemset(n->d.err, 0, 4);
         n->state_valid = false;
         return fail(n, SNN_ERR_TIMEOUT,
-                    "a grid barrier of the persistent kernel timed out (code 0x%x); the state of "
-                    "that run is invalid", e);
+                    "a bounded device wait gave up (code 0x%x: 1 a grid barrier of the persistent "
+                    "kernel, 4 a pipeline wait of the tensor form); the state of that run is "
+                    "invalid", e);
     }
     return SNN_OK;
 }
@@ -375,9 +410,11 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     if (reduce < SNN_REDUCE_SUM || reduce > SNN_REDUCE_MAX)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown reduce %d", reduce);
     const unsigned known = SNN_CONTINUE | SNN_RECORD_RASTER | SNN_RECORD_INPUT | SNN_HOST_INPUTS |
-                           SNN_PROFILE | SNN_TEST_BARRIER_TIMEOUT | SNN_MODE_MASK;
+                           SNN_PROFILE | SNN_TEST_BARRIER_TIMEOUT | SNN_TENSOR_GATHER | SNN_MODE_MASK;
     if (flags & ~known)
         return fail(n, SNN_ERR_ARG, "snn_run: unknown flag bits 0x%x", flags & ~known);
+    if ((flags & SNN_MODE_MASK) > SNN_MODE_TENSOR)
+        return fail(n, SNN_ERR_ARG, "snn_run: unknown mode 0x%x", flags & SNN_MODE_MASK);
     const int R_e = steps_of(n->spec.e_refrac_ms, dt), R_i = steps_of(n->spec.i_refrac_ms, dt);
     if (R_e > 255 || R_i > 255)
         return fail(n, SNN_ERR_ARG, "snn_run: refractory period exceeds 255 steps at this dt");
@@ -454,10 +491,20 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
         pp = &prof;
     }
     const snn::Consts c = make_consts(n, B, dt, learn, reduce, flags);
+    unsigned mode = flags & SNN_MODE_MASK;
+    const int dense = (flags & SNN_TENSOR_GATHER) ? 0 : 1;
+    if (mode == SNN_MODE_TENSOR) {
+        if (!snn::tensor_supports(c))
+            return fail(n, SNN_ERR_ARG,
+                        "snn_run: the tensor form takes the pair rule, the sum or mean reduction and "
+                        "FP32 or BF16 weights");
+        if (n->last) CUDA_TRY(n, cudaStreamSynchronize(n->last));
+        snn_status r = ensure_tensor(n, c, dense);
+        if (r != SNN_OK) return r;
+    }
     const snn::Bufs d = run_bufs(n);
     CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st, pp));
 
-    unsigned mode = flags & SNN_MODE_MASK;
     if (mode == SNN_MODE_PERSISTENT || mode == SNN_MODE_AUTO) {
         int used = 0;
         CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used, pp));
@@ -468,12 +515,15 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
                         "or step mode)");
         mode = used ? SNN_MODE_PERSISTENT : SNN_MODE_GRAPH;
     }
+    if (mode == SNN_MODE_TENSOR) CUDA_TRY(n, snn::launch_tensor_begin(c, d, n->tb, st, pp));
     if (mode == SNN_MODE_STEP) {
         for (int t = 0; t < T; ++t) CUDA_TRY(n, snn::launch_step(c, d, t, st, pp));
-    } else if (mode == SNN_MODE_GRAPH) {
+    } else if (mode == SNN_MODE_GRAPH || mode == SNN_MODE_TENSOR) {
+        const bool tensor = mode == SNN_MODE_TENSOR;
         GraphKey key;
         key.B = B; key.T = T; key.learn = c.learn; key.reduce = reduce;
         key.rec_raster = c.rec_raster; key.rec_input = c.rec_input; key.profile = profile ? 1 : 0;
+        key.form = tensor ? (dense ? 1 : 2) : 0;
         std::memcpy(&key.dt_bits, &dt, 4);
         key.generation = n->generation;
         if (!n->gexec || !(key == n->gkey)) {
@@ -487,7 +537,8 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
             cudaError_t le = cudaSuccess;
             if (pp) pp->capturing = true;
             for (int t = 0; t < T && le == cudaSuccess; ++t)
-                le = snn::launch_step(c, d, t, n->cap, pp);
+                le = tensor ? snn::launch_tensor_step(c, d, n->tb, t, n->cap, pp)
+                            : snn::launch_step(c, d, t, n->cap, pp);
             if (pp) pp->capturing = false;
             cudaError_t ee = cudaStreamEndCapture(n->cap, &g);
             CUDA_TRY(n, le);

@@ -34,8 +34,11 @@ SNN_MODE_STEP = 0 << 8
 SNN_MODE_GRAPH = 1 << 8
 SNN_MODE_PERSISTENT = 2 << 8
 SNN_MODE_AUTO = 3 << 8
+SNN_MODE_TENSOR = 4 << 8
+SNN_TENSOR_GATHER = 1 << 6
 MODES = {"step": SNN_MODE_STEP, "graph": SNN_MODE_GRAPH, "persistent": SNN_MODE_PERSISTENT,
-         "auto": SNN_MODE_AUTO}
+         "auto": SNN_MODE_AUTO, "tensor": SNN_MODE_TENSOR,
+         "tensor_gather": SNN_MODE_TENSOR | SNN_TENSOR_GATHER}
 
 (SNN_FIELD_V_EXC, SNN_FIELD_V_INH, SNN_FIELD_REF_EXC, SNN_FIELD_REF_INH, SNN_FIELD_X_PRE,
  SNN_FIELD_X_POST, SNN_FIELD_THETA, SNN_FIELD_SPIKE_COUNTS, SNN_FIELD_RASTER_EXC,
