@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="persistent", choices=["step", "graph", "persistent", "auto"])
+    ap.add_argument("--mode", default="persistent",
+                    choices=["step", "graph", "persistent", "auto", "tensor", "tensor_gather"])
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--n-exc", type=int, default=6400)
     ap.add_argument("--T", type=int, default=250)
@@ -78,6 +79,10 @@ def parse():
                          "instead (one JSON line)")
     ap.add_argument("--no-gather", action="store_true",
                     help="with --rec: skip the exact gather form's presentation")
+    ap.add_argument("--sweep", action="store_true",
+                    help="the batch sweep instead: 784->400 at B=1..1024 (mean and sum) and "
+                         "784->6400 at B=256 and 1024 in every run form (one JSON line)")
+    ap.add_argument("--sweep-modes", default="step,graph,persistent,tensor,tensor_gather")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="the CPU oracle against batch size (784->100 and 784->400) instead "
                          "(one JSON line; needs no GPU)")
@@ -228,6 +233,8 @@ def streaming_bytes_per_sample_step(B: int, N: int, NI: int, learn: bool,
 def launches_per_run(mode: str, T: int, learn: bool) -> int:
     if mode == "persistent":
         return 2
+    if mode.startswith("tensor"):
+        return 2 + T * (4 if learn else 2)
     return 1 + T * (3 if learn else 2)
 
 
@@ -274,6 +281,73 @@ def time_oracle(a, seconds: float, max_T: int | None = None):
                                                "learning off" if a.no_learn else "learning on",
                                                a.reduce, cores, el),
             "single_thread": {"value": v1, "sample": "first %d steps, %.1f s" % (T1, el1)}}
+
+
+def sweep_point(snn, torch, flush, B, N, T, mode, reduce, learn, reps=3, warm=2):
+    """Device time of one presentation of the B x 784 -> N workload in one run
+    form (W and theta restored before each, L2 flushed), and the per-kernel
+    split of a profiled presentation; None where the form does not take it."""
+    from paper_1909_02549_gb300 import synth
+    p, r, s, w = synth.workload(B, N)
+    net = snn.Network(p, w_init=w)
+    rd = torch.from_numpy(r).cuda()
+    sd = torch.from_numpy(s.view(np.int64)).cuda()
+    w0 = torch.from_numpy(w).cuda()
+    th0 = torch.zeros(N, dtype=torch.float64, device="cuda")
+    try:
+        def one(profile=False):
+            snn.snn_write_weights(net.handle, w0)
+            snn.snn_write_state(net.handle, snn.SNN_FIELD_THETA, th0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.run(rd, sd, T, learn=learn, reduce=reduce, mode=mode, profile=profile)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+        for _ in range(warm):
+            one()
+        ms = min(one() for _ in range(reps))
+        one(profile=True)
+        prof = {k: round(v[0], 4) for k, v in snn.snn_profile(net.handle).items() if v[1]}
+    except snn.SNNError as e:
+        return {"B": B, "n_exc": N, "mode": mode, "reduce": reduce, "error": str(e)[:160]}
+    finally:
+        net.close()
+    per = streaming_bytes_per_sample_step(B, N, 784, learn)
+    return {"B": B, "n_exc": N, "mode": mode, "reduce": reduce, "learn": learn,
+            "ms_per_presentation": ms, "sample_timesteps_per_s": B * T / (ms * 1e-3),
+            "roofline_frac": per * B * T / (ms * 1e-3) / peaks()["hbm_gbs"] / 1e9,
+            "kernel_ms": prof}
+
+
+def sweep_leg(a):
+    """sample-timesteps/s against batch size (784 -> 400, B = 1 .. 1024, pair
+    STDP with mean and sum reductions) and at 784 -> 6400 (B = 256, 1024), T =
+    250, in every run form; the fraction of the HBM roofline uses the
+    per-sample-step streaming bytes (FP32 master)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1909_02549_gb300 import snn
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    modes = a.sweep_modes.split(",")
+    rows = []
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    with ClockSampler(visible.split(",")[0] if visible else "0") as clk:
+        for reduce in ("mean", "sum"):
+            for B in (1, 4, 16, 64, 256, 1024):
+                for mode in modes:
+                    rows.append(sweep_point(snn, torch, flush, B, 400, a.T, mode, reduce, True))
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        for B in (256, 1024):
+            for mode in modes:
+                if mode == "step" and B == 1024:
+                    continue
+                rows.append(sweep_point(snn, torch, flush, B, 6400, a.T, mode, "mean", True, reps=2, warm=1))
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "batch sweep, 784->400 and 784->6400, pair STDP, T=%d, FP32" % a.T,
+                      "unit": UNIT, "rows": rows, "clocks": clk.summary()}), flush=True)
 
 
 def cpu_sweep_leg(a):
@@ -812,6 +886,9 @@ def main():
     a = parse()
     if a.cpu_sweep:
         cpu_sweep_leg(a)
+        return
+    if a.sweep:
+        sweep_leg(a)
         return
     if a.rec:
         rec_leg(a)

@@ -294,6 +294,38 @@ enum {
  * run was not profiled), SNN_ERR_CUDA. */
 SNN_API snn_status snn_profile(snn_net* net, double* ms, int* launches, int n);
 
+/* Tune the automatic choice (SNN_MODE_AUTO) for this network at batch B: runs
+ * T steps of each form that takes the run -- the graph of per-step launches,
+ * the persistent kernel, and the tensor form with the product and with the
+ * gathered current -- twice each (the first warms up allocation and graph
+ * capture), times the second with CUDA events on `cuda_stream`, and restores
+ * W and theta before every run and at the end, so tuning leaves them as they
+ * were.  It records the fastest form with the batch's measured densities
+ * (expected input spikes per input and step, from the Poisson thresholds, and
+ * excitatory spikes per neuron and step) under the key (B, learn, reduce);
+ * the layer widths are the network's own.  A later SNN_MODE_AUTO run with the
+ * same key takes the recorded form measured at the input density nearest to
+ * that of the last run (measured after each run of a tuned network and read
+ * back without synchronising); without an entry AUTO takes the persistent
+ * form where it fits, else the graph form.
+ *   rates_hz, seeds, B, T, dt_ms, learn, reduce: as for snn_run;
+ *   flags: 0 or SNN_HOST_INPUTS;
+ *   mode:  (may be NULL) the winner's SNN_MODE_* bits (| SNN_TENSOR_GATHER);
+ *   ms_per_step: (may be NULL) [4] device ms per time step of the graph,
+ *          persistent, tensor and tensor-gather forms (NaN where a form does
+ *          not take the run).
+ * Synchronises.  Afterwards the batch holds the state of the last timed run.
+ * Errors: those of snn_run, SNN_ERR_ARG (T <= 0, other flags, no form takes
+ * the run), SNN_ERR_OOM (the copies of W and theta). */
+SNN_API snn_status snn_tune(snn_net* net, const float* rates_hz, const uint64_t* seeds, int B, int T,
+                            float dt_ms, int learn, int reduce, unsigned flags, void* cuda_stream,
+                            unsigned* mode, double* ms_per_step);
+
+/* The form the last run took (SNN_MODE_STEP, _GRAPH, _PERSISTENT or _TENSOR,
+ * with SNN_TENSOR_GATHER for the gathered current); AUTO runs report the form
+ * they chose.  SNN_MODE_AUTO before any run or for NULL (no run reports it). */
+SNN_API unsigned snn_last_mode(const snn_net* net);
+
 /* Allocation-free, learning-off presentation of a batch.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory,
  * such as a plug-in running inside another runtime that owns all device

@@ -18,6 +18,7 @@ namespace snn {
 cudaError_t launch_clip_weights(float* W, size_t n, float w_min, float w_max, cudaStream_t s);
 cudaError_t launch_insert(const Consts& c, const Bufs& d, int field, const void* in, cudaStream_t s);
 cudaError_t launch_derive(const Consts& c, const Bufs& d, cudaStream_t s);
+cudaError_t launch_density(const Consts& c, const Bufs& d, double* out, cudaStream_t s);
 cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_t s,
                               int* used_persistent, Prof* prof);
 }
@@ -37,6 +38,15 @@ struct GraphKey {
                form == o.form && dt_bits == o.dt_bits &&
                generation == o.generation;
     }
+};
+
+// One measurement of snn_tune: the fastest form for a batch size, learning
+// flag and reduction at the measured input density.
+struct TuneEntry {
+    int B = 0, learn = 0, reduce = 0;
+    double rho_in = 0.0;       // expected input spikes per input and step
+    double rho_post = 0.0;     // excitatory spikes per neuron and step
+    unsigned mode = 0;         // the winner's mode bits (SNN_MODE_* | SNN_TENSOR_GATHER)
 };
 
 }  // namespace
@@ -64,6 +74,15 @@ struct snn_net {
     void* tb_mem = nullptr;
     int tb_B = 0, tb_dense = -1, tb_wprec = -1;
     int num_sms = 0;
+    // automatic choice: snn_tune's measurements and the last run's densities
+    std::vector<TuneEntry> tune;
+    double* dens_dev = nullptr;      // [2] device sums of the last measured run
+    double* dens_host = nullptr;     // [2] pinned copy
+    cudaEvent_t dens_ev = nullptr;
+    bool dens_pending = false;
+    double rho_in_last = -1.0, rho_post_last = -1.0;
+    int dens_B = 0, dens_T = 0;
+    unsigned last_mode = SNN_MODE_AUTO;   // the form the last run took (AUTO: none yet)
     // graph cache
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -283,6 +302,56 @@ size_t field_bytes(const snn_net* n, int field) {
     }
 }
 
+// Takes in the densities of an earlier measured run once its copy has landed
+// (never waits for it).
+void collect_density(snn_net* n) {
+    if (!n->dens_pending || cudaEventQuery(n->dens_ev) != cudaSuccess) return;
+    n->dens_pending = false;
+    const double bi = (double)n->dens_B * n->spec.n_in, bn = (double)n->dens_B * n->spec.n_exc;
+    if (bi > 0.0 && bn > 0.0 && n->dens_T > 0) {
+        n->rho_in_last = n->dens_host[0] / bi;
+        n->rho_post_last = n->dens_host[1] / (bn * n->dens_T);
+    }
+}
+
+// Launches the measurement of this run's densities and its copy to pinned
+// memory, read by a later call (one measurement in flight at a time).
+snn_status measure_density(snn_net* n, const snn::Consts& c, const snn::Bufs& d, int T, cudaStream_t st) {
+    collect_density(n);
+    if (n->dens_pending) return SNN_OK;
+    if (!n->dens_dev) {
+        CUDA_TRY(n, cudaMalloc((void**)&n->dens_dev, 2 * sizeof(double)));
+        CUDA_TRY(n, cudaMallocHost((void**)&n->dens_host, 2 * sizeof(double)));
+        CUDA_TRY(n, cudaEventCreateWithFlags(&n->dens_ev, cudaEventDisableTiming));
+    }
+    CUDA_TRY(n, snn::launch_density(c, d, n->dens_dev, st));
+    CUDA_TRY(n, cudaMemcpyAsync(n->dens_host, n->dens_dev, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(n, cudaEventRecord(n->dens_ev, st));
+    n->dens_pending = true;
+    n->dens_B = c.B;
+    n->dens_T = T;
+    return SNN_OK;
+}
+
+// SNN_MODE_AUTO: among snn_tune's entries for this batch size, learning flag
+// and reduction, the one measured at the input density nearest (in ratio) to
+// the last measured run's; 0 when there is none (then the persistent form if
+// it fits, else the graph form).
+unsigned auto_choice(snn_net* n, int B, int learn, int reduce, const snn::Consts& c) {
+    collect_density(n);
+    const TuneEntry* best = nullptr;
+    double best_d = 0.0;
+    for (const TuneEntry& e : n->tune) {
+        if (e.B != B || e.learn != learn || (learn && e.reduce != reduce)) continue;
+        const double dd = n->rho_in_last > 0.0 && e.rho_in > 0.0
+                              ? std::fabs(std::log(n->rho_in_last / e.rho_in)) : 0.0;
+        if (!best || dd < best_d) { best = &e; best_d = dd; }
+    }
+    if (!best) return 0u;
+    if ((best->mode & SNN_MODE_MASK) == SNN_MODE_TENSOR && !snn::tensor_supports(c)) return 0u;
+    return best->mode;
+}
+
 }  // namespace
 
 namespace snn {
@@ -392,6 +461,9 @@ snn_status snn_destroy(snn_net* n) {
     for (void* p : ptrs) if (p) cudaFree(p);
     if (n->gexec) cudaGraphExecDestroy(n->gexec);
     if (n->cap) cudaStreamDestroy(n->cap);
+    if (n->dens_dev) cudaFree(n->dens_dev);
+    if (n->dens_host) cudaFreeHost(n->dens_host);
+    if (n->dens_ev) cudaEventDestroy(n->dens_ev);
     for (cudaEvent_t e : n->prof_ev) cudaEventDestroy(e);
     delete n;
     return SNN_OK;
@@ -492,7 +564,18 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     }
     const snn::Consts c = make_consts(n, B, dt, learn, reduce, flags);
     unsigned mode = flags & SNN_MODE_MASK;
-    const int dense = (flags & SNN_TENSOR_GATHER) ? 0 : 1;
+    int dense = (flags & SNN_TENSOR_GATHER) ? 0 : 1;
+    bool auto_fallback = false;        // AUTO: persistent if it fits, else graph
+    if (mode == SNN_MODE_AUTO) {
+        const unsigned pick = auto_choice(n, B, c.learn, reduce, c);
+        if (pick == 0u) {
+            auto_fallback = true;
+            mode = SNN_MODE_PERSISTENT;
+        } else {
+            mode = pick & SNN_MODE_MASK;
+            dense = (pick & SNN_TENSOR_GATHER) ? 0 : 1;
+        }
+    }
     if (mode == SNN_MODE_TENSOR) {
         if (!snn::tensor_supports(c))
             return fail(n, SNN_ERR_ARG,
@@ -505,10 +588,10 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     const snn::Bufs d = run_bufs(n);
     CUDA_TRY(n, snn::launch_begin_run(c, d, r_dev, s_dev, cont ? 0 : 1, T, st, pp));
 
-    if (mode == SNN_MODE_PERSISTENT || mode == SNN_MODE_AUTO) {
+    if (mode == SNN_MODE_PERSISTENT) {
         int used = 0;
         CUDA_TRY(n, snn::launch_persistent(c, d, T, st, &used, pp));
-        if (!used && mode == SNN_MODE_PERSISTENT)
+        if (!used && !auto_fallback)
             return fail(n, SNN_ERR_ARG,
                         "snn_run: the persistent form needs the weight columns and traces of one "
                         "CTA in shared memory; this batch and layer do not fit (use the graph "
@@ -556,6 +639,11 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
     if (pp) {
         n->prof_n = pp->n;
         n->last_profiled = true;
+    }
+    n->last_mode = mode | (mode == SNN_MODE_TENSOR && !dense ? SNN_TENSOR_GATHER : 0u);
+    if (!n->tune.empty() && T > 0) {     // this run's densities, for the next automatic choice
+        snn_status r = measure_density(n, c, d, T, st);
+        if (r != SNN_OK) return r;
     }
     n->last = st;
     n->state_valid = true;
@@ -732,6 +820,106 @@ snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes,
     CUDA_TRY(n, cudaStreamSynchronize(st));
     return SNN_OK;
 }
+
+snn_status snn_tune(snn_net* n, const float* rates, const uint64_t* seeds, int B, int T, float dt,
+                    int learn, int reduce, unsigned flags, void* stream_, unsigned* mode_out,
+                    double* ms_out) {
+    if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_tune: net is NULL");
+    n->err.clear();
+    if (T <= 0) return fail(n, SNN_ERR_ARG, "snn_tune: T must be > 0");
+    if (flags & ~SNN_HOST_INPUTS) return fail(n, SNN_ERR_ARG, "snn_tune: only SNN_HOST_INPUTS is accepted");
+    cudaStream_t st = (cudaStream_t)stream_;
+    CUDA_TRY(n, cudaSetDevice(n->device));
+    if (n->last) CUDA_TRY(n, cudaStreamSynchronize(n->last));
+    const size_t nw = (size_t)n->spec.n_in * n->spec.n_exc, nt = (size_t)n->spec.n_exc;
+    float* w0 = nullptr;
+    double* th0 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    struct Cleanup {
+        float*& w; double*& th; cudaEvent_t& a; cudaEvent_t& b;
+        ~Cleanup() {
+            if (w) cudaFree(w);
+            if (th) cudaFree(th);
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } cleanup{w0, th0, e0, e1};
+    CUDA_TRY(n, cudaMalloc((void**)&w0, nw * 4));
+    CUDA_TRY(n, cudaMalloc((void**)&th0, nt * 8));
+    CUDA_TRY(n, cudaEventCreate(&e0));
+    CUDA_TRY(n, cudaEventCreate(&e1));
+    CUDA_TRY(n, cudaMemcpyAsync(w0, n->d.W, nw * 4, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(n, cudaMemcpyAsync(th0, n->d.theta, nt * 8, cudaMemcpyDeviceToDevice, st));
+    auto restore = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(n->d.W, w0, nw * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(n->d.theta, th0, nt * 8, cudaMemcpyDeviceToDevice, st);
+        return e;
+    };
+    const unsigned cand[4] = {SNN_MODE_GRAPH, SNN_MODE_PERSISTENT, SNN_MODE_TENSOR,
+                              SNN_MODE_TENSOR | SNN_TENSOR_GATHER};
+    double ms[4];
+    int best = -1;
+    for (int k = 0; k < 4; ++k) {
+        ms[k] = std::nan("");
+        for (int rep = 0; rep < 2; ++rep) {          // the first run warms (allocation, capture)
+            CUDA_TRY(n, restore());
+            CUDA_TRY(n, cudaEventRecord(e0, st));
+            const snn_status r = snn_run(n, rates, seeds, B, T, dt, learn, reduce,
+                                         cand[k] | (flags & SNN_HOST_INPUTS), st);
+            if (r == SNN_ERR_ARG) { n->err.clear(); break; }   // this form does not take the run
+            if (r != SNN_OK) return r;
+            CUDA_TRY(n, cudaEventRecord(e1, st));
+            CUDA_TRY(n, cudaStreamSynchronize(st));
+            if (snn_status de = check_device_error(n)) return de;
+            if (rep == 1) {
+                float t = 0.0f;
+                CUDA_TRY(n, cudaEventElapsedTime(&t, e0, e1));
+                ms[k] = (double)t / T;
+                if (best < 0 || ms[k] < ms[best]) best = k;
+            }
+        }
+    }
+    if (best < 0) return fail(n, SNN_ERR_ARG, "snn_tune: no form takes this run");
+    // the batch's densities, from the last run (same rates and seeds)
+    if (!n->dens_dev) {
+        CUDA_TRY(n, cudaMalloc((void**)&n->dens_dev, 2 * sizeof(double)));
+        CUDA_TRY(n, cudaMallocHost((void**)&n->dens_host, 2 * sizeof(double)));
+        CUDA_TRY(n, cudaEventCreateWithFlags(&n->dens_ev, cudaEventDisableTiming));
+    }
+    collect_density(n);
+    if (n->dens_pending) CUDA_TRY(n, cudaEventSynchronize(n->dens_ev));
+    n->dens_pending = false;
+    const snn::Consts c = make_consts(n, B, dt, learn, reduce, 0u);
+    double h[2] = {0.0, 0.0};
+    CUDA_TRY(n, snn::launch_density(c, run_bufs(n), n->dens_dev, st));
+    CUDA_TRY(n, cudaMemcpyAsync(h, n->dens_dev, sizeof h, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(n, cudaStreamSynchronize(st));
+    TuneEntry en;
+    en.B = B;
+    en.learn = learn ? 1 : 0;
+    en.reduce = reduce;
+    en.rho_in = h[0] / ((double)B * n->spec.n_in);
+    en.rho_post = h[1] / ((double)B * n->spec.n_exc * T);
+    en.mode = cand[best];
+    bool replaced = false;                           // one entry per key and density (within 1.5x)
+    for (TuneEntry& e : n->tune)
+        if (e.B == en.B && e.learn == en.learn && e.reduce == en.reduce && e.rho_in > 0.0 &&
+            std::fabs(std::log(en.rho_in / e.rho_in)) < std::log(1.5)) {
+            e = en;
+            replaced = true;
+        }
+    if (!replaced) n->tune.push_back(en);
+    n->rho_in_last = en.rho_in;
+    n->rho_post_last = en.rho_post;
+    CUDA_TRY(n, restore());
+    CUDA_TRY(n, cudaStreamSynchronize(st));
+    if (mode_out) *mode_out = cand[best];
+    if (ms_out)
+        for (int k = 0; k < 4; ++k) ms_out[k] = ms[k];
+    return SNN_OK;
+}
+
+unsigned snn_last_mode(const snn_net* n) { return n ? n->last_mode : SNN_MODE_AUTO; }
 
 snn_status snn_profile(snn_net* n, double* ms, int* launches, int count) {
     if (!n) return fail(nullptr, SNN_ERR_ARG, "snn_profile: net is NULL");

@@ -42,4 +42,13 @@ __device__ __forceinline__ bool poisson_spike(uint64_t seed, unsigned long long 
     return (uint32_t)(splitmix64(seed ^ splitmix64(ctr)) >> 32) < thr;
 }
 
+// The same draw with the sample-independent half SM(t * n_in + i) computed
+// once by the caller (poisson_counter_hash) and reused across samples.
+__device__ __forceinline__ uint64_t poisson_counter_hash(unsigned long long tt, int n_in, int i) {
+    return splitmix64((uint64_t)tt * (uint64_t)n_in + (uint64_t)i);
+}
+__device__ __forceinline__ bool poisson_spike_hashed(uint64_t seed, uint64_t counter_hash, uint32_t thr) {
+    return thr != 0u && (uint32_t)(splitmix64(seed ^ counter_hash) >> 32) < thr;
+}
+
 }  // namespace snn

@@ -199,15 +199,16 @@ inline cudaError_t prof_stop(Prof* p, cudaStream_t s) {
 // matrices with K contiguous; FP32 values enter as a sum of bfloat16 terms
 // (three terms hold every FP32 value exactly).
 //   current  I[j][b] = sum_s WT_s[j][:] . SIN[b][:]          (M = neurons, N = samples)
-//   update   DW[i][j] = sum_s XPRE_s[i][:] . SPOST[j][:] + sum_q SINT[i][:] . XPOST_q[j][:]
-//            (M = inputs, N = neurons, K = samples), XPRE = nu_post * x_pre and
-//            XPOST = -(nu_pre * x_post), split over KS slices of the batch whose
-//            partial sums are added in slice order before the weight update.
+//   update   DW[j][i] = sum_s SPOST[j][:] . XPRE_s[i][:] + sum_q XPOST_q[j][:] . SINT[i][:]
+//            (M = neurons, N = inputs, K = samples), XPRE = nu_post * x_pre and
+//            XPOST = -(nu_pre * x_post), split over KS slices of the batch (a
+//            thread-block cluster) whose partial tiles are added in slice order
+//            through distributed shared memory before the weight update.
 struct TBufs {
     int NW, NXP, NXQ;       // bfloat16 terms of W, of XPRE and of XPOST
     int Np, Kp, Bp;         // neurons padded to 128, inputs to 64, samples to 64
     int TB;                 // samples per tile of the current
-    int TNJ, ntj, mti, KS;  // update: neurons per tile, neuron tiles, input tiles, batch slices
+    int TNI, nti, KS;       // update: inputs per tile, input tiles, batch slices
     int dense;              // 1: the current is the tcgen05 product; 0: the ordered gather
     uint16_t* wt;           // [NW][Np][Kp]   W transposed, split
     uint16_t* sin;          // [Bp][Kp]       input spikes of the step (0/1)
@@ -215,7 +216,6 @@ struct TBufs {
     uint16_t* xpre;         // [NXP][n_in][Bp] nu_post * x_pre, split
     uint16_t* spost;        // [Np][Bp]       excitatory spikes of the step (0/1)
     uint16_t* xpost;        // [NXQ][Np][Bp]  -(nu_pre * x_post), split
-    float* part;            // [KS][n_in][N]  the update's per-slice sums
     uint32_t* colcnt;       // [N]            excitatory spikes of column j in the step
     CUtensorMap m_wt, m_sin, m_xpre, m_sint, m_spost, m_xpost;
 };

@@ -380,6 +380,25 @@ __global__ void k_clip_weights(float* W, size_t n, float w_min, float w_max) {
     }
 }
 
+// The run's measured densities for the automatic choice: out[0] += the
+// inputs' expected spikes per step (sum of thr / 2^32), out[1] += the
+// excitatory spikes of the run (sum of the counts); out is zeroed by the caller.
+__global__ void k_density(Consts c, Bufs d, double* out) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    double a = 0.0, b = 0.0;
+    for (size_t k = tid; k < (size_t)c.B * c.n_in; k += nth) a += (double)d.thr[k] * 0x1.0p-32;
+    for (size_t k = tid; k < (size_t)c.B * c.N; k += nth) b += (double)d.counts[k];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL, a, o);
+        b += __shfl_xor_sync(FULL, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], a);
+        atomicAdd(&out[1], b);
+    }
+}
+
 int grid_for(size_t n, int threads, int cap) {
     size_t g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -452,6 +471,14 @@ cudaError_t launch_insert(const Consts& c, const Bufs& d, int field, const void*
 cudaError_t launch_derive(const Consts& c, const Bufs& d, cudaStream_t s) {
     const size_t n = (size_t)c.N * c.Bw > (size_t)c.B ? (size_t)c.N * c.Bw : (size_t)c.B;
     k_derive<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(c, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density(const Consts& c, const Bufs& d, double* out, cudaStream_t s) {
+    const cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    const size_t n = (size_t)c.B * (c.n_in > c.N ? c.n_in : c.N);
+    k_density<<<grid_for(n, 256, 152 * 2), 256, 0, s>>>(c, d, out);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
                  : "r"(taddr) : "memory");
 }
 
+// Thread-block clusters: every thread of every CTA of the cluster arrives and
+// waits (release / acquire: shared-memory writes before the barrier are seen
+// by other CTAs' reads after it).  Without .aligned, so a warp need not be
+// converged.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// The address in CTA `rank`'s shared memory of this CTA's shared address.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float4 ld_cluster_f32x4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+    return v;
+}
+
 // Host: a [rows][K] bfloat16 matrix (row pitch K elements, K a multiple of 8)
 // as a tensor map of 64 x box_rows tiles with the 128-byte swizzle; rows and K
 // past the end read as zero.  False if the driver's encoder is unavailable or

@@ -15,12 +15,14 @@
 //   k_t_gcurrent  the same epilogue with the current gathered over the active
 //                 inputs in ascending order (no tensor cores; exact);
 //   k_t_dw        the STDP update reduced over the batch as one product with K =
-//                 samples (Sec. "Reduction methods"): DW[i][j] = sum_b
-//                 XPRE[b][i] SPOST[b][j] + SIN[b][i] XPOST[b][j] for one slice of
-//                 the batch per CTA;
-//   k_t_apply     the slices' sums added in slice order, the mean (or sum), the
-//                 clipped weight update, theta, and W's transposed split for the
-//                 next step.
+//                 samples (Sec. "Reduction methods"): DW[j][i] = sum_b
+//                 SPOST[b][j] XPRE[b][i] + XPOST[b][j] SIN[b][i], one slice of the
+//                 batch per CTA and the slices of a tile in one thread-block
+//                 cluster; the slices' partial tiles are added in slice order
+//                 through distributed shared memory, followed by the mean (or
+//                 sum), the clipped weight update, theta, and W's transposed split
+//                 for the next step;
+//   k_t_pack      at a run's start, W's transposed split from the master W.
 //
 // Precision: the spike operands are exact in bfloat16, and three bfloat16 terms
 // hold every FP32 value exactly, so each product term equals the definition's
@@ -107,7 +109,7 @@ __device__ __forceinline__ void split_bf16(float x, int n, uint16_t* out) {
 
 __host__ __device__ __forceinline__ int cur_stage_bytes(const TBufs& t) { return t.NW * TILE_BYTES + t.TB * 128; }
 __host__ __device__ __forceinline__ int dw_stage_bytes(const TBufs& t) {
-    return (t.NXP + 1) * TILE_BYTES + (1 + t.NXQ) * t.TNJ * 128;
+    return (1 + t.NXQ) * TILE_BYTES + (t.NXP + 1) * t.TNI * 128;
 }
 
 // ---------------------------------------------------------------- encode ---
@@ -130,15 +132,29 @@ __global__ void __launch_bounds__(256) k_t_encode(Consts c, Bufs d, TBufs t, int
     for (int tile = blockIdx.x; tile < c.Iw * nbt; tile += gridDim.x) {
         const int iw = tile % c.Iw, bb = tile / c.Iw;
         const int i = iw * 32 + lane;
-        for (int r = warp; r < 32; r += 8) {
+        const uint64_t hc = poisson_counter_hash(tt, c.n_in, i);   // shared by the tile's samples
+        uint32_t thr4[4];
+        float x4[4];
+        uint64_t seed4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {                  // the warp's four rows: loads first
+            const int b = bb * 32 + warp + 8 * q;
+            const bool ok = b < c.B && i < c.n_in;
+            const size_t o = (size_t)b * c.n_in + i;
+            thr4[q] = ok ? d.thr[o] : 0u;
+            x4[q] = ok ? d.x_pre[(size_t)xp * nbi + o] : 0.0f;
+            seed4[q] = b < c.B ? d.seeds[b] : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = warp + 8 * q;
             const int b = bb * 32 + r;
             bool s = false;
             float xv = 0.0f;
             if (b < c.B && i < c.n_in) {
                 const size_t o = (size_t)b * c.n_in + i;
-                s = poisson_spike(d.seeds[b], tt, c.n_in, i, d.thr[o]);
-                float x = d.x_pre[(size_t)xp * nbi + o];
-                x = __fmul_rn(x, c.a_x);
+                s = poisson_spike_hashed(seed4[q], hc, thr4[q]);
+                float x = __fmul_rn(x4[q], c.a_x);
                 x = __fadd_rn(x, s ? 1.0f : 0.0f);
                 d.x_pre[(size_t)xc * nbi + o] = x;
                 xv = __fmul_rn(c.nu_post, x);
@@ -173,42 +189,69 @@ __global__ void __launch_bounds__(256) k_t_encode(Consts c, Bufs d, TBufs t, int
 
 // -------------------------------------------------------- neuron epilogue ---
 
-// Neuron j (this lane; warp-uniform sample range) over the 16 samples b0 ..
-// b0+15 with currents I[u]: snn_run's neuron update, postsynaptic trace and
-// spike bookkeeping, and the update's operands of the step.  ncol counts the
-// column's spikes for theta.
-__device__ __forceinline__ void neuron_chunk(const Consts& c, const Bufs& d, const TBufs& t, int j, int b0,
-                                             const float (&I)[16], float th, int p3, int t_local,
-                                             uint32_t& ncol) {
-    const int lane = threadIdx.x & 31;
+// The state of neuron j (this lane) for the 16 samples b0 .. b0+15
+// (warp-uniform range): loaded before any of it is used, so the loads are in
+// flight together, and -- in the product form -- while the current is still
+// being accumulated.
+struct ChunkState {
+    float ve[16], vi[16], xq[16];
+    uint32_t sw[16];
+    int C[16];
+};
+
+__device__ __forceinline__ void chunk_load(const Consts& c, const Bufs& d, int j, int b0, int p3,
+                                           ChunkState& cs) {
     const bool vj = j < c.N;
     const int pc = (p3 + 2) % 3;
-    uint32_t fired = 0u;
-    float xq[16];
+    const int nb = c.B - b0 < 16 ? c.B - b0 : 16;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
+        const size_t idx = (size_t)(b0 + u) * c.N + j;
+        const bool ok = vj && u < nb;
+        cs.ve[u] = ok ? d.v_e[idx] : 0.0f;
+        cs.vi[u] = ok ? d.v_i[idx] : 0.0f;
+        cs.xq[u] = ok ? d.x_post[idx] : 0.0f;
+        cs.sw[u] = ok ? d.st[idx] : 0u;
+        cs.C[u] = u < nb ? (int)d.cnt[(size_t)pc * c.B + b0 + u] : 0;
+    }
+}
+
+// Neuron j over the chunk's samples with currents I[u]: snn_run's neuron
+// update, postsynaptic trace and spike bookkeeping, and the update's operands
+// of the step.  ncol counts the column's spikes for theta.
+__device__ __forceinline__ void chunk_update(const Consts& c, const Bufs& d, const TBufs& t, int j, int b0,
+                                             const float (&I)[16], float th, int p3, int t_local,
+                                             ChunkState& cs, uint32_t& ncol) {
+    const int lane = threadIdx.x & 31;
+    const bool vj = j < c.N;
+    const int nb = c.B - b0 < 16 ? c.B - b0 : 16;            // samples of the chunk (uniform)
+    float* ve = cs.ve;
+    float* vi = cs.vi;
+    float* xq = cs.xq;
+    uint32_t* sw = cs.sw;
+    int* C = cs.C;
+    uint32_t fired = 0u;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        if (u >= nb) break;                                   // uniform over the warp
         const int b = b0 + u;
-        xq[u] = 0.0f;
-        if (b >= c.B) break;                                  // uniform over the warp
         bool se = false, si = false;
         if (vj) {
             const size_t idx = (size_t)b * c.N + j;
-            float v = d.v_e[idx], vi = d.v_i[idx];
-            const int C = (int)d.cnt[(size_t)pc * c.B + b];
-            const uint32_t st = pair_update(c, v, vi, d.st[idx], I[u], C, th);
+            const uint32_t st = pair_update(c, ve[u], vi[u], sw[u], I[u], C[u], th);
             se = (st & ST_SE) != 0u;
             si = (st & ST_SI) != 0u;
-            float x = __fmul_rn(d.x_post[idx], c.a_x);
+            float x = __fmul_rn(xq[u], c.a_x);
             x = __fadd_rn(x, se ? 1.0f : 0.0f);
-            d.v_e[idx] = v;
-            d.v_i[idx] = vi;
+            xq[u] = x;
+            d.v_e[idx] = ve[u];
+            d.v_i[idx] = vi[u];
             d.x_post[idx] = x;
             d.st[idx] = st;
             if (se) {
                 d.counts[idx] += 1u;
                 fired |= 1u << u;
             }
-            xq[u] = x;
         }
         const uint32_t we = __ballot_sync(FULL, se), wi = __ballot_sync(FULL, si);
         if (lane == 0) {
@@ -224,6 +267,7 @@ __device__ __forceinline__ void neuron_chunk(const Consts& c, const Bufs& d, con
     ncol += (uint32_t)__popc(fired);
     if (!c.learn) return;
     // the update's operands: spikes and -(nu_pre * x_post) of the 16 samples
+    // (samples past the batch: 0)
     uint32_t sp[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
@@ -232,10 +276,17 @@ __device__ __forceinline__ void neuron_chunk(const Consts& c, const Bufs& d, con
     uint4* so = (uint4*)(t.spost + (size_t)j * t.Bp + b0);    // b0 % 16 == 0, Bp % 64 == 0: 32-byte aligned
     so[0] = make_uint4(sp[0], sp[1], sp[2], sp[3]);
     so[1] = make_uint4(sp[4], sp[5], sp[6], sp[7]);
-    uint16_t h[16][3];
+    uint16_t h[16][2];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) split_bf16(-__fmul_rn(c.nu_pre, xq[u]), t.NXQ, h[u]);
-    for (int q = 0; q < t.NXQ; ++q) {
+    for (int u = 0; u < 16; ++u) {
+        const float e = u < nb ? -__fmul_rn(c.nu_pre, xq[u]) : 0.0f;
+        const uint16_t h0 = bf16_bits(e);
+        h[u][0] = h0;
+        h[u][1] = bf16_bits(__fsub_rn(e, bf16_float(h0)));
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q >= t.NXQ) break;
         uint32_t w[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) w[u] = (uint32_t)h[2 * u][q] | ((uint32_t)h[2 * u + 1][q] << 16);
@@ -333,6 +384,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_current(const __grid_consta
     } else {                                                  // epilogue: neuron update
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         const int j = tm * 128 + quarter * 32 + lane;
+        ChunkState cs;
+        const int bfirst = tbi * t.TB + half * 16;
+        if (bfirst < c.B) chunk_load(c, d, j, bfirst, p3, cs);   // overlaps the product
         const bool got = __all_sync(FULL, mbar_wait(accf, 0, WAIT_NS) ? 1 : 0) != 0;
         if (!got) {
             if (lane == 0) atomicOr(d.err, ERR_TENSOR);
@@ -349,7 +403,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_current(const __grid_consta
                 float I[16];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) I[u] = __uint_as_float(r[u]);
-                neuron_chunk(c, d, t, j, b0, I, th, p3, t_local, ncol);
+                if (ch != half) chunk_load(c, d, j, b0, p3, cs);   // the first chunk is in flight already
+                chunk_update(c, d, t, j, b0, I, th, p3, t_local, cs, ncol);
             }
             if (c.learn && ncol && j < c.N) atomicAdd(&t.colcnt[j], ncol);
         }
@@ -364,7 +419,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_current(const __grid_consta
 
 // The same neuron update with the current gathered over the sample's active
 // inputs in ascending order (the definition's sum, bit for bit): grid (Np/128,
-// ceil(B/TB)), 128 threads, thread = neuron.
+// ceil(B/16)), 128 threads, thread = neuron, block = 16 samples.
 __global__ void __launch_bounds__(128) k_t_gcurrent(Consts c, Bufs d, TBufs t, int t_local) {
     const int j = blockIdx.x * 128 + threadIdx.x;
     const unsigned long long tt = d.step[0] + (unsigned long long)t_local;
@@ -372,7 +427,10 @@ __global__ void __launch_bounds__(128) k_t_gcurrent(Consts c, Bufs d, TBufs t, i
     const float th = threshold_of(c, d, j);
     const float* Wj = d.W + (j < c.N ? j : 0);
     uint32_t ncol = 0u;
-    for (int b0 = blockIdx.y * t.TB; b0 < min(c.B, (int)(blockIdx.y + 1) * t.TB); b0 += 16) {
+    {
+        const int b0 = blockIdx.y * 16;
+        ChunkState cs;
+        chunk_load(c, d, j, b0, p3, cs);
         float I[16];
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -392,19 +450,75 @@ __global__ void __launch_bounds__(128) k_t_gcurrent(Consts c, Bufs d, TBufs t, i
             }
             I[u] = acc;
         }
-        neuron_chunk(c, d, t, j, b0, I, th, p3, t_local, ncol);
+        chunk_update(c, d, t, j, b0, I, th, p3, t_local, cs, ncol);
     }
     if (c.learn && ncol && j < c.N) atomicAdd(&t.colcnt[j], ncol);
 }
 
 // --------------------------------------------------------------- the update ---
 
-// grid (mti input tiles of 128, ntj neuron tiles of TNJ, KS batch slices),
-// TC_THREADS threads.  Writes part[ks][i][j] for the CTA's slice.
-__global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ CUtensorMap mXP,
-                                                        const __grid_constant__ CUtensorMap mSIT,
-                                                        const __grid_constant__ CUtensorMap mSP,
+// grid (Np/128 neuron tiles, nti input tiles of TNI, KS batch slices),
+// clusters of the KS slices of one tile, TC_THREADS threads.  Each CTA
+// accumulates its slice of the batch in tensor memory.  With one slice its
+// epilogue applies the update straight from the accumulator; otherwise every
+// CTA leaves its partial tile in shared memory, and after a cluster barrier CTA
+// k updates the 16-input chunks k, k+KS, ... of the tile, adding the slices'
+// partial tiles in slice order through distributed shared memory (a second
+// barrier keeps every tile readable until all are read).  An epilogue thread
+// owns one neuron j of the tile: W[i0..i0+15][j] of its next chunk is loaded
+// before it is needed (a warp's 32 neurons make each load and store one
+// 128-byte line), the clipped update written back, and W's transposed split,
+// W^T[j][i0..i0+15], written as 32 contiguous bytes per term.  The tiles of
+// input tile 0, slice 0 also update theta.
+constexpr int DW_KSMAX = 4;                                    // batch slices per tile (cluster size)
+
+// W[i0 .. i0+15][j] (zeros outside the layer).
+struct WChunk { float w[16]; };
+
+__device__ __forceinline__ void wchunk_load(const Consts& c, const Bufs& d, int j, int i0, WChunk& wc) {
+    const bool vj = j < c.N;
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+        wc.w[u] = (vj && i0 + u < c.n_in) ? d.W[(size_t)(i0 + u) * c.N + j] : 0.0f;
+}
+
+// W[i0 + u][j] += reduce(D[u]), clipped; then W^T's split for the next step's
+// current (inputs past the layer stay 0).
+__device__ __forceinline__ void wchunk_update(const Consts& c, const Bufs& d, const TBufs& t, int j, int i0,
+                                              const float (&D)[16], WChunk& wc) {
+    if (j >= c.N) return;
+    const int nu = c.n_in - i0 < 16 ? c.n_in - i0 : 16;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        float x = D[u];
+        if (c.reduce == SNN_REDUCE_MEAN) x = batch_mean(c, x);
+        float w = __fadd_rn(wc.w[u], x);
+        w = w < c.w_min ? c.w_min : w;
+        w = w > c.w_max ? c.w_max : w;
+        if (u < nu) d.W[(size_t)(i0 + u) * c.N + j] = w;
+        wc.w[u] = u < nu ? w : 0.0f;
+    }
+    uint16_t h[16][3];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        float v = wc.w[u];
+        if (c.wprec == SNN_W_BF16) v = w_read_bf16(v);
+        split_bf16(v, 3, h[u]);
+    }
+    for (int k = 0; k < t.NW; ++k) {
+        uint32_t q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = (uint32_t)h[2 * u][k] | ((uint32_t)h[2 * u + 1][k] << 16);
+        uint4* o = (uint4*)(t.wt + ((size_t)k * t.Np + j) * t.Kp + i0);   // i0 % 16 == 0: 32-byte aligned
+        o[0] = make_uint4(q[0], q[1], q[2], q[3]);
+        o[1] = make_uint4(q[4], q[5], q[6], q[7]);
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ CUtensorMap mSP,
                                                         const __grid_constant__ CUtensorMap mXQ,
+                                                        const __grid_constant__ CUtensorMap mXP,
+                                                        const __grid_constant__ CUtensorMap mSIT,
                                                         Consts c, Bufs d, TBufs t) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -415,12 +529,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ 
     uint64_t* drain = accf + 1;
     __shared__ uint32_t s_tmem;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tmi = blockIdx.x, tj = blockIdx.y, ks = blockIdx.z;
-    const uint32_t ncols = t.TNJ <= 32 ? 32u : t.TNJ <= 64 ? 64u : t.TNJ <= 128 ? 128u : 256u;
+    const int tm = blockIdx.x, tn = blockIdx.y, ks = blockIdx.z;
+    const uint32_t ncols = t.TNI <= 32 ? 32u : t.TNI <= 64 ? 64u : t.TNI <= 128 ? 128u : 256u;
     const int nkb = t.Bp / KB;
     const int k0 = (int)((long long)ks * nkb / t.KS), k1 = (int)((long long)(ks + 1) * nkb / t.KS);
     const int nk = k1 - k0;
-    const int BT = (t.NXP + 1) * TILE_BYTES, BTJ = t.TNJ * 128;   // offset of the B tiles, B tile bytes
+    const int BT = (1 + t.NXQ) * TILE_BYTES, BTI = t.TNI * 128;   // offset of the B tiles, B tile bytes
+    const int PS = t.TNI + 4;                                     // row stride of the partial tile
     if (tid == 0) {
         for (int s = 0; s < DW_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         mbar_init(accf, 1);
@@ -432,6 +547,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ 
     __syncthreads();
     fence_after();
     const uint32_t tmem = s_tmem;
+    // the epilogue thread's neuron and 16-input chunks: ks + KS * (half + 2m)
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int row = quarter * 32 + lane;
+    const int j = tm * 128 + row;
+    const int nch = t.TNI / 16;
+    const int ch0 = ks + t.KS * half, chs = 2 * t.KS;
+    WChunk wc;
     if (warp == 0) {
         if (lane == 0) {                                      // TMA producer
             int it = 0;
@@ -442,31 +564,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ 
                 uint64_t* f = &full[it % DW_STAGES];
                 const int kx = (k0 + it) * KB;
                 mbar_expect_tx(f, (uint32_t)SB);
-                for (int s = 0; s < t.NXP; ++s) tma_2d(st + s * TILE_BYTES, &mXP, kx, s * c.n_in + tmi * 128, f);
-                tma_2d(st + t.NXP * TILE_BYTES, &mSIT, kx, tmi * 128, f);
-                tma_2d(st + BT, &mSP, kx, tj * t.TNJ, f);
-                for (int q = 0; q < t.NXQ; ++q) tma_2d(st + BT + (1 + q) * BTJ, &mXQ, kx, q * t.Np + tj * t.TNJ, f);
+                tma_2d(st, &mSP, kx, tm * 128, f);
+                for (int q = 0; q < t.NXQ; ++q) tma_2d(st + (1 + q) * TILE_BYTES, &mXQ, kx, q * t.Np + tm * 128, f);
+                for (int p = 0; p < t.NXP; ++p) tma_2d(st + BT + p * BTI, &mXP, kx, p * c.n_in + tn * t.TNI, f);
+                tma_2d(st + BT + t.NXP * BTI, &mSIT, kx, tn * t.TNI, f);
             }
             if (!ok) atomicOr(d.err, ERR_TENSOR);
             drain_loads(full, it, DW_STAGES);
         }
     } else if (warp == 1) {
         if (lane == 0) {                                      // MMA issuer
-            const uint32_t idesc = idesc_bf16(t.TNJ);
+            const uint32_t idesc = idesc_bf16(t.TNI);
             bool ok = true;
             for (int it = 0; it < nk; ++it) {
                 const int s = it % DW_STAGES;
                 if (!(ok = mbar_wait(&full[s], (it / DW_STAGES) & 1, WAIT_NS))) break;
                 fence_after();
                 const uint32_t a0 = su32(smem + s * SB), b0 = a0 + BT;
-                const uint32_t sit = a0 + t.NXP * TILE_BYTES;
+                const uint32_t sit = b0 + t.NXP * BTI;
 #pragma unroll
                 for (int k = 0; k < KB / 16; ++k) {
-                    for (int p = 0; p < t.NXP; ++p)           // potentiation: XPRE_p . SPOST
-                        mma_bf16(tmem, sdesc(a0 + p * TILE_BYTES) + (uint64_t)(2 * k), sdesc(b0) + (uint64_t)(2 * k),
+                    for (int p = 0; p < t.NXP; ++p)           // potentiation: SPOST . XPRE_p
+                        mma_bf16(tmem, sdesc(a0) + (uint64_t)(2 * k), sdesc(b0 + p * BTI) + (uint64_t)(2 * k),
                                  idesc, (it | k | p) != 0 ? 1u : 0u);
-                    for (int q = 0; q < t.NXQ; ++q)           // depression: SINT . XPOST_q
-                        mma_bf16(tmem, sdesc(sit) + (uint64_t)(2 * k), sdesc(b0 + (1 + q) * BTJ) + (uint64_t)(2 * k),
+                    for (int q = 0; q < t.NXQ; ++q)           // depression: XPOST_q . SINT
+                        mma_bf16(tmem, sdesc(a0 + (1 + q) * TILE_BYTES) + (uint64_t)(2 * k), sdesc(sit) + (uint64_t)(2 * k),
                                  idesc, 1u);
                 }
                 mma_commit(&empty[s]);
@@ -476,48 +598,93 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ 
             mma_commit(drain);
             if (!mbar_wait(drain, 0, WAIT_NS)) atomicOr(d.err, ERR_TENSOR);
         }
-    } else {                                                  // epilogue: the slice's sums
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
-        const int i = tmi * 128 + quarter * 32 + lane;
+    } else {                                                  // epilogue, part 1
+        if (ch0 < nch) wchunk_load(c, d, j, tn * t.TNI + ch0 * 16, wc);   // in flight during the product
+        if (tn == 0 && ks == 0 && half == 0 && j < c.N) {    // theta of the neuron (independent of W)
+            const int n = (int)t.colcnt[j];
+            double rr;
+            if (c.reduce == SNN_REDUCE_SUM) rr = (double)n;
+            else rr = c.B_pow2 ? __dmul_rn((double)n, (double)c.inv_B) : __ddiv_rn((double)n, (double)c.B);
+            d.theta[j] = __dadd_rn(__dmul_rn(d.theta[j], c.a_th), __dmul_rn(c.theta_plus, rr));
+            t.colcnt[j] = 0u;
+        }
         const bool got = __all_sync(FULL, mbar_wait(accf, 0, WAIT_NS) ? 1 : 0) != 0;
         if (!got) {
             if (lane == 0) atomicOr(d.err, ERR_TENSOR);
         } else {
             fence_after();
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16);
-            float* row = t.part + ((size_t)ks * c.n_in + (i < c.n_in ? i : 0)) * c.N;
-            for (int ch = half; ch < t.TNJ / 16; ch += 2) {
-                const int j0 = tj * t.TNJ + ch * 16;
-                if (j0 >= c.N) break;
-                uint32_t r[16];
-                tmem_ld16(tbase + (uint32_t)(ch * 16), r);
-                if (i >= c.n_in) continue;
-                if (j0 + 16 <= c.N && (c.N & 3) == 0) {
-                    float4* o = (float4*)(row + j0);
+            if (t.KS == 1) {                                  // the update from the accumulator
+                for (int ch = ch0; ch < nch; ch += chs) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + (uint32_t)(ch * 16), r);
+                    float D[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) D[u] = __uint_as_float(r[u]);
+                    const int i0 = tn * t.TNI + ch * 16;
+                    if (i0 < c.n_in) wchunk_update(c, d, t, j, i0, D, wc);
+                    if (ch + chs < nch) wchunk_load(c, d, j, tn * t.TNI + (ch + chs) * 16, wc);
+                }
+            } else {                                          // the partial tile for the cluster;
+                // every MMA has completed and every load was consumed, so the
+                // stage memory is free
+                float* P = (float*)smem + (size_t)row * PS;
+                for (int ch = half; ch < nch; ch += 2) {
+                    uint32_t r[16];
+                    tmem_ld16(tbase + (uint32_t)(ch * 16), r);
+                    float4* o = (float4*)(P + ch * 16);
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
                         o[u] = make_float4(__uint_as_float(r[4 * u]), __uint_as_float(r[4 * u + 1]),
                                            __uint_as_float(r[4 * u + 2]), __uint_as_float(r[4 * u + 3]));
-                } else {
-                    for (int u = 0; u < 16 && j0 + u < c.N; ++u) row[j0 + u] = __uint_as_float(r[u]);
                 }
             }
         }
     }
     fence_before();
-    __syncthreads();
+    __syncthreads();                                          // every partial tile of this CTA written
+    if (t.KS > 1) {
+        cluster_sync();                                       // ... and of every CTA of the cluster
+        if (warp >= 2) {                                      // epilogue, part 2: slices in order
+            const uint32_t prow = su32(smem) + (uint32_t)(row * PS) * 4u;
+            for (int ch = ch0; ch < nch; ch += chs) {
+                float D[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t off = prow + (uint32_t)(ch * 16 + 4 * q) * 4u;
+                    float4 v[DW_KSMAX];
+#pragma unroll
+                    for (int k = 0; k < DW_KSMAX; ++k)
+                        v[k] = k < t.KS ? ld_cluster_f32x4(cluster_map(off, (uint32_t)k))
+                                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    float4 a = v[0];
+#pragma unroll
+                    for (int k = 1; k < DW_KSMAX; ++k)
+                        if (k < t.KS) {
+                            a.x = __fadd_rn(a.x, v[k].x); a.y = __fadd_rn(a.y, v[k].y);
+                            a.z = __fadd_rn(a.z, v[k].z); a.w = __fadd_rn(a.w, v[k].w);
+                        }
+                    D[4 * q] = a.x; D[4 * q + 1] = a.y; D[4 * q + 2] = a.z; D[4 * q + 3] = a.w;
+                }
+                const int i0 = tn * t.TNI + ch * 16;
+                if (i0 < c.n_in) wchunk_update(c, d, t, j, i0, D, wc);
+                if (ch + chs < nch) wchunk_load(c, d, j, tn * t.TNI + (ch + chs) * 16, wc);
+            }
+        }
+        __syncthreads();
+        cluster_sync();                                       // no tile is read after its CTA leaves
+    }
     if (warp == 1) {
         fence_after();
         tmem_free(tmem, ncols);
     }
 }
 
-// 256 threads, tile = 32 inputs x 32 neurons (lanes = neurons).  W[i][j] +=
-// reduce(sum over slices of part), clipped; then W's transposed split for the
-// next step's current through shared memory; the tiles of the first input
-// tile also update theta (FP64) and clear the column counters.  apply = 0: no
-// update, only the split of the current W (a run's start).
-__global__ void __launch_bounds__(256) k_t_apply(Consts c, Bufs d, TBufs t, int apply) {
+// At a run's start: W's transposed split for the current from the master W
+// (which other forms or snn_write_weights may have changed) and the column
+// counters cleared.  256 threads, tile = 32 inputs x 32 neurons, transposed
+// through shared memory so both sides are coalesced.
+__global__ void __launch_bounds__(256) k_t_pack(Consts c, Bufs d, TBufs t) {
     __shared__ float ws[32][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntj = (c.N + 31) / 32, nti = (c.n_in + 31) / 32;
@@ -526,21 +693,7 @@ __global__ void __launch_bounds__(256) k_t_apply(Consts c, Bufs d, TBufs t, int 
         const int j = j0 + lane;
         for (int r = warp; r < 32; r += 8) {
             const int i = i0 + r;
-            float w = 0.0f;
-            if (i < c.n_in && j < c.N) {
-                const size_t k = (size_t)i * c.N + j;
-                w = d.W[k];
-                if (apply) {
-                    float D = t.part[k];
-                    for (int s = 1; s < t.KS; ++s) D = __fadd_rn(D, t.part[(size_t)s * c.n_in * c.N + k]);
-                    if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
-                    w = __fadd_rn(w, D);
-                    w = w < c.w_min ? c.w_min : w;
-                    w = w > c.w_max ? c.w_max : w;
-                    d.W[k] = w;
-                }
-            }
-            ws[r][lane] = w;
+            ws[r][lane] = (i < c.n_in && j < c.N) ? d.W[(size_t)i * c.N + j] : 0.0f;
         }
         __syncthreads();
         for (int r = warp; r < 32; r += 8) {                  // neuron row r, lanes = inputs
@@ -553,16 +706,7 @@ __global__ void __launch_bounds__(256) k_t_apply(Consts c, Bufs d, TBufs t, int 
                 for (int k = 0; k < t.NW; ++k) t.wt[((size_t)k * t.Np + j2) * t.Kp + i2] = h[k];
             }
         }
-        if (i0 == 0 && warp == 0 && j < c.N) {
-            if (apply) {
-                const int n = (int)t.colcnt[j];
-                double rr;
-                if (c.reduce == SNN_REDUCE_SUM) rr = (double)n;
-                else rr = c.B_pow2 ? __dmul_rn((double)n, (double)c.inv_B) : __ddiv_rn((double)n, (double)c.B);
-                d.theta[j] = __dadd_rn(__dmul_rn(d.theta[j], c.a_th), __dmul_rn(c.theta_plus, rr));
-            }
-            t.colcnt[j] = 0u;
-        }
+        if (i0 == 0 && warp == 0 && j < c.N) t.colcnt[j] = 0u;
         __syncthreads();
     }
 }
@@ -591,18 +735,22 @@ TBufs tensor_plan(const Consts& c, int dense, int sms) {
     TBufs t{};
     t.NW = c.wprec == SNN_W_BF16 ? 1 : 3;
     t.NXP = 3;
-    t.NXQ = 2;
+    t.NXQ = 2;                                    // the epilogue writes at most two terms
     t.Np = (int)up((size_t)c.N, 128);
     t.Kp = (int)up((size_t)c.n_in, 64);
     t.Bp = (int)up((size_t)c.B, 64);
-    t.TB = 128;                                   // CUR_SMEM_MAX and the tensor memory assume <= 128
-    t.ntj = (c.N + 127) / 128;                    // TNJ <= 128 (DW_SMEM_MAX)
-    t.TNJ = (int)up((size_t)((c.N + t.ntj - 1) / t.ntj), 16);
-    t.mti = (c.n_in + 127) / 128;
-    const int tiles = t.mti * t.ntj, nkb = t.Bp / 64;
+    // samples per tile of the current: the largest of 128, 64, 32 that still
+    // gives about one CTA per SM (W's tiles are re-read once per sample tile)
+    t.TB = 32;
+    for (int tb = 128; tb >= 64; tb /= 2)
+        if ((size_t)(t.Np / 128) * ((c.B + tb - 1) / tb) >= (size_t)sms * 3 / 4) { t.TB = tb; break; }
+    t.nti = (c.n_in + 127) / 128;                 // TNI <= 128 (DW_SMEM_MAX)
+    t.TNI = (int)up((size_t)((c.n_in + t.nti - 1) / t.nti), 16);
+    const int tiles = (t.Np / 128) * t.nti, nkb = t.Bp / 64;
     int ks = (sms + tiles / 2) / (tiles > 0 ? tiles : 1);
     if (ks < 1) ks = 1;
     if (ks > nkb) ks = nkb;
+    if (ks > DW_KSMAX) ks = DW_KSMAX;             // clusters of at most four slices
     t.KS = ks;
     t.dense = dense;
     return t;
@@ -616,7 +764,6 @@ size_t tensor_bytes(const TBufs& t, const Consts& c) {
     n += up((size_t)t.NXP * c.n_in * t.Bp * 2, 256);
     n += up((size_t)t.Np * t.Bp * 2, 256);
     n += up((size_t)t.NXQ * t.Np * t.Bp * 2, 256);
-    n += up((size_t)t.KS * c.n_in * c.N * 4, 256);
     n += up((size_t)c.N * 4, 256);
     return n;
 }
@@ -630,25 +777,24 @@ bool tensor_bind(TBufs& t, const Consts& c, void* base) {
     t.xpre = (uint16_t*)take((size_t)t.NXP * c.n_in * t.Bp * 2);
     t.spost = (uint16_t*)take((size_t)t.Np * t.Bp * 2);
     t.xpost = (uint16_t*)take((size_t)t.NXQ * t.Np * t.Bp * 2);
-    t.part = (float*)take((size_t)t.KS * c.n_in * c.N * 4);
     t.colcnt = (uint32_t*)take((size_t)c.N * 4);
     return encode_bf16_map(&t.m_wt, t.wt, t.NW * t.Np, t.Kp, 128) &&
            encode_bf16_map(&t.m_sin, t.sin, t.Bp, t.Kp, t.TB) &&
-           encode_bf16_map(&t.m_xpre, t.xpre, t.NXP * c.n_in, t.Bp, 128) &&
-           encode_bf16_map(&t.m_sint, t.sint, c.n_in, t.Bp, 128) &&
-           encode_bf16_map(&t.m_spost, t.spost, t.Np, t.Bp, t.TNJ) &&
-           encode_bf16_map(&t.m_xpost, t.xpost, t.NXQ * t.Np, t.Bp, t.TNJ);
+           encode_bf16_map(&t.m_xpre, t.xpre, t.NXP * c.n_in, t.Bp, t.TNI) &&
+           encode_bf16_map(&t.m_sint, t.sint, c.n_in, t.Bp, t.TNI) &&
+           encode_bf16_map(&t.m_spost, t.spost, t.Np, t.Bp, 128) &&
+           encode_bf16_map(&t.m_xpost, t.xpost, t.NXQ * t.Np, t.Bp, 128);
 }
 
 cudaError_t launch_tensor_begin(const Consts& c, const Bufs& d, const TBufs& t, cudaStream_t s, Prof* prof) {
     (void)prof;
     const size_t tiles = (size_t)((c.n_in + 31) / 32) * ((c.N + 31) / 32);
-    k_t_apply<<<grid_cap(tiles, 1, 152 * 8), 256, 0, s>>>(c, d, t, 0);
+    k_t_pack<<<grid_cap(tiles, 1, 152 * 8), 256, 0, s>>>(c, d, t);
     return cudaGetLastError();
 }
 
 // Dynamic shared memory of the two products at their largest tiles (three W
-// terms and 128 samples; four A tiles and three B tiles of 128 neurons): set
+// terms and 128 samples; three A tiles and four B tiles of 128 inputs): set
 // once per device, under a lock shared by every host thread.
 constexpr int CUR_SMEM_MAX = CUR_STAGES * (3 * TILE_BYTES + 128 * 128) + 1024 + 64;
 constexpr int DW_SMEM_MAX = DW_STAGES * (4 * TILE_BYTES + 3 * 128 * 128) + 1024 + 64;
@@ -678,23 +824,30 @@ cudaError_t launch_tensor_step(const Consts& c, const Bufs& d, const TBufs& t, i
     TT_TRY(cudaGetLastError());
     TT_TRY(prof_stop(prof, s));
     TT_TRY(prof_start(prof, SNN_KERNEL_NEURON, s));
-    const dim3 gc(t.Np / 128, (c.B + t.TB - 1) / t.TB);
     if (t.dense) {
         const size_t sm = (size_t)CUR_STAGES * cur_stage_bytes(t) + 1024 + 64;
-        k_t_current<<<gc, TC_THREADS, sm, s>>>(t.m_wt, t.m_sin, c, d, t, t_local);
+        k_t_current<<<dim3(t.Np / 128, (c.B + t.TB - 1) / t.TB), TC_THREADS, sm, s>>>(t.m_wt, t.m_sin, c, d, t,
+                                                                                    t_local);
     } else {
-        k_t_gcurrent<<<gc, 128, 0, s>>>(c, d, t, t_local);
+        k_t_gcurrent<<<dim3(t.Np / 128, (c.B + 15) / 16), 128, 0, s>>>(c, d, t, t_local);
     }
     TT_TRY(cudaGetLastError());
     TT_TRY(prof_stop(prof, s));
     if (c.learn) {
         TT_TRY(prof_start(prof, SNN_KERNEL_STDP, s));
-        const size_t sm = (size_t)DW_STAGES * dw_stage_bytes(t) + 1024 + 64;
-        k_t_dw<<<dim3(t.mti, t.ntj, t.KS), TC_THREADS, sm, s>>>(t.m_xpre, t.m_sint, t.m_spost, t.m_xpost, c, d, t);
-        TT_TRY(cudaGetLastError());
-        const size_t tiles = (size_t)((c.n_in + 31) / 32) * ((c.N + 31) / 32);
-        k_t_apply<<<grid_cap(tiles, 1, 152 * 8), 256, 0, s>>>(c, d, t, 1);
-        TT_TRY(cudaGetLastError());
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(t.Np / 128, t.nti, t.KS);
+        cfg.blockDim = dim3(TC_THREADS);
+        cfg.dynamicSmemBytes = (size_t)DW_STAGES * dw_stage_bytes(t) + 1024 + 64;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 1;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = (unsigned)t.KS;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        TT_TRY(cudaLaunchKernelEx(&cfg, k_t_dw, t.m_spost, t.m_xpost, t.m_xpre, t.m_sint, c, d, t));
         TT_TRY(prof_stop(prof, s));
     }
     return cudaSuccess;

@@ -60,7 +60,7 @@ FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
 
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
             "snn_read_state", "snn_write_state", "snn_read_weights", "snn_write_weights",
-            "snn_profile",
+            "snn_profile", "snn_tune", "snn_last_mode",
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
             "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
@@ -135,6 +135,12 @@ def lib():
         L.snn_read_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_write_weights.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int]
         L.snn_profile.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_int]
+        L.snn_tune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float,
+                               C.c_int, C.c_int, C.c_uint, C.c_void_p, C.POINTER(C.c_uint),
+                               C.POINTER(C.c_double)]
+        L.snn_tune.restype = C.c_int
+        L.snn_last_mode.argtypes = [C.c_void_p]
+        L.snn_last_mode.restype = C.c_uint
         L.snn_infer_noalloc.argtypes = [C.POINTER(snn_spec), C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_int, C.c_int, C.c_float, C.c_void_p,
                                         C.c_void_p]
@@ -272,6 +278,31 @@ def snn_profile(net) -> dict:
     la = (C.c_int * n)()
     _check(net, lib().snn_profile(net, ms, la, n))
     return {KERNEL_NAMES[k]: (ms[k], la[k]) for k in range(n)}
+
+
+TUNE_FORMS = ("graph", "persistent", "tensor", "tensor_gather")
+MODE_NAMES = {SNN_MODE_STEP: "step", SNN_MODE_GRAPH: "graph", SNN_MODE_PERSISTENT: "persistent",
+              SNN_MODE_TENSOR: "tensor", SNN_MODE_TENSOR | SNN_TENSOR_GATHER: "tensor_gather"}
+
+
+def snn_tune(net, rates, seeds, B: int, T: int, dt: float = 1.0, learn: int = 1,
+             reduce: int = SNN_REDUCE_MEAN, flags: int = 0, stream=None):
+    """Times every form on this batch, records the fastest for SNN_MODE_AUTO;
+    returns (winner's name, {form: device ms per step or nan})."""
+    pr, _, dev_r = _buf(rates)
+    ps, _, dev_s = _buf(seeds)
+    if not (dev_r and dev_s):
+        flags |= SNN_HOST_INPUTS
+    mode = C.c_uint(0)
+    ms = (C.c_double * 4)()
+    _check(net, lib().snn_tune(net, pr, ps, B, T, dt, learn, reduce, flags, _stream(stream),
+                               C.byref(mode), ms))
+    return MODE_NAMES[mode.value], {TUNE_FORMS[k]: ms[k] for k in range(4)}
+
+
+def snn_last_mode(net) -> str:
+    """The form the last run took ("" before any run)."""
+    return MODE_NAMES.get(lib().snn_last_mode(net), "")
 
 
 def snn_infer_noalloc(spec: snn_spec, w, theta, rates, seeds, B: int, T: int, dt_ms: float,

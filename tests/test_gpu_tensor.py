@@ -235,3 +235,48 @@ def test_profile_reports_the_tensor_launches():
         prof = m.snn_profile(net.handle)
         for k in ("encode", "neuron", "stdp"):
             assert prof[k][1] == 12 and prof[k][0] > 0.0, (k, prof[k])
+
+
+def test_tuner_times_every_form_and_auto_takes_the_winner():
+    """snn_tune times each form on the caller's batch, leaves W and theta as
+    they were, and a later AUTO run with the same batch size takes the
+    recorded winner (snn_last_mode reports it); a batch size without an
+    entry falls back to the persistent form."""
+    m = snn()
+    p, r, s, w = synth.workload(256, 400)
+    net = m.Network(p, w_init=w)
+    net.run(dev(r), dev(s), 5, mode="persistent")       # W and theta move once before tuning
+    torch.cuda.synchronize()
+    w1, th1 = net.weights(), net.read("theta")
+    winner, ms = m.snn_tune(net.handle, dev(r), dev(s), 256, 20)
+    assert winner in ms and ms[winner] == min(v for v in ms.values() if v == v)
+    for form in ("graph", "persistent", "tensor", "tensor_gather"):
+        assert ms[form] > 0.0, form                       # every form takes this run
+    assert np.array_equal(net.weights(), w1) and np.array_equal(net.read("theta"), th1)
+    net.run(dev(r), dev(s), 20, mode="auto")
+    torch.cuda.synchronize()
+    assert m.snn_last_mode(net.handle) == winner
+    net.run(dev(r[:64]), dev(s[:64]), 20, mode="auto")    # no entry for B = 64
+    torch.cuda.synchronize()
+    assert m.snn_last_mode(net.handle) == "persistent"
+    # the max reduction is not taken by the tensor form: the tuner skips it
+    _, ms2 = m.snn_tune(net.handle, dev(r), dev(s), 256, 10, reduce=m.SNN_REDUCE_MAX)
+    assert ms2["tensor"] != ms2["tensor"] and ms2["persistent"] > 0.0   # nan: not taken
+
+
+def test_auto_choice_is_keyed_by_the_measured_input_density():
+    """Two tunings at the same batch size with inputs 8x apart in rate are
+    two entries; after a run at either density, AUTO takes that density's
+    winner."""
+    m = snn()
+    p, r, s, w = synth.workload(128, 400)
+    r8 = np.minimum(r * 8.0, 1000.0).astype(np.float32)
+    net = m.Network(p, w_init=w)
+    win1, _ = m.snn_tune(net.handle, dev(r), dev(s), 128, 12, learn=0)
+    win8, _ = m.snn_tune(net.handle, dev(r8), dev(s), 128, 12, learn=0)
+    for rates, win in ((r, win1), (r8, win8), (r, win1)):
+        net.run(dev(rates), dev(s), 12, learn=False, mode="persistent")   # a measured run
+        torch.cuda.synchronize()
+        net.run(dev(rates), dev(s), 12, learn=False, mode="auto")
+        torch.cuda.synchronize()
+        assert m.snn_last_mode(net.handle) == win
