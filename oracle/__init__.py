@@ -45,14 +45,15 @@ class _Params(C.Structure):
             "e_rest", "e_reset", "e_thresh", "e_tau", "e_refrac", "theta_plus", "theta_tau",
             "i_rest", "i_reset", "i_thresh", "i_tau", "i_refrac", "w_ei", "w_ie",
             "trace_tau", "nu_pre", "nu_post", "w_min", "w_max", "dt")] + [
-        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32)]
+        ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32),
+        ("wmaster", C.c_int32)]
 
 
 class _State(C.Structure):
     _fields_ = [("v_e", C.c_void_p), ("v_i", C.c_void_p), ("ref_e", C.c_void_p),
                 ("ref_i", C.c_void_p), ("s_e", C.c_void_p), ("s_i", C.c_void_p),
                 ("x_pre", C.c_void_p), ("x_post", C.c_void_p), ("w", C.c_void_p),
-                ("theta", C.c_void_p), ("step", C.c_uint64)]
+                ("theta", C.c_void_p), ("step", C.c_uint64), ("w_lo", C.c_void_p)]
 
 
 class _Record(C.Structure):
@@ -80,6 +81,8 @@ def lib():
         _lib.oracle_poisson_thresholds.argtypes = [C.c_void_p, C.c_float, C.c_void_p, C.c_int64]
         for name in ("oracle_round_bf16", "oracle_round_e4m3", "oracle_e4m3_column_scale"):
             getattr(_lib, name).argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        _lib.oracle_master_add_f32.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                               C.c_float, C.c_float]
     return _lib
 
 
@@ -106,6 +109,7 @@ class State:
     w: np.ndarray
     theta: np.ndarray
     step: int = 0
+    w_lo: np.ndarray | None = None      # low parts of the compensated master (O10)
 
     def copy(self) -> "State":
         return State(**{k: (v.copy() if isinstance(v, np.ndarray) else v)
@@ -123,6 +127,7 @@ def new_state(params: dict, batch: int, w: np.ndarray, dtype=np.float32,
         x_pre=np.zeros((batch, ni), dtype), x_post=np.zeros((batch, n), dtype),
         w=np.array(w, dtype=dtype, copy=True, order="C"),
         theta=np.zeros(n, np.float64) if theta is None else np.array(theta, np.float64),
+        w_lo=np.zeros((ni, n), dtype),
     )
 
 
@@ -147,11 +152,13 @@ def run(params: dict, state: State, rates: np.ndarray, seeds: np.ndarray, T: int
     rates = np.ascontiguousarray(rates, np.float32)
     seeds = np.ascontiguousarray(seeds, np.uint64)
     P = _Params(**{k: params[k] for k, _ in _Params._fields_
-                   if k not in ("dt", "wprec", "rule", "w_norm", "neuron")},
+                   if k not in ("dt", "wprec", "rule", "w_norm", "neuron", "wmaster")},
                 dt=dt, wprec=wprec, rule=int(params.get("rule", 0)), w_norm=float(params.get("w_norm", 0.0)),
-                neuron=int(params.get("neuron", 0)))
+                neuron=int(params.get("neuron", 0)), wmaster=int(params.get("wmaster", 0)))
+    if state.w_lo is None:
+        state.w_lo = np.zeros_like(state.w)
     arrs = {k: getattr(state, k) for k in ("v_e", "v_i", "ref_e", "ref_i", "s_e", "s_i",
-                                            "x_pre", "x_post", "w", "theta")}
+                                            "x_pre", "x_post", "w", "theta", "w_lo")}
     for k, a in arrs.items():
         assert a.flags["C_CONTIGUOUS"], k
     S = _State(**{k: _ptr(a) for k, a in arrs.items()}, step=state.step)
@@ -200,6 +207,16 @@ def e4m3_column_scale(m) -> np.ndarray:
     out = np.empty_like(m)
     lib().oracle_e4m3_column_scale(m.ctypes.data, out.ctypes.data, m.size)
     return out
+
+
+def master_add(h, l, d, w_min: float = 0.0, w_max: float = 1.0):
+    """O10 on FP32 arrays: returns the new (h, l) after adding d."""
+    h = np.array(h, np.float32, copy=True, order="C")
+    l = np.array(l, np.float32, copy=True, order="C")
+    d = np.ascontiguousarray(d, np.float32)
+    assert h.shape == l.shape == d.shape
+    lib().oracle_master_add_f32(h.ctypes.data, l.ctypes.data, d.ctypes.data, h.size, w_min, w_max)
+    return h, l
 
 
 def poisson_thresholds(rates, dt: float = 1.0) -> np.ndarray:

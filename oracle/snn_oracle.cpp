@@ -53,6 +53,14 @@
 //   O9 weight precision of the current (W itself stays in R for STDP):
 //              BF16: I_in sums round_bf16(W); FP8: I_in = s_j * sum round_e4m3(W/s_j),
 //              s_j = smallest 2^k with 448*2^k >= max_i |W[i,j]|, from this step's W.
+//   O10 compensated master (wmaster = 1; the long-run accumulation of the
+//              updates into W, which the specification asks for in compensated
+//              FP32 or FP64): W is the pair (h, l), the current reads h, and each
+//              update D is added as s = h + D with its exact rounding error e
+//              (Knuth's TwoSum: b = s - h, e = (h - (s - b)) + (D - b)), l = l + e,
+//              then renormalised (Dekker's Fast2Sum: h' = s + l, l' = l - (h' - s))
+//              and clipped as a pair: below w_min (or at it with l' < 0) gives
+//              (w_min, 0), above w_max (or at it with l' > 0) gives (w_max, 0).
 //
 // Each line of the per-step update is one IEEE operation in the order written;
 // the file is compiled with -ffp-contract=off and without -ffast-math so the
@@ -91,6 +99,7 @@ struct oracle_params {
     float w_norm;    // rule 1: the incoming-weight sum of every column after its update
     int32_t neuron;  // excitatory neuron: 0 leaky with reset to a value (O3), 1 IF with
                      // reset by subtraction (O3')
+    int32_t wmaster; // 0: W is one value of R; 1: the compensated pair of O10
 };
 
 // Complete simulation state; every array is owned by the caller.
@@ -107,6 +116,7 @@ struct oracle_state {
     void* w;          // [n_in][N] R shared input->excitatory weights
     double* theta;    // [N]        shared adaptive thresholds (FP64)
     uint64_t step;    // step counter of the next step within the episode
+    void* w_lo;       // [n_in][N] R low parts of the compensated master (wmaster = 1)
 };
 
 // Optional per-step records (any pointer may be NULL).
@@ -190,6 +200,21 @@ double e4m3_column_scale(double m) {
     return std::ldexp(1.0, f <= 0.875 ? e - 9 : e - 8);
 }
 
+// O10: W = clip(W + D) on the master pair (h, l), each line one operation.
+template <typename R>
+void master_add(R& h, R& l, R D, R w_min, R w_max) {
+    R s = h + D;
+    R b = s - h;
+    R e = (h - (s - b)) + (D - b);
+    R l1 = l + e;
+    R h2 = s + l1;
+    R l2 = l1 - (h2 - s);
+    if (h2 < w_min || (h2 == w_min && l2 < (R)0)) { h2 = w_min; l2 = (R)0; }
+    if (h2 > w_max || (h2 == w_max && l2 > (R)0)) { h2 = w_max; l2 = (R)0; }
+    h = h2;
+    l = l2;
+}
+
 template <typename R>
 R decay_factor(float dt, float tau) {
     return (R)std::exp(-(double)dt / (double)tau);
@@ -204,12 +229,14 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
     if (reduce < 0 || reduce > 2) return 1;
     if (P->rule < 0 || P->rule > 1 || (P->rule == 1 && !(P->w_norm > 0.0f))) return 1;
     if (P->neuron < 0 || P->neuron > 1) return 1;
+    if (P->wmaster < 0 || P->wmaster > 1 || (P->wmaster == 1 && (!S->w_lo || P->rule == 1))) return 1;
     if (P && (P->wprec < 0 || P->wprec > 2)) return 1;
     const int NI = P->n_in, N = P->n_exc;
     if (NI <= 0 || N <= 0 || !(P->dt > 0.0f)) return 1;
 
     R* v_e = (R*)S->v_e;  R* v_i = (R*)S->v_i;
     R* x_pre = (R*)S->x_pre;  R* x_post = (R*)S->x_post;  R* W = (R*)S->w;
+    R* WL = (R*)S->w_lo;
     int32_t* ref_e = S->ref_e;  int32_t* ref_i = S->ref_i;
     uint8_t* s_e = S->s_e;  uint8_t* s_i = S->s_i;
     double* theta = S->theta;
@@ -408,6 +435,10 @@ int run(const oracle_params* P, int B, int T, const float* rates, const uint64_t
                 R d = D[k];
                 if (reduce != 2) d = d - Q[k];
                 if (reduce == 1) d = d / (R)B;
+                if (P->wmaster == 1) {                 // O10
+                    master_add<R>(W[k], WL[k], d, w_min, w_max);
+                    continue;
+                }
                 R w = W[k] + d;
                 w = w < w_min ? w_min : w;
                 w = w > w_max ? w_max : w;
@@ -474,6 +505,11 @@ int oracle_run_f64(const oracle_params* P, int B, int T, const float* rates,
                    const uint64_t* seeds, int learn, int reduce, int episodic,
                    oracle_state* S, oracle_record* rec) {
     return run<double>(P, B, T, rates, seeds, learn, reduce, episodic, S, rec);
+}
+
+// O10 element by element (float): h, l updated in place by d.
+void oracle_master_add_f32(float* h, float* l, const float* d, int64_t n, float w_min, float w_max) {
+    for (int64_t k = 0; k < n; ++k) master_add<float>(h[k], l[k], d[k], w_min, w_max);
 }
 
 // Number of OpenMP threads of later runs (n >= 1).

@@ -53,6 +53,13 @@ MISTAKES = {
     "no lower clip": (
         "snn_oracle.cpp", "w = w < w_min ? w_min : w;\n                w = w > w_max ? w_max : w;",
         "w = w > w_max ? w_max : w;", PINS),
+    "compensated master without the rounding error of the sum": (
+        "snn_oracle.cpp", "R l1 = l + e;", "R l1 = l;", PINS),
+    "compensated master not renormalised": (
+        "snn_oracle.cpp", "R l2 = l1 - (h2 - s);", "R l2 = (R)0;", PINS),
+    "compensated master clipped on the high part alone": (
+        "snn_oracle.cpp", "if (h2 > w_max || (h2 == w_max && l2 > (R)0)) { h2 = w_max; l2 = (R)0; }",
+        "if (h2 > w_max) { h2 = w_max; l2 = (R)0; }", PINS),
     "theta without decay": (
         "snn_oracle.cpp", "double decayed = theta[j] * a_th;", "double decayed = theta[j];", PINS),
     "theta summed under the mean": (
