@@ -132,6 +132,22 @@ typedef enum { SNN_RULE_PAIR = 0, SNN_RULE_POST_NORM = 1 } snn_rule;
  *                      excess over the threshold is kept.  e_tau_ms is not used. */
 typedef enum { SNN_NEURON_LIF = 0, SNN_NEURON_IF_SUB = 1 } snn_neuron;
 
+/* Master copy of the input->excitatory weights, into which the batch-reduced
+ * STDP updates accumulate over many steps and presentations (the long-run
+ * accumulation the precision plan keeps in compensated FP32 or FP64).
+ *   SNN_WMASTER_FP32:        one FP32 value per weight, W = clip(W + D) (the default).
+ *   SNN_WMASTER_COMPENSATED: the pair (h, l), W = h + l; the current reads h.
+ *                            Each update D adds s = h + D with its exact
+ *                            rounding error (TwoSum: b = s - h, e = (h - (s -
+ *                            b)) + (D - b)) to l, then renormalises (Fast2Sum:
+ *                            h' = s + (l + e), l' = (l + e) - (h' - s)) and
+ *                            clips the pair (below w_min, or at it with l' < 0:
+ *                            (w_min, 0); above w_max, or at it with l' > 0:
+ *                            (w_max, 0)).  Each line is one IEEE FP32 operation,
+ *                            so the ordered forms match the definition bit for
+ *                            bit.  Pair rule only. */
+typedef enum { SNN_WMASTER_FP32 = 0, SNN_WMASTER_COMPENSATED = 1 } snn_wmaster;
+
 typedef struct snn_spec {
     int32_t n_in, n_exc, n_inh;                  /* n_inh must equal n_exc */
     float e_rest, e_reset, e_thresh, e_tau_ms, e_refrac_ms;
@@ -147,6 +163,7 @@ typedef struct snn_spec {
     const float* w_init;                         /* host [n_in][n_exc], or NULL: seeded init,
                                                     uniform [0,0.3] on the 2^-12 grid */
     const double* theta_init;                    /* host [n_exc], or NULL: zeros */
+    int32_t wmaster;                             /* snn_wmaster */
 } snn_spec;
 
 /* Fill *spec with the adaptive-threshold network parameters for n_exc
@@ -198,7 +215,9 @@ enum {
     SNN_FIELD_STEP = 11,        /* [1] uint64, step counter after the last run */
     SNN_FIELD_SPIKES_EXC = 12,  /* [B][n_exc] uint8, excitatory spikes of the last step */
     SNN_FIELD_SPIKES_INH = 13,  /* [B][n_exc] uint8, inhibitory spikes of the last step */
-    SNN_FIELD_COUNT = 14
+    SNN_FIELD_W_LO = 14,        /* [n_in][n_exc] float, low parts l of a compensated master
+                                   (W = h + l, h from snn_read_weights); zeros otherwise */
+    SNN_FIELD_COUNT = 15
 };
 
 /* Bytes of a field for the current batch (rasters: of the last recorded run).
@@ -216,7 +235,8 @@ SNN_API snn_status snn_read_state(snn_net* net, int field, void* dst, size_t byt
  * in the layout snn_read_state gives it; with snn_read_state this checkpoints
  * and resumes a simulation.  Writable: V_EXC, V_INH, X_PRE, X_POST, REF_EXC,
  * REF_INH, SPIKES_EXC, SPIKES_INH (the network must hold a batch: run once
- * with it, T may be 0), THETA, and STEP (the step counter a continuing run
+ * with it, T may be 0), THETA, W_LO (a compensated master's low parts), and
+ * STEP (the step counter a continuing run
  * starts from; the other fields keep their values, so fields and STEP may be
  * written in either order).  The library re-derives what it keeps alongside
  * (which samples have a non-zero postsynaptic trace, the previous step's
@@ -232,7 +252,9 @@ SNN_API snn_status snn_write_state(snn_net* net, int field, const void* src, siz
 SNN_API snn_status snn_read_weights(snn_net* net, float* dst, size_t bytes, int dst_on_device);
 
 /* Replace the master weights with src [n_in][n_exc] (device or host) and
- * refresh any reduced-precision copy.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+ * refresh any reduced-precision copy; a compensated master's low parts are
+ * cleared (write SNN_FIELD_W_LO afterwards to restore them).  Errors:
+ * SNN_ERR_ARG, SNN_ERR_CUDA. */
 SNN_API snn_status snn_write_weights(snn_net* net, const float* src, size_t bytes, int src_on_device);
 
 /* ---- Serving: continuous batching of inference presentations ----------

@@ -258,6 +258,7 @@ snn::Consts make_consts(const snn_net* n, int B, float dt, int learn, int reduce
     c.rule = s.rule;
     c.w_norm = s.w_norm;
     c.neuron = s.neuron;
+    c.wmaster = s.wmaster;
     return c;
 }
 
@@ -298,6 +299,7 @@ size_t field_bytes(const snn_net* n, int field) {
         case SNN_FIELD_RASTER_INPUT:
             return n->last_rec_input ? (size_t)n->last_T * B * Iw * 4 : 0;
         case SNN_FIELD_STEP: return 8;
+        case SNN_FIELD_W_LO: return NI * N * 4;
         default: return 0;
     }
 }
@@ -413,6 +415,10 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
         return fail(nullptr, SNN_ERR_ARG, "snn_create: SNN_RULE_POST_NORM needs w_norm > 0");
     if (s.neuron != SNN_NEURON_LIF && s.neuron != SNN_NEURON_IF_SUB)
         return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown neuron %d", (int)s.neuron);
+    if (s.wmaster != SNN_WMASTER_FP32 && s.wmaster != SNN_WMASTER_COMPENSATED)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: unknown wmaster %d", (int)s.wmaster);
+    if (s.wmaster == SNN_WMASTER_COMPENSATED && s.rule != SNN_RULE_PAIR)
+        return fail(nullptr, SNN_ERR_ARG, "snn_create: the compensated master takes the pair rule");
 
     snn_net* n = new (std::nothrow) snn_net();
     if (!n) return fail(nullptr, SNN_ERR_OOM, "snn_create: host allocation failed");
@@ -426,6 +432,10 @@ snn_status snn_create(const snn_spec* spec, snn_net** out) {
     if (e == cudaSuccess) e = dalloc(&n->d.step, 2);
     if (e == cudaSuccess) e = dalloc(&n->d.err, 64);
     if (e == cudaSuccess) e = dalloc(&n->d.wscale, (size_t)s.n_exc);
+    if (e == cudaSuccess && s.wmaster == SNN_WMASTER_COMPENSATED) {
+        e = dalloc(&n->d.W_lo, nw);
+        if (e == cudaSuccess) e = cudaMemset(n->d.W_lo, 0, nw * 4);
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&n->cap, cudaStreamNonBlocking);
     std::vector<float> w;
     if (e == cudaSuccess) {
@@ -456,8 +466,8 @@ snn_status snn_destroy(snn_net* n) {
     if (!n) return SNN_OK;
     if (n->last) cudaStreamSynchronize(n->last);
     free_batch(n);
-    void* ptrs[] = {n->d.W, n->d.theta, n->d.step, n->d.err, n->d.wscale, n->d.raster_e, n->d.raster_i,
-                    n->d.raster_in, n->scratch};
+    void* ptrs[] = {n->d.W, n->d.W_lo, n->d.theta, n->d.step, n->d.err, n->d.wscale, n->d.raster_e,
+                    n->d.raster_i, n->d.raster_in, n->scratch};
     for (void* p : ptrs) if (p) cudaFree(p);
     if (n->gexec) cudaGraphExecDestroy(n->gexec);
     if (n->cap) cudaStreamDestroy(n->cap);
@@ -655,7 +665,8 @@ snn_status snn_run(snn_net* n, const float* rates, const uint64_t* seeds, int B,
 
 size_t snn_field_bytes(const snn_net* n, int field) {
     if (!n || field < 0 || field >= SNN_FIELD_COUNT) return 0;
-    if (field != SNN_FIELD_THETA && field != SNN_FIELD_STEP && n->B == 0) return 0;
+    if (field != SNN_FIELD_THETA && field != SNN_FIELD_STEP && field != SNN_FIELD_W_LO && n->B == 0)
+        return 0;
     return field_bytes(n, field);
 }
 
@@ -665,7 +676,7 @@ snn_status snn_read_state(snn_net* n, int field, void* dst, size_t bytes, int ds
     if (!dst) return fail(n, SNN_ERR_ARG, "snn_read_state: dst is NULL");
     if (field < 0 || field >= SNN_FIELD_COUNT)
         return fail(n, SNN_ERR_ARG, "snn_read_state: unknown field %d", field);
-    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP;
+    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP && field != SNN_FIELD_W_LO;
     if (per_sample && !n->state_valid)
         return fail(n, SNN_ERR_STATE, "snn_read_state: no run has produced this state yet");
     const size_t want = field_bytes(n, field);
@@ -691,6 +702,13 @@ snn_status snn_read_state(snn_net* n, int field, void* dst, size_t bytes, int ds
         case SNN_FIELD_STEP: src = n->d.step + 1; break;
         default: break;
     }
+    if (field == SNN_FIELD_W_LO && !n->d.W_lo) {   // a plain master: its low parts are zero
+        if (dst_on_device) CUDA_TRY(n, cudaMemsetAsync(dst, 0, want, st));
+        else std::memset(dst, 0, want);
+        CUDA_TRY(n, cudaStreamSynchronize(st));
+        return SNN_OK;
+    }
+    if (field == SNN_FIELD_W_LO) src = n->d.W_lo;
     if (!src) {   // fields stored in another layout: extract on the device
         const snn::Consts c = make_consts(n, n->B, 1.0f, 0, 0, 0);
         void* out = dst;
@@ -741,6 +759,7 @@ snn_status snn_write_weights(snn_net* n, const float* src, size_t bytes, int src
                                 src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                 n->last));
     CUDA_TRY(n, snn::launch_clip_weights(n->d.W, count, n->spec.w_min, n->spec.w_max, n->last));
+    if (n->d.W_lo) CUDA_TRY(n, cudaMemsetAsync(n->d.W_lo, 0, count * 4, n->last));
     CUDA_TRY(n, cudaStreamSynchronize(n->last));
     return SNN_OK;
 }
@@ -754,10 +773,13 @@ snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes,
         case SNN_FIELD_REF_EXC: case SNN_FIELD_REF_INH: case SNN_FIELD_SPIKES_EXC:
         case SNN_FIELD_SPIKES_INH: case SNN_FIELD_THETA: case SNN_FIELD_STEP:
             break;
+        case SNN_FIELD_W_LO:
+            if (n->d.W_lo) break;
+            return fail(n, SNN_ERR_ARG, "snn_write_state: W_LO needs a compensated master");
         default:
             return fail(n, SNN_ERR_ARG, "snn_write_state: field %d is not writable", field);
     }
-    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP;
+    const bool per_sample = field != SNN_FIELD_THETA && field != SNN_FIELD_STEP && field != SNN_FIELD_W_LO;
     if (per_sample && n->B == 0)
         return fail(n, SNN_ERR_STATE,
                     "snn_write_state: no batch is allocated (run once with this batch, T may be 0)");
@@ -777,6 +799,7 @@ snn_status snn_write_state(snn_net* n, int field, const void* src, size_t bytes,
         case SNN_FIELD_X_POST: dst = n->d.x_post; break;
         case SNN_FIELD_THETA: dst = n->d.theta; break;
         case SNN_FIELD_STEP: dst = n->d.step + 1; break;
+        case SNN_FIELD_W_LO: dst = n->d.W_lo; break;
         default: break;
     }
     const snn::Consts c = make_consts(n, n->B, 1.0f, 0, 0, 0);

@@ -34,6 +34,7 @@ struct Consts {
     int rule;           // snn_rule of the weight update
     float w_norm;       // SNN_RULE_POST_NORM: incoming weight sum of an updated column
     int neuron;         // snn_neuron of the excitatory population
+    int wmaster;        // snn_wmaster: 1 = the compensated pair (W, W_lo)
 };
 
 // One step of an excitatory membrane (every run form uses it): the leaky
@@ -99,12 +100,37 @@ __device__ __forceinline__ uint32_t pair_update(const Consts& c, float& v, float
     return (uint32_t)ref_e | ((uint32_t)ref_i << 8) | (se ? ST_SE : 0u) | (si ? ST_SI : 0u);
 }
 
+// W = clip(W + D) on a compensated master pair (h, l), each line one FP32
+// operation: TwoSum of h + D (exact error e), l + e, Fast2Sum renormalisation,
+// and the clip of the pair (below w_min or at it with a negative low part:
+// (w_min, 0); above w_max or at it with a positive low part: (w_max, 0)).
+__device__ __forceinline__ void master_add(float& h, float& l, float D, float w_min, float w_max) {
+    const float s = __fadd_rn(h, D);
+    const float b = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, b)), __fsub_rn(D, b));
+    const float l1 = __fadd_rn(l, e);
+    float h2 = __fadd_rn(s, l1);
+    float l2 = __fsub_rn(l1, __fsub_rn(h2, s));
+    if (h2 < w_min || (h2 == w_min && l2 < 0.0f)) { h2 = w_min; l2 = 0.0f; }
+    if (h2 > w_max || (h2 == w_max && l2 > 0.0f)) { h2 = w_max; l2 = 0.0f; }
+    h = h2;
+    l = l2;
+}
+
+// W = clip(W + D) on a plain FP32 master.
+__device__ __forceinline__ float plain_add(float w, float D, float w_min, float w_max) {
+    w = __fadd_rn(w, D);
+    w = w < w_min ? w_min : w;
+    return w > w_max ? w_max : w;
+}
+
 // Device buffers of one network.  Batch-major "[B][N]" arrays index b*N + j.
 // Buffers indexed by the absolute step tt rotate so that one step's writers
 // never overwrite what the previous step's readers may still use:
 //   [2]: buffer tt&1 holds the value of step tt;  [3]: buffer tt%3.
 struct Bufs {
-    float* W;            // [n_in][N]  FP32 master weights
+    float* W;            // [n_in][N]  FP32 master weights (the high parts h of a compensated master)
+    float* W_lo;         // [n_in][N]  low parts l of a compensated master (NULL otherwise)
     double* theta;       // [N]        adaptive thresholds (FP64)
     uint32_t* thr;       // [B][n_in]  Poisson thresholds of this run
     uint64_t* seeds;     // [B]        per-sample Poisson seeds

@@ -52,7 +52,7 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 struct Layout {
     int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
     int nst;                     // row stride (floats) of the weight and depression-term tiles
-    size_t o_ws, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
+    size_t o_ws, o_wlo, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
     // phase-local region: neuron-phase staging, encode scratch, STDP mask copy
     size_t o_cnts, o_actn, o_acts;    // neuron phase
     size_t o_pres;                    // STDP phase (max reduction, list overflow)
@@ -78,6 +78,7 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.nst = (L.ncmax + 3) & ~3;                           // 16-byte rows: 4 columns per load
     size_t o = 0;
     L.o_ws = o;  o = align16(o + (size_t)c.n_in * L.nst * 4);
+    L.o_wlo = o; o = align16(o + (c.wmaster ? (size_t)c.n_in * L.nst * 4 : 0));   // compensated master
     L.o_es = o;  o = align16(o + (size_t)c.B * L.nst * 4);
     L.o_sm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
     L.o_qm = o;  o = align16(o + (size_t)c.Bw * L.ncmax * 4);
@@ -338,7 +339,7 @@ __device__ __forceinline__ float deposit(float acc, float e) {
 
 template <int RED, bool LISTS, bool NARROW>
 __device__ __noinline__ void depress_quiet_columns(
-        const Consts& c, float* Ws, const float* Es, const uint32_t* preS, const int* offs,
+        const Consts& c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
     const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
@@ -406,10 +407,28 @@ __device__ __noinline__ void depress_quiet_columns(
             float* wr = Ws + i * nst + (j < nst ? j : 0);
             const float4 w = *(const float4*)wr;
             float4 u;
-            u.x = fminf(fmaxf(__fadd_rn(w.x, a0), c.w_min), c.w_max);
-            u.y = fminf(fmaxf(__fadd_rn(w.y, a1), c.w_min), c.w_max);
-            u.z = fminf(fmaxf(__fadd_rn(w.z, a2), c.w_min), c.w_max);
-            u.w = fminf(fmaxf(__fadd_rn(w.w, a3), c.w_min), c.w_max);
+            if (WLs) {                                   // compensated master: the pairs
+                float* lr = WLs + i * nst + (j < nst ? j : 0);
+                float4 l = *(const float4*)lr;
+                u = w;
+                master_add(u.x, l.x, a0, c.w_min, c.w_max);
+                master_add(u.y, l.y, a1, c.w_min, c.w_max);
+                master_add(u.z, l.z, a2, c.w_min, c.w_max);
+                master_add(u.w, l.w, a3, c.w_min, c.w_max);
+                if (all4) {
+                    *(float4*)lr = l;
+                } else {
+                    if (v0) lr[0] = l.x;
+                    if (v1) lr[1] = l.y;
+                    if (v2) lr[2] = l.z;
+                    if (v3) lr[3] = l.w;
+                }
+            } else {
+                u.x = fminf(fmaxf(__fadd_rn(w.x, a0), c.w_min), c.w_max);
+                u.y = fminf(fmaxf(__fadd_rn(w.y, a1), c.w_min), c.w_max);
+                u.z = fminf(fmaxf(__fadd_rn(w.z, a2), c.w_min), c.w_max);
+                u.w = fminf(fmaxf(__fadd_rn(w.w, a3), c.w_min), c.w_max);
+            }
             // columns with a post spike belong to the other pass: store only ours
             if (all4) {
                 *(float4*)wr = u;
@@ -432,7 +451,7 @@ __device__ __noinline__ void depress_quiet_columns(
 // is 0 where a column has not fired).  Wide layers only: with at most four
 // columns a CTA has too few groups to keep its warps busy.
 __device__ __forceinline__ void update_post_column_groups(
-        const Consts& c, float* Ws, const float* Es, const uint32_t* Qm, const int* pcol, const int* offs,
+        const Consts& c, float* Ws, float* WLs, const float* Es, const uint32_t* Qm, const int* pcol, const int* offs,
         const uint16_t* lst, const float* xpre, int npc, int NI, int nc, int nst, int Bw, bool dep_on,
         int warp, int lane) {
     const int nch = (NI + 31) / 32, ngr = (npc + PG - 1) / PG;
@@ -502,10 +521,8 @@ __device__ __forceinline__ void update_post_column_groups(
             float D = __fsub_rn(pot[k], dep[k]);
             if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
             float* wp = Ws + i * nst + jls[k];
-            float wv = __fadd_rn(*wp, D);
-            wv = wv < c.w_min ? c.w_min : wv;
-            wv = wv > c.w_max ? c.w_max : wv;
-            *wp = wv;
+            if (WLs) master_add(*wp, WLs[i * nst + jls[k]], D, c.w_min, c.w_max);
+            else *wp = plain_add(*wp, D, c.w_min, c.w_max);
         }
     }
 }
@@ -712,6 +729,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
              const __grid_constant__ Layout L) {
     extern __shared__ __align__(16) unsigned char sm[];
     float* Ws = (float*)(sm + L.o_ws);
+    float* WLs = c.wmaster ? (float*)(sm + L.o_wlo) : nullptr;   // low parts of a compensated master
     float* Es = (float*)(sm + L.o_es);               // e_bj = nu_pre x_post[b][j] of this step
     uint32_t* Sm = (uint32_t*)(sm + L.o_sm);
     uint32_t* Qm = (uint32_t*)(sm + L.o_qm);
@@ -746,6 +764,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     for (int k = tid; k < NI * nst; k += PT) {
         const int i = k / nst, jl = k % nst;
         Ws[k] = jl < nc ? d.W[(size_t)i * N + j0 + jl] : 0.0f;
+        if (WLs) WLs[k] = jl < nc ? d.W_lo[(size_t)i * N + j0 + jl] : 0.0f;
     }
     for (int k = tid; k < B * nst; k += PT) Es[k] = 0.0f;
     for (int k = tid; k < Bw * nc; k += PT) {
@@ -1007,8 +1026,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 }
             } else {
 #define SNN_PASS_A_N(R, NR)                                                                        \
-    (lists ? depress_quiet_columns<R, true, NR>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
-           : depress_quiet_columns<R, false, NR>(c, Ws, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+    (lists ? depress_quiet_columns<R, true, NR>(c, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
+           : depress_quiet_columns<R, false, NR>(c, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
 #define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)
                 if (c.reduce == SNN_REDUCE_MAX) SNN_PASS_A(RED_MAX);
                 else if (c.reduce == SNN_REDUCE_SUM) SNN_PASS_A(RED_SUM);
@@ -1028,7 +1047,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 const bool grouped = !NARROW && lists && c.reduce != SNN_REDUCE_MAX;
                 if constexpr (!NARROW)
                     if (grouped)
-                        update_post_column_groups(c, Ws, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw,
+                        update_post_column_groups(c, Ws, WLs, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw,
                                                   dep_on, warp, lane);
                 // Otherwise task = (column, 32 rows): potentiation over the column's
                 // post-spiking samples, the same for every lane, XC at a time with
@@ -1113,10 +1132,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     float D = is_max ? pot : __fsub_rn(pot, dep);
                     if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
                     if (is_max && nev < B) D = fmaxf(D, 0.0f);
-                    float wv = __fadd_rn(Ws[i * nst + jl], D);
-                    wv = wv < c.w_min ? c.w_min : wv;
-                    wv = wv > c.w_max ? c.w_max : wv;
-                    Ws[i * nst + jl] = wv;
+                    if (WLs) master_add(Ws[i * nst + jl], WLs[i * nst + jl], D, c.w_min, c.w_max);
+                    else Ws[i * nst + jl] = plain_add(Ws[i * nst + jl], D, c.w_min, c.w_max);
                 }
             }
             __syncthreads();
@@ -1180,6 +1197,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         for (int k = tid; k < NI * nc; k += PT) {
             const int i = k / nc, jl = k % nc;
             d.W[(size_t)i * N + j0 + jl] = Ws[i * nst + jl];
+            if (WLs) d.W_lo[(size_t)i * N + j0 + jl] = WLs[i * nst + jl];
         }
         for (int jl = tid; jl < nc; jl += PT) d.theta[j0 + jl] = thS[jl];
     }

@@ -260,11 +260,15 @@ __global__ void __launch_bounds__(256) k_stdp(Consts c, Bufs d, int t_local) {
             float D = REDUCE == SNN_REDUCE_MAX ? acc : __fsub_rn(acc, dep_sum);
             if (REDUCE == SNN_REDUCE_MEAN) D = batch_mean(c, D);
             if (REDUCE == SNN_REDUCE_MAX && nev < c.B) D = fmaxf(D, 0.0f);  // idle samples add 0
-            float wv = d.W[(size_t)i * c.N + j];
-            wv = __fadd_rn(wv, D);
-            wv = wv < c.w_min ? c.w_min : wv;
-            wv = wv > c.w_max ? c.w_max : wv;
-            d.W[(size_t)i * c.N + j] = wv;
+            const size_t k = (size_t)i * c.N + j;
+            if (c.wmaster) {
+                float h = d.W[k], l = d.W_lo[k];
+                master_add(h, l, D, c.w_min, c.w_max);
+                d.W[k] = h;
+                d.W_lo[k] = l;
+            } else {
+                d.W[k] = plain_add(d.W[k], D, c.w_min, c.w_max);
+            }
         }
     }
 }

@@ -472,14 +472,19 @@ __global__ void __launch_bounds__(128) k_t_gcurrent(Consts c, Bufs d, TBufs t, i
 // input tile 0, slice 0 also update theta.
 constexpr int DW_KSMAX = 4;                                    // batch slices per tile (cluster size)
 
-// W[i0 .. i0+15][j] (zeros outside the layer).
-struct WChunk { float w[16]; };
+// W[i0 .. i0+15][j] and, for a compensated master, its low parts (zeros
+// outside the layer).
+struct WChunk { float w[16], l[16]; };
 
 __device__ __forceinline__ void wchunk_load(const Consts& c, const Bufs& d, int j, int i0, WChunk& wc) {
     const bool vj = j < c.N;
 #pragma unroll
-    for (int u = 0; u < 16; ++u)
-        wc.w[u] = (vj && i0 + u < c.n_in) ? d.W[(size_t)(i0 + u) * c.N + j] : 0.0f;
+    for (int u = 0; u < 16; ++u) {
+        const bool ok = vj && i0 + u < c.n_in;
+        const size_t k = (size_t)(i0 + u) * c.N + j;
+        wc.w[u] = ok ? d.W[k] : 0.0f;
+        wc.l[u] = (ok && c.wmaster) ? d.W_lo[k] : 0.0f;
+    }
 }
 
 // W[i0 + u][j] += reduce(D[u]), clipped; then W^T's split for the next step's
@@ -492,10 +497,16 @@ __device__ __forceinline__ void wchunk_update(const Consts& c, const Bufs& d, co
     for (int u = 0; u < 16; ++u) {
         float x = D[u];
         if (c.reduce == SNN_REDUCE_MEAN) x = batch_mean(c, x);
-        float w = __fadd_rn(wc.w[u], x);
-        w = w < c.w_min ? c.w_min : w;
-        w = w > c.w_max ? c.w_max : w;
-        if (u < nu) d.W[(size_t)(i0 + u) * c.N + j] = w;
+        const size_t k = (size_t)(i0 + u) * c.N + j;
+        float w = wc.w[u];
+        if (c.wmaster) {
+            float l = wc.l[u];
+            master_add(w, l, x, c.w_min, c.w_max);
+            if (u < nu) d.W_lo[k] = l;
+        } else {
+            w = plain_add(w, x, c.w_min, c.w_max);
+        }
+        if (u < nu) d.W[k] = w;
         wc.w[u] = u < nu ? w : 0.0f;
     }
     uint16_t h[16][3];

@@ -43,20 +43,23 @@ MODES = {"step": SNN_MODE_STEP, "graph": SNN_MODE_GRAPH, "persistent": SNN_MODE_
 (SNN_FIELD_V_EXC, SNN_FIELD_V_INH, SNN_FIELD_REF_EXC, SNN_FIELD_REF_INH, SNN_FIELD_X_PRE,
  SNN_FIELD_X_POST, SNN_FIELD_THETA, SNN_FIELD_SPIKE_COUNTS, SNN_FIELD_RASTER_EXC,
  SNN_FIELD_RASTER_INH, SNN_FIELD_RASTER_INPUT, SNN_FIELD_STEP, SNN_FIELD_SPIKES_EXC,
- SNN_FIELD_SPIKES_INH) = range(14)
+ SNN_FIELD_SPIKES_INH, SNN_FIELD_W_LO) = range(15)
+SNN_WMASTER_FP32, SNN_WMASTER_COMPENSATED = 0, 1
 FIELDS = {"v_exc": SNN_FIELD_V_EXC, "v_inh": SNN_FIELD_V_INH, "ref_exc": SNN_FIELD_REF_EXC,
           "ref_inh": SNN_FIELD_REF_INH, "x_pre": SNN_FIELD_X_PRE, "x_post": SNN_FIELD_X_POST,
           "theta": SNN_FIELD_THETA, "spike_counts": SNN_FIELD_SPIKE_COUNTS,
           "raster_exc": SNN_FIELD_RASTER_EXC, "raster_inh": SNN_FIELD_RASTER_INH,
           "raster_input": SNN_FIELD_RASTER_INPUT, "step": SNN_FIELD_STEP,
-          "spikes_exc": SNN_FIELD_SPIKES_EXC, "spikes_inh": SNN_FIELD_SPIKES_INH}
+          "spikes_exc": SNN_FIELD_SPIKES_EXC, "spikes_inh": SNN_FIELD_SPIKES_INH,
+          "w_lo": SNN_FIELD_W_LO}
 FIELD_DTYPE = {SNN_FIELD_V_EXC: np.float32, SNN_FIELD_V_INH: np.float32,
                SNN_FIELD_REF_EXC: np.uint8, SNN_FIELD_REF_INH: np.uint8,
                SNN_FIELD_X_PRE: np.float32, SNN_FIELD_X_POST: np.float32,
                SNN_FIELD_THETA: np.float64, SNN_FIELD_SPIKE_COUNTS: np.uint32,
                SNN_FIELD_RASTER_EXC: np.uint32, SNN_FIELD_RASTER_INH: np.uint32,
                SNN_FIELD_RASTER_INPUT: np.uint32, SNN_FIELD_STEP: np.uint64,
-               SNN_FIELD_SPIKES_EXC: np.uint8, SNN_FIELD_SPIKES_INH: np.uint8}
+               SNN_FIELD_SPIKES_EXC: np.uint8, SNN_FIELD_SPIKES_INH: np.uint8,
+               SNN_FIELD_W_LO: np.float32}
 
 EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_field_bytes",
             "snn_read_state", "snn_write_state", "snn_read_weights", "snn_write_weights",
@@ -78,7 +81,7 @@ class snn_spec(C.Structure):
             "w_ei", "w_ie", "trace_tau_ms", "nu_pre", "nu_post", "w_min", "w_max")] + [
         ("wprec", C.c_int32), ("rule", C.c_int32), ("w_norm", C.c_float), ("neuron", C.c_int32),
         ("w_seed", C.c_uint64), ("w_init", C.c_void_p),
-        ("theta_init", C.c_void_p)]
+        ("theta_init", C.c_void_p), ("wmaster", C.c_int32)]
 
 
 class snn_rec_spec(C.Structure):
@@ -431,6 +434,8 @@ class Network:
             return out
         if f == SNN_FIELD_X_PRE:
             return out.reshape(self.B, NI)
+        if f == SNN_FIELD_W_LO:
+            return out.reshape(NI, N)
         if f in (SNN_FIELD_RASTER_EXC, SNN_FIELD_RASTER_INH):
             return out.reshape(self.T, self.B, (N + 31) // 32)
         if f == SNN_FIELD_RASTER_INPUT:

@@ -54,7 +54,7 @@ def read_all(net):
                 ref_e=net.read("ref_exc"), ref_i=net.read("ref_inh"), w=net.weights(),
                 theta=net.read("theta"), counts=net.read("spike_counts"),
                 s_e=net.read("spikes_exc"), s_i=net.read("spikes_inh"),
-                step=int(net.read("step")[0]))
+                step=int(net.read("step")[0]), w_lo=net.read("w_lo"))
 
 
 def gpu_run(p, rates, seeds, w, T, *, learn=True, reduce="mean", mode="step", theta=None,
@@ -90,7 +90,8 @@ def assert_parity(g, st, rec):
             name, first_diff_step(g[name], ref))
     expect = dict(v_e=st.v_e, v_i=st.v_i, x_pre=st.x_pre, x_post=st.x_post,
                   ref_e=st.ref_e.astype(np.uint8), ref_i=st.ref_i.astype(np.uint8),
-                  w=st.w, theta=st.theta, counts=rec.counts_e, s_e=st.s_e, s_i=st.s_i)
+                  w=st.w, theta=st.theta, counts=rec.counts_e, s_e=st.s_e, s_i=st.s_i,
+                  w_lo=st.w_lo)
     for k, ref in expect.items():
         got = g[k]
         assert got.shape == ref.shape, k
@@ -213,6 +214,43 @@ def test_reduced_precision_weights_bit_exact(wprec):
     oracle computing with the same weight precision, learning on."""
     p, r, s, w = synth.workload(16, 400)
     parity_all_modes(p, r, s, w, 250, wprec=wprec)
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+@pytest.mark.parametrize("N", [400, 1500])
+def test_compensated_master_bit_exact(reduce, N):
+    """The compensated FP32 master (TwoSum of W + D into a low part, Fast2Sum
+    renormalisation, the pair clipped): high and low parts bit-exact with the
+    oracle in every ordered form, in the narrow (784 -> 400) and the wide
+    (784 -> 1500, grouped post columns) persistent instantiations."""
+    p, r, s, w = synth.workload(16, N)
+    p = dict(p, wmaster=1)
+    st, rec = parity_all_modes(p, r, s, w, 150 if N > 1000 else 250, reduce=reduce)
+    assert np.any(st.w_lo != 0)
+
+
+def test_compensated_master_checkpoint_fields():
+    """snn_write_weights clears the low parts; SNN_FIELD_W_LO writes them back,
+    so a fresh network continues a compensated run bit for bit."""
+    m = snn()
+    p, r, s, w = synth.workload(8, 100)
+    p = dict(p, wmaster=1)
+    a = m.Network(p, w_init=w)
+    a.run(dev(r), dev(s), 120, mode="persistent")
+    lo = a.read("w_lo")
+    assert np.any(lo != 0)
+    b = m.Network(p, w_init=a.weights(), theta_init=a.read("theta"))
+    assert not np.any(b.read("w_lo"))
+    b.write("w_lo", lo)
+    for net in (a, b):
+        net.run(dev(r), dev(s), 100, mode="step", record=True)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.raster(), b.raster())
+    assert np.array_equal(bits(a.weights()), bits(b.weights()))
+    assert np.array_equal(bits(a.read("w_lo")), bits(b.read("w_lo")))
+    c = m.Network(synth.diehl_cook_params(100), w_init=w)     # a plain master refuses the field
+    with pytest.raises(m.SNNError):
+        c.write("w_lo", lo)
 
 
 def test_bf16_weights_on_the_bf16_exact_grid_equal_fp32():

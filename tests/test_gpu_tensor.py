@@ -171,6 +171,23 @@ def test_bf16_weights_bit_exact_on_the_bf16_grid_and_close_off_it():
     assert_within_tolerance(g, st, rec, 150, w)
 
 
+def test_compensated_master_within_tolerance():
+    """The tensor form with the compensated master: h + l against the oracle's
+    within the stated tolerance (the update products sum in the tensor cores'
+    order; the accumulation into the pair is the same operation sequence)."""
+    p, r, s, w = synth.workload(32, 400)
+    p = dict(p, wmaster=1)
+    st = oracle.new_state(p, 32, w)
+    rec = oracle.run(p, st, r, s, 250, learn=True, reduce="mean")
+    net, g = run_gpu(p, r, s, w, 250, mode="tensor")
+    div, _ = assert_within_tolerance(g, st, rec, 250, w)
+    if div is None:
+        lo = net.read("w_lo")
+        full = g["w"].astype(np.float64) + lo
+        assert np.abs(full - (st.w.astype(np.float64) + st.w_lo)).max() <= 1e-5
+        assert np.any(lo != 0)
+
+
 @pytest.mark.parametrize("modes", [("tensor", "persistent", "tensor"), ("step", "tensor", "graph"),
                                    ("tensor_gather", "tensor", "persistent")])
 def test_continuing_runs_switch_forms(modes):
