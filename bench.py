@@ -83,6 +83,9 @@ def parse():
                     help="the batch sweep instead: 784->400 at B=1..1024 (mean and sum) and "
                          "784->6400 at B=256 and 1024 in every run form (one JSON line)")
     ap.add_argument("--sweep-modes", default="step,graph,persistent,tensor,tensor_gather")
+    ap.add_argument("--precision", action="store_true",
+                    help="each weight precision and master against the FP64 oracle, and the "
+                         "master drift over presentations (one JSON line)")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="the CPU oracle against batch size (784->100 and 784->400) instead "
                          "(one JSON line; needs no GPU)")
@@ -348,6 +351,158 @@ def sweep_leg(a):
                 print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     print(json.dumps({"experiment": "batch sweep, 784->400 and 784->6400, pair STDP, T=%d, FP32" % a.T,
                       "unit": UNIT, "rows": rows, "clocks": clk.summary()}), flush=True)
+
+
+def _chunked_gpu(snn, torch, p, r, s, w, T, chunks, mode, wprec):
+    """Run T steps in continuing chunks of the given lengths; the excitatory
+    raster of every step and the excitatory voltages after each chunk; the
+    final W (h + l for a compensated master) and theta."""
+    net = snn.Network(p, w_init=w, wprec=wprec)
+    rd = torch.from_numpy(r).cuda()
+    sd = torch.from_numpy(s.view(np.int64)).cuda()
+    rasters, volts = [], []
+    t0 = 0
+    for n in chunks:
+        n = min(n, T - t0)
+        if n <= 0:
+            break
+        net.run(rd, sd, n, mode=mode, record=True, continue_=t0 > 0)
+        torch.cuda.synchronize()
+        rasters.append(net.raster("raster_exc"))
+        volts.append(net.read("v_exc").astype(np.float64))
+        t0 += n
+    wf = net.weights().astype(np.float64) + net.read("w_lo").astype(np.float64)
+    th = net.read("theta")
+    net.close()
+    return np.concatenate(rasters), volts, wf, th
+
+
+def _replay_drift(raster_in, raster_e, p, w0, B, reduce="mean"):
+    """W after each presentation, replaying recorded spike trains through the
+    pair-trace update in FP64, in FP32 with a plain master, in FP32 with the
+    compensated master, and the FP32 updates accumulated in FP64 (so that the
+    last two differ from it by the accumulation alone)."""
+    a_x = np.float32(np.exp(-1.0 / p["trace_tau"]))
+    a64 = float(np.exp(-1.0 / p["trace_tau"]))
+    nup, nun = p["nu_post"], p["nu_pre"]
+    w64 = w0.astype(np.float64)
+    w32 = w0.astype(np.float32)
+    h, l = w0.astype(np.float32), np.zeros_like(w0, np.float32)
+    acc = w0.astype(np.float64)
+    rows = []
+    f32 = np.float32
+    for pres in range(raster_in.shape[0]):
+        xp64 = np.zeros((B, p["n_in"])); xq64 = np.zeros((B, p["n_exc"]))
+        xp32 = np.zeros((B, p["n_in"]), f32); xq32 = np.zeros((B, p["n_exc"]), f32)
+        for t in range(raster_in.shape[1]):
+            si, se = raster_in[pres, t].astype(np.float64), raster_e[pres, t].astype(np.float64)
+            xp64 = xp64 * a64 + si
+            xq64 = xq64 * a64 + se
+            d64 = (nup * xp64.T @ se - nun * si.T @ xq64)
+            xp32 = (xp32 * a_x + si.astype(f32)).astype(f32)
+            xq32 = (xq32 * a_x + se.astype(f32)).astype(f32)
+            d32 = ((f32(nup) * xp32).T @ se.astype(f32) - si.T.astype(f32) @ (f32(nun) * xq32)).astype(f32)
+            if reduce == "mean":
+                d64 = d64 / B
+                d32 = (d32 / f32(B)).astype(f32)
+            w64 = np.clip(w64 + d64, p["w_min"], p["w_max"])
+            w32 = np.clip((w32 + d32).astype(f32), p["w_min"], p["w_max"]).astype(f32)
+            acc = np.clip(acc + d32.astype(np.float64), p["w_min"], p["w_max"])
+            s_ = (h + d32).astype(f32)
+            b_ = (s_ - h).astype(f32)
+            e_ = ((h - (s_ - b_)) + (d32 - b_)).astype(f32)
+            l1 = (l + e_).astype(f32)
+            h2 = (s_ + l1).astype(f32)
+            l2 = (l1 - (h2 - s_)).astype(f32)
+            lo = (h2 < p["w_min"]) | ((h2 == p["w_min"]) & (l2 < 0))
+            hi = (h2 > p["w_max"]) | ((h2 == p["w_max"]) & (l2 > 0))
+            h2[lo], l2[lo] = p["w_min"], 0.0
+            h2[hi], l2[hi] = p["w_max"], 0.0
+            h, l = h2, l2
+        full = h.astype(np.float64) + l
+        rows.append({"presentation": pres + 1,
+                     "plain_vs_fp64": float(np.abs(w32 - w64).max()),
+                     "compensated_vs_fp64": float(np.abs(full - w64).max()),
+                     "plain_accumulation_error": float(np.abs(w32 - acc).max()),
+                     "compensated_accumulation_error": float(np.abs(full - acc).max())})
+    return rows
+
+
+def precision_leg(a):
+    """Each precision form against the FP64 oracle on the 784 -> 6400, B = 256,
+    T = 250 workload (pair STDP, mean reduction), and the drift of the plain
+    and compensated FP32 masters over many presentations."""
+    import torch
+    import oracle
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1909_02549_gb300 import snn, synth
+    B, N, T = a.batch, a.n_exc, a.T
+    # checkpoints: every step for the first 10, every 5 to 50, then every 25
+    chunks = [1] * 10 + [5] * 8 + [25] * ((T - 50 + 24) // 25)
+    p, r, s, w = synth.workload(B, N)
+    oracle.build()
+    oracle.set_threads(host_cores())
+    t0 = time.perf_counter()
+    st = oracle.new_state(p, B, w, dtype=np.float64)
+    ras64, v64 = [], []
+    t_done = 0
+    for k, n in enumerate(chunks):
+        n = min(n, T - t_done)
+        if n <= 0:
+            break
+        rec = oracle.run(p, st, r, s, n, learn=True, reduce="mean", episodic=k == 0)
+        ras64.append(rec.raster_e)
+        v64.append(st.v_e.copy())
+        t_done += n
+    ras64 = np.concatenate(ras64)
+    oracle_s = time.perf_counter() - t0
+    forms = [("FP32, plain master, persistent", "persistent", 0, 0),
+             ("FP32, plain master, tensor form", "tensor", 0, 0),
+             ("FP32, compensated master, graph", "graph", 0, 1),
+             ("FP32, compensated master, tensor form", "tensor", 0, 1),
+             ("BF16 weights, tensor form (one bfloat16 term)", "tensor", 1, 0),
+             ("BF16 weights, persistent", "persistent", 1, 0),
+             ("FP8 E4M3 + column scales, persistent", "persistent", 2, 0)]
+    rows = []
+    for name, mode, wprec, master in forms:
+        pp = dict(p, wmaster=master)
+        ras, volts, wf, th = _chunked_gpu(snn, torch, pp, r, s, w, T, chunks, mode, wprec)
+        diff = (ras != ras64).reshape(T, -1).any(1)
+        first = int(np.flatnonzero(diff)[0]) if diff.any() else None
+        vrel, t_end = 0.0, 0
+        for n, vg, vo in zip(chunks, volts, v64):
+            t_end += n
+            if first is not None and t_end > first:      # the checkpoint after the divergence
+                break
+            vrel = max(vrel, float((np.abs(vg - vo) / np.abs(vo)).max()))
+        rows.append({"form": name, "first_raster_divergence": first,
+                     "raster_agreement": float((ras == ras64).mean()),
+                     "max_rel_v_error_before_divergence": vrel,
+                     "max_abs_w_error_at_T": float(np.abs(wf - st.w).max()),
+                     "max_abs_theta_error_at_T": float(np.abs(th - st.theta).max())})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    # drift over presentations: 784 -> 400, B = 16, spike trains of a persistent run
+    P, Bd, Nd = 30, 16, 400
+    pd, rd_, sd_, wd = synth.workload(Bd, Nd)
+    net = snn.Network(pd, w_init=wd)
+    rin, rex = [], []
+    for _ in range(P):
+        net.run(torch.from_numpy(rd_).cuda(), torch.from_numpy(sd_.view(np.int64)).cuda(), T,
+                mode="persistent", record=True, record_input=True)
+        torch.cuda.synchronize()
+        rin.append(net.raster("raster_input"))
+        rex.append(net.raster("raster_exc"))
+    net.close()
+    drift = _replay_drift(np.stack(rin), np.stack(rex), pd, wd, Bd)
+    oracle.set_threads(1)
+    print(json.dumps({"experiment": "precision forms vs the FP64 oracle: 784->%d, B=%d, T=%d, pair "
+                                    "STDP, mean reduction (voltage checkpoints after steps 1..10, "
+                                    "every 5 to 50, then every 25)" % (N, B, T),
+                      "fp64_oracle_seconds": oracle_s, "threads": host_cores(), "rows": rows,
+                      "drift": {"workload": "784->400, B=16, %d presentations of T=%d, spike trains "
+                                            "of a persistent FP32 run replayed" % (P, T),
+                                "rows": drift}}), flush=True)
 
 
 def cpu_sweep_leg(a):
@@ -889,6 +1044,9 @@ def main():
         return
     if a.sweep:
         sweep_leg(a)
+        return
+    if a.precision:
+        precision_leg(a)
         return
     if a.rec:
         rec_leg(a)
