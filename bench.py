@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--precision", action="store_true",
                     help="each weight precision and master against the FP64 oracle, and the "
                          "master drift over presentations (one JSON line)")
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="serving latency and throughput against the arrival rate (one JSON line)")
     ap.add_argument("--cpu-sweep", action="store_true",
                     help="the CPU oracle against batch size (784->100 and 784->400) instead "
                          "(one JSON line; needs no GPU)")
@@ -690,17 +692,18 @@ def profile_roofline(a, net, snn, flush, run, restore, B, N, T, learn):
                 "traffic": None, "error": str(e)[:300]}
 
 
-def serving_leg(a, torch, snn, synth):
+def serving_point(torch, snn, synth, rate: float, dur: float, cap_bytes: int, k: int = 10,
+                  max_requests: int = 6000, seed: int = 11):
     """Continuous batching on the frozen 784->400 network: requests arrive as a
-    Poisson process at 2000/s, each one image with a length uniform in
-    50..500 steps; p50/p99 latency and throughput, beside the plain
-    fixed-batch form (batches of 256 in arrival order, each run to its
-    longest member) on the same arrivals."""
+    Poisson process at `rate` per second, each one image with a length uniform
+    in 50..500 steps; p50/p99 latency and throughput, beside the plain
+    fixed-batch form (batches of 256 in arrival order, each run to its longest
+    member) on the same arrivals."""
     import time as _t
-    N, rate, dur = 400, 2000.0, a.serve_seconds
-    rng = np.random.default_rng(11)
-    gaps = rng.exponential(1.0 / rate, int(rate * dur * 1.5) + 16)
-    arr = np.cumsum(gaps)
+    N = 400
+    rng = np.random.default_rng(seed)
+    n_max = min(max_requests, int(rate * dur * 1.5) + 16)
+    arr = np.cumsum(rng.exponential(1.0 / rate, n_max))
     arr = arr[arr < dur]
     n = len(arr)
     lengths = rng.integers(50, 501, n)
@@ -708,11 +711,10 @@ def serving_leg(a, torch, snn, synth):
     seeds = synth.sample_seeds(n, first=20000)
     p = synth.diehl_cook_params(N)
     net = snn.Network(p, w_init=synth.weights(784, N))
-    srv = snn.snn_serve_create(net.handle, 4096, 64 << 30)
+    srv = snn.snn_serve_create(net.handle, 4096, cap_bytes)
     slots = snn.snn_serve_status(srv)["slots"]
     lat = np.zeros(n)
-    done = 0
-    q = 0
+    done = q = peak = 0
     id2q = {}
     t0 = _t.perf_counter()
     while done < n:
@@ -721,25 +723,27 @@ def serving_leg(a, torch, snn, synth):
             id2q[snn.snn_serve_submit(srv, rates[q], int(seeds[q]), int(lengths[q]))] = q
             q += 1
         st = snn.snn_serve_status(srv)
+        peak = max(peak, st["active"])
         if st["active"] == 0 and st["queued"] == 0:
-            if q < n:
+            if st["done"] == 0 and q < n:
                 while _t.perf_counter() - t0 < arr[q]:
                     pass
-            continue
-        snn.snn_serve_step(srv, 10)
+                continue
+        else:
+            snn.snn_serve_step(srv, k)
         ids, _ = snn.snn_serve_poll(srv, N)
         tnow = _t.perf_counter() - t0
         for rid in ids:
-            k = id2q[int(rid)]
-            lat[k] = tnow - arr[k]
+            kq = id2q[int(rid)]
+            lat[kq] = tnow - arr[kq]
             done += 1
     wall = _t.perf_counter() - t0
     snn.snn_serve_destroy(srv)
     steps = int(lengths.sum())
     cont = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "requests": n, "req_per_s": n / wall, "sample_timesteps_per_s": steps / wall,
-            "wall_s": wall, "slots": slots, "slot_bytes": snn.snn_serve_slot_bytes(net.handle)}
-    # fixed-batch form on the same arrivals
+            "wall_s": wall, "slots": slots, "peak_active_slots": peak,
+            "slot_bytes": snn.snn_serve_slot_bytes(net.handle)}
     Bf = 256
     lat2 = np.zeros(n)
     t0 = _t.perf_counter()
@@ -758,9 +762,37 @@ def serving_leg(a, torch, snn, synth):
              "p99_ms": float(np.percentile(lat2, 99) * 1e3), "req_per_s": n / wall2,
              "sample_timesteps_per_s": steps / wall2}
     net.close()
-    return {"workload": "frozen 784->400, Poisson arrivals %.0f/s for %.1f s, lengths U{50..500}, "
-                        "state cap 64 GB" % (rate, dur),
+    return {"arrivals_per_s": rate, "seconds": dur, "state_cap_bytes": cap_bytes,
             "continuous": cont, "fixed_batch": fixed}
+
+
+def serving_leg(a, torch, snn, synth):
+    """The serving workload: frozen 784->400, Poisson arrivals at 2000/s for a
+    few seconds, lengths U{50..500}, a 64 GB state cap."""
+    r = serving_point(torch, snn, synth, 2000.0, a.serve_seconds, 64 << 30)
+    r["workload"] = ("frozen 784->400, Poisson arrivals 2000/s for %.1f s, lengths U{50..500}, "
+                     "state cap 64 GB" % a.serve_seconds)
+    return r
+
+
+def serve_sweep_leg(a):
+    """p50/p99 latency and throughput against the arrival rate, with the 64 GB
+    cap (slots bounded at 4096) and with a cap of 128 slots that binds."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1909_02549_gb300 import snn, synth
+    net = snn.Network(synth.diehl_cook_params(400), w_init=synth.weights(784, 400))
+    per = snn.snn_serve_slot_bytes(net.handle)
+    net.close()
+    rows = []
+    for cap_name, cap in (("64 GB", 64 << 30), ("128 slots", 128 * per)):
+        for rate in (2000.0, 10000.0, 50000.0, 200000.0):
+            dur = min(3.0, 5000.0 / rate)
+            rows.append(dict(serving_point(torch, snn, synth, rate, dur, cap), cap=cap_name))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"experiment": "serving latency against load, frozen 784->400, lengths "
+                                    "U{50..500}, k=10 steps per call", "rows": rows}), flush=True)
 
 
 # ------------------------------------------------------------ our arm ---
@@ -1047,6 +1079,9 @@ def main():
         return
     if a.precision:
         precision_leg(a)
+        return
+    if a.serve_sweep:
+        serve_sweep_leg(a)
         return
     if a.rec:
         rec_leg(a)

@@ -267,7 +267,10 @@ SNN_API snn_status snn_write_weights(snn_net* net, const float* src, size_t byte
  * size", Sec. "Episodic vs. continuing simulation").  The network is frozen
  * (learning off) and must not be modified while a server uses it.  Each slot
  * counts its own steps, so a request's spike counts equal those of running it
- * alone with snn_run (B = 1, learning off).  Not thread-safe per server. */
+ * alone with snn_run (B = 1, learning off).  The device work of a call grows
+ * with the live slots, not with S (one CTA per live slot).  Calls do not wait
+ * for the device; all calls of a server must be ordered on the device (use
+ * one stream).  Not thread-safe per server. */
 typedef struct snn_server snn_server;
 
 /* Device bytes of one slot's state (what admission counts against the cap). */
@@ -284,18 +287,28 @@ SNN_API snn_status snn_serve_destroy(snn_server* server);
 SNN_API snn_status snn_serve_submit(snn_server* server, const float* rates_hz, uint64_t seed,
                                     int T, uint64_t* id);
 
-/* Admit queued requests into free slots, advance every active slot by up to
- * k steps (fewer if all active presentations end sooner; *steps_run, if not
- * NULL, receives the number), and retire the finished slots.  Synchronises
- * cuda_stream before returning.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+/* Admit queued requests into free slots, enqueue up to k steps of every
+ * active slot on cuda_stream (fewer if all active presentations end sooner;
+ * *steps_run, if not NULL, receives the number), and retire the slots whose
+ * presentation ends within them; their spike counts are copied to the host
+ * behind the steps.  Returns once the work is enqueued; it waits only when the
+ * call three calls back has not yet finished on the device (its host staging
+ * is reused), which bounds how far the host runs ahead.  Errors: SNN_ERR_ARG,
+ * SNN_ERR_CUDA. */
 SNN_API snn_status snn_serve_step(snn_server* server, int k, void* cuda_stream, int* steps_run);
 
-/* Drain up to max finished requests: ids [max], excitatory spike counts
- * [max][n_exc] (host); *n_out receives how many were written. */
+/* Drain up to max finished requests whose counts have reached the host: ids
+ * [max], excitatory spike counts [max][n_exc] (host); *n_out receives how
+ * many were written.  Does not wait. */
 SNN_API snn_status snn_serve_poll(snn_server* server, uint64_t* ids, uint32_t* counts, int max,
                                   int* n_out);
 
-/* Slots, active slots, queued and finished-but-unpolled requests (any may be NULL). */
+/* Wait until every enqueued step has finished and every retired request's
+ * counts are ready for snn_serve_poll.  Errors: SNN_ERR_ARG, SNN_ERR_CUDA. */
+SNN_API snn_status snn_serve_wait(snn_server* server);
+
+/* Slots, active slots, queued requests, and retired-but-unpolled requests
+ * (including those whose counts are still being copied); any may be NULL. */
 SNN_API snn_status snn_serve_status(const snn_server* server, int* slots, int* active,
                                     int* queued, int* done);
 

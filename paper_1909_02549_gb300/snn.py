@@ -66,6 +66,7 @@ EXPORTED = ["snn_spec_default", "snn_create", "snn_destroy", "snn_run", "snn_fie
             "snn_profile", "snn_tune", "snn_last_mode",
             "snn_infer_noalloc", "snn_serve_slot_bytes", "snn_serve_create", "snn_serve_destroy",
             "snn_serve_submit", "snn_serve_step", "snn_serve_poll", "snn_serve_status",
+            "snn_serve_wait",
             "snn_rec_create", "snn_rec_destroy", "snn_rec_run", "snn_rec_field_bytes",
             "snn_rec_read", "snn_rec_write", "snn_rec_form", "snn_rec_profile", "snn_rec_tune",
             "snn_rec_last_error",
@@ -159,8 +160,9 @@ def lib():
         L.snn_serve_poll.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
                                      C.POINTER(C.c_int)]
         L.snn_serve_status.argtypes = [C.c_void_p] + [C.POINTER(C.c_int)] * 4
+        L.snn_serve_wait.argtypes = [C.c_void_p]
         for name in ("snn_serve_create", "snn_serve_destroy", "snn_serve_submit",
-                     "snn_serve_step", "snn_serve_poll", "snn_serve_status"):
+                     "snn_serve_step", "snn_serve_poll", "snn_serve_status", "snn_serve_wait"):
             getattr(L, name).restype = C.c_int
         L.snn_last_error.argtypes = [C.c_void_p]
         L.snn_last_error.restype = C.c_char_p
@@ -352,6 +354,11 @@ def snn_serve_poll(server, n_exc: int, max_n: int = 4096):
     _check(None, lib().snn_serve_poll(server, ids.ctypes.data, counts.ctypes.data, max_n,
                                       C.byref(n)))
     return ids[:n.value], counts[:n.value]
+
+
+def snn_serve_wait(server) -> None:
+    """Wait for every enqueued step and every retired request's counts."""
+    _check(None, lib().snn_serve_wait(server))
 
 
 def snn_serve_status(server) -> dict:

@@ -59,16 +59,48 @@ def test_each_request_equals_its_alone_run_in_the_mix(wprec, neuron):
         if st["active"] == 0 and st["queued"] == 0 and q < nreq:
             continue
         m.snn_serve_step(srv, 7)                            # retirements fall mid-chunk
-        done_ids, counts = m.snn_serve_poll(srv, N)
+        done_ids, counts = m.snn_serve_poll(srv, N)         # (counts whose copy has landed)
         for rid, c in zip(done_ids, counts):
             got[ids[int(rid)]] = c
+        if q == nreq and len(got) < nreq and st["active"] == 0 and st["queued"] == 0:
+            m.snn_serve_wait(srv)
+    m.snn_serve_wait(srv)
     st = m.snn_serve_status(srv)
-    assert st["slots"] == 8 and st["active"] == 0 and st["queued"] == 0
+    assert st["slots"] == 8 and st["active"] == 0 and st["queued"] == 0 and st["done"] == 0
     m.snn_serve_destroy(srv)
     assert sum(int(c.sum()) for c in got.values()) > 0
     for k in range(nreq):
         want = alone_counts(p, w, wprec, rates[k], int(seeds[k]), int(lengths[k]))
         assert np.array_equal(got[k], want), k
+
+
+def test_calls_enqueue_without_waiting_and_results_arrive_in_order_of_retirement():
+    """Many calls enqueued back to back (the host does not wait for each);
+    after snn_serve_wait every request is ready, each equal to the oracle's
+    run of it alone, with capacity for only 3 slots (admission waits for
+    retirements: the slots bind)."""
+    m = snn()
+    N, nreq = 100, 12
+    p = synth.diehl_cook_params(N)
+    w = synth.weights(784, N)
+    net = m.Network(p, w_init=w)
+    srv = m.snn_serve_create(net.handle, 1000, 3 * m.snn_serve_slot_bytes(net.handle))
+    assert m.snn_serve_status(srv)["slots"] == 3
+    rates = synth.rates_from_images(synth.images(nreq))
+    seeds = synth.sample_seeds(nreq, first=7000)
+    lengths = np.arange(nreq) * 13 + 30
+    ids = {m.snn_serve_submit(srv, rates[q], int(seeds[q]), int(lengths[q])): q for q in range(nreq)}
+    calls = 0
+    while m.snn_serve_status(srv)["active"] or m.snn_serve_status(srv)["queued"]:
+        m.snn_serve_step(srv, 11)
+        calls += 1
+    m.snn_serve_wait(srv)
+    done_ids, counts = m.snn_serve_poll(srv, N, max_n=nreq)
+    assert len(done_ids) == nreq and calls > nreq // 3
+    for rid, c in zip(done_ids, counts):
+        k = ids[int(rid)]
+        assert np.array_equal(c, alone_counts(p, w, 0, rates[k], int(seeds[k]), int(lengths[k]))), k
+    m.snn_serve_destroy(srv)
 
 
 def test_slots_are_counted_against_the_state_byte_cap():
