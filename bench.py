@@ -288,18 +288,23 @@ def time_oracle(a, seconds: float, max_T: int | None = None):
             "single_thread": {"value": v1, "sample": "first %d steps, %.1f s" % (T1, el1)}}
 
 
-def sweep_point(snn, torch, flush, B, N, T, mode, reduce, learn, reps=3, warm=2):
+def sweep_point(snn, torch, flush, B, N, T, mode, reduce, learn, reps=3, warm=2, wprec=0, tune=False):
     """Device time of one presentation of the B x 784 -> N workload in one run
     form (W and theta restored before each, L2 flushed), and the per-kernel
-    split of a profiled presentation; None where the form does not take it."""
+    split of a profiled presentation; None where the form does not take it.
+    tune: snn_tune first (50 steps) and time the AUTO choice."""
     from paper_1909_02549_gb300 import synth
     p, r, s, w = synth.workload(B, N)
-    net = snn.Network(p, w_init=w)
+    net = snn.Network(p, w_init=w, wprec=wprec)
     rd = torch.from_numpy(r).cuda()
     sd = torch.from_numpy(s.view(np.int64)).cuda()
     w0 = torch.from_numpy(w).cuda()
     th0 = torch.zeros(N, dtype=torch.float64, device="cuda")
+    chosen = None
     try:
+        if tune:
+            chosen, _ = snn.snn_tune(net.handle, rd, sd, B, 50, learn=int(learn), reduce=snn.REDUCE[reduce])
+
         def one(profile=False):
             snn.snn_write_weights(net.handle, w0)
             snn.snn_write_state(net.handle, snn.SNN_FIELD_THETA, th0)
@@ -313,6 +318,7 @@ def sweep_point(snn, torch, flush, B, N, T, mode, reduce, learn, reps=3, warm=2)
         for _ in range(warm):
             one()
         ms = min(one() for _ in range(reps))
+        taken = snn.snn_last_mode(net.handle)
         one(profile=True)
         prof = {k: round(v[0], 4) for k, v in snn.snn_profile(net.handle).items() if v[1]}
     except snn.SNNError as e:
@@ -321,6 +327,7 @@ def sweep_point(snn, torch, flush, B, N, T, mode, reduce, learn, reps=3, warm=2)
         net.close()
     per = streaming_bytes_per_sample_step(B, N, 784, learn)
     return {"B": B, "n_exc": N, "mode": mode, "reduce": reduce, "learn": learn,
+            "weights": ("fp32", "bf16", "fp8")[wprec], "tuned_choice": chosen, "form_taken": taken,
             "ms_per_presentation": ms, "sample_timesteps_per_s": B * T / (ms * 1e-3),
             "roofline_frac": per * B * T / (ms * 1e-3) / peaks()["hbm_gbs"] / 1e9,
             "kernel_ms": prof}
@@ -338,19 +345,30 @@ def sweep_leg(a):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     modes = a.sweep_modes.split(",")
     rows = []
+
+    def add(row):
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+
     visible = os.environ.get("CUDA_VISIBLE_DEVICES")
     with ClockSampler(visible.split(",")[0] if visible else "0") as clk:
         for reduce in ("mean", "sum"):
             for B in (1, 4, 16, 64, 256, 1024):
                 for mode in modes:
-                    rows.append(sweep_point(snn, torch, flush, B, 400, a.T, mode, reduce, True))
-                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                    add(sweep_point(snn, torch, flush, B, 400, a.T, mode, reduce, True))
+                add(sweep_point(snn, torch, flush, B, 400, a.T, "auto", reduce, True, tune=True))
         for B in (256, 1024):
             for mode in modes:
                 if mode == "step" and B == 1024:
                     continue
-                rows.append(sweep_point(snn, torch, flush, B, 6400, a.T, mode, "mean", True, reps=2, warm=1))
-                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                add(sweep_point(snn, torch, flush, B, 6400, a.T, mode, "mean", True, reps=2, warm=1))
+            add(sweep_point(snn, torch, flush, B, 6400, a.T, "auto", "mean", True, reps=2, warm=1, tune=True))
+        # BF16 weights: one bfloat16 term in the tensor form's product
+        for B, N in ((1024, 400), (256, 6400), (1024, 6400)):
+            for mode in ("tensor", "persistent"):
+                if mode == "persistent" and (B, N) == (1024, 6400):
+                    continue
+                add(sweep_point(snn, torch, flush, B, N, a.T, mode, "mean", True, reps=2, warm=1, wprec=1))
     print(json.dumps({"experiment": "batch sweep, 784->400 and 784->6400, pair STDP, T=%d, FP32" % a.T,
                       "unit": UNIT, "rows": rows, "clocks": clk.summary()}), flush=True)
 
