@@ -94,6 +94,22 @@ def test_streaming_bytes_reproduce_the_stated_figures():
     assert abs(comp - big - 8 * 784 * 6400 / 256) < 1e-6
 
 
+def test_recurrent_bytes_reproduce_the_stated_figure():
+    """The recurrent drive's HBM roofline counts 545.7 MB per launch at
+    1024 -> 4096 -> 10, B = 4096: 402.7 MB of state (v, I, counts read and
+    written), 41.9 MB of next operands, 16.8 MB of thresholds, 41.9 MB each for
+    S and Wt, and the readout's 0.4 MB."""
+    import bench
+    p = {"n_in": 1024, "n_hid": 4096, "n_out": 10}
+    b = bench.rec_bytes_per_launch(p, 4096)
+    parts = (24 * 4096 * 4096, 2 * 4096 * 5120, 4 * 4096 * 1024, 2 * 4096 * 5120,
+             2 * 4096 * 5120, 2 * 10 * 4096, 8 * 4096 * 10)
+    assert b == sum(parts)
+    assert round(b / 1e6, 1) == 545.7
+    # a sample more costs its state, operands, threshold and S row; no weights
+    assert bench.rec_bytes_per_launch(p, 4097) - b == 24 * 4096 + 2 * 5120 + 4 * 1024 + 2 * 5120 + 80
+
+
 def test_issue_figures_come_with_the_traffic(tmp_path, monkeypatch):
     """The limiter figures of the summary (issue slots, warp instructions) are
     reported with its traffic and dropped with it once the kernel changes."""
