@@ -41,6 +41,9 @@ constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
 static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
+#ifndef SNN_QPL
+#define SNN_QPL 2
+#endif
 constexpr int PG = 4;                      // post columns that share a walk over their samples
 constexpr int LW = 16;                     // input-mask words per round trip, counting a list's row
 constexpr int LWL = 8;                     // nonzero words per round trip, writing a list
@@ -92,7 +95,8 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
     L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
-    L.tstate = (size_t)c.B * L.ncmax <= (size_t)QT * PT;
+    // tensor memory holds QT / 4 units of four items per thread (see units_of)
+    L.tstate = (long long)c.B * ((L.ncmax + 3) / 4) <= (long long)(QT / 4) * PT;
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_enc ? u_neuron : u_enc;
@@ -152,7 +156,7 @@ __device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigne
     return s_fail == 0;
 }
 
-__device__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
+__device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
                              unsigned long long tt, int t_local) {
     const int cta = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cur = (int)(tt & 1ull);
@@ -295,24 +299,8 @@ __device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I
 
 // Tensor memory as per-thread storage of the neuron state.  A thread's items
 // live in its own TMEM lane (32 x (warp mod 4) + lane id: the lanes a warp may
-// access) at columns 4q .. 4q+3 of its warp group's block (warp / 4); the
-// 32x32b shape moves four consecutive columns of each lane of the warp.  The
-// wait is in the same statement as the load, so no register is read early.
-__device__ __forceinline__ void tmem_ld4(uint32_t ta, Item& it) {
-    uint32_t a, b, x, st;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
-                 "tcgen05.wait::ld.sync.aligned;"
-                 : "=r"(a), "=r"(b), "=r"(x), "=r"(st) : "r"(ta) : "memory");
-    it.v = __uint_as_float(a);
-    it.vi = __uint_as_float(b);
-    it.x = __uint_as_float(x);
-    it.st = st;
-}
-__device__ __forceinline__ void tmem_st4(uint32_t ta, const Item& it) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
-                 :: "r"(ta), "r"(__float_as_uint(it.v)), "r"(__float_as_uint(it.vi)),
-                    "r"(__float_as_uint(it.x)), "r"(it.st) : "memory");
-}
+// access) in its warp group's block of QT x 4 columns (warp / 4); the 32x32b
+// shape moves consecutive columns of each lane of the warp.
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -332,6 +320,15 @@ __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence
 // own inside the large kernel.
 enum { RED_SUM = 0, RED_MEAN_MUL = 1, RED_MEAN_DIV = 2, RED_MAX = 3 };
 
+// The constants the out-of-line STDP passes read, passed by value: read
+// through a reference to the kernel's parameters they would be loaded again
+// after every shared-memory store (which the compiler cannot prove leaves
+// them unchanged), each load a round trip to memory.
+struct StdpK {
+    float inv_B, w_min, w_max;
+    int B;
+};
+
 template <int RED>
 __device__ __forceinline__ float deposit(float acc, float e) {
     return RED == RED_MAX ? fmaxf(acc, __fsub_rn(0.0f, e)) : __fsub_rn(acc, e);
@@ -339,7 +336,7 @@ __device__ __forceinline__ float deposit(float acc, float e) {
 
 template <int RED, bool LISTS, bool NARROW>
 __device__ __noinline__ void depress_quiet_columns(
-        const Consts& c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const int* offs,
+        const StdpK c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
     const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
@@ -442,35 +439,143 @@ __device__ __noinline__ void depress_quiet_columns(
     }
 }
 
+// The same pass with the per-input lists, for wide layers of up to 128
+// columns: L = ceil(nq / QPL) lanes per input row (nq column quads), lane l
+// taking the QPL quads l, l + L, ... (one 16-byte load of e each per sample),
+// and R = 32 / L rows per warp, so that a warp's lanes are busy on several rows
+// at once (with 42 columns and QPL = 2: six lanes per row, five rows per warp,
+// where the half-warp mapping above keeps five of every sixteen lanes idle).
+// The rows' sums, the reduction and the clip are those of
+// depress_quiet_columns.
+template <int RED, int QPL>
+__device__ __noinline__ void depress_quiet_rows(
+        const StdpK c, float* Ws, float* WLs, const float* Es, const int* offs, const uint16_t* lst,
+        const uint32_t* nzQ, int NI, int nc, int nst, int warp, int lane) {
+    const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
+    const int nq = (nc + 3) / 4, L = (nq + QPL - 1) / QPL, R = 32 / L;
+    const int r = lane / L, l = lane % L;
+    const bool on = r < R;
+    bool v[4 * QPL], any[QPL], all[QPL], has[QPL];
+#pragma unroll
+    for (int m = 0; m < QPL; ++m) {
+        const int jq = 4 * (l + m * L);
+        has[m] = on && jq < nc;
+        any[m] = false;
+        all[m] = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[4 * m + k] = has[m] && jq + k < nc && nzQ[jq + k] == 0u;
+            any[m] = any[m] || v[4 * m + k];
+            all[m] = all[m] && v[4 * m + k];
+        }
+    }
+    bool anyq = false;
+#pragma unroll
+    for (int m = 0; m < QPL; ++m) anyq = anyq || any[m];
+    if (!__any_sync(FULL, anyq)) return;
+    for (int i0 = R * warp; i0 < NI; i0 += R * NW) {
+        const int i = i0 + r;
+        if (!on || i >= NI) continue;
+        float a[4 * QPL];
+#pragma unroll
+        for (int k = 0; k < 4 * QPL; ++k) a[k] = init;
+        const int e0 = offs[i], e1 = offs[i + 1];
+        for (int e = e0; e < e1; ++e) {
+            const float* er = Es + (int)lst[e] * nst + 4 * l;
+#pragma unroll
+            for (int m = 0; m < QPL; ++m) {
+                if (!has[m]) continue;
+                const float4 x = *(const float4*)(er + 4 * m * L);
+                a[4 * m] = deposit<RED>(a[4 * m], x.x);
+                a[4 * m + 1] = deposit<RED>(a[4 * m + 1], x.y);
+                a[4 * m + 2] = deposit<RED>(a[4 * m + 2], x.z);
+                a[4 * m + 3] = deposit<RED>(a[4 * m + 3], x.w);
+            }
+        }
+        const int n = e1 - e0;
+        if (n == 0) continue;
+#pragma unroll
+        for (int k = 0; k < 4 * QPL; ++k) {
+            if (RED == RED_MEAN_MUL) a[k] = __fmul_rn(a[k], c.inv_B);
+            else if (RED == RED_MEAN_DIV) a[k] = __fdiv_rn(a[k], (float)c.B);
+            else if (RED == RED_MAX && n < c.B) a[k] = fmaxf(a[k], 0.0f);
+        }
+#pragma unroll
+        for (int m = 0; m < QPL; ++m) {
+            if (!any[m]) continue;
+            const int jq = 4 * (l + m * L);
+            const float* ak = a + 4 * m;
+            const bool* vk = v + 4 * m;
+            float* wr = Ws + i * nst + jq;
+            const float4 w = *(const float4*)wr;
+            float4 u;
+            if (WLs) {                                   // compensated master: the pairs
+                float* lr = WLs + i * nst + jq;
+                float4 lo = *(const float4*)lr;
+                u = w;
+                master_add(u.x, lo.x, ak[0], c.w_min, c.w_max);
+                master_add(u.y, lo.y, ak[1], c.w_min, c.w_max);
+                master_add(u.z, lo.z, ak[2], c.w_min, c.w_max);
+                master_add(u.w, lo.w, ak[3], c.w_min, c.w_max);
+                if (all[m]) {
+                    *(float4*)lr = lo;
+                } else {
+                    if (vk[0]) lr[0] = lo.x;
+                    if (vk[1]) lr[1] = lo.y;
+                    if (vk[2]) lr[2] = lo.z;
+                    if (vk[3]) lr[3] = lo.w;
+                }
+            } else {
+                u.x = fminf(fmaxf(__fadd_rn(w.x, ak[0]), c.w_min), c.w_max);
+                u.y = fminf(fmaxf(__fadd_rn(w.y, ak[1]), c.w_min), c.w_max);
+                u.z = fminf(fmaxf(__fadd_rn(w.z, ak[2]), c.w_min), c.w_max);
+                u.w = fminf(fmaxf(__fadd_rn(w.w, ak[3]), c.w_min), c.w_max);
+            }
+            if (all[m]) {
+                *(float4*)wr = u;
+            } else {
+                if (vk[0]) wr[0] = u.x;
+                if (vk[1]) wr[1] = u.y;
+                if (vk[2]) wr[2] = u.z;
+                if (vk[3]) wr[3] = u.w;
+            }
+        }
+    }
+}
+
 // Pass B for the sum and mean reductions with per-input sample lists: task =
 // (PG post columns, 32 rows), lanes = rows.  The union of the columns' post
 // samples is walked once in ascending b, XC at a time with their x_pre loads
 // issued together, so each x_pre value is loaded once for the PG columns, and
 // each column adds only its own samples (its potentiation sum keeps ascending
-// b).  The depression walks the lane's input list once for the PG columns (e
-// is 0 where a column has not fired).  Wide layers only: with at most four
-// columns a CTA has too few groups to keep its warps busy.
-__device__ __forceinline__ void update_post_column_groups(
-        const Consts& c, float* Ws, float* WLs, const float* Es, const uint32_t* Qm, const int* pcol, const int* offs,
-        const uint16_t* lst, const float* xpre, int npc, int NI, int nc, int nst, int Bw, bool dep_on,
+// b).  The columns' spike words of the 32 samples that hold the walk's current
+// sample stay in registers until the walk leaves them.  The depression then
+// walks the lane's input list once for the PG columns (e is 0 where a column
+// has not fired).  Wide layers only: with at most four columns a CTA has too
+// few groups to keep its warps busy.  Out of line, with its constants passed by
+// value (see StdpK), so that its loops get the registers of their own.
+struct PostK {
+    float nu_post, inv_B, w_min, w_max;
+    int B, B_pow2, mean, dep_on;
+};
+
+__device__ __noinline__ void update_post_column_groups(
+        const PostK c, float* Ws, float* WLs, const float* Es, const uint32_t* Qm, const int* pcol,
+        const int* offs, const uint16_t* lst, const float* xpre, int npc, int NI, int nc, int nst, int Bw,
         int warp, int lane) {
     const int nch = (NI + 31) / 32, ngr = (npc + PG - 1) / PG;
     for (int u = warp; u < ngr * nch; u += NW) {
         const int k0 = (u / nch) * PG, kn = min(PG, npc - k0);
+        const int* pc = pcol + k0;
         const int i = (u % nch) * 32 + lane;
         const bool vi = i < NI;
-        int jls[PG];
-        float pot[PG], dep[PG];
+        float pot[PG];
 #pragma unroll
-        for (int k = 0; k < PG; ++k) {
-            jls[k] = pcol[k0 + (k < kn ? k : 0)];   // padding repeats a live column
-            pot[k] = 0.0f;
-            dep[k] = 0.0f;
-        }
-        int w = 0;
-        uint32_t un = 0u;
+        for (int k = 0; k < PG; ++k) pot[k] = 0.0f;
+        int w = 0, wc = -1;
+        uint32_t un = 0u, cw[PG];
 #pragma unroll
-        for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[jls[k]] : 0u;
+        for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[pc[k]] : 0u;
         for (;;) {
             int bs[XC];
             int n = 0;
@@ -479,7 +584,7 @@ __device__ __forceinline__ void update_post_column_groups(
                 while (un == 0u && w + 1 < Bw) {
                     ++w;
 #pragma unroll
-                    for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[w * nc + jls[k]] : 0u;
+                    for (int k = 0; k < PG; ++k) un |= k < kn ? Qm[w * nc + pc[k]] : 0u;
                 }
                 bs[z] = -1;
                 if (un) {
@@ -497,17 +602,29 @@ __device__ __forceinline__ void update_post_column_groups(
 #pragma unroll
             for (int z = 0; z < XC; ++z) {
                 if (bs[z] < 0) continue;
+                const int wz = bs[z] >> 5;
+                if (wz != wc) {             // the same for every lane of the warp
+                    wc = wz;
+#pragma unroll
+                    for (int k = 0; k < PG; ++k) cw[k] = k < kn ? Qm[wz * nc + pc[k]] : 0u;
+                }
+                const uint32_t m = 1u << (bs[z] & 31);
                 const float a = __fmul_rn(c.nu_post, xv[z]);
-                const uint32_t* qw = Qm + (bs[z] >> 5) * nc;
-                const int bit = bs[z] & 31;
 #pragma unroll
                 for (int k = 0; k < PG; ++k)
-                    if ((qw[jls[k]] >> bit) & 1u) pot[k] = __fadd_rn(pot[k], a);
+                    if (cw[k] & m) pot[k] = __fadd_rn(pot[k], a);
             }
             if (n < XC) break;
         }
         if (!vi) continue;
-        if (dep_on) {   // every input-spike sample (e is 0 where j has not fired)
+        int jls[PG];
+        float dep[PG];
+#pragma unroll
+        for (int k = 0; k < PG; ++k) {
+            jls[k] = pc[k < kn ? k : 0];            // padding repeats a live column
+            dep[k] = 0.0f;
+        }
+        if (c.dep_on) {   // every input-spike sample (e is 0 where j has not fired)
             const int e1 = offs[i + 1];
             for (int e = offs[i]; e < e1; ++e) {
                 const float* er = Es + (int)lst[e] * nst;
@@ -519,7 +636,7 @@ __device__ __forceinline__ void update_post_column_groups(
         for (int k = 0; k < PG; ++k) {
             if (k >= kn) break;
             float D = __fsub_rn(pot[k], dep[k]);
-            if (c.reduce == SNN_REDUCE_MEAN) D = batch_mean(c, D);
+            if (c.mean) D = c.B_pow2 ? __fmul_rn(D, c.inv_B) : __fdiv_rn(D, (float)c.B);
             float* wp = Ws + i * nst + jls[k];
             if (WLs) master_add(*wp, WLs[i * nst + jls[k]], D, c.w_min, c.w_max);
             else *wp = plain_add(*wp, D, c.w_min, c.w_max);
@@ -527,31 +644,79 @@ __device__ __forceinline__ void update_post_column_groups(
     }
 }
 
-// Synaptic currents: I[b][j] = sum over the active inputs a of sample b,
-// ascending, of W[a][j] (in the weight precision), into the e tile, which the
-// neuron update then reads and overwrites with e.  One sample per half-warp and
-// four adjacent columns per lane: the active list is the same for the
-// half-warp and each weight row is one 16-byte load.
-__device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d, const float* Ws,
-                                               float* Es, const float* wsc, int ncmax,
-                                               const uint32_t* actN, const uint16_t* actS,
-                                               int caps, int nc, int nst, int cur) {
-    const int B = c.B, NI = c.n_in, tid = threadIdx.x;
-    {
-        const int warp = tid >> 5, lane = tid & 31, h = lane >> 4;
-        for (int g0 = 0; g0 < nc; g0 += 64) {
-            const int j = g0 + 4 * (lane & 15);
-            if (j >= nc) continue;                  // no column of the tile: idle lane
-            for (int b = 2 * warp + h; b < B; b += 2 * NW) {
+// The units of the neuron phase: unit u = (sample b, column quad q), the four
+// columns 4q .. 4q+3 of the CTA, numbered u = b * nq + q (nq quads per sample)
+// and dealt to the threads densely: thread tid takes u = tid + k * PT in its
+// slot k.  Lanes of a warp then cover consecutive quads of two or three
+// samples, every lane busy.  With tensor-memory state, slot k holds the
+// unit's four (v, vi, x, st) items in columns 16k .. 16k+15 of the thread's
+// lane.  The walk over a thread's slots steps (b, q) without a division.
+struct Units {
+    int nq, nslot, db, dq;
+};
+
+__device__ __forceinline__ Units units_of(int B, int nc) {
+    Units u;
+    u.nq = (nc + 3) / 4;
+    u.nslot = (int)(((long long)B * u.nq + PT - 1) / PT);
+    u.db = PT / u.nq;
+    u.dq = PT % u.nq;
+    return u;
+}
+__device__ __forceinline__ void unit_next(const Units& U, int& b, int& q) {
+    b += U.db;
+    q += U.dq;
+    if (q >= U.nq) { q -= U.nq; ++b; }
+}
+
+// Sixteen consecutive tensor-memory columns of the warp's lanes (a unit's four
+// items); the wait is in the same statement as the load.
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(ta) : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t ta, const uint32_t (&r)[16]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+                 :: "r"(ta), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                    "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+                 : "memory");
+}
+
+// The neuron phase of one step, fused: for each unit, the synaptic currents
+// I[b][j] = sum over the active inputs a of sample b, ascending, of W[a][j] (in
+// the weight precision), then the pair update of its four items with the state
+// from tensor memory (or global memory), e = nu_pre x_post into the e tile,
+// the spikes into the masks and counters.  Same sums and updates, in the same
+// order, as the per-step kernels.  Inlined: a call would have to save the
+// kernel's live values around it, through L1 that the shared memory leaves
+// small.
+__device__ __forceinline__ void neuron_phase(const Consts& c, const Bufs& d, const float* Ws, float* Es,
+                                          const float* wsc, int ncmax, const uint32_t* actN,
+                                          const uint16_t* actS, int caps, uint32_t* Qm, uint32_t* Sm,
+                                          const uint32_t* cntS, const float* thj, uint32_t tq,
+                                          bool tstate, int nc, int nst, int j0, int cur, int t, int p3) {
+    const int B = c.B, N = c.N, NI = c.n_in;
+    const Units U = units_of(B, nc);
+    int b = threadIdx.x / U.nq, qd = threadIdx.x % U.nq;
+    for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
+        {
+            const int j = 4 * qd;
+            const bool live = b < B;
+            // ---- currents (the padding columns' weights are 0)
+            float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+            if (live) {
                 const int na = (int)actN[b];
                 const int ns = na < caps ? na : caps;
                 const uint16_t* al = actS + b * CAPS;
                 const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
-                float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+                const float* wc = Ws + j;
                 if (c.wprec == SNN_W_FP32) {
                     for (int a = 0; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w.x);
                         I1 = __fadd_rn(I1, w.y);
                         I2 = __fadd_rn(I2, w.z);
@@ -560,7 +725,7 @@ __device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d
                 } else if (c.wprec == SNN_W_BF16) {
                     for (int a = 0; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w_read_bf16(w.x));
                         I1 = __fadd_rn(I1, w_read_bf16(w.y));
                         I2 = __fadd_rn(I2, w_read_bf16(w.z));
@@ -573,7 +738,7 @@ __device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d
                     const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
                     for (int a = 0; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
                         I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
                         I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
@@ -584,128 +749,75 @@ __device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d
                     I2 = __fmul_rn(I2, j + 2 < nc ? wsc[j + 2] : 1.0f);
                     I3 = __fmul_rn(I3, j + 3 < nc ? wsc[j + 3] : 1.0f);
                 }
-                *(float4*)(Es + b * nst + j) = make_float4(I0, I1, I2, I3);
             }
-        }
-    }
-}
-
-// The synaptic currents when the CTA has at most four columns (narrow layers):
-// one sample per lane, its columns in one 16-byte load per active input, the
-// same sums in the same order as synaptic_currents (which would leave 15 of 16
-// lanes idle here).
-__device__ __forceinline__ void synaptic_currents_narrow(const Consts& c, const Bufs& d, const float* Ws,
-                                                      float* Es, const float* wsc, int ncmax,
-                                                      const uint32_t* actN, const uint16_t* actS,
-                                                      int caps, int nc, int nst, int cur) {
-    const int B = c.B, NI = c.n_in;
-    for (int b = threadIdx.x; b < B; b += PT) {
-        const int na = (int)actN[b];
-        const int ns = na < caps ? na : caps;
-        const uint16_t* al = actS + b * CAPS;
-        const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
-        float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
-        if (c.wprec == SNN_W_FP32) {
-            for (int a = 0; a < na; ++a) {
-                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                const float4 w = *(const float4*)(Ws + r * nst);
-                I0 = __fadd_rn(I0, w.x);
-                I1 = __fadd_rn(I1, w.y);
-                I2 = __fadd_rn(I2, w.z);
-                I3 = __fadd_rn(I3, w.w);
-            }
-        } else if (c.wprec == SNN_W_BF16) {
-            for (int a = 0; a < na; ++a) {
-                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                const float4 w = *(const float4*)(Ws + r * nst);
-                I0 = __fadd_rn(I0, w_read_bf16(w.x));
-                I1 = __fadd_rn(I1, w_read_bf16(w.y));
-                I2 = __fadd_rn(I2, w_read_bf16(w.z));
-                I3 = __fadd_rn(I3, w_read_bf16(w.w));
-            }
-        } else {
-            const float* inv = wsc + ncmax;
-            const float v0 = inv[0], v1 = 1 < nc ? inv[1] : 1.0f;
-            const float v2 = 2 < nc ? inv[2] : 1.0f, v3 = 3 < nc ? inv[3] : 1.0f;
-            for (int a = 0; a < na; ++a) {
-                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
-                const float4 w = *(const float4*)(Ws + r * nst);
-                I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
-                I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
-                I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
-                I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
-            }
-            I0 = __fmul_rn(I0, wsc[0]);
-            I1 = __fmul_rn(I1, 1 < nc ? wsc[1] : 1.0f);
-            I2 = __fmul_rn(I2, 2 < nc ? wsc[2] : 1.0f);
-            I3 = __fmul_rn(I3, 3 < nc ? wsc[3] : 1.0f);
-        }
-        *(float4*)(Es + b * nst) = make_float4(I0, I1, I2, I3);
-    }
-}
-
-// The neuron update of the CTA's (sample, column) items: state from tensor
-// memory (or global memory), the current from the e tile, e = nu_pre x_post
-// back into it, spikes into the masks and counters.  Inlined: a call would have
-// to save the kernel's live values around it, through L1 that the shared
-// memory leaves small, which costs more than the loop's own register pressure.
-__device__ __forceinline__ void neuron_items(const Consts& c, const Bufs& d, float* Es, uint32_t* Qm,
-                                          uint32_t* Sm, const uint32_t* cntS, const float* thj,
-                                          uint32_t tq, bool tstate, int QN, int BN, int nc, int nst,
-                                          int j0, int dq, int dr, int t, int p3) {
-    const int B = c.B, N = c.N, tid = threadIdx.x;
-    {
-        int b = tid / nc, jl = tid % nc;
-        for (int q = 0; q < QN; ++q) {
-            const bool valid = tid + q * PT < BN;
-            const int j = j0 + jl;
-            const size_t idx = (size_t)b * N + j;
-            Item it{0.0f, 0.0f, 0.0f, 0u};
+            // ---- state of the unit's four items
+            uint32_t r[16];
+            const uint32_t ta = tq + 16u * (uint32_t)sl;
             if (tstate) {
                 __syncwarp();
-                tmem_ld4(tq + 4 * q, it);
-            } else if (valid) {
-                it.st = d.st[idx];
-                it.v = d.v_e[idx];
-                it.vi = d.v_i[idx];
-                it.x = d.x_post[idx];
+                tmem_ld16(ta, r);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    r[4 * q] = r[4 * q + 1] = r[4 * q + 2] = r[4 * q + 3] = 0u;
+                    if (live && j + q < nc) {
+                        const size_t idx = (size_t)b * N + j0 + j + q;
+                        r[4 * q] = __float_as_uint(d.v_e[idx]);
+                        r[4 * q + 1] = __float_as_uint(d.v_i[idx]);
+                        r[4 * q + 2] = __float_as_uint(d.x_post[idx]);
+                        r[4 * q + 3] = d.st[idx];
+                    }
+                }
             }
-            if (valid) {
-                const float I = Es[b * nst + jl];
-                const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
-                const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
-                Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
-                if (!tstate) {
-                    d.x_post[idx] = o.x;
-                    d.v_e[idx] = o.v;
-                    d.v_i[idx] = o.vi;
-                    d.st[idx] = o.st;
+            // ---- the pair updates
+            int nsi = 0;
+            if (live) {
+                const int C = (int)cntS[b];
+                const float Iq[4] = {I0, I1, I2, I3};
+                float e[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jl = j + q;
+                    if (jl >= nc) break;
+                    Item it{__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                            __uint_as_float(r[4 * q + 2]), r[4 * q + 3]};
+                    const Item o = neuron_update(&c, it, Iq[q], C, thj[jl]);
+                    e[q] = __fmul_rn(c.nu_pre, o.x);
+                    r[4 * q] = __float_as_uint(o.v);
+                    r[4 * q + 1] = __float_as_uint(o.vi);
+                    r[4 * q + 2] = __float_as_uint(o.x);
+                    r[4 * q + 3] = o.st;
+                    const size_t idx = (size_t)b * N + j0 + jl;
+                    if (o.st & ST_SE) {
+                        d.counts[idx] += 1u;
+                        const uint32_t bit = 1u << (b & 31);
+                        atomicOr(&Qm[(b >> 5) * nc + jl], bit);
+                        atomicOr(&Sm[(b >> 5) * nc + jl], bit);
+                        if (c.rec_raster)
+                            atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + ((j0 + jl) >> 5)], 1u << ((j0 + jl) & 31));
+                    }
+                    if (o.st & ST_SI) {
+                        ++nsi;
+                        if (c.rec_raster)
+                            atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + ((j0 + jl) >> 5)], 1u << ((j0 + jl) & 31));
+                    }
+                    if (!tstate) {
+                        d.v_e[idx] = o.v;
+                        d.v_i[idx] = o.vi;
+                        d.x_post[idx] = o.x;
+                        d.st[idx] = o.st;
+                    }
                 }
-                if (se) {
-                    d.counts[idx] += 1u;
-                    const uint32_t bit = 1u << (b & 31);
-                    atomicOr(&Qm[(b >> 5) * nc + jl], bit);
-                    atomicOr(&Sm[(b >> 5) * nc + jl], bit);
-                    if (c.rec_raster)
-                        atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
-                }
-                if (si) {
-                    atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
-                    if (c.rec_raster)
-                        atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
-                }
-                it = o;
+                *(float4*)(Es + b * nst + j) = make_float4(e[0], e[1], e[2], e[3]);
             }
+            if (nsi) atomicAdd(&d.cnt[(size_t)p3 * B + b], (uint32_t)nsi);
             if (tstate) {
                 __syncwarp();
-                tmem_st4(tq + 4 * q, it);
+                tmem_st16(ta, r);
             }
-            b += dq;
-            jl += dr;
-            if (jl >= nc) { jl -= nc; ++b; }
         }
-        if (tstate) tmem_wait_st();
     }
+    if (tstate) tmem_wait_st();
 }
 
 // The adaptive thresholds after the STDP of a step: theta_j <- theta_j a_theta +
@@ -757,8 +869,6 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     uint32_t* const bar = d.err + 32;             // own 128-byte line
     if (ld_acquire(d.err) != 0u) return;          // an earlier run failed: do nothing
     const unsigned long long base = d.step[0];
-    // strides of the division-free walk over (sample, column) items
-    const int dq = PT / nc, dr = PT % nc;
 
     // ---- the CTA's columns: weights (padding columns 0), masks, thresholds
     for (int k = tid; k < NI * nst; k += PT) {
@@ -773,9 +883,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     }
     for (int jl = tid; jl < nc; jl += PT) thS[jl] = d.theta[j0 + jl];
 
-    // ---- neuron state of the CTA's (sample, column) items into tensor memory
+    // ---- neuron state of the CTA's units into tensor memory
     const bool tstate = L.tstate != 0;
-    const int BN = B * nc, QN = (BN + PT - 1) / PT;   // items, and items per thread
+    const Units U = units_of(B, nc);
     uint32_t tq = 0;                                  // this thread's tensor-memory block
     if (tstate) {
         if (tid < 32) {
@@ -787,21 +897,23 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         __syncthreads();
         tmem_fence_after();
         tq = s_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * QT * 4);
-        int b = tid / nc, jl = tid % nc;
-        for (int q = 0; q < QN; ++q) {
-            Item it{0.0f, 0.0f, 0.0f, 0u};
-            if (tid + q * PT < BN) {
-                const size_t idx = (size_t)b * N + j0 + jl;
-                it.v = d.v_e[idx];
-                it.vi = d.v_i[idx];
-                it.x = d.x_post[idx];
-                it.st = d.st[idx];
+        int b = tid / U.nq, qd = tid % U.nq;
+        for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
+            const int j = 4 * qd;
+            uint32_t r[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                r[4 * q] = r[4 * q + 1] = r[4 * q + 2] = r[4 * q + 3] = 0u;
+                if (b < B && j + q < nc) {
+                    const size_t idx = (size_t)b * N + j0 + j + q;
+                    r[4 * q] = __float_as_uint(d.v_e[idx]);
+                    r[4 * q + 1] = __float_as_uint(d.v_i[idx]);
+                    r[4 * q + 2] = __float_as_uint(d.x_post[idx]);
+                    r[4 * q + 3] = d.st[idx];
+                }
             }
             __syncwarp();
-            tmem_st4(tq + 4 * q, it);
-            b += dq;
-            jl += dr;
-            if (jl >= nc) { jl -= nc; ++b; }
+            tmem_st16(tq + 16u * (uint32_t)sl, r);
         }
         tmem_wait_st();
     }
@@ -964,11 +1076,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
-        if (NARROW) synaptic_currents_narrow(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
-        else synaptic_currents(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
-        __syncthreads();
-
-        neuron_items(c, d, Es, Qm, Sm, cntS, thj, tq, tstate, QN, BN, nc, nst, j0, dq, dr, t, p3);
+        neuron_phase(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, Qm, Sm, cntS, thj, tq, tstate, nc, nst, j0,
+                     cur, t, p3);
         __syncthreads();
 
         // ================= next step's input, signalled before this step's STDP
@@ -1025,9 +1134,11 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     if (nzQ[jl] == 0u) Ws[i * nst + jl] = fminf(fmaxf(Ws[i * nst + jl], c.w_min), c.w_max);
                 }
             } else {
+                const StdpK sk{c.inv_B, c.w_min, c.w_max, c.B};
 #define SNN_PASS_A_N(R, NR)                                                                        \
-    (lists ? depress_quiet_columns<R, true, NR>(c, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
-           : depress_quiet_columns<R, false, NR>(c, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+    (lists && !NR && nc <= 128 ? depress_quiet_rows<R, SNN_QPL>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
+     : lists ? depress_quiet_columns<R, true, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
+             : depress_quiet_columns<R, false, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
 #define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)
                 if (c.reduce == SNN_REDUCE_MAX) SNN_PASS_A(RED_MAX);
                 else if (c.reduce == SNN_REDUCE_SUM) SNN_PASS_A(RED_SUM);
@@ -1047,8 +1158,10 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 const bool grouped = !NARROW && lists && c.reduce != SNN_REDUCE_MAX;
                 if constexpr (!NARROW)
                     if (grouped)
-                        update_post_column_groups(c, Ws, WLs, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw,
-                                                  dep_on, warp, lane);
+                        update_post_column_groups(
+                                PostK{c.nu_post, c.inv_B, c.w_min, c.w_max, c.B, c.B_pow2,
+                                      c.reduce == SNN_REDUCE_MEAN ? 1 : 0, dep_on ? 1 : 0},
+                                Ws, WLs, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw, warp, lane);
                 // Otherwise task = (column, 32 rows): potentiation over the column's
                 // post-spiking samples, the same for every lane, XC at a time with
                 // their x_pre loads issued together; depression over the lane's own
@@ -1169,21 +1282,22 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     // ---- write the CTA's columns back, and the neuron state held in tensor memory
     __syncthreads();
     if (tstate) {
-        int b = tid / nc, jl = tid % nc;
-        for (int q = 0; q < QN; ++q) {
-            Item it;
+        int b = tid / U.nq, qd = tid % U.nq;
+        for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
+            const int j = 4 * qd;
+            uint32_t r[16];
             __syncwarp();
-            tmem_ld4(tq + 4 * q, it);
-            if (tid + q * PT < BN) {
-                const size_t idx = (size_t)b * N + j0 + jl;
-                d.v_e[idx] = it.v;
-                d.v_i[idx] = it.vi;
-                d.x_post[idx] = it.x;
-                d.st[idx] = it.st;
+            tmem_ld16(tq + 16u * (uint32_t)sl, r);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (b < B && j + q < nc) {
+                    const size_t idx = (size_t)b * N + j0 + j + q;
+                    d.v_e[idx] = __uint_as_float(r[4 * q]);
+                    d.v_i[idx] = __uint_as_float(r[4 * q + 1]);
+                    d.x_post[idx] = __uint_as_float(r[4 * q + 2]);
+                    d.st[idx] = r[4 * q + 3];
+                }
             }
-            b += dq;
-            jl += dr;
-            if (jl >= nc) { jl -= nc; ++b; }
         }
         tmem_fence_before();
         __syncthreads();
