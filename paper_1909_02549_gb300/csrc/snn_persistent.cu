@@ -65,6 +65,7 @@ struct Layout {
     int ps;                           // row stride of the staged input-major masks
     int lcap;                         // list entries that fit
     int tstate;                       // neuron state held in tensor memory (else in global memory)
+    int masks;                        // STDP walks the spike words, no per-input lists (see make_layout)
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
@@ -97,6 +98,10 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
     // tensor memory holds QT / 4 units of four items per thread (see units_of)
     L.tstate = (long long)c.B * ((L.ncmax + 3) / 4) <= (long long)(QT / 4) * PT;
+    // Narrow layers at large batches: the STDP passes walk the step's spike
+    // words instead of per-input lists.  Every CTA would build the same lists
+    // from rows of Bw words, which costs more there than the walk saves.
+    L.masks = L.ncmax <= 4 && c.Bw >= 16;
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_enc ? u_neuron : u_enc;
@@ -551,18 +556,18 @@ __device__ __noinline__ void depress_quiet_rows(
 // b).  The columns' spike words of the 32 samples that hold the walk's current
 // sample stay in registers until the walk leaves them.  The depression then
 // walks the lane's input list once for the PG columns (e is 0 where a column
-// has not fired).  Wide layers only: with at most four columns a CTA has too
-// few groups to keep its warps busy.  Out of line, with its constants passed by
-// value (see StdpK), so that its loops get the registers of their own.
+// has not fired), from the per-input lists or, where they did not fit, from
+// the row's spike words.  Out of line, with its constants passed by value (see
+// StdpK), so that its loops get the registers of their own.
 struct PostK {
     float nu_post, inv_B, w_min, w_max;
     int B, B_pow2, mean, dep_on;
 };
 
 __device__ __noinline__ void update_post_column_groups(
-        const PostK c, float* Ws, float* WLs, const float* Es, const uint32_t* Qm, const int* pcol,
-        const int* offs, const uint16_t* lst, const float* xpre, int npc, int NI, int nc, int nst, int Bw,
-        int warp, int lane) {
+        const PostK c, float* Ws, float* WLs, const float* Es, const uint32_t* Qm, const uint32_t* Sm,
+        const int* pcol, bool lists, const int* offs, const uint16_t* lst, const uint32_t* preS, int PS,
+        const uint32_t* nzP, const float* xpre, int npc, int NI, int nc, int nst, int Bw, int warp, int lane) {
     const int nch = (NI + 31) / 32, ngr = (npc + PG - 1) / PG;
     for (int u = warp; u < ngr * nch; u += NW) {
         const int k0 = (u / nch) * PG, kn = min(PG, npc - k0);
@@ -624,12 +629,33 @@ __device__ __noinline__ void update_post_column_groups(
             jls[k] = pc[k < kn ? k : 0];            // padding repeats a live column
             dep[k] = 0.0f;
         }
-        if (c.dep_on) {   // every input-spike sample (e is 0 where j has not fired)
+        if (c.dep_on && lists) {   // every input-spike sample (e is 0 where j has not fired)
             const int e1 = offs[i + 1];
             for (int e = offs[i]; e < e1; ++e) {
                 const float* er = Es + (int)lst[e] * nst;
 #pragma unroll
                 for (int k = 0; k < PG; ++k) dep[k] = __fadd_rn(dep[k], er[jls[k]]);
+            }
+        } else if (c.dep_on) {   // the row's spike words, ascending b, restricted to the samples
+                                 // in which a column of the group has fired (e is 0 elsewhere)
+            const uint32_t* Pi = preS + i * PS;
+            uint32_t words = Bw <= 32 ? nzP[i] : 0xFFFFFFFFu;
+            for (int ww = 0; ww < Bw; ++ww) {
+                if (Bw <= 32) {
+                    if (!words) break;
+                    ww = __ffs(words) - 1;
+                    words &= words - 1;
+                }
+                uint32_t fired = 0u;
+#pragma unroll
+                for (int k = 0; k < PG; ++k) fired |= k < kn ? Sm[ww * nc + jls[k]] : 0u;
+                uint32_t m = Pi[ww] & fired;
+                while (m) {
+                    const float* er = Es + (ww * 32 + __ffs(m) - 1) * nst;
+                    m &= m - 1;
+#pragma unroll
+                    for (int k = 0; k < PG; ++k) dep[k] = __fadd_rn(dep[k], er[jls[k]]);
+                }
             }
         }
 #pragma unroll
@@ -987,8 +1013,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         // counts (the step's input-major masks are complete since the barrier).
         // One thread per row reads the row's words once.  Lists are written
         // only while they fit; the STDP passes walk the spike words instead when
-        // the step's total exceeds the space.  (Learning off: nothing reads them.)
-        if (c.learn) {
+        // the step's total exceeds the space.  (Learning off: nothing reads them;
+        // with L.masks the STDP phase reads the masks themselves.)
+        if (c.learn && !L.masks) {
             const uint32_t* src = pre_src;
             const bool vec = pre_vec;
             const int wp = tid >> 5, ln = tid & 31;
@@ -1095,7 +1122,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             int* pcol = (int*)(sm + L.o_pcol);
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
             const int PS = L.ps;
-            const bool lists = offs[NI] <= L.lcap;
+            const bool lists = !L.masks && offs[NI] <= L.lcap;
             if (tid < 32) {   // which columns fired, and the list of those columns
                 int npc = 0;
                 for (int jl0 = 0; jl0 < nc; jl0 += 32) {
@@ -1118,7 +1145,41 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 }
                 if (tid == 0) s_nq = npc;
             }
-            if (c.reduce == SNN_REDUCE_MAX || !lists) {   // the step's masks, padded rows
+            if (L.masks) {   // the step's masks, padded rows, and each row's nonzero words:
+                             // a thread per row, its words in 16-byte loads issued together
+                const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
+                for (int i = tid; i < NI; i += PT) {
+                    const uint32_t* row = src + (size_t)i * Bw;
+                    uint32_t nz = 0u;
+                    if ((Bw & 3) == 0) {
+                        for (int w0 = 0; w0 < Bw; w0 += 16) {
+                            uint4 q[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                q[k] = w0 + 4 * k < Bw ? __ldcg((const uint4*)(row + w0) + k) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const uint32_t m4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    const int w = w0 + 4 * k + e;
+                                    if (w < Bw) {
+                                        preS[i * PS + w] = m4[e];
+                                        if (m4[e] && w < 32) nz |= 1u << w;
+                                    }
+                                }
+                            }
+                        }
+                    } else {
+                        for (int w = 0; w < Bw; ++w) {
+                            const uint32_t m = __ldcg(&row[w]);
+                            preS[i * PS + w] = m;
+                            if (m && w < 32) nz |= 1u << w;
+                        }
+                    }
+                    nzP[i] = nz;
+                }
+            } else if (c.reduce == SNN_REDUCE_MAX || !lists) {   // the step's masks, padded rows
                 const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
                 for (int k = tid; k < NI * Bw; k += PT) preS[(k / Bw) * PS + (k % Bw)] = __ldcg(&src[k]);
             }
@@ -1154,14 +1215,15 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 const int nch = (NI + 31) / 32;
                 const int ntask = npc * nch;
                 const bool dep_on = c.rule != SNN_RULE_POST_NORM;   // that rule only potentiates
-                // Sum and mean with input lists, wide layers: groups of PG post columns
-                const bool grouped = !NARROW && lists && c.reduce != SNN_REDUCE_MAX;
-                if constexpr (!NARROW)
-                    if (grouped)
-                        update_post_column_groups(
-                                PostK{c.nu_post, c.inv_B, c.w_min, c.w_max, c.B, c.B_pow2,
-                                      c.reduce == SNN_REDUCE_MEAN ? 1 : 0, dep_on ? 1 : 0},
-                                Ws, WLs, Es, Qm, pcol, offs, lst, xpre, npc, NI, nc, nst, Bw, warp, lane);
+                // Sum and mean, wide layers: groups of PG post columns (with at most
+                // four columns a CTA has too few groups to keep its warps busy)
+                const bool grouped = !NARROW && c.reduce != SNN_REDUCE_MAX;
+                if (grouped)
+                    update_post_column_groups(
+                            PostK{c.nu_post, c.inv_B, c.w_min, c.w_max, c.B, c.B_pow2,
+                                  c.reduce == SNN_REDUCE_MEAN ? 1 : 0, dep_on ? 1 : 0},
+                            Ws, WLs, Es, Qm, Sm, pcol, lists, offs, lst, preS, PS, nzP, xpre, npc, NI, nc, nst,
+                            Bw, warp, lane);
                 // Otherwise task = (column, 32 rows): potentiation over the column's
                 // post-spiking samples, the same for every lane, XC at a time with
                 // their x_pre loads issued together; depression over the lane's own

@@ -493,6 +493,21 @@ def test_784x6400_batch256_learning_off_sampled():
         assert np.array_equal(bits(g["x_post"][b:b + 1]), bits(st.x_post)), b
 
 
+@pytest.mark.parametrize("reduce", ["mean", "max"])
+def test_784x6400_batch256_lists_overflow(reduce):
+    """784 -> 6400 at B = 256 with four times the image rates: a step carries
+    about 7,700 input events, more than the per-input lists that the
+    persistent form's shared memory holds beside the weight columns (about
+    4,300), so its STDP walks the step's spike words; 20 steps take the
+    early burst."""
+    p, r, s, w = synth.workload(256, 6400)
+    r = (r * np.float32(4)).astype(np.float32)
+    st, rec = oracle_run(p, r, s, w, 20, reduce=reduce)
+    assert rec.raster_e.sum() > 0 and not np.array_equal(st.w, w)
+    _, g = gpu_run(p, r, s, w, 20, reduce=reduce, mode="persistent")
+    assert_parity(g, st, rec)
+
+
 def test_784x6400_batch256_learning_first_steps():
     """Learning on at full size for the first 12 steps (the first excitatory
     spikes and the first weight updates fall inside)."""
@@ -528,6 +543,17 @@ def test_784x400_batch1024_learning_off_sampled():
         assert np.array_equal(g["raster_e"][:, b:b + 1], rec.raster_e), b
         assert np.array_equal(bits(g["v_e"][b:b + 1]), bits(st.v_e)), b
         assert np.array_equal(bits(g["x_post"][b:b + 1]), bits(st.x_post)), b
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+def test_narrow_layer_large_batch_walks_spike_words(reduce):
+    """784 -> 400 at B = 600 (19 mask words per input row, two or three columns
+    per SM): the persistent form's STDP walks the step's spike words instead of
+    per-input lists.  60 steps cover the early burst in which most columns
+    fire; every mode bit-exact with the oracle."""
+    p, r, s, w = synth.workload(600, 400)
+    _, rec = parity_all_modes(p, r, s, w, 60, reduce=reduce)
+    assert rec.raster_e.sum() > 1000
 
 
 @pytest.mark.parametrize("reduce", ["mean", "sum"])
