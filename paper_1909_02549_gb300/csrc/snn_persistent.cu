@@ -34,22 +34,21 @@
 namespace snn {
 namespace {
 
-constexpr int PT = 1024;                   // threads per CTA
+constexpr int PT = 1024;                   // threads per CTA (fewer, with more registers each, ran slower)
 constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
 constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
-static_assert(NW == 32, "the block scan of the STDP phase has one warp total per lane");
+static_assert(NW <= 32 && PT % 128 == 0, "the block scan of the STDP phase has one warp total per lane");
 constexpr int XC = 8;                      // post samples whose x_pre loads are issued together
-#ifndef SNN_QPL
-#define SNN_QPL 2
-#endif
 constexpr int PG = 4;                      // post columns that share a walk over their samples
 constexpr int LW = 16;                     // input-mask words per round trip, counting a list's row
 constexpr int LWL = 8;                     // nonzero words per round trip, writing a list
-constexpr int QT = 16;                     // neuron items per thread that tensor memory holds
-constexpr int TMEM_COLS = 512;             // all of the SM's tensor memory: 8 warp groups x QT x 4 words
-static_assert(8 * QT * 4 == TMEM_COLS, "tensor-memory columns per warp group");
+constexpr int TMEM_COLS = 512;             // all of the SM's tensor memory
+// neuron items per thread that tensor memory holds: each warp group (128
+// lanes) gets an equal block of whole 16-column slots of four items
+constexpr int QT = (TMEM_COLS / (PT / 128) / 16) * 4;
+static_assert(QT >= 4 && (PT / 128) * QT * 4 <= TMEM_COLS, "tensor-memory columns per warp group");
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct Layout {
@@ -882,7 +881,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     int* offs = (int*)(sm + L.o_off);
     uint16_t* lst = (uint16_t*)(sm + L.o_lst);
     __shared__ int s_nq;
-    __shared__ int s_scan[NW];
+    __shared__ int s_scan[32];
     __shared__ uint32_t s_tmem;
 
     const int cta = blockIdx.x, tid = threadIdx.x;
@@ -1055,7 +1054,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 if (ln == 31) s_scan[wp] = x;
                 __syncthreads();
                 if (wp == 0) {                               // ... and over the warps
-                    int v = s_scan[ln];
+                    int v = ln < NW ? s_scan[ln] : 0;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int y = __shfl_up_sync(FULL, v, o);
@@ -1197,7 +1196,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             } else {
                 const StdpK sk{c.inv_B, c.w_min, c.w_max, c.B};
 #define SNN_PASS_A_N(R, NR)                                                                        \
-    (lists && !NR && nc <= 128 ? depress_quiet_rows<R, SNN_QPL>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
+    (lists && !NR && nc <= 128 ? depress_quiet_rows<R, 2>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
      : lists ? depress_quiet_columns<R, true, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
              : depress_quiet_columns<R, false, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
 #define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)

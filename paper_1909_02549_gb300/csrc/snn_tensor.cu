@@ -472,25 +472,28 @@ __global__ void __launch_bounds__(128) k_t_gcurrent(Consts c, Bufs d, TBufs t, i
 // input tile 0, slice 0 also update theta.
 constexpr int DW_KSMAX = 4;                                    // batch slices per tile (cluster size)
 
-// W[i0 .. i0+15][j] and, for a compensated master, its low parts (zeros
-// outside the layer).
-struct WChunk { float w[16], l[16]; };
+// W[i0 .. i0+15][j] and, for a compensated master (MASTER), its low parts
+// (zeros outside the layer).  The two masters are two instantiations of the
+// kernel, so that the plain one carries no registers for the low parts.
+template <bool MASTER> struct WChunk { float w[16], l[MASTER ? 16 : 1]; };
 
-__device__ __forceinline__ void wchunk_load(const Consts& c, const Bufs& d, int j, int i0, WChunk& wc) {
+template <bool MASTER>
+__device__ __forceinline__ void wchunk_load(const Consts& c, const Bufs& d, int j, int i0, WChunk<MASTER>& wc) {
     const bool vj = j < c.N;
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
         const bool ok = vj && i0 + u < c.n_in;
         const size_t k = (size_t)(i0 + u) * c.N + j;
         wc.w[u] = ok ? d.W[k] : 0.0f;
-        wc.l[u] = (ok && c.wmaster) ? d.W_lo[k] : 0.0f;
+        if (MASTER) wc.l[u] = ok ? d.W_lo[k] : 0.0f;
     }
 }
 
 // W[i0 + u][j] += reduce(D[u]), clipped; then W^T's split for the next step's
 // current (inputs past the layer stay 0).
+template <bool MASTER>
 __device__ __forceinline__ void wchunk_update(const Consts& c, const Bufs& d, const TBufs& t, int j, int i0,
-                                              const float (&D)[16], WChunk& wc) {
+                                              const float (&D)[16], WChunk<MASTER>& wc) {
     if (j >= c.N) return;
     const int nu = c.n_in - i0 < 16 ? c.n_in - i0 : 16;
 #pragma unroll
@@ -499,7 +502,7 @@ __device__ __forceinline__ void wchunk_update(const Consts& c, const Bufs& d, co
         if (c.reduce == SNN_REDUCE_MEAN) x = batch_mean(c, x);
         const size_t k = (size_t)(i0 + u) * c.N + j;
         float w = wc.w[u];
-        if (c.wmaster) {
+        if (MASTER) {
             float l = wc.l[u];
             master_add(w, l, x, c.w_min, c.w_max);
             if (u < nu) d.W_lo[k] = l;
@@ -526,6 +529,7 @@ __device__ __forceinline__ void wchunk_update(const Consts& c, const Bufs& d, co
     }
 }
 
+template <bool MASTER>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ CUtensorMap mSP,
                                                         const __grid_constant__ CUtensorMap mXQ,
                                                         const __grid_constant__ CUtensorMap mXP,
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_t_dw(const __grid_constant__ 
     const int j = tm * 128 + row;
     const int nch = t.TNI / 16;
     const int ch0 = ks + t.KS * half, chs = 2 * t.KS;
-    WChunk wc;
+    WChunk<MASTER> wc;
     if (warp == 0) {
         if (lane == 0) {                                      // TMA producer
             int it = 0;
@@ -820,7 +824,8 @@ cudaError_t ensure_attributes() {
     std::lock_guard<std::mutex> lock(mu);
     if (!done[dev]) {
         TT_TRY(cudaFuncSetAttribute(k_t_current, cudaFuncAttributeMaxDynamicSharedMemorySize, CUR_SMEM_MAX));
-        TT_TRY(cudaFuncSetAttribute(k_t_dw, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM_MAX));
+        TT_TRY(cudaFuncSetAttribute(k_t_dw<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM_MAX));
+        TT_TRY(cudaFuncSetAttribute(k_t_dw<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, DW_SMEM_MAX));
         done[dev] = true;
     }
     return cudaSuccess;
@@ -858,7 +863,8 @@ cudaError_t launch_tensor_step(const Consts& c, const Bufs& d, const TBufs& t, i
         at[0].val.clusterDim.z = (unsigned)t.KS;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        TT_TRY(cudaLaunchKernelEx(&cfg, k_t_dw, t.m_spost, t.m_xpost, t.m_xpre, t.m_sint, c, d, t));
+        if (c.wmaster) TT_TRY(cudaLaunchKernelEx(&cfg, k_t_dw<true>, t.m_spost, t.m_xpost, t.m_xpre, t.m_sint, c, d, t));
+        else TT_TRY(cudaLaunchKernelEx(&cfg, k_t_dw<false>, t.m_spost, t.m_xpost, t.m_xpre, t.m_sint, c, d, t));
         TT_TRY(prof_stop(prof, s));
     }
     return cudaSuccess;
