@@ -739,7 +739,18 @@ __device__ __forceinline__ void neuron_phase(const Consts& c, const Bufs& d, con
                 const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
                 const float* wc = Ws + j;
                 if (c.wprec == SNN_W_FP32) {
-                    for (int a = 0; a < na; ++a) {
+                    // the staged entries two at a time (both weight rows in flight,
+                    // the sums in order), then any beyond them from global memory
+                    int a = 0;
+                    for (; a + 1 < ns; a += 2) {
+                        const float4 w = *(const float4*)(wc + (int)al[a] * nst);
+                        const float4 v = *(const float4*)(wc + (int)al[a + 1] * nst);
+                        I0 = __fadd_rn(__fadd_rn(I0, w.x), v.x);
+                        I1 = __fadd_rn(__fadd_rn(I1, w.y), v.y);
+                        I2 = __fadd_rn(__fadd_rn(I2, w.z), v.z);
+                        I3 = __fadd_rn(__fadd_rn(I3, w.w), v.w);
+                    }
+                    for (; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
                         const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w.x);
@@ -748,7 +759,16 @@ __device__ __forceinline__ void neuron_phase(const Consts& c, const Bufs& d, con
                         I3 = __fadd_rn(I3, w.w);
                     }
                 } else if (c.wprec == SNN_W_BF16) {
-                    for (int a = 0; a < na; ++a) {
+                    int a = 0;
+                    for (; a + 1 < ns; a += 2) {
+                        const float4 w = *(const float4*)(wc + (int)al[a] * nst);
+                        const float4 v = *(const float4*)(wc + (int)al[a + 1] * nst);
+                        I0 = __fadd_rn(__fadd_rn(I0, w_read_bf16(w.x)), w_read_bf16(v.x));
+                        I1 = __fadd_rn(__fadd_rn(I1, w_read_bf16(w.y)), w_read_bf16(v.y));
+                        I2 = __fadd_rn(__fadd_rn(I2, w_read_bf16(w.z)), w_read_bf16(v.z));
+                        I3 = __fadd_rn(__fadd_rn(I3, w_read_bf16(w.w)), w_read_bf16(v.w));
+                    }
+                    for (; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
                         const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w_read_bf16(w.x));
@@ -761,7 +781,16 @@ __device__ __forceinline__ void neuron_phase(const Consts& c, const Bufs& d, con
                     const float* inv = wsc + ncmax;
                     const float v0 = inv[j], v1 = j + 1 < nc ? inv[j + 1] : 1.0f;
                     const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
-                    for (int a = 0; a < na; ++a) {
+                    int a = 0;
+                    for (; a + 1 < ns; a += 2) {
+                        const float4 w = *(const float4*)(wc + (int)al[a] * nst);
+                        const float4 u = *(const float4*)(wc + (int)al[a + 1] * nst);
+                        I0 = __fadd_rn(__fadd_rn(I0, w_read_e4m3(w.x, v0)), w_read_e4m3(u.x, v0));
+                        I1 = __fadd_rn(__fadd_rn(I1, w_read_e4m3(w.y, v1)), w_read_e4m3(u.y, v1));
+                        I2 = __fadd_rn(__fadd_rn(I2, w_read_e4m3(w.z, v2)), w_read_e4m3(u.z, v2));
+                        I3 = __fadd_rn(__fadd_rn(I3, w_read_e4m3(w.w, v3)), w_read_e4m3(u.w, v3));
+                    }
+                    for (; a < na; ++a) {
                         const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
                         const float4 w = *(const float4*)(wc + r * nst);
                         I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
