@@ -65,6 +65,7 @@ struct Layout {
     int lcap;                         // list entries that fit
     int tstate;                       // neuron state held in tensor memory (else in global memory)
     int masks;                        // STDP walks the spike words, no per-input lists (see make_layout)
+    int fused;                        // the neuron phase walks (sample, column-quad) units (see make_layout)
     size_t o_wbuf;                    // encode phase
     size_t bytes;
 };
@@ -95,8 +96,17 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
     L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
-    // tensor memory holds QT / 4 units of four items per thread (see units_of)
-    L.tstate = (long long)c.B * ((L.ncmax + 3) / 4) <= (long long)(QT / 4) * PT;
+    // The neuron phase: fused over (sample, column-quad) units when there are
+    // enough units to busy half the threads and tensor memory holds them (QT / 4
+    // units of four items per thread, see units_of); otherwise the currents and
+    // the update run as two passes over single (sample, column) items, which
+    // keeps more threads busy at small batches and coalesces the state's
+    // global-memory accesses where tensor memory does not hold it.
+    {
+        const long long units = (long long)c.B * ((L.ncmax + 3) / 4);
+        L.fused = units >= PT / 2 && units <= (long long)(QT / 4) * PT;
+        L.tstate = L.fused || (size_t)c.B * L.ncmax <= (size_t)QT * PT;
+    }
     // Narrow layers at large batches: the STDP passes walk the step's spike
     // words instead of per-input lists.  Every CTA would build the same lists
     // from rows of Bw words, which costs more there than the walk saves.
@@ -170,25 +180,53 @@ __device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, con
     const int nmy = cta < c.B ? (c.B - cta + L.G - 1) / L.G : 0;
     const size_t nbi = (size_t)c.B * c.n_in;
     const int units = nmy * c.Iw;
-    for (int u = warp; u < units; u += PT / 32) {
-        const int r = u / c.Iw, iw = u % c.Iw;
-        const int b = cta + L.G * r;
-        const int i = iw * 32 + lane;
-        uint32_t s = 0;
-        if (i < c.n_in) {
-            const size_t o = (size_t)b * c.n_in + i;
-            s = poisson_spike(d.seeds[b], tt, c.n_in, i, d.thr[o]) ? 1u : 0u;
-            float x = __ldcg(&d.x_pre[(size_t)xp * nbi + o]);
-            x = __fmul_rn(x, c.a_x);
-            x = __fadd_rn(x, s ? 1.0f : 0.0f);
-            d.x_pre[(size_t)xc * nbi + o] = x;
-            if (s) atomicOr(&d.preT[((size_t)pm * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
+    // a warp takes two (sample, 32-input word) units per pass: the loads of
+    // both are issued before either draw is used
+    for (int u0 = warp; u0 < units; u0 += 2 * (PT / 32)) {
+        int rr[2], iws[2], bs[2];
+        bool on[2];
+        uint64_t seed[2];
+        uint32_t thr[2];
+        float xo[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int u = u0 + h * (PT / 32);
+            rr[h] = u / c.Iw;
+            iws[h] = u % c.Iw;
+            bs[h] = cta + L.G * rr[h];
+            const int i = iws[h] * 32 + lane;
+            on[h] = u < units && i < c.n_in;
+            seed[h] = 0ull;
+            thr[h] = 0u;
+            xo[h] = 0.0f;
+            if (on[h]) {
+                const size_t o = (size_t)bs[h] * c.n_in + i;
+                seed[h] = d.seeds[bs[h]];
+                thr[h] = d.thr[o];
+                xo[h] = __ldcg(&d.x_pre[(size_t)xp * nbi + o]);
+            }
         }
-        const uint32_t word = __ballot_sync(FULL, s);
-        if (lane == 0) {
-            wbuf[r * c.Iw + iw] = word;
-            d.inb[((size_t)cur * c.B + b) * c.Iw + iw] = word;
-            if (c.rec_input) d.raster_in[((size_t)t_local * c.B + b) * c.Iw + iw] = word;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int u = u0 + h * (PT / 32);
+            if (u >= units) break;                       // the same for the whole warp
+            const int b = bs[h], iw = iws[h];
+            const int i = iw * 32 + lane;
+            uint32_t s = 0;
+            if (on[h]) {
+                const size_t o = (size_t)b * c.n_in + i;
+                s = poisson_spike(seed[h], tt, c.n_in, i, thr[h]) ? 1u : 0u;
+                float x = __fmul_rn(xo[h], c.a_x);
+                x = __fadd_rn(x, s ? 1.0f : 0.0f);
+                d.x_pre[(size_t)xc * nbi + o] = x;
+                if (s) atomicOr(&d.preT[((size_t)pm * c.n_in + i) * c.Bw + (b >> 5)], 1u << (b & 31));
+            }
+            const uint32_t word = __ballot_sync(FULL, s);
+            if (lane == 0) {
+                wbuf[rr[h] * c.Iw + iw] = word;
+                d.inb[((size_t)cur * c.B + b) * c.Iw + iw] = word;
+                if (c.rec_input) d.raster_in[((size_t)t_local * c.B + b) * c.Iw + iw] = word;
+            }
         }
     }
     __syncthreads();
@@ -305,6 +343,23 @@ __device__ __forceinline__ Item neuron_update(const Consts* cp, Item it, float I
 // live in its own TMEM lane (32 x (warp mod 4) + lane id: the lanes a warp may
 // access) in its warp group's block of QT x 4 columns (warp / 4); the 32x32b
 // shape moves consecutive columns of each lane of the warp.
+// The item layout (the separate current and update passes): item q of a
+// thread at columns 4q .. 4q+3 of its block, one 32x32b.x4 move per item.
+__device__ __forceinline__ void tmem_ld4(uint32_t ta, Item& it) {
+    uint32_t a, b, x, st;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(a), "=r"(b), "=r"(x), "=r"(st) : "r"(ta) : "memory");
+    it.v = __uint_as_float(a);
+    it.vi = __uint_as_float(b);
+    it.x = __uint_as_float(x);
+    it.st = st;
+}
+__device__ __forceinline__ void tmem_st4(uint32_t ta, const Item& it) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};"
+                 :: "r"(ta), "r"(__float_as_uint(it.v)), "r"(__float_as_uint(it.vi)),
+                    "r"(__float_as_uint(it.x)), "r"(it.st) : "memory");
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -340,7 +395,8 @@ __device__ __forceinline__ float deposit(float acc, float e) {
 
 template <int RED, bool LISTS, bool NARROW>
 __device__ __noinline__ void depress_quiet_columns(
-        const StdpK c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const int* offs,
+        const StdpK c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const uint32_t* nzP,
+        const int* offs,
         const uint16_t* lst, const uint32_t* nzQ, int NI, int nc, int nst, int Bw, int PS,
         int warp, int lane) {
     const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
@@ -380,7 +436,13 @@ __device__ __noinline__ void depress_quiet_columns(
                 }
             } else {
                 const uint32_t* Pi = preS + i * PS;
+                uint32_t words = Bw <= 32 ? nzP[i] : 0xFFFFFFFFu;   // the row's nonzero words
                 for (int w = 0; w < Bw; ++w) {
+                    if (Bw <= 32) {
+                        if (!words) break;
+                        w = __ffs(words) - 1;
+                        words &= words - 1;
+                    }
                     uint32_t m = Pi[w];
                     while (m) {
                         const float4 x = *(const float4*)(E + (w * 32 + __ffs(m) - 1) * nst);
@@ -443,8 +505,8 @@ __device__ __noinline__ void depress_quiet_columns(
     }
 }
 
-// The same pass with the per-input lists, for wide layers of up to 128
-// columns: L = ceil(nq / QPL) lanes per input row (nq column quads), lane l
+// The same pass with the per-input lists, for layers of 21 to 128 columns per
+// CTA: L = ceil(nq / QPL) lanes per input row (nq column quads), lane l
 // taking the QPL quads l, l + L, ... (one 16-byte load of e each per sample),
 // and R = 32 / L rows per warp, so that a warp's lanes are busy on several rows
 // at once (with 42 columns and QPL = 2: six lanes per row, five rows per warp,
@@ -669,6 +731,187 @@ __device__ __noinline__ void update_post_column_groups(
     }
 }
 
+// Synaptic currents: I[b][j] = sum over the active inputs a of sample b,
+// ascending, of W[a][j] (in the weight precision), into the e tile, which the
+// neuron update then reads and overwrites with e.  One sample per half-warp and
+// four adjacent columns per lane: the active list is the same for the
+// half-warp and each weight row is one 16-byte load.
+__device__ __forceinline__ void synaptic_currents(const Consts& c, const Bufs& d, const float* Ws,
+                                               float* Es, const float* wsc, int ncmax,
+                                               const uint32_t* actN, const uint16_t* actS,
+                                               int caps, int nc, int nst, int cur) {
+    const int B = c.B, NI = c.n_in, tid = threadIdx.x;
+    {
+        const int warp = tid >> 5, lane = tid & 31, h = lane >> 4;
+        for (int g0 = 0; g0 < nc; g0 += 64) {
+            const int j = g0 + 4 * (lane & 15);
+            if (j >= nc) continue;                  // no column of the tile: idle lane
+            for (int b = 2 * warp + h; b < B; b += 2 * NW) {
+                const int na = (int)actN[b];
+                const int ns = na < caps ? na : caps;
+                const uint16_t* al = actS + b * CAPS;
+                const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+                float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+                if (c.wprec == SNN_W_FP32) {
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w.x);
+                        I1 = __fadd_rn(I1, w.y);
+                        I2 = __fadd_rn(I2, w.z);
+                        I3 = __fadd_rn(I3, w.w);
+                    }
+                } else if (c.wprec == SNN_W_BF16) {
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w_read_bf16(w.x));
+                        I1 = __fadd_rn(I1, w_read_bf16(w.y));
+                        I2 = __fadd_rn(I2, w_read_bf16(w.z));
+                        I3 = __fadd_rn(I3, w_read_bf16(w.w));
+                    }
+                } else {
+                    // padding columns take scale 1 (their currents are never used)
+                    const float* inv = wsc + ncmax;
+                    const float v0 = inv[j], v1 = j + 1 < nc ? inv[j + 1] : 1.0f;
+                    const float v2 = j + 2 < nc ? inv[j + 2] : 1.0f, v3 = j + 3 < nc ? inv[j + 3] : 1.0f;
+                    for (int a = 0; a < na; ++a) {
+                        const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                        const float4 w = *(const float4*)(Ws + r * nst + j);
+                        I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
+                        I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
+                        I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
+                        I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
+                    }
+                    I0 = __fmul_rn(I0, wsc[j]);
+                    I1 = __fmul_rn(I1, j + 1 < nc ? wsc[j + 1] : 1.0f);
+                    I2 = __fmul_rn(I2, j + 2 < nc ? wsc[j + 2] : 1.0f);
+                    I3 = __fmul_rn(I3, j + 3 < nc ? wsc[j + 3] : 1.0f);
+                }
+                *(float4*)(Es + b * nst + j) = make_float4(I0, I1, I2, I3);
+            }
+        }
+    }
+}
+
+// The synaptic currents when the CTA has at most four columns (narrow layers):
+// one sample per lane, its columns in one 16-byte load per active input, the
+// same sums in the same order as synaptic_currents (which would leave 15 of 16
+// lanes idle here).
+__device__ __forceinline__ void synaptic_currents_narrow(const Consts& c, const Bufs& d, const float* Ws,
+                                                      float* Es, const float* wsc, int ncmax,
+                                                      const uint32_t* actN, const uint16_t* actS,
+                                                      int caps, int nc, int nst, int cur) {
+    const int B = c.B, NI = c.n_in;
+    for (int b = threadIdx.x; b < B; b += PT) {
+        const int na = (int)actN[b];
+        const int ns = na < caps ? na : caps;
+        const uint16_t* al = actS + b * CAPS;
+        const uint16_t* ag = d.act_idx + ((size_t)cur * B + b) * NI;
+        float I0 = 0.0f, I1 = 0.0f, I2 = 0.0f, I3 = 0.0f;
+        if (c.wprec == SNN_W_FP32) {
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w.x);
+                I1 = __fadd_rn(I1, w.y);
+                I2 = __fadd_rn(I2, w.z);
+                I3 = __fadd_rn(I3, w.w);
+            }
+        } else if (c.wprec == SNN_W_BF16) {
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w_read_bf16(w.x));
+                I1 = __fadd_rn(I1, w_read_bf16(w.y));
+                I2 = __fadd_rn(I2, w_read_bf16(w.z));
+                I3 = __fadd_rn(I3, w_read_bf16(w.w));
+            }
+        } else {
+            const float* inv = wsc + ncmax;
+            const float v0 = inv[0], v1 = 1 < nc ? inv[1] : 1.0f;
+            const float v2 = 2 < nc ? inv[2] : 1.0f, v3 = 3 < nc ? inv[3] : 1.0f;
+            for (int a = 0; a < na; ++a) {
+                const int r = a < ns ? (int)al[a] : (int)__ldcg(&ag[a]);
+                const float4 w = *(const float4*)(Ws + r * nst);
+                I0 = __fadd_rn(I0, w_read_e4m3(w.x, v0));
+                I1 = __fadd_rn(I1, w_read_e4m3(w.y, v1));
+                I2 = __fadd_rn(I2, w_read_e4m3(w.z, v2));
+                I3 = __fadd_rn(I3, w_read_e4m3(w.w, v3));
+            }
+            I0 = __fmul_rn(I0, wsc[0]);
+            I1 = __fmul_rn(I1, 1 < nc ? wsc[1] : 1.0f);
+            I2 = __fmul_rn(I2, 2 < nc ? wsc[2] : 1.0f);
+            I3 = __fmul_rn(I3, 3 < nc ? wsc[3] : 1.0f);
+        }
+        *(float4*)(Es + b * nst) = make_float4(I0, I1, I2, I3);
+    }
+}
+
+// The neuron update of the CTA's (sample, column) items: state from tensor
+// memory (or global memory), the current from the e tile, e = nu_pre x_post
+// back into it, spikes into the masks and counters.  Inlined: a call would have
+// to save the kernel's live values around it, through L1 that the shared
+// memory leaves small, which costs more than the loop's own register pressure.
+__device__ __forceinline__ void neuron_items(const Consts& c, const Bufs& d, float* Es, uint32_t* Qm,
+                                          uint32_t* Sm, const uint32_t* cntS, const float* thj,
+                                          uint32_t tq, bool tstate, int QN, int BN, int nc, int nst,
+                                          int j0, int dq, int dr, int t, int p3) {
+    const int B = c.B, N = c.N, tid = threadIdx.x;
+    {
+        int b = tid / nc, jl = tid % nc;
+        for (int q = 0; q < QN; ++q) {
+            const bool valid = tid + q * PT < BN;
+            const int j = j0 + jl;
+            const size_t idx = (size_t)b * N + j;
+            Item it{0.0f, 0.0f, 0.0f, 0u};
+            if (tstate) {
+                __syncwarp();
+                tmem_ld4(tq + 4 * q, it);
+            } else if (valid) {
+                it.st = d.st[idx];
+                it.v = d.v_e[idx];
+                it.vi = d.v_i[idx];
+                it.x = d.x_post[idx];
+            }
+            if (valid) {
+                const float I = Es[b * nst + jl];
+                const Item o = neuron_update(&c, it, I, (int)cntS[b], thj[jl]);
+                const bool se = (o.st & ST_SE) != 0u, si = (o.st & ST_SI) != 0u;
+                Es[b * nst + jl] = __fmul_rn(c.nu_pre, o.x);
+                if (!tstate) {
+                    d.x_post[idx] = o.x;
+                    d.v_e[idx] = o.v;
+                    d.v_i[idx] = o.vi;
+                    d.st[idx] = o.st;
+                }
+                if (se) {
+                    d.counts[idx] += 1u;
+                    const uint32_t bit = 1u << (b & 31);
+                    atomicOr(&Qm[(b >> 5) * nc + jl], bit);
+                    atomicOr(&Sm[(b >> 5) * nc + jl], bit);
+                    if (c.rec_raster)
+                        atomicOr(&d.raster_e[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                }
+                if (si) {
+                    atomicAdd(&d.cnt[(size_t)p3 * B + b], 1u);
+                    if (c.rec_raster)
+                        atomicOr(&d.raster_i[((size_t)t * B + b) * c.Nw + (j >> 5)], 1u << (j & 31));
+                }
+                it = o;
+            }
+            if (tstate) {
+                __syncwarp();
+                tmem_st4(tq + 4 * q, it);
+            }
+            b += dq;
+            jl += dr;
+            if (jl >= nc) { jl -= nc; ++b; }
+        }
+        if (tstate) tmem_wait_st();
+    }
+}
+
 // The units of the neuron phase: unit u = (sample b, column quad q), the four
 // columns 4q .. 4q+3 of the CTA, numbered u = b * nq + q (nq quads per sample)
 // and dealt to the threads densely: thread tid takes u = tid + k * PT in its
@@ -887,9 +1130,10 @@ __device__ __forceinline__ double theta_next(const Consts& c, double th, int n) 
 }
 
 // NARROW: the CTAs own at most four columns each (narrow layers); the currents
-// and the quiet-column pass then map a lane to a sample or a row.  Two
-// instantiations, so that wide layers run code without the narrow paths.
-template <bool NARROW>
+// and the quiet-column pass then map a lane to a sample or a row.  FUSED: the
+// neuron phase walks (sample, column-quad) units (Layout::fused).  Four
+// instantiations, so that each runs without the registers of the others' paths.
+template <bool NARROW, bool FUSED>
 __global__ void __launch_bounds__(PT, 1)
 k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, const int T,
              const __grid_constant__ Layout L) {
@@ -940,6 +1184,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     // ---- neuron state of the CTA's units into tensor memory
     const bool tstate = L.tstate != 0;
     const Units U = units_of(B, nc);
+    const int BN = B * nc, QN = (BN + PT - 1) / PT;   // items, and items per thread (item layout)
+    const int dq = PT / nc, dr = PT % nc;             // strides of the division-free walk over items
     uint32_t tq = 0;                                  // this thread's tensor-memory block
     if (tstate) {
         if (tid < 32) {
@@ -951,23 +1197,42 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         __syncthreads();
         tmem_fence_after();
         tq = s_tmem + ((uint32_t)(32 * ((tid >> 5) & 3)) << 16) + (uint32_t)((tid >> 7) * QT * 4);
-        int b = tid / U.nq, qd = tid % U.nq;
-        for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
-            const int j = 4 * qd;
-            uint32_t r[16];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                r[4 * q] = r[4 * q + 1] = r[4 * q + 2] = r[4 * q + 3] = 0u;
-                if (b < B && j + q < nc) {
-                    const size_t idx = (size_t)b * N + j0 + j + q;
-                    r[4 * q] = __float_as_uint(d.v_e[idx]);
-                    r[4 * q + 1] = __float_as_uint(d.v_i[idx]);
-                    r[4 * q + 2] = __float_as_uint(d.x_post[idx]);
-                    r[4 * q + 3] = d.st[idx];
+        if (FUSED) {
+            int b = tid / U.nq, qd = tid % U.nq;
+            for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
+                const int j = 4 * qd;
+                uint32_t r[16];
+    #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    r[4 * q] = r[4 * q + 1] = r[4 * q + 2] = r[4 * q + 3] = 0u;
+                    if (b < B && j + q < nc) {
+                        const size_t idx = (size_t)b * N + j0 + j + q;
+                        r[4 * q] = __float_as_uint(d.v_e[idx]);
+                        r[4 * q + 1] = __float_as_uint(d.v_i[idx]);
+                        r[4 * q + 2] = __float_as_uint(d.x_post[idx]);
+                        r[4 * q + 3] = d.st[idx];
+                    }
                 }
+                __syncwarp();
+                tmem_st16(tq + 16u * (uint32_t)sl, r);
             }
-            __syncwarp();
-            tmem_st16(tq + 16u * (uint32_t)sl, r);
+        } else {
+            int b = tid / nc, jl = tid % nc;
+            for (int q = 0; q < QN; ++q) {
+                Item it{0.0f, 0.0f, 0.0f, 0u};
+                if (tid + q * PT < BN) {
+                    const size_t idx = (size_t)b * N + j0 + jl;
+                    it.v = d.v_e[idx];
+                    it.vi = d.v_i[idx];
+                    it.x = d.x_post[idx];
+                    it.st = d.st[idx];
+                }
+                __syncwarp();
+                tmem_st4(tq + 4 * q, it);
+                b += dq;
+                jl += dr;
+                if (jl >= nc) { jl -= nc; ++b; }
+            }
         }
         tmem_wait_st();
     }
@@ -1131,8 +1396,15 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
-        neuron_phase(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, Qm, Sm, cntS, thj, tq, tstate, nc, nst, j0,
-                     cur, t, p3);
+        if (FUSED) {
+            neuron_phase(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, Qm, Sm, cntS, thj, tq, tstate, nc, nst,
+                         j0, cur, t, p3);
+        } else {
+            if (NARROW) synaptic_currents_narrow(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
+            else synaptic_currents(c, d, Ws, Es, wsc, L.ncmax, actN, actS, caps, nc, nst, cur);
+            __syncthreads();
+            neuron_items(c, d, Es, Qm, Sm, cntS, thj, tq, tstate, QN, BN, nc, nst, j0, dq, dr, t, p3);
+        }
         __syncthreads();
 
         // ================= next step's input, signalled before this step's STDP
@@ -1222,12 +1494,12 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     const int i = k / nc, jl = k % nc;
                     if (nzQ[jl] == 0u) Ws[i * nst + jl] = fminf(fmaxf(Ws[i * nst + jl], c.w_min), c.w_max);
                 }
-            } else {
+            } else if (!lists || offs[NI] > 0) {   // (with the lists: no input spike, nothing to do)
                 const StdpK sk{c.inv_B, c.w_min, c.w_max, c.B};
 #define SNN_PASS_A_N(R, NR)                                                                        \
-    (lists && !NR && nc <= 128 ? depress_quiet_rows<R, 2>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
-     : lists ? depress_quiet_columns<R, true, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
-             : depress_quiet_columns<R, false, NR>(sk, Ws, WLs, Es, preS, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
+    (lists && !NR && nc > 20 && nc <= 128 ? depress_quiet_rows<R, 2>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
+     : lists ? depress_quiet_columns<R, true, NR>(sk, Ws, WLs, Es, preS, nzP, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
+             : depress_quiet_columns<R, false, NR>(sk, Ws, WLs, Es, preS, nzP, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
 #define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)
                 if (c.reduce == SNN_REDUCE_MAX) SNN_PASS_A(RED_MAX);
                 else if (c.reduce == SNN_REDUCE_SUM) SNN_PASS_A(RED_SUM);
@@ -1246,7 +1518,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 // Sum and mean, wide layers: groups of PG post columns (with at most
                 // four columns a CTA has too few groups to keep its warps busy)
                 const bool grouped = !NARROW && c.reduce != SNN_REDUCE_MAX;
-                if (grouped)
+                if (grouped && npc > 0)   // (no call, and no saving of live values, without work)
                     update_post_column_groups(
                             PostK{c.nu_post, c.inv_B, c.w_min, c.w_max, c.B, c.B_pow2,
                                   c.reduce == SNN_REDUCE_MEAN ? 1 : 0, dep_on ? 1 : 0},
@@ -1372,21 +1644,40 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     // ---- write the CTA's columns back, and the neuron state held in tensor memory
     __syncthreads();
     if (tstate) {
-        int b = tid / U.nq, qd = tid % U.nq;
-        for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
-            const int j = 4 * qd;
-            uint32_t r[16];
-            __syncwarp();
-            tmem_ld16(tq + 16u * (uint32_t)sl, r);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (b < B && j + q < nc) {
-                    const size_t idx = (size_t)b * N + j0 + j + q;
-                    d.v_e[idx] = __uint_as_float(r[4 * q]);
-                    d.v_i[idx] = __uint_as_float(r[4 * q + 1]);
-                    d.x_post[idx] = __uint_as_float(r[4 * q + 2]);
-                    d.st[idx] = r[4 * q + 3];
+        if (FUSED) {
+            int b = tid / U.nq, qd = tid % U.nq;
+            for (int sl = 0; sl < U.nslot; ++sl, unit_next(U, b, qd)) {
+                const int j = 4 * qd;
+                uint32_t r[16];
+                __syncwarp();
+                tmem_ld16(tq + 16u * (uint32_t)sl, r);
+    #pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (b < B && j + q < nc) {
+                        const size_t idx = (size_t)b * N + j0 + j + q;
+                        d.v_e[idx] = __uint_as_float(r[4 * q]);
+                        d.v_i[idx] = __uint_as_float(r[4 * q + 1]);
+                        d.x_post[idx] = __uint_as_float(r[4 * q + 2]);
+                        d.st[idx] = r[4 * q + 3];
+                    }
                 }
+            }
+        } else {
+            int b = tid / nc, jl = tid % nc;
+            for (int q = 0; q < QN; ++q) {
+                Item it;
+                __syncwarp();
+                tmem_ld4(tq + 4 * q, it);
+                if (tid + q * PT < BN) {
+                    const size_t idx = (size_t)b * N + j0 + jl;
+                    d.v_e[idx] = it.v;
+                    d.v_i[idx] = it.vi;
+                    d.x_post[idx] = it.x;
+                    d.st[idx] = it.st;
+                }
+                b += dq;
+                jl += dr;
+                if (jl >= nc) { jl -= nc; ++b; }
             }
         }
         tmem_fence_before();
@@ -1425,7 +1716,7 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     // Device properties and the kernel's shared-memory opt-in are looked up
     // once per device and layout size, not on every run; the cache is shared
     // by every host thread, so its reads and writes hold a lock.
-    struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes = 0, attr_narrow = 0; };
+    struct Setup { int sms = 0, smem_optin = 0; size_t attr_bytes[4] = {0, 0, 0, 0}; };   // per instantiation
     static Setup setup[64];
     static std::mutex setup_mutex;
     int dev = 0;
@@ -1445,8 +1736,9 @@ cudaError_t launch_persistent(const Consts& c, const Bufs& d, int T, cudaStream_
     const Layout L = make_layout(c, G, budget);
     if (L.bytes > budget) return cudaSuccess;
     const bool narrow = L.ncmax <= 4;
-    const void* kern = narrow ? (const void*)k_persistent<true> : (const void*)k_persistent<false>;
-    size_t& attr = narrow ? su.attr_narrow : su.attr_bytes;
+    const void* kern = narrow ? (L.fused ? (const void*)k_persistent<true, true> : (const void*)k_persistent<true, false>)
+                              : (L.fused ? (const void*)k_persistent<false, true> : (const void*)k_persistent<false, false>);
+    size_t& attr = su.attr_bytes[(narrow ? 2 : 0) + (L.fused ? 1 : 0)];
     if (attr < L.bytes) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
         if (e != cudaSuccess) return e;
