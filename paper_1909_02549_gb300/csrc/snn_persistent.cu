@@ -128,6 +128,12 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
         if (cap > most) cap = most;
         if (cap > ((size_t)1 << 30)) cap = (size_t)1 << 30;
         if (c.B > 65536) cap = 0;                         // sample indices are 16-bit
+        // Lists for up to 1 in 16 input events (at least 8192 entries); denser
+        // steps walk the spike words.  The shared memory left over goes to L1,
+        // which holds the kernel's spills and the x_pre lines of the STDP.
+        const size_t enough = most / 16 > 8192 ? most / 16 : 8192;
+        if (cap > enough) cap = enough;
+        if (L.masks) cap = 0;   // no lists at all
         L.lcap = (int)(cap & ~(size_t)7);
         o = align16(o + (size_t)L.lcap * 2);
     }
