@@ -1267,10 +1267,22 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             pq0 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw));
             if (Bw == 8) pq1 = __ldcg((const uint4*)(pre_src + (size_t)tid * Bw) + 1);
         }
-        for (int b = tid; b < B; b += PT) {
-            cntS[b] = __ldcg(&d.cnt[(size_t)((p3 + 2) % 3) * B + b]);
-            actN[b] = __ldcg(&d.act_cnt[(size_t)cur * B + b]);
+        // The staging loads of the thread's first sample and first list entries
+        // are issued with the mask rows above and stored after the work that
+        // does not need them, so that their round trips overlap.
+        const uint32_t* cnt_src = d.cnt + (size_t)((p3 + 2) % 3) * B;
+        const uint32_t* actn_src = d.act_cnt + (size_t)cur * B;
+        const uint16_t* acts_src = d.act_idx + (size_t)cur * B * NI;
+        const bool acts_vec = caps == CAPS && (NI & 7) == 0;   // rows 16-byte aligned: 8 entries per load
+        const int acts_per = CAPS / 8, acts_n = B * acts_per;
+        uint32_t cn0 = 0u, an0 = 0u;
+        if (tid < B) {
+            cn0 = __ldcg(&cnt_src[tid]);
+            an0 = __ldcg(&actn_src[tid]);
         }
+        uint4 av0 = make_uint4(0u, 0u, 0u, 0u);
+        if (acts_vec && tid < acts_n)
+            av0 = __ldcg((const uint4*)(acts_src + (size_t)(tid / acts_per) * NI) + (tid % acts_per));
         for (int k = tid; k < Bw * nc; k += PT) Qm[k] = 0u;
         for (int jl = tid; jl < nc; jl += PT) {   // thresholds after the previous step's STDP
             if (c.learn && t > 0) thS[jl] = theta_next(c, thS[jl], (int)nzQ[jl]);
@@ -1284,28 +1296,35 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             uint32_t* z = d.preT + (size_t)((tt + 2ull) % PRET_SLOTS) * n_pre;
             for (size_t k = (size_t)cta * PT + tid; k < n_pre; k += (size_t)G * PT) z[k] = 0u;
         }
-        {   // first entries of every sample's active-input list (in bounds: caps <= n_in)
-            const uint16_t* src = d.act_idx + (size_t)cur * B * NI;
-            if (caps == CAPS && (NI & 7) == 0) {      // rows 16-byte aligned: 8 entries per load
-                const int per = CAPS / 8, n = B * per;
-                for (int k0 = tid; k0 < n; k0 += 2 * PT) {
-                    uint4 v4[2];
+        // the previous step's inhibitory counts and this step's active-input counts
+        if (tid < B) {
+            cntS[tid] = cn0;
+            actN[tid] = an0;
+        }
+        for (int b = tid + PT; b < B; b += PT) {
+            cntS[b] = __ldcg(&cnt_src[b]);
+            actN[b] = __ldcg(&actn_src[b]);
+        }
+        // first entries of every sample's active-input list (in bounds: caps <= n_in)
+        if (acts_vec) {
+            if (tid < acts_n) ((uint4*)actS)[tid] = av0;
+            for (int k0 = tid + PT; k0 < acts_n; k0 += 2 * PT) {
+                uint4 v4[2];
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int k = k0 + q * PT;
-                        if (k < n) v4[q] = __ldcg((const uint4*)(src + (size_t)(k / per) * NI) + (k % per));
-                    }
-#pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        const int k = k0 + q * PT;
-                        if (k < n) ((uint4*)actS)[k] = v4[q];
-                    }
+                for (int q = 0; q < 2; ++q) {
+                    const int k = k0 + q * PT;
+                    if (k < acts_n) v4[q] = __ldcg((const uint4*)(acts_src + (size_t)(k / acts_per) * NI) + (k % acts_per));
                 }
-            } else {
-                const int n = B * caps;
-                for (int k = tid; k < n; k += PT)
-                    actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&src[(size_t)(k / caps) * NI + (k % caps)]);
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int k = k0 + q * PT;
+                    if (k < acts_n) ((uint4*)actS)[k] = v4[q];
+                }
             }
+        } else {
+            const int n = B * caps;
+            for (int k = tid; k < n; k += PT)
+                actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&acts_src[(size_t)(k / caps) * NI + (k % caps)]);
         }
         // Per input i: the samples whose input i fired this step, ascending, in
         // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
@@ -1436,6 +1455,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     int n = 0;
                     if (jl < nc) {
                         uint32_t nz = 0;
+#pragma unroll 8
                         for (int w = 0; w < Bw; ++w) {
                             const uint32_t q = Qm[w * nc + jl];
                             n += __popc(q);
