@@ -182,14 +182,14 @@ def test_ragged_shapes_learning(B, N):
 
 @pytest.mark.parametrize("B,N,n_in", [(300, 1000, 784), (40, 10000, 100), (300, 10000, 100)])
 def test_neuron_units_in_and_beyond_tensor_memory(B, N, n_in):
-    """The persistent form's neuron phase walks (sample, four-column) units,
-    one sample per half-warp and one column quad per lane in groups of 64
-    columns; tensor memory holds four units per thread.  1000 neurons at
-    B = 300 need five sample slots (the state stays in global memory); 10000
-    neurons (66 columns per SM) need two column groups, with the state in
-    tensor memory at B = 40 and in global memory at B = 300 (100 inputs at
-    eight times the image rates, so that the narrow input layer drives
-    spikes)."""
+    """The persistent form's neuron phase in both layouts.  Fused: (sample,
+    four-column) units dealt densely to the threads, four per thread in tensor
+    memory at most, used where the units busy half the threads: 1000 neurons at
+    B = 300 (600 units), 10000 neurons at B = 40 (66 columns per SM, 680
+    units).  Items: the separate current and update passes, where the units do
+    not fit: 10000 neurons at B = 300 (5100 units), the state then in global
+    memory (100 inputs at eight times the image rates, so that the narrow input
+    layer drives spikes)."""
     p, r, s, w = synth.workload(B, N, n_in=n_in)
     if n_in < 784:
         r = (r * np.float32(8)).astype(np.float32)
