@@ -381,8 +381,10 @@ __device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence
 // subtracts e directly: acc - e equals acc + (0 - e) bit for bit.  The clip
 // min(max(u, w_min), w_max) is the comparison form's value, u being neither
 // NaN nor -0.  LISTS: the row's samples come from the per-input lists, else
-// from its spike words.  Out of line, so that its loops get registers of their
-// own inside the large kernel.
+// from its spike words (only its nonzero words).  Used where the row-grouped
+// pass below is not: narrow layers, the max reduction with the spike words,
+// and layers outside its column range.  Out of line, so that its loops get
+// registers of their own inside the large kernel.
 enum { RED_SUM = 0, RED_MEAN_MUL = 1, RED_MEAN_DIV = 2, RED_MAX = 3 };
 
 // The constants the out-of-line STDP passes read, passed by value: read
