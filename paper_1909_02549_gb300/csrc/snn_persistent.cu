@@ -107,10 +107,11 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
         L.fused = units >= PT / 2 && units <= (long long)(QT / 4) * PT;
         L.tstate = L.fused || (size_t)c.B * L.ncmax <= (size_t)QT * PT;
     }
-    // Narrow layers at large batches: the STDP passes walk the step's spike
-    // words instead of per-input lists.  Every CTA would build the same lists
-    // from rows of Bw words, which costs more there than the walk saves.
-    L.masks = L.ncmax <= 4 && c.Bw >= 16;
+    // Narrow layers, and any layer at up to 64 samples: the STDP passes walk
+    // the step's spike words instead of per-input lists.  Every CTA would build
+    // the same lists (two block barriers and a scan per step), which costs more
+    // there than the walk saves; wide layers at larger batches keep the lists.
+    L.masks = L.ncmax <= 4 || c.Bw <= 2;
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_enc ? u_neuron : u_enc;
