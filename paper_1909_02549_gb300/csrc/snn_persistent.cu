@@ -522,9 +522,10 @@ __device__ __noinline__ void depress_quiet_columns(
 // where the half-warp mapping above keeps five of every sixteen lanes idle).
 // The rows' sums, the reduction and the clip are those of
 // depress_quiet_columns.
-template <int RED, int QPL>
+template <int RED, int QPL, bool LISTS>
 __device__ __noinline__ void depress_quiet_rows(
         const StdpK c, float* Ws, float* WLs, const float* Es, const int* offs, const uint16_t* lst,
+        const uint32_t* preS, const uint32_t* nzP, int PS, int Bw,
         const uint32_t* nzQ, int NI, int nc, int nst, int warp, int lane) {
     const float init = RED == RED_MAX ? -FLT_MAX : 0.0f;
     const int nq = (nc + 3) / 4, L = (nq + QPL - 1) / QPL, R = 32 / L;
@@ -554,20 +555,48 @@ __device__ __noinline__ void depress_quiet_rows(
         float a[4 * QPL];
 #pragma unroll
         for (int k = 0; k < 4 * QPL; ++k) a[k] = init;
-        const int e0 = offs[i], e1 = offs[i + 1];
-        for (int e = e0; e < e1; ++e) {
-            const float* er = Es + (int)lst[e] * nst + 4 * l;
+        int n = 0;
+        if (LISTS) {
+            const int e0 = offs[i], e1 = offs[i + 1];
+            for (int e = e0; e < e1; ++e) {
+                const float* er = Es + (int)lst[e] * nst + 4 * l;
 #pragma unroll
-            for (int m = 0; m < QPL; ++m) {
-                if (!has[m]) continue;
-                const float4 x = *(const float4*)(er + 4 * m * L);
-                a[4 * m] = deposit<RED>(a[4 * m], x.x);
-                a[4 * m + 1] = deposit<RED>(a[4 * m + 1], x.y);
-                a[4 * m + 2] = deposit<RED>(a[4 * m + 2], x.z);
-                a[4 * m + 3] = deposit<RED>(a[4 * m + 3], x.w);
+                for (int m = 0; m < QPL; ++m) {
+                    if (!has[m]) continue;
+                    const float4 x = *(const float4*)(er + 4 * m * L);
+                    a[4 * m] = deposit<RED>(a[4 * m], x.x);
+                    a[4 * m + 1] = deposit<RED>(a[4 * m + 1], x.y);
+                    a[4 * m + 2] = deposit<RED>(a[4 * m + 2], x.z);
+                    a[4 * m + 3] = deposit<RED>(a[4 * m + 3], x.w);
+                }
+            }
+            n = e1 - e0;
+        } else {   // the row's spike words, its nonzero words only, ascending b
+            const uint32_t* Pi = preS + i * PS;
+            uint32_t words = Bw <= 32 ? nzP[i] : 0xFFFFFFFFu;
+            for (int w = 0; w < Bw; ++w) {
+                if (Bw <= 32) {
+                    if (!words) break;
+                    w = __ffs(words) - 1;
+                    words &= words - 1;
+                }
+                uint32_t mk = Pi[w];
+                while (mk) {
+                    const float* er = Es + (w * 32 + __ffs(mk) - 1) * nst + 4 * l;
+                    mk &= mk - 1;
+                    ++n;
+#pragma unroll
+                    for (int m = 0; m < QPL; ++m) {
+                        if (!has[m]) continue;
+                        const float4 x = *(const float4*)(er + 4 * m * L);
+                        a[4 * m] = deposit<RED>(a[4 * m], x.x);
+                        a[4 * m + 1] = deposit<RED>(a[4 * m + 1], x.y);
+                        a[4 * m + 2] = deposit<RED>(a[4 * m + 2], x.z);
+                        a[4 * m + 3] = deposit<RED>(a[4 * m + 3], x.w);
+                    }
+                }
             }
         }
-        const int n = e1 - e0;
         if (n == 0) continue;
 #pragma unroll
         for (int k = 0; k < 4 * QPL; ++k) {
@@ -1526,7 +1555,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             } else if (!lists || offs[NI] > 0) {   // (with the lists: no input spike, nothing to do)
                 const StdpK sk{c.inv_B, c.w_min, c.w_max, c.B};
 #define SNN_PASS_A_N(R, NR)                                                                        \
-    (lists && !NR && nc > 20 && nc <= 128 ? depress_quiet_rows<R, 2>(sk, Ws, WLs, Es, offs, lst, nzQ, NI, nc, nst, warp, lane) \
+    (!NR && nc > 20 && nc <= 128                                                                   \
+         ? (lists ? depress_quiet_rows<R, 2, true>(sk, Ws, WLs, Es, offs, lst, preS, nzP, PS, Bw, nzQ, NI, nc, nst, warp, lane) \
+                  : depress_quiet_rows<R, 2, false>(sk, Ws, WLs, Es, offs, lst, preS, nzP, PS, Bw, nzQ, NI, nc, nst, warp, lane)) \
      : lists ? depress_quiet_columns<R, true, NR>(sk, Ws, WLs, Es, preS, nzP, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane) \
              : depress_quiet_columns<R, false, NR>(sk, Ws, WLs, Es, preS, nzP, offs, lst, nzQ, NI, nc, nst, Bw, PS, warp, lane))
 #define SNN_PASS_A(R) SNN_PASS_A_N(R, NARROW)
