@@ -731,6 +731,13 @@ def serving_point(torch, snn, synth, rate: float, dur: float, cap_bytes: int, k:
     net = snn.Network(p, w_init=synth.weights(784, N))
     srv = snn.snn_serve_create(net.handle, 4096, cap_bytes)
     slots = snn.snn_serve_status(srv)["slots"]
+    # warm-up outside the clock: one short request through admission, a chunk
+    # and retirement, so that no first launch (module load) lands in the run
+    snn.snn_serve_submit(srv, rates[0], int(seeds[0]), 2 * k)
+    for _ in range(3):
+        snn.snn_serve_step(srv, k)
+    snn.snn_serve_wait(srv)
+    snn.snn_serve_poll(srv, N)
     lat = np.zeros(n)
     done = q = peak = 0
     id2q = {}
@@ -764,6 +771,10 @@ def serving_point(torch, snn, synth, rate: float, dur: float, cap_bytes: int, k:
             "slot_bytes": snn.snn_serve_slot_bytes(net.handle)}
     Bf = 256
     lat2 = np.zeros(n)
+    # warm-up outside the clock: one full-size batch (its launches loaded, AUTO's choice made)
+    net.run(torch.from_numpy(rates[:Bf]).cuda(), torch.from_numpy(seeds[:Bf].view(np.int64)).cuda(), 20,
+            learn=False, mode="auto")
+    net.read("spike_counts")
     t0 = _t.perf_counter()
     for b0 in range(0, n, Bf):
         b1 = min(n, b0 + Bf)
