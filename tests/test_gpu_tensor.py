@@ -155,6 +155,20 @@ def test_learning_large_batch_within_tolerance():
     assert_within_tolerance(g, st, rec, 40, w)
 
 
+@pytest.mark.parametrize("B", [256, 1024])
+def test_wide_layer_large_batch_within_tolerance(B):
+    """784 -> 6400 (50 neuron tiles, 7 input tiles of the update, one batch
+    slice per tile), the first 20 steps against the whole-batch oracle: the
+    current's 64- and 128-sample tiles (two and four 16-sample chunks per
+    epilogue thread) and the update straight from tensor memory."""
+    p, r, s, w = synth.workload(B, 6400)
+    st = oracle.new_state(p, B, w)
+    rec = oracle.run(p, st, r, s, 20, learn=True, reduce="mean")
+    _, g = run_gpu(p, r, s, w, 20, mode="tensor")
+    assert rec.raster_e.sum() > 0
+    assert_within_tolerance(g, st, rec, 20, w)
+
+
 def test_bf16_weights_bit_exact_on_the_bf16_grid_and_close_off_it():
     """BF16 weights feed the product as one bfloat16 term: on the 2^-9 grid
     (BF16-exact) learning off equals the oracle's BF16 run bit for bit."""
