@@ -129,6 +129,7 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
         if (cap > most) cap = most;
         if (cap > ((size_t)1 << 30)) cap = (size_t)1 << 30;
         if (c.B > 65536) cap = 0;                         // sample indices are 16-bit
+        if (cap > 65535) cap = 65535;                     // 16-bit list offsets (row_span)
         // Lists for up to 1 in 16 input events (at least 8192 entries); denser
         // steps walk the spike words.  The shared memory left over goes to L1,
         // which holds the kernel's spills and the x_pre lines of the STDP.
@@ -402,6 +403,14 @@ __device__ __forceinline__ float deposit(float acc, float e) {
     return RED == RED_MAX ? fmaxf(acc, __fsub_rn(0.0f, e)) : __fsub_rn(acc, e);
 }
 
+// Row i's listed samples are lst[e0, e1): offs[i] packs the start (low 16 bits)
+// and the count (high 16 bits); the lists never exceed 65535 entries.
+__device__ __forceinline__ void row_span(const int* offs, int i, int& e0, int& e1) {
+    const uint32_t o = (uint32_t)offs[i];
+    e0 = (int)(o & 0xFFFFu);
+    e1 = e0 + (int)(o >> 16);
+}
+
 template <int RED, bool LISTS, bool NARROW>
 __device__ __noinline__ void depress_quiet_columns(
         const StdpK c, float* Ws, float* WLs, const float* Es, const uint32_t* preS, const uint32_t* nzP,
@@ -425,8 +434,8 @@ __device__ __noinline__ void depress_quiet_columns(
             float a0 = init, a1 = init, a2 = init, a3 = init;
             int n = 0;
             if (LISTS) {
-                int e = offs[i];
-                const int e1 = offs[i + 1];
+                int e, e1;
+                row_span(offs, i, e, e1);
                 n = e1 - e;
                 for (; e + 1 < e1; e += 2) {             // two loads in flight, then in order
                     const float4 x = *(const float4*)(E + (int)lst[e] * nst);
@@ -557,7 +566,8 @@ __device__ __noinline__ void depress_quiet_rows(
         for (int k = 0; k < 4 * QPL; ++k) a[k] = init;
         int n = 0;
         if (LISTS) {
-            const int e0 = offs[i], e1 = offs[i + 1];
+            int e0, e1;
+            row_span(offs, i, e0, e1);
             for (int e = e0; e < e1; ++e) {
                 const float* er = Es + (int)lst[e] * nst + 4 * l;
 #pragma unroll
@@ -729,8 +739,9 @@ __device__ __noinline__ void update_post_column_groups(
             dep[k] = 0.0f;
         }
         if (c.dep_on && lists) {   // every input-spike sample (e is 0 where j has not fired)
-            const int e1 = offs[i + 1];
-            for (int e = offs[i]; e < e1; ++e) {
+            int e0, e1;
+            row_span(offs, i, e0, e1);
+            for (int e = e0; e < e1; ++e) {
                 const float* er = Es + (int)lst[e] * nst;
 #pragma unroll
                 for (int k = 0; k < PG; ++k) dep[k] = __fadd_rn(dep[k], er[jls[k]]);
@@ -1192,7 +1203,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     int* offs = (int*)(sm + L.o_off);
     uint16_t* lst = (uint16_t*)(sm + L.o_lst);
     __shared__ int s_nq;
-    __shared__ int s_scan[32];
+    __shared__ int s_lovf[2], s_lany[2];   // by step parity: the lists overflowed; an input fired
     __shared__ uint32_t s_tmem;
 
     const int cta = blockIdx.x, tid = threadIdx.x;
@@ -1279,6 +1290,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     if (cta == 0)
         for (int b = tid; b < B; b += PT) d.cnt[(size_t)(base % 3ull) * B + b] = 0u;
     encode_phase(c, d, L, sm, base, 0);
+    if (tid == 0) s_lovf[0] = s_lany[0] = 0;
     unsigned nbar = 1;
     grid_arrive(bar);
     // (test knob: wait for one arrival more than there are CTAs, with a short limit)
@@ -1288,6 +1300,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
     for (int t = 0; t < T && ok; ++t) {
         const unsigned long long tt = base + (unsigned long long)t;
         const int cur = (int)(tt & 1ull), p3 = (int)(tt % 3ull);
+        // the list flags of step t+1 (last read by step t-1's STDP, before the barrier)
+        if (tid == 0) s_lovf[(t + 1) & 1] = s_lany[(t + 1) & 1] = 0;
 
         // ================= neuron phase =================
         // (the step's input-mask rows for the lists below, loaded first so that
@@ -1359,17 +1373,20 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 actS[(k / caps) * CAPS + (k % caps)] = __ldcg(&acts_src[(size_t)(k / caps) * NI + (k % caps)]);
         }
         // Per input i: the samples whose input i fired this step, ascending, in
-        // lst[offs[i], offs[i+1]), from a block-wide scan of the rows' spike
-        // counts (the step's input-major masks are complete since the barrier).
-        // One thread per row reads the row's words once.  Lists are written
-        // only while they fit; the STDP passes walk the spike words instead when
-        // the step's total exceeds the space.  (Learning off: nothing reads them;
-        // with L.masks the STDP phase reads the masks themselves.)
+        // lst[row_span(i)] (the step's input-major masks are complete since the
+        // barrier).  One thread per row reads the row's words once; each warp
+        // lists its rows in a region of its own (a scan within the warp, no
+        // block barrier).  A warp whose rows do not fit its region sets the
+        // overflow flag, and the STDP passes walk the spike words instead.
+        // (Learning off: nothing reads them; with L.masks the STDP phase reads
+        // the masks themselves.)
         if (c.learn && !L.masks) {
             const uint32_t* src = pre_src;
             const bool vec = pre_vec;
             const int wp = tid >> 5, ln = tid & 31;
-            int n_ev = 0;
+            const int nwr = NI < PT ? (NI + 31) / 32 : NW;   // warps with rows
+            const int capw = L.lcap / nwr, reg0 = wp * capw;
+            int run = 0;                                     // the warp's entries so far
             for (int r0 = 0; r0 < NI; r0 += PT) {
                 const int i = r0 + tid;
                 uint32_t wr[8];                              // the row's words
@@ -1402,22 +1419,11 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     const int y = __shfl_up_sync(FULL, x, o);
                     if (ln >= o) x += y;
                 }
-                if (ln == 31) s_scan[wp] = x;
-                __syncthreads();
-                if (wp == 0) {                               // ... and over the warps
-                    int v = ln < NW ? s_scan[ln] : 0;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(FULL, v, o);
-                        if (ln >= o) v += y;
-                    }
-                    s_scan[ln] = v;
-                }
-                __syncthreads();
-                const int start = n_ev + (wp ? s_scan[wp - 1] : 0) + x - n;
-                if (i < NI) {
-                    offs[i] = start;
-                    if (start + n <= L.lcap) {
+                const int tot = __shfl_sync(FULL, x, 31);
+                if (run + tot <= capw) {                     // (uniform over the warp)
+                    if (i < NI) {
+                        const int start = reg0 + run + x - n;
+                        offs[i] = start | (n << 16);
                         int q = start;
                         if (vec) {
 #pragma unroll
@@ -1432,11 +1438,12 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                             wide_row_list(src + (size_t)i * Bw, Bw, nz, lst + q);
                         }
                     }
+                } else if (ln == 0) {
+                    s_lovf[t & 1] = 1;
                 }
-                n_ev += s_scan[NW - 1];
-                if (r0 + PT < NI) __syncthreads();           // s_scan is rewritten by the next rows
+                run += tot;
             }
-            if (tid == 0) offs[NI] = n_ev;
+            if (ln == 0 && run > 0) s_lany[t & 1] = 1;
         }
         if (c.wprec == SNN_W_FP8E4M3) {   // column scales of this step's weights
             const int warp = tid >> 5, lane = tid & 31;
@@ -1479,7 +1486,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             int* pcol = (int*)(sm + L.o_pcol);
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
             const int PS = L.ps;
-            const bool lists = !L.masks && offs[NI] <= L.lcap;
+            const bool lists = !L.masks && s_lovf[t & 1] == 0;
             if (tid < 32) {   // which columns fired, and the list of those columns
                 int npc = 0;
                 for (int jl0 = 0; jl0 < nc; jl0 += 32) {
@@ -1552,7 +1559,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     const int i = k / nc, jl = k % nc;
                     if (nzQ[jl] == 0u) Ws[i * nst + jl] = fminf(fmaxf(Ws[i * nst + jl], c.w_min), c.w_max);
                 }
-            } else if (!lists || offs[NI] > 0) {   // (with the lists: no input spike, nothing to do)
+            } else if (!lists || s_lany[t & 1] != 0) {   // (with the lists: no input spike, nothing to do)
                 const StdpK sk{c.inv_B, c.w_min, c.w_max, c.B};
 #define SNN_PASS_A_N(R, NR)                                                                        \
     (!NR && nc > 20 && nc <= 128                                                                   \
@@ -1637,8 +1644,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     // depression: input i fired in b, and j has fired in b this episode
                     float dep = 0.0f;
                     if (lists && dep_on) {   // every input-spike sample (e is 0 where j has not fired)
-                        const int e1 = offs[i + 1];
-                        for (int e = offs[i]; e < e1; ++e) {
+                        int e0, e1;
+                        row_span(offs, i, e0, e1);
+                        for (int e = e0; e < e1; ++e) {
                             const int b = lst[e];
                             if (is_max && ((Qm[(b >> 5) * nc + jl] >> (b & 31)) & 1u)) continue;
                             const float ev = Es[b * nst + jl];
