@@ -178,8 +178,11 @@ __device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigne
     return s_fail == 0;
 }
 
-__device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
-                             unsigned long long tt, int t_local) {
+// The encode of step tt in two parts, a block barrier between them: the
+// (sample, 32-input) words of the CTA's samples, then one warp per sample
+// listing its active inputs from those words.
+__device__ __forceinline__ void encode_words(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
+                                             unsigned long long tt, int t_local) {
     const int cta = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cur = (int)(tt & 1ull);
     const int xc = (int)(tt % XPRE_SLOTS), xp = (int)((tt + XPRE_SLOTS - 1) % XPRE_SLOTS);
@@ -237,7 +240,14 @@ __device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, con
             }
         }
     }
-    __syncthreads();
+}
+
+__device__ __forceinline__ void encode_lists(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
+                                             unsigned long long tt) {
+    const int cta = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cur = (int)(tt & 1ull);
+    const uint32_t* wbuf = (const uint32_t*)(sm + L.o_wbuf);
+    const int nmy = cta < c.B ? (c.B - cta + L.G - 1) / L.G : 0;
     for (int r = warp; r < nmy; r += PT / 32) {       // one warp per sample
         const int b = cta + L.G * r;
         uint16_t* out = d.act_idx + ((size_t)cur * c.B + b) * c.n_in;
@@ -261,6 +271,42 @@ __device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, con
         }
         if (lane == 0) d.act_cnt[(size_t)cur * c.B + b] = running;
     }
+}
+
+__device__ __forceinline__ void encode_phase(const Consts& c, const Bufs& d, const Layout& L, unsigned char* sm,
+                                             unsigned long long tt, int t_local) {
+    encode_words(c, d, L, sm, tt, t_local);
+    __syncthreads();
+    encode_lists(c, d, L, sm, tt);
+}
+
+// Which of the CTA's columns fired this step (one warp, after the neuron
+// phase): nzQ[jl] = column jl's post spikes (theta follows at the next step's
+// start), nzQw[jl] = the batch words holding them, pcol = the fired columns
+// ascending, *npc = their number.
+__device__ __forceinline__ void list_post_columns(const uint32_t* Qm, int nc, int Bw, uint32_t* nzQ,
+                                                  uint32_t* nzQw, int* pcol, int* npc_out, int lane) {
+    int npc = 0;
+    for (int jl0 = 0; jl0 < nc; jl0 += 32) {
+        const int jl = jl0 + lane;
+        int n = 0;
+        if (jl < nc) {
+            uint32_t nz = 0;
+#pragma unroll 8
+            for (int w = 0; w < Bw; ++w) {
+                const uint32_t q = Qm[w * nc + jl];
+                n += __popc(q);
+                if (q && w < 32) nz |= 1u << w;
+            }
+            nzQ[jl] = n;
+            nzQw[jl] = nz;
+        }
+        const bool f = jl < nc && n != 0;
+        const uint32_t bal = __ballot_sync(FULL, f);
+        if (f) pcol[npc + __popc(bal & ((1u << lane) - 1u))] = jl;
+        npc += __popc(bal);
+    }
+    if (lane == 0) *npc_out = npc;
 }
 
 // Rows of the step's input-major masks wider than 8 words (B > 256), for the
@@ -1473,8 +1519,18 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
 
         // ================= next step's input, signalled before this step's STDP
         // (which needs nothing from other CTAs' next step), waited for after it
+        // The STDP phase's post columns are listed by the last warp while the
+        // others list the next step's active inputs, wherever nothing else has
+        // to be staged for the passes (the lists fit and the reduction is a sum):
+        // the grid arrival's block barrier then orders them before the passes.
+        const bool lists = !L.masks && s_lovf[t & 1] == 0;
+        const bool early = c.learn && lists && c.reduce != SNN_REDUCE_MAX && t + 1 < T;
         if (t + 1 < T) {
-            encode_phase(c, d, L, sm, tt + 1, t + 1);
+            encode_words(c, d, L, sm, tt + 1, t + 1);
+            __syncthreads();
+            if (early && tid >= PT - 32)
+                list_post_columns(Qm, nc, Bw, nzQ, (uint32_t*)(sm + L.o_nzqw), (int*)(sm + L.o_pcol), &s_nq, tid & 31);
+            encode_lists(c, d, L, sm, tt + 1);
             ++nbar;
             grid_arrive(bar);
         }
@@ -1486,30 +1542,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             int* pcol = (int*)(sm + L.o_pcol);
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
             const int PS = L.ps;
-            const bool lists = !L.masks && s_lovf[t & 1] == 0;
-            if (tid < 32) {   // which columns fired, and the list of those columns
-                int npc = 0;
-                for (int jl0 = 0; jl0 < nc; jl0 += 32) {
-                    const int jl = jl0 + tid;
-                    int n = 0;
-                    if (jl < nc) {
-                        uint32_t nz = 0;
-#pragma unroll 8
-                        for (int w = 0; w < Bw; ++w) {
-                            const uint32_t q = Qm[w * nc + jl];
-                            n += __popc(q);
-                            if (q && w < 32) nz |= 1u << w;
-                        }
-                        nzQ[jl] = n;                  // post spikes of column jl this step (theta
-                        nzQw[jl] = nz;                // follows at the next step's start) and the
-                    }                                 // batch words holding them
-                    const bool f = jl < nc && n != 0;
-                    const uint32_t bal = __ballot_sync(FULL, f);
-                    if (f) pcol[npc + __popc(bal & ((1u << tid) - 1u))] = jl;
-                    npc += __popc(bal);
-                }
-                if (tid == 0) s_nq = npc;
-            }
+            if (!early && tid < 32) list_post_columns(Qm, nc, Bw, nzQ, nzQw, pcol, &s_nq, tid);
             if (L.masks) {   // the step's masks, padded rows, and each row's nonzero words:
                              // a thread per row, its words in 16-byte loads issued together
                 const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
@@ -1548,7 +1581,7 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                 const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
                 for (int k = tid; k < NI * Bw; k += PT) preS[(k / Bw) * PS + (k % Bw)] = __ldcg(&src[k]);
             }
-            __syncthreads();
+            if (!early) __syncthreads();
             const int warp = tid >> 5, lane = tid & 31;
 
             // (A) columns without a post spike: depression only (the post-triggered
@@ -1679,11 +1712,13 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
                     else Ws[i * nst + jl] = plain_add(Ws[i * nst + jl], D, c.w_min, c.w_max);
                 }
             }
-            __syncthreads();
+            // (no block barrier here otherwise: what the passes read is next
+            // written after the grid barrier's, and the end of the run has its own)
 
             // the post-triggered rule: each updated column back to the weight sum
             // w_norm, S_j = sum_i W[i][j] in ascending i, W[i][j] *= w_norm / S_j
             if (c.rule == SNN_RULE_POST_NORM) {
+                __syncthreads();
                 float* nrm = (float*)(sm + L.o_nrm);
                 const int npc = s_nq;
                 for (int u = tid; u < npc; u += PT) {
