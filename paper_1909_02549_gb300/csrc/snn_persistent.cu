@@ -35,7 +35,8 @@ namespace snn {
 namespace {
 
 constexpr int PT = 1024;                   // threads per CTA (fewer, with more registers each, ran slower)
-constexpr int CAPS = 32;                   // active inputs per sample staged in shared memory
+constexpr int CAPS = 16;                   // active inputs per sample staged in shared memory (the rest
+                                           // are read from global memory; 32 staged ran slower at B = 1024)
 constexpr unsigned SPIN_LIMIT = 1u << 22;  // bounded grid-barrier wait (polls with back-off: ~2 s)
 constexpr unsigned TEST_SPIN_LIMIT = 1u << 12;   // the test knob's wait (~2 ms)
 constexpr int NW = PT / 32;                // warps per CTA
@@ -107,11 +108,13 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
         L.fused = units >= PT / 2 && units <= (long long)(QT / 4) * PT;
         L.tstate = L.fused || (size_t)c.B * L.ncmax <= (size_t)QT * PT;
     }
-    // Narrow layers, and any layer at up to 64 samples: the STDP passes walk
-    // the step's spike words instead of per-input lists.  Every CTA would build
-    // the same lists (two block barriers and a scan per step), which costs more
-    // there than the walk saves; wide layers at larger batches keep the lists.
-    L.masks = L.ncmax <= 4 || c.Bw <= 2;
+    // The STDP passes walk the step's spike words instead of per-input lists at
+    // up to 32 samples, and in narrow layers (at most four columns per CTA) at
+    // up to 96 samples and above 512: every CTA builds the same lists, which
+    // costs more there than walking the words saves (measured: 784->400 at
+    // B = 64, 128 and 1024: lists 2.75, 2.77 and 9.60 ms per presentation,
+    // spike words 2.42, 2.92 and 8.68 ms).
+    L.masks = c.Bw <= 1 || (L.ncmax <= 4 && (c.Bw <= 3 || c.Bw > 16));
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_enc ? u_neuron : u_enc;

@@ -556,6 +556,29 @@ def test_narrow_layer_large_batch_walks_spike_words(reduce):
     assert rec.raster_e.sum() > 1000
 
 
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+@pytest.mark.parametrize("B,N", [(256, 400), (64, 1000)])
+def test_per_input_lists_narrow_layer_and_small_batch(B, N, reduce):
+    """Batches at which the persistent form's STDP walks per-input sample lists
+    (built per warp): a narrow layer (784 -> 400, two or three columns per SM)
+    at B = 256 and a wide one (784 -> 1000) at B = 64.  60 steps cover the
+    early burst in which most columns fire; every mode bit-exact with the
+    oracle."""
+    p, r, s, w = synth.workload(B, N)
+    _, rec = parity_all_modes(p, r, s, w, 60, reduce=reduce)
+    assert rec.raster_e.sum() > 100
+
+
+def test_narrow_layer_lists_overflow():
+    """784 -> 400 at B = 256 with sixteen times the image rates: a warp's input
+    rows carry more events than its list region holds, so the STDP of those
+    steps walks the spike words; bit-exact with the oracle."""
+    p, r, s, w = synth.workload(256, 400)
+    r = r * 16.0
+    _, rec = parity_all_modes(p, r, s, w, 20)
+    assert rec.raster_in.sum() > 200_000     # ~0.077 per input and step
+
+
 @pytest.mark.parametrize("reduce", ["mean", "sum"])
 def test_784x400_batch1024_learning_first_steps(reduce):
     """Learning on at B = 1024 for the first 10 steps against the whole-batch
