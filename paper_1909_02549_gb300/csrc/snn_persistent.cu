@@ -172,8 +172,10 @@ __device__ bool grid_wait(uint32_t* ctr, uint32_t* err, unsigned target, unsigne
         while (ld_acquire(ctr) < target) {
             if ((++spins & 31u) == 0u && ld_acquire(err) != 0u) { fail = 1; break; }
             if (spins > limit) { atomicOr(err, 1u); fail = 1; break; }
-            __nanosleep(ns);
-            if (ns < 512) ns <<= 1;
+            if (spins > 64) {                  // (a short wait is polled without sleeping)
+                __nanosleep(ns);
+                if (ns < 512) ns <<= 1;
+            }
         }
         s_fail = fail;
     }
