@@ -58,7 +58,8 @@ struct Layout {
     size_t o_ws, o_wlo, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
     // phase-local region: neuron-phase staging, encode scratch, STDP mask copy
     size_t o_cnts, o_actn, o_acts;    // neuron phase
-    size_t o_pres;                    // STDP phase (max reduction, list overflow)
+    size_t o_pres;                    // STDP phase (max reduction, list overflow); with amask
+                                      // a region of its own, after the phase-local one
     // per-step region: built before the neuron phase, read by the STDP phase
     size_t o_nzp, o_pcol, o_nzqw, o_nrm;
     size_t o_off, o_lst;              // per-input lists of spiking samples
@@ -66,6 +67,7 @@ struct Layout {
     int lcap;                         // list entries that fit
     int tstate;                       // neuron state held in tensor memory (else in global memory)
     int masks;                        // STDP walks the spike words, no per-input lists (see make_layout)
+    int amask;                        // the masks copied asynchronously into a region of their own
     int fused;                        // the neuron phase walks (sample, column-quad) units (see make_layout)
     size_t o_wbuf;                    // encode phase
     size_t bytes;
@@ -75,7 +77,7 @@ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // `budget` is the dynamic shared memory one CTA may take; what the fixed parts
 // leave of it holds the per-input sample lists of the STDP phase.
-Layout make_layout(const Consts& c, int G, size_t budget) {
+Layout make_layout_with(const Consts& c, int G, size_t budget, bool allow_amask) {
     Layout L{};
     L.G = G;
     L.ncmax = (c.N + G - 1) / G;
@@ -96,7 +98,6 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.o_cnts = o;                u_neuron = align16((size_t)c.B * 4);
     L.o_actn = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * 4);
     L.o_acts = o + u_neuron;     u_neuron = align16(u_neuron + (size_t)c.B * CAPS * 2);
-    L.ps = c.Bw | 1;                                      // odd row stride: no bank conflicts
     // The neuron phase: fused over (sample, column-quad) units when there are
     // enough units to busy half the threads and tensor memory holds them (QT / 4
     // units of four items per thread, see units_of); otherwise the currents and
@@ -115,10 +116,23 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     // B = 64, 128 and 1024: lists 2.75, 2.77 and 9.60 ms per presentation,
     // spike words 2.42, 2.92 and 8.68 ms).
     L.masks = c.Bw <= 1 || (L.ncmax <= 4 && (c.Bw <= 3 || c.Bw > 16));
+    // With 32 mask words per input row (993 to 1024 samples) the step's masks
+    // are copied into a region of their own by 16-byte asynchronous copies
+    // issued at the step's start, which overlap the neuron phase and the
+    // encode (rows padded to 36 words, 16-byte aligned).  Otherwise the STDP
+    // phase copies them into the phase-local region when it needs them (odd
+    // row stride: no bank conflicts).
+    L.amask = allow_amask && c.learn && L.masks && c.Bw == 32;
+    L.ps = L.amask ? c.Bw + 4 : (c.Bw | 1);
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
     L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
     size_t u = u_neuron > u_enc ? u_neuron : u_enc;
-    if (u_pres > u) u = u_pres;
+    if (L.amask) {
+        L.o_pres = o + u;
+        u += u_pres;
+    } else if (u_pres > u) {
+        u = u_pres;
+    }
     o += u;
     L.o_nzp = o;                 o = align16(o + (size_t)c.n_in * 4);
     L.o_pcol = o;                o = align16(o + (size_t)L.ncmax * 4);
@@ -145,6 +159,21 @@ Layout make_layout(const Consts& c, int G, size_t budget) {
     L.bytes = o;
     return L;
 }
+
+// The layout, without the asynchronous mask copy where its region would not fit.
+Layout make_layout(const Consts& c, int G, size_t budget) {
+    const Layout L = make_layout_with(c, G, budget, true);
+    return L.amask && L.bytes > budget ? make_layout_with(c, G, budget, false) : L;
+}
+
+// 16-byte asynchronous global-to-shared copies (through L2 only), and the wait
+// for all of the calling thread's copies.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -1358,6 +1387,13 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         // (the step's input-mask rows for the lists below, loaded first so that
         // their latency overlaps the staging)
         const uint32_t* pre_src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
+        if (L.amask) {   // the step's masks for the STDP phase: chunk k of 8 per row,
+                         // from the thread that reads it back there
+            uint32_t* preA = (uint32_t*)(sm + L.o_pres);
+            for (int k = tid; k < NI * 8; k += PT)
+                cp_async16(preA + (k >> 3) * L.ps + 4 * (k & 7), pre_src + 4 * k);
+            cp_async_commit();
+        }
         const bool pre_vec = Bw == 4 || Bw == 8;         // rows of 16 or 32 bytes, 16-byte aligned
         uint4 pq0 = make_uint4(0u, 0u, 0u, 0u), pq1 = make_uint4(0u, 0u, 0u, 0u);
         if (c.learn && pre_vec && tid < NI) {
@@ -1548,7 +1584,24 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             uint32_t* nzQw = (uint32_t*)(sm + L.o_nzqw);
             const int PS = L.ps;
             if (!early && tid < 32) list_post_columns(Qm, nc, Bw, nzQ, nzQw, pcol, &s_nq, tid);
-            if (L.masks) {   // the step's masks, padded rows, and each row's nonzero words:
+            if (L.amask) {   // the copies issued at the step's start: this thread's chunks
+                             // read back, each row's nonzero words from the 8 lanes of its row
+                cp_async_wait_all();
+                const int nch = NI * 8;
+                for (int k0 = tid - (tid & 31); k0 < nch; k0 += PT) {
+                    const int k = k0 + (tid & 31);
+                    uint32_t nz = 0u;
+                    if (k < nch) {
+                        const uint4 q = *(const uint4*)(preS + (k >> 3) * PS + 4 * (k & 7));
+                        nz = (q.x ? 1u : 0u) | (q.y ? 2u : 0u) | (q.z ? 4u : 0u) | (q.w ? 8u : 0u);
+                        nz <<= 4 * (k & 7);
+                    }
+                    nz |= __shfl_xor_sync(FULL, nz, 1);
+                    nz |= __shfl_xor_sync(FULL, nz, 2);
+                    nz |= __shfl_xor_sync(FULL, nz, 4);
+                    if (k < nch && (k & 7) == 0) nzP[k >> 3] = nz;
+                }
+            } else if (L.masks) {   // the step's masks, padded rows, and each row's nonzero words:
                              // a thread per row, its words in 16-byte loads issued together
                 const uint32_t* src = d.preT + (size_t)(tt % PRET_SLOTS) * NI * Bw;
                 for (int i = tid; i < NI; i += PT) {
@@ -1744,6 +1797,8 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
 
         if (t + 1 < T) ok = grid_wait(bar, d.err, G * nbar, SPIN_LIMIT);
     }
+
+    if (L.amask) cp_async_wait_all();   // (every step's copies were waited for by its STDP)
 
     // ---- thresholds after the last step's STDP
     if (c.learn && T > 0)

@@ -557,6 +557,18 @@ def test_narrow_layer_large_batch_walks_spike_words(reduce):
 
 
 @pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
+def test_narrow_layer_32_word_masks_copied_ahead(reduce):
+    """784 -> 400 at B = 1000 (32 mask words per input row, the last one
+    ragged): the persistent form copies each step's masks into shared memory
+    with asynchronous copies issued at the step's start, and the STDP walks
+    them.  60 steps cover the early burst in which most columns fire; every
+    mode bit-exact with the oracle."""
+    p, r, s, w = synth.workload(1000, 400)
+    _, rec = parity_all_modes(p, r, s, w, 60, reduce=reduce)
+    assert rec.raster_e.sum() > 1000
+
+
+@pytest.mark.parametrize("reduce", ["mean", "sum", "max"])
 @pytest.mark.parametrize("B,N", [(256, 400), (64, 1000)])
 def test_per_input_lists_narrow_layer_and_small_batch(B, N, reduce):
     """Batches at which the persistent form's STDP walks per-input sample lists
