@@ -56,7 +56,7 @@ struct Layout {
     int G, ncmax, spc;           // CTAs, max columns per CTA, max samples per CTA
     int nst;                     // row stride (floats) of the weight and depression-term tiles
     size_t o_ws, o_wlo, o_es, o_sm, o_qm, o_nzq, o_ths, o_thj, o_wsc, o_u;   // byte offsets
-    // phase-local region: neuron-phase staging, encode scratch, STDP mask copy
+    // phase-local region: neuron-phase staging, STDP mask copy
     size_t o_cnts, o_actn, o_acts;    // neuron phase
     size_t o_pres;                    // STDP phase (max reduction, list overflow); with amask
                                       // a region of its own, after the phase-local one
@@ -69,7 +69,7 @@ struct Layout {
     int masks;                        // STDP walks the spike words, no per-input lists (see make_layout)
     int amask;                        // the masks copied asynchronously into a region of their own
     int fused;                        // the neuron phase walks (sample, column-quad) units (see make_layout)
-    size_t o_wbuf;                    // encode phase
+    size_t o_wbuf;                    // the encode's words (a region of their own: drawn during the staging)
     size_t bytes;
 };
 
@@ -125,8 +125,8 @@ Layout make_layout_with(const Consts& c, int G, size_t budget, bool allow_amask)
     L.amask = allow_amask && c.learn && L.masks && c.Bw == 32;
     L.ps = L.amask ? c.Bw + 4 : (c.Bw | 1);
     L.o_pres = o;                u_pres = align16((size_t)c.n_in * L.ps * 4);
-    L.o_wbuf = o;                u_enc = align16((size_t)L.spc * c.Iw * 4);
-    size_t u = u_neuron > u_enc ? u_neuron : u_enc;
+    u_enc = align16((size_t)L.spc * c.Iw * 4);
+    size_t u = u_neuron;
     if (L.amask) {
         L.o_pres = o + u;
         u += u_pres;
@@ -134,6 +134,7 @@ Layout make_layout_with(const Consts& c, int G, size_t budget, bool allow_amask)
         u = u_pres;
     }
     o += u;
+    L.o_wbuf = o;                o += u_enc;   // the encode's words, written at the step's start
     L.o_nzp = o;                 o = align16(o + (size_t)c.n_in * 4);
     L.o_pcol = o;                o = align16(o + (size_t)L.ncmax * 4);
     L.o_nzqw = o;                o = align16(o + (size_t)L.ncmax * 4);
@@ -1532,6 +1533,11 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
             }
             if (ln == 0 && run > 0) s_lany[t & 1] = 1;
         }
+        // The input words of step t+1 for the CTA's samples: they need only the
+        // CTA's own traces of step t and the constant thresholds, and the slot
+        // they go to was cleared by every CTA in step t-1, so they are drawn
+        // here, before the neuron phase, sharing its block barrier.
+        if (t + 1 < T) encode_words(c, d, L, sm, tt + 1, t + 1);
         if (c.wprec == SNN_W_FP8E4M3) {   // column scales of this step's weights
             const int warp = tid >> 5, lane = tid & 31;
             for (int jl = warp; jl < nc; jl += NW) {
@@ -1558,8 +1564,9 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         }
         __syncthreads();
 
-        // ================= next step's input, signalled before this step's STDP
-        // (which needs nothing from other CTAs' next step), waited for after it
+        // ================= next step's input (its words drawn during the staging),
+        // listed and signalled before this step's STDP (which needs nothing from
+        // other CTAs' next step), waited for after it.
         // The STDP phase's post columns are listed by the last warp while the
         // others list the next step's active inputs, wherever nothing else has
         // to be staged for the passes (the lists fit and the reduction is a sum):
@@ -1567,8 +1574,6 @@ k_persistent(const __grid_constant__ Consts c, const __grid_constant__ Bufs d, c
         const bool lists = !L.masks && s_lovf[t & 1] == 0;
         const bool early = c.learn && lists && c.reduce != SNN_REDUCE_MAX && t + 1 < T;
         if (t + 1 < T) {
-            encode_words(c, d, L, sm, tt + 1, t + 1);
-            __syncthreads();
             if (early && tid >= PT - 32)
                 list_post_columns(Qm, nc, Bw, nzQ, (uint32_t*)(sm + L.o_nzqw), (int*)(sm + L.o_pcol), &s_nq, tid & 31);
             encode_lists(c, d, L, sm, tt + 1);
